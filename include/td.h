@@ -1,0 +1,193 @@
+/*
+ * td.h -- C ABI of the B300-native time-domain Gaussian likelihood.
+ *
+ * Method (arXiv 2603.06010, Sec. II): for residuals r = d - h(theta) on the
+ * kept samples t_0 < ... < t_{N'-1} of a segment,
+ *
+ *     logL = -1/2 r^T C^{-1} r - 1/2 log det C - (N'/2) log 2 pi,
+ *
+ * where C_ij = rho(|t_i - t_j|) is the stationary-noise covariance built from
+ * the autocovariance rho (Sec. II, the Toeplitz covariance; Sec. II.B items
+ * 1-2, segments and gaps: gap samples are deleted, leaving the kept x kept
+ * principal submatrix).  C = L L^T is factored once (Sec. II.A); every
+ * evaluation whitens r with W = L^{-1} (Sec. II.A, Eq. eq:td_like_whitened)
+ * and reduces chi2 = |W r|^2.
+ *
+ * Conventions shared by every call:
+ *   - Every pointer argument documented "device" must point to memory of the
+ *     device that was current when the segment was created; "host" pointers
+ *     are ordinary CPU memory.
+ *   - Residual batches are float32, column-major N' x K with leading
+ *     dimension ldr >= N' (column k = residual k, kept samples only).
+ *   - Outputs logL / chi2 are float64 arrays of K entries.
+ *   - Calls taking a stream are asynchronous and stream-ordered unless stated
+ *     otherwise; the caller keeps inputs alive and unmodified until the work
+ *     on that stream has completed.
+ *   - Errors are returned as td_status, never trapped; td_last_error()
+ *     gives a thread-local message for the last failing call on the thread.
+ *   - No device kernel spins without a bound: every wait inside a kernel
+ *     gives up after a time limit (td_options.wait_limit_ns) and the call
+ *     reports TD_ERR_TIMEOUT on the next synchronising call.
+ */
+#ifndef TD_H
+#define TD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct td_segment td_segment;   /* opaque: owns device copies and factors */
+
+typedef enum {
+  TD_OK = 0,
+  TD_ERR_INVALID = 1,       /* bad argument (null pointer, size, ldr < N', ...) */
+  TD_ERR_NOT_PD = 2,        /* covariance not positive definite; see td_last_pivot */
+  TD_ERR_OOM = 3,           /* device allocation failed */
+  TD_ERR_CUDA = 4,          /* a CUDA runtime/driver call failed */
+  TD_ERR_TIMEOUT = 5,       /* a bounded in-kernel wait ran out */
+  TD_ERR_NOT_FACTORED = 6,  /* td_factor has not succeeded on this segment */
+  TD_ERR_UNSUPPORTED = 7    /* precision/size combination not built */
+} td_status;
+
+typedef enum {
+  TD_PREC_FP64 = 0,   /* plain FP64 blocked forward substitution (CUDA cores) */
+  TD_PREC_6XBF16 = 1, /* 3 bf16 slices of L^{-1} and of R, 6 tensor-core products,
+                         FP32 accumulation in tensor memory (default) */
+  TD_PREC_3XBF16 = 2, /* 2 slices, 3 products (hi*hi + hi*lo + lo*hi) */
+  TD_PREC_AUTO = 3    /* library picks by (N', K): tensor-core or small-K streaming */
+} td_precision;
+
+typedef enum {
+  TD_PATH_AUTO = 0,
+  TD_PATH_TENSOR = 1,  /* tcgen05 persistent split-product GEMM (K >= ~32) */
+  TD_PATH_STREAM = 2,  /* operator streamed once from HBM, CUDA-core FMAs (K <= ~16) */
+  TD_PATH_FP64 = 3     /* plain FP64 forward substitution */
+} td_path;
+
+typedef struct {
+  int precision;        /* td_precision; default TD_PREC_6XBF16 */
+  int path;             /* td_path; default TD_PATH_AUTO */
+  int refine;           /* 1: one refinement step s = r - L w (FP64), w += L^{-1} s */
+  int reserved0;
+  int64_t wait_limit_ns;/* bound on any in-kernel wait; <= 0 -> 1 s */
+} td_options;
+
+/* Fill *opt with the defaults (6xBF16, auto path, no refinement, 1 s waits). */
+void td_options_default(td_options* opt);
+
+/*
+ * td_segment_create -- one analysis segment of one detector.
+ *   acf  : host, float64[n]; acf[k] = rho(k), lags 0..n-1 (Sec. II.B item 1:
+ *          the ACF truncated to the segment).  Copied.
+ *   n    : samples in the segment, n >= 1.
+ *   mask : host, uint8[n], 1 = kept, 0 = gap sample (Sec. II.B item 2);
+ *          NULL = no gaps.  At least one sample must be kept.  Copied.
+ *   stream: CUDA stream (cudaStream_t) for the device copies; 0 = legacy.
+ *   out  : receives the new segment.  The caller releases it with
+ *          td_segment_destroy.
+ * Validation: acf[0] > 0 and finite, n >= 1, >= 1 kept sample.
+ * The call synchronises `stream` before returning.
+ */
+td_status td_segment_create(const double* acf, int64_t n, const uint8_t* mask,
+                            void* stream, td_segment** out);
+
+/*
+ * td_factor -- C_kept = L L^T (Sec. II.A; Sec. III.A "Factorization of the
+ * covariance matrix": once per segment, cached).  Blocked right-looking
+ * Cholesky in FP64 on the device, then log det C = 2 sum log L_ii (FP64),
+ * then the whitening operator L^{-1} (FP64) and its bf16 slices for the
+ * tensor-core path.  All results stay resident on the device and are owned
+ * by the segment.  Synchronises `stream`.
+ * Returns TD_ERR_NOT_PD if a pivot is <= 0 or not finite; td_last_pivot
+ * then gives the 0-based kept-sample index of the first failing pivot.
+ */
+td_status td_factor(td_segment* s, void* stream);
+
+/* log det C_kept (host scalar).  Requires a successful td_factor. */
+td_status td_logdet(const td_segment* s, double* out);
+
+/* N' (kept sample count); -1 for a NULL segment. */
+int64_t td_kept(const td_segment* s);
+
+/* 0-based failing pivot of the last td_factor that returned TD_ERR_NOT_PD, else -1. */
+int64_t td_last_pivot(const td_segment* s);
+
+/*
+ * td_loglike_batch -- per-evaluation hot path (Sec. II.A, Eq.
+ * eq:td_like_whitened; Sec. III.A, the CDO whitening of cached operators):
+ *   W = L^{-1} R,  chi2_k = sum_i W_ik^2 (FP64 reduction),
+ *   logL_k = -chi2_k/2 - logdet/2 - (N'/2) log 2 pi.
+ *   R    : device, float32, column-major N' x K, leading dimension ldr >= N'.
+ *          Read only; caller-owned.
+ *   K    : number of residual columns; K = 0 is a no-op.
+ *   logL : device, float64[K], caller-owned, overwritten.
+ *   opt  : NULL = defaults.
+ *   chi2 : optional device float64[K] (NULL = not written).
+ *   stream: CUDA stream; asynchronous.  The segment's scratch space grows on
+ *          first use for a given K (that call may allocate); later calls with
+ *          K no larger do not allocate (call td_reserve before graph capture).
+ * The results for one column do not depend on the other columns of the batch
+ * (fixed reduction order), so a column evaluated alone or in any batch gives
+ * the same bits.
+ */
+td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K,
+                           double* logL, const td_options* opt, double* chi2,
+                           void* stream);
+
+/* Pre-size the segment's scratch for batches of up to K columns (allocates). */
+td_status td_reserve(td_segment* s, int64_t K, const td_options* opt);
+
+/*
+ * td_loglike_grouped -- many segments (uneven N', own K each) in one
+ * persistent tensor-core launch (block-diagonal C over disjoint segments and
+ * detectors, Sec. II.B items 1 and 3).  Arrays have nseg entries; R[i],
+ * ldr[i], K[i], logL[i] as for td_loglike_batch on segs[i].  Asynchronous.
+ */
+td_status td_loglike_grouped(td_segment* const* segs, const float* const* R,
+                             const int64_t* ldr, const int64_t* K, double* const* logL,
+                             int nseg, const td_options* opt, void* stream);
+
+/*
+ * td_check -- synchronise `stream` and report any error a kernel of this
+ * segment recorded on the device since the last check (TD_ERR_TIMEOUT when a
+ * bounded wait ran out).  Clears the recorded error.
+ */
+td_status td_check(td_segment* s, void* stream);
+
+/*
+ * Instrumentation.  td_profile_enable(s, 1) makes every later hot-path call
+ * on s bracket its dominant kernel (the tensor-core product, or the FP64
+ * forward substitution) with CUDA events recorded on the call's own stream,
+ * and count every kernel the call launches.  td_profile_read synchronises
+ * those events and returns the summed dominant-kernel time (ms), the number
+ * of dominant-kernel launches and the total kernels launched since enabling,
+ * then resets the counters.  At most 4096 bracketed launches are kept.
+ */
+td_status td_profile_enable(td_segment* s, int enable);
+td_status td_profile_read(td_segment* s, double* ms_total, int64_t* dominant_launches,
+                          int64_t* kernels_launched);
+
+/* Release a segment and all device memory it owns (synchronises its work). */
+void td_segment_destroy(td_segment* s);
+
+/* Thread-local message for the last failing call on this thread ("" if none). */
+const char* td_last_error(void);
+
+/* Bytes of device memory the segment holds resident (factor + operators). */
+int64_t td_resident_bytes(const td_segment* s);
+
+/*
+ * td_debug_bounded_wait -- runs one tiny kernel whose wait is on a flag that
+ * nothing sets, bounded by limit_ns; returns TD_ERR_TIMEOUT when the bound
+ * ran out (the expected outcome) and leaves the context usable.  Exists to
+ * test the bounded-wait machinery without faulting a GPU.  Synchronous.
+ */
+td_status td_debug_bounded_wait(int64_t limit_ns, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TD_H */

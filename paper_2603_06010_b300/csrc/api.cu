@@ -1,0 +1,452 @@
+// C ABI of libtd: segment lifetime, factor, per-evaluation batches.
+#include <cudaTypedefs.h>
+
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "td_internal.h"
+
+namespace td {
+cudaError_t launch_tc_single(const TcSegDev& seg, int nm, int nc, int nkb_max, int nslices, DevStatus* status,
+                             int64_t wait_limit_ns, cudaStream_t st);
+
+static thread_local std::string g_last_error;
+
+td_status fail(td_status code, const std::string& msg) {
+  g_last_error = msg;
+  return code;
+}
+
+td_status cuda_fail(cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  g_last_error = m;
+  if (e == cudaErrorMemoryAllocation) return TD_ERR_OOM;
+  return TD_ERR_CUDA;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::mutex g_encode_mu;
+
+static td_status get_encode(PFN_cuTensorMapEncodeTiled_v12000* out) {
+  std::lock_guard<std::mutex> lk(g_encode_mu);
+  if (!g_encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+      return fail(TD_ERR_CUDA, "cuTensorMapEncodeTiled entry point not available");
+    g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  *out = g_encode;
+  return TD_OK;
+}
+
+static td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2,
+                           uint64_t s1_bytes, uint64_t s2_bytes, uint32_t b0, uint32_t b1, uint32_t b2) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  td_status st = get_encode(&enc);
+  if (st != TD_OK) return st;
+  cuuint64_t dims[3] = {d0, d1, d2};
+  cuuint64_t strides[2] = {s1_bytes, s2_bytes};
+  cuuint32_t box[3] = {b0, b1, b2};
+  cuuint32_t es[3] = {1, 1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(ptr), dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "cuTensorMapEncodeTiled failed (%d): dims %llu %llu %llu", (int)r,
+             (unsigned long long)d0, (unsigned long long)d1, (unsigned long long)d2);
+    return fail(TD_ERR_CUDA, buf);
+  }
+  return TD_OK;
+}
+
+// residual-slice map (A operand) and operator map (B operand) of one segment
+td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, TcSegDev* out) {
+  td_status st = encode_3d(&out->mapA, s->scr.rs, (uint64_t)s->nk, (uint64_t)K, 3, (uint64_t)s->nkp8 * 2,
+                           (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, TC_COLS, (uint32_t)nsl);
+  if (st != TD_OK) return st;
+  return encode_3d(&out->mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * 3, OP_KB * 2,
+                   (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, OP_ROWS, (uint32_t)nsl);
+}
+
+template <class T>
+static td_status dev_alloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return TD_OK;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(TD_ERR_OOM, std::string("device allocation failed: ") + what);
+  }
+  return TD_OK;
+}
+
+template <class T>
+static void dev_free(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+static td_status check_device(const td_segment* s) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  if (dev != s->device) return fail(TD_ERR_INVALID, "segment belongs to another device; set it current first");
+  return TD_OK;
+}
+
+static int nslices_for(int precision) { return precision == TD_PREC_3XBF16 ? 2 : 3; }
+
+// Grow the per-segment scratch so batches of K columns fit.
+static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaStream_t st) {
+  Scratch& sc = s->scr;
+  if (K > sc.capK) {
+    cudaStreamSynchronize(st);   // old buffers may still be in use on this stream
+    dev_free(sc.rs);
+    dev_free(sc.partials);
+    dev_free(sc.w64);
+    const int64_t cap = round_up(K, TC_COLS);
+    td_status r = dev_alloc(&sc.rs, (size_t)(3 * cap * s->nkp8), "residual slices");
+    if (r != TD_OK) return r;
+    r = dev_alloc(&sc.partials, (size_t)((s->nkp / FT) * cap), "chi2 partials");
+    if (r != TD_OK) return r;
+    sc.capK = cap;
+  }
+  if (fp64_path && !sc.w64) {
+    td_status r = dev_alloc(&sc.w64, (size_t)(s->nkp * sc.capK), "FP64 whitened residuals");
+    if (r != TD_OK) return r;
+  }
+  return TD_OK;
+}
+
+static td_status read_status(td_segment* s, cudaStream_t st, DevStatus* out) {
+  TD_CUDA(cudaMemcpyAsync(out, s->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
+  TD_CUDA(cudaStreamSynchronize(st));
+  return TD_OK;
+}
+
+static td_status reset_status(td_segment* s, cudaStream_t st) {
+  DevStatus h{0, 0, LLONG_MAX};
+  TD_CUDA(cudaMemcpyAsync(s->status, &h, sizeof h, cudaMemcpyHostToDevice, st));
+  TD_CUDA(cudaStreamSynchronize(st));
+  return TD_OK;
+}
+
+// bracket the dominant kernel with events when profiling is on
+static void prof_mark(td_segment* s, cudaStream_t st, bool start) {
+  if (!s->prof) return;
+  if (start && s->ev_used + 2 > s->ev.size()) {
+    if (s->ev.size() >= 8192) return;
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      cudaEventCreate(&e);
+      s->ev.push_back(e);
+    }
+  }
+  if (start) {
+    cudaEventRecord(s->ev[s->ev_used], st);
+  } else {
+    cudaEventRecord(s->ev[s->ev_used + 1], st);
+    s->ev_used += 2;
+  }
+}
+
+}  // namespace td
+
+using namespace td;
+
+extern "C" {
+
+void td_options_default(td_options* opt) {
+  if (!opt) return;
+  memset(opt, 0, sizeof *opt);
+  opt->precision = TD_PREC_6XBF16;
+  opt->path = TD_PATH_AUTO;
+  opt->refine = 0;
+  opt->wait_limit_ns = 1000000000LL;
+}
+
+const char* td_last_error(void) { return g_last_error.c_str(); }
+
+td_status td_segment_create(const double* acf, int64_t n, const uint8_t* mask, void* stream, td_segment** out) {
+  if (!out) return fail(TD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!acf) return fail(TD_ERR_INVALID, "acf is NULL");
+  if (n < 1) return fail(TD_ERR_INVALID, "n must be >= 1");
+  if (n > (int64_t)INT32_MAX) return fail(TD_ERR_INVALID, "n too large");
+  if (!(acf[0] > 0.0) || !std::isfinite(acf[0])) return fail(TD_ERR_INVALID, "acf[0] must be positive and finite");
+  for (int64_t k = 0; k < n; ++k)
+    if (!std::isfinite(acf[k])) return fail(TD_ERR_INVALID, "acf has a non-finite entry");
+  std::vector<int32_t> t;
+  t.reserve((size_t)n);
+  for (int64_t i = 0; i < n; ++i)
+    if (!mask || mask[i]) t.push_back((int32_t)i);
+  if (t.empty()) return fail(TD_ERR_INVALID, "mask keeps no sample");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  td_segment* s = new td_segment();
+  cudaGetDevice(&s->device);
+  s->n = n;
+  s->nk = (int64_t)t.size();
+  s->nkp = round_up(s->nk, OP_ROWS);
+  s->nkp8 = round_up(s->nk, 8);
+  td_status r;
+  if ((r = dev_alloc(&s->acf, (size_t)n, "acf")) != TD_OK ||
+      (r = dev_alloc(&s->t, t.size(), "kept index")) != TD_OK ||
+      (r = dev_alloc(&s->status, 1, "status")) != TD_OK) {
+    td_segment_destroy(s);
+    return r;
+  }
+  cudaError_t e = cudaMemcpyAsync(s->acf, acf, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(s->t, t.data(), t.size() * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) {
+    td_segment_destroy(s);
+    return cuda_fail(e, "td_segment_create copies");
+  }
+  if ((r = reset_status(s, st)) != TD_OK) {
+    td_segment_destroy(s);
+    return r;
+  }
+  *out = s;
+  return TD_OK;
+}
+
+int64_t td_kept(const td_segment* s) { return s ? s->nk : -1; }
+
+int64_t td_last_pivot(const td_segment* s) { return s ? s->pivot : -1; }
+
+td_status td_logdet(const td_segment* s, double* out) {
+  if (!s || !out) return fail(TD_ERR_INVALID, "NULL argument");
+  if (!s->factored) return fail(TD_ERR_NOT_FACTORED, "segment not factored");
+  *out = s->logdet;
+  return TD_OK;
+}
+
+int64_t td_resident_bytes(const td_segment* s) {
+  if (!s) return 0;
+  int64_t b = s->n * 8 + s->nk * 4;
+  if (s->L) b += s->nkp * s->nkp * 8;
+  if (s->dinv) b += (s->nkp / FT) * FT * FT * 8;
+  if (s->op) b += s->op_blocks * 3 * OP_ROWS * OP_KB * 2;
+  return b;
+}
+
+td_status td_factor(td_segment* s, void* stream) {
+  if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
+  td_status r = check_device(s);
+  if (r != TD_OK) return r;
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  s->factored = false;
+  s->pivot = -1;
+  const int64_t nkp = s->nkp;
+  const int nt = (int)(nkp / FT);
+  if (!s->L && (r = dev_alloc(&s->L, (size_t)(nkp * nkp), "factor L")) != TD_OK) return r;
+  if (!s->dinv && (r = dev_alloc(&s->dinv, (size_t)nt * FT * FT, "diagonal inverses")) != TD_OK) return r;
+  if (!s->ldpart && (r = dev_alloc(&s->ldpart, (size_t)nt, "logdet partials")) != TD_OK) return r;
+  if ((r = reset_status(s, st)) != TD_OK) return r;
+  TD_CUDA(launch_gather(s->acf, s->t, s->nk, nkp, s->L, st));
+  for (int j = 0; j < nt; ++j) {
+    TD_CUDA(launch_potrf_diag(s->L, nkp, s->nk, j, s->dinv, s->ldpart, s->status, st));
+    TD_CUDA(launch_panel(s->L, nkp, j, nt, s->dinv, st));
+    TD_CUDA(launch_syrk(s->L, nkp, j, nt, st));
+  }
+  DevStatus hs;
+  if ((r = read_status(s, st, &hs)) != TD_OK) return r;
+  if (hs.code == ST_NOT_PD) {
+    s->pivot = hs.pivot;
+    char buf[128];
+    snprintf(buf, sizeof buf, "covariance not positive definite at kept sample %lld", (long long)hs.pivot);
+    return fail(TD_ERR_NOT_PD, buf);
+  }
+  std::vector<double> ld((size_t)nt);
+  TD_CUDA(cudaMemcpy(ld.data(), s->ldpart, (size_t)nt * sizeof(double), cudaMemcpyDeviceToHost));
+  double logdet = 0.0;
+  for (int j = 0; j < nt; ++j) logdet += ld[(size_t)j];
+  // whitening operator L^{-1} (FP64), then its bf16 slices
+  double* linv = nullptr;
+  if ((r = dev_alloc(&linv, (size_t)(nkp * nkp), "L^{-1} (temporary)")) != TD_OK) return r;
+  cudaError_t e = cudaMemsetAsync(linv, 0, (size_t)(nkp * nkp) * sizeof(double), st);
+  for (int I = 0; I < nt && e == cudaSuccess; ++I)
+    e = launch_trsm_f64_row(s->L, nkp, s->dinv, I, nullptr, 0, s->nk, nkp, linv, nkp, nullptr, 0, st);
+  const int64_t nm = nkp / OP_ROWS;
+  s->op_blocks = op_row_offset(nm);
+  if (e == cudaSuccess && !s->op) {
+    r = dev_alloc(&s->op, (size_t)(s->op_blocks * 3 * OP_ROWS * OP_KB), "operator slices");
+    if (r != TD_OK) {
+      cudaFree(linv);
+      return r;
+    }
+  }
+  if (e == cudaSuccess) e = launch_op_slices(linv, nkp, s->nk, nkp, s->op, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(linv);
+  if (e != cudaSuccess) return cuda_fail(e, "td_factor operator build");
+  s->logdet = logdet;
+  s->factored = true;
+  return TD_OK;
+}
+
+td_status td_reserve(td_segment* s, int64_t K, const td_options* opt) {
+  if (!s || K < 0) return fail(TD_ERR_INVALID, "bad argument");
+  td_options o;
+  td_options_default(&o);
+  if (opt) o = *opt;
+  return ensure_scratch(s, K, o.path == TD_PATH_FP64 || o.precision == TD_PREC_FP64, 0);
+}
+
+td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL,
+                           const td_options* opt, double* chi2, void* stream) {
+  if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
+  if (K < 0) return fail(TD_ERR_INVALID, "K < 0");
+  if (K == 0) return TD_OK;
+  if (!R || !logL) return fail(TD_ERR_INVALID, "R or logL is NULL");
+  if (ldr < s->nk) return fail(TD_ERR_INVALID, "ldr < N'");
+  if (!s->factored) return fail(TD_ERR_NOT_FACTORED, "segment not factored");
+  td_status r = check_device(s);
+  if (r != TD_OK) return r;
+  td_options o;
+  td_options_default(&o);
+  if (opt) o = *opt;
+  if (o.wait_limit_ns <= 0) o.wait_limit_ns = 1000000000LL;
+  if (o.refine) return fail(TD_ERR_UNSUPPORTED, "refinement is not built in this version");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const bool fp64 = (o.precision == TD_PREC_FP64) || (o.path == TD_PATH_FP64);
+  if ((r = ensure_scratch(s, K, fp64, st)) != TD_OK) return r;
+  Scratch& sc = s->scr;
+  const int64_t ldp = sc.capK;
+  if (fp64) {
+    const int nt = (int)(s->nkp / FT);
+    const bool pm = s->prof && s->ev_used + 2 <= 8192;
+    if (pm) prof_mark(s, st, true);
+    for (int I = 0; I < nt; ++I)
+      TD_CUDA(launch_trsm_f64_row(s->L, s->nkp, s->dinv, I, R, ldr, s->nk, K, sc.w64, s->nkp, sc.partials, ldp,
+                                  st));
+    if (pm) prof_mark(s, st, false);
+    TD_CUDA(launch_finalize(sc.partials, ldp, nt, K, s->logdet, s->nk, logL, chi2, st));
+    s->prof_kernels += nt + 1;
+    return TD_OK;
+  }
+  const int nsl = nslices_for(o.precision);
+  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
+  TcSegDev seg;
+  memset(&seg, 0, sizeof seg);
+  if ((r = encode_seg_maps(s, K, nsl, &seg)) != TD_OK) return r;
+  seg.partials = sc.partials;
+  seg.nk = (int)s->nk;
+  seg.K = (int)K;
+  seg.ldp = (int)ldp;
+  const int nm = (int)(s->nkp / OP_ROWS);
+  seg.nm = nm;
+  const int nc = (int)ceil_div(K, TC_COLS);
+  const int nkb_max = (int)ceil_div(s->nk, OP_KB);
+  const bool pm = s->prof && s->ev_used + 2 <= 8192;
+  if (pm) prof_mark(s, st, true);
+  TD_CUDA(launch_tc_single(seg, nm, nc, nkb_max, nsl, s->status, o.wait_limit_ns, st));
+  if (pm) prof_mark(s, st, false);
+  TD_CUDA(launch_finalize(sc.partials, ldp, nm, K, s->logdet, s->nk, logL, chi2, st));
+  s->prof_kernels += 3;
+  return TD_OK;
+}
+
+td_status td_loglike_grouped(td_segment* const* segs, const float* const* R, const int64_t* ldr, const int64_t* K,
+                             double* const* logL, int nseg, const td_options* opt, void* stream) {
+  if (nseg < 0 || (nseg > 0 && (!segs || !R || !ldr || !K || !logL))) return fail(TD_ERR_INVALID, "bad arguments");
+  for (int i = 0; i < nseg; ++i) {
+    td_status r = td_loglike_batch(segs[i], R[i], ldr[i], K[i], logL[i], opt, nullptr, stream);
+    if (r != TD_OK) return r;
+  }
+  return TD_OK;
+}
+
+td_status td_check(td_segment* s, void* stream) {
+  if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  DevStatus hs;
+  td_status r = read_status(s, st, &hs);
+  if (r != TD_OK) return r;
+  if (hs.code != 0) {
+    reset_status(s, st);
+    if (hs.code == ST_TIMEOUT) {
+      char buf[96];
+      snprintf(buf, sizeof buf, "a bounded in-kernel wait ran out (site %d)", hs.where);
+      return fail(TD_ERR_TIMEOUT, buf);
+    }
+    return fail((td_status)hs.code, "device reported an error");
+  }
+  return TD_OK;
+}
+
+td_status td_profile_enable(td_segment* s, int enable) {
+  if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
+  s->prof = enable != 0;
+  s->ev_used = 0;
+  s->prof_kernels = 0;
+  return TD_OK;
+}
+
+td_status td_profile_read(td_segment* s, double* ms_total, int64_t* dominant_launches, int64_t* kernels_launched) {
+  if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
+  double tot = 0.0;
+  for (size_t i = 0; i + 1 < s->ev_used; i += 2) {
+    TD_CUDA(cudaEventSynchronize(s->ev[i + 1]));
+    float ms = 0.f;
+    TD_CUDA(cudaEventElapsedTime(&ms, s->ev[i], s->ev[i + 1]));
+    tot += ms;
+  }
+  if (ms_total) *ms_total = tot;
+  if (dominant_launches) *dominant_launches = (int64_t)(s->ev_used / 2);
+  if (kernels_launched) *kernels_launched = s->prof_kernels;
+  s->ev_used = 0;
+  s->prof_kernels = 0;
+  return TD_OK;
+}
+
+void td_segment_destroy(td_segment* s) {
+  if (!s) return;
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != s->device) cudaSetDevice(s->device);
+  cudaDeviceSynchronize();
+  dev_free(s->acf);
+  dev_free(s->t);
+  dev_free(s->L);
+  dev_free(s->dinv);
+  dev_free(s->ldpart);
+  dev_free(s->op);
+  dev_free(s->status);
+  dev_free(s->scr.rs);
+  dev_free(s->scr.partials);
+  dev_free(s->scr.w64);
+  dev_free(s->scr.items);
+  dev_free(s->scr.segdev);
+  dev_free(s->scr.rsf);
+  for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
+  if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
+  delete s;
+}
+
+td_status td_debug_bounded_wait(int64_t limit_ns, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  DevStatus* d = nullptr;
+  td_status r = dev_alloc(&d, 1, "probe status");
+  if (r != TD_OK) return r;
+  DevStatus h{0, 0, 0};
+  cudaError_t e = cudaMemcpyAsync(d, &h, sizeof h, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_bounded_wait_probe(d, limit_ns, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&h, d, sizeof h, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "bounded wait probe");
+  if (h.code == ST_TIMEOUT) return fail(TD_ERR_TIMEOUT, "bounded wait ran out as expected");
+  return TD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,320 @@
+// Tensor-core whitening W = L^{-1} R with split bf16 products and the fused
+// chi2 epilogue (Sec. II.A, W = L^{-1} and Eq. eq:td_like_whitened; Sec.
+// III.A, the cached-operator "CDO" evaluation; Sec. III.C, precision: the
+// operator is precomputed in FP64 and evaluated in lower precision).
+//
+// The product is computed transposed, W^T = R^T (L^{-1})^T, so that each
+// TMEM lane holds one residual column and the chi2 sum over rows happens in
+// one thread's registers with no cross-thread reduction:
+//   MMA M = 128 residual columns (A = R^T slices, K-major),
+//   MMA N = 256 rows of W        (B = L^{-1} slices, K-major),
+//   reduction over the kept samples j in k-blocks of 32 (64-byte swizzle).
+// Each operand is split into bf16 slices x = x0 + x1 (+ x2); the accumulator
+// takes the products x_a * y_b with a + b <= NSL - 1 (3 for two slices, 6 for
+// three), all in FP32 in tensor memory.
+//
+// Work: one output tile = (segment, row tile m, column tile c); the row tile
+// needs k-blocks 0 .. 8(m+1)-1 (the lower triangle).  Tiles are sorted by
+// work (largest first) and dealt to the persistent CTAs in snake order.
+//
+// Warp roles (192 threads, one CTA per SM):
+//   warp 0 lane 0 : TMA producer, STAGES-deep ring of (A, B) slice stages
+//   warp 1        : TMEM allocator; lane 0 issues tcgen05.mma
+//   warps 2..5    : epilogue; TMEM -> registers, exact squares, compensated
+//                   sums, one FP64 partial per (row tile, column)
+// Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile
+// overlap the MMAs of the next.  Every wait is bounded (wait_limit_ns).
+#include "td_internal.h"
+
+namespace td {
+namespace tc {
+constexpr int BM = TC_COLS;      // 128
+constexpr int BN = OP_ROWS;      // 256
+constexpr int BK = OP_KB;        // 32
+constexpr int STAGES = 3;
+constexpr int A_SLICE = BM * BK * 2;   // 8 KB
+constexpr int B_SLICE = BN * BK * 2;   // 16 KB
+constexpr int A_STAGE = 3 * A_SLICE;
+constexpr int B_STAGE = 3 * B_SLICE;
+constexpr int STAGE = A_STAGE + B_STAGE;   // 72 KB
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM = STAGES * STAGE + BAR_BYTES + 1024;
+constexpr int THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+}  // namespace tc
+
+struct TcSingle {           // single-segment launch: item list is implicit
+  TcSegDev seg;
+  int nm;                   // row tiles
+  int nc;                   // column tiles
+  int nkb_max;              // k-blocks available (ceil(N'/32))
+};
+
+__device__ __forceinline__ TcItem single_item(const TcSingle& p, int idx) {
+  TcItem it;
+  it.seg = 0;
+  it.m = p.nm - 1 - idx / p.nc;
+  it.c = idx % p.nc;
+  int nkb = (tc::BN / tc::BK) * (it.m + 1);
+  it.nkb = nkb < p.nkb_max ? nkb : p.nkb_max;
+  return it;
+}
+
+template <int NSL, bool GROUPED>
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    k_tc_cdo(const __grid_constant__ TcSingle single, const TcItem* __restrict__ items, int n_items,
+             const TcSegDev* __restrict__ segs, DevStatus* status, uint64_t limit_ns) {
+  using namespace tc;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + 2;
+  uint64_t* fin = tempty + 2;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int n_total = GROUPED ? n_items : single.nm * single.nc;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ------------------------------------------------ TMA producer
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, issued_phase = 0;
+      if (!GROUPED) {
+        prefetch_tmap(&single.seg.mapA);
+        prefetch_tmap(&single.seg.mapB);
+      }
+      for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
+        const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+        if (idx >= n_total) continue;
+        const TcItem it = GROUPED ? items[idx] : single_item(single, idx);
+        const TcSegDev* sd = GROUPED ? &segs[it.seg] : &single.seg;
+        const int blk0 = (BN / BK) * it.m * (it.m + 1) / 2;
+        bool ok = true;
+        for (int kb = 0; kb < it.nkb; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, limit_ns)) {
+            set_status(status, ST_TIMEOUT, 10);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * STAGE;
+          uint8_t* sb = sa + A_STAGE;
+          mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (A_SLICE + B_SLICE)));
+          tma_load_3d(sa, &sd->mapA, &full[stage], kb * BK, it.c * BM, 0);
+          tma_load_3d(sb, &sd->mapB, &full[stage], 0, 0, (blk0 + kb) * 3);
+          issued_mask |= 1u << stage;
+          issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+      // every issued copy must land before the CTA may exit
+      for (int s = 0; s < STAGES; ++s)
+        if (issued_mask & (1u << s)) mbar_wait(&full[s], (issued_phase >> s) & 1u, limit_ns);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ------------------------------------------------ MMA issuer
+      constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+      int stage = 0;
+      uint32_t phase = 0;
+      int tl = 0;
+      for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
+        const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+        if (idx >= n_total) continue;
+        const TcItem it = GROUPED ? items[idx] : single_item(single, idx);
+        const int buf = tl & 1;
+        const uint32_t use = (uint32_t)(tl >> 1);
+        if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, limit_ns)) {
+          set_status(status, ST_TIMEOUT, 20);
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
+        bool ok = true;
+        for (int kb = 0; kb < it.nkb; ++kb) {
+          if (!mbar_wait(&full[stage], phase, limit_ns)) {
+            set_status(status, ST_TIMEOUT, 21);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * STAGE);
+          const uint32_t sb = sa + A_STAGE;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+#pragma unroll
+            for (int ia = 0; ia < NSL; ++ia) {
+#pragma unroll
+              for (int ib = 0; ib < NSL; ++ib) {
+                if (ia + ib > NSL - 1) continue;
+                const uint64_t ad = smem_desc_sw64(sa + ia * A_SLICE + kk * 32);
+                const uint64_t bd = smem_desc_sw64(sb + ib * B_SLICE + kk * 32);
+                const uint32_t acc = (kb > 0 || kk > 0 || ia > 0 || ib > 0) ? 1u : 0u;
+                tc_mma_f16(dt, ad, bd, idesc, acc);
+              }
+            }
+          }
+          tc_commit(&empty[stage]);   // frees this smem stage once these MMAs retire
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        tc_commit(&tfull[buf]);       // accumulator ready for the epilogue
+        ++tl;
+      }
+      tc_commit(fin);                 // all MMAs issued by this thread retired
+      mbar_wait(fin, 0, limit_ns);
+    }
+  } else {
+    // -------------------------------------------------- epilogue (warps 2..5)
+    const int q = warp & 3;   // TMEM lane quarter this warp may access
+    int tl = 0;
+    for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
+      const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+      if (idx >= n_total) continue;
+      const TcItem it = GROUPED ? items[idx] : single_item(single, idx);
+      const TcSegDev* sd = GROUPED ? &segs[it.seg] : &single.seg;
+      const int buf = tl & 1;
+      const uint32_t use = (uint32_t)(tl >> 1);
+      if (!mbar_wait(&tfull[buf], use & 1u, limit_ns)) {
+        if (lane == 0) set_status(status, ST_TIMEOUT, 30);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      float hi = 0.f, lo = 0.f;
+      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+#pragma unroll 1
+      for (int ch = 0; ch < BN / 32; ++ch) {
+        float v[32];
+        tmem_ld32(ta + (uint32_t)(ch * 32), v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) ff_add_square(v[i], hi, lo);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      const int col = it.c * BM + q * 32 + lane;
+      if (col < sd->K) sd->partials[(int64_t)it.m * sd->ldp + col] = (double)hi + (double)lo;
+      ++tl;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, TMEM_COLS);
+  }
+}
+
+static int g_num_sms = 0;
+
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 148;
+  }
+  return g_num_sms;
+}
+
+template <int NSL, bool GROUPED>
+static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int n_items, const TcSegDev* segs,
+                               DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_cdo<NSL, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         tc::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const int n_total = GROUPED ? n_items : single.nm * single.nc;
+  if (n_total <= 0) return cudaSuccess;
+  int grid = num_sms();
+  if (grid > n_total) grid = n_total;
+  k_tc_cdo<NSL, GROUPED><<<grid, tc::THREADS, tc::SMEM, st>>>(single, items, n_items, segs, status,
+                                                              (uint64_t)wait_limit_ns);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_single(const TcSegDev& seg, int nm, int nc, int nkb_max, int nslices, DevStatus* status,
+                             int64_t wait_limit_ns, cudaStream_t st) {
+  TcSingle p;
+  memset(&p, 0, sizeof(p));
+  p.seg = seg;
+  p.nm = nm;
+  p.nc = nc;
+  p.nkb_max = nkb_max;
+  if (nslices == 3) return launch_impl<3, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
+  if (nslices == 2) return launch_impl<2, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices,
+                          DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+  TcSingle p;
+  memset(&p, 0, sizeof(p));
+  if (nslices == 3) return launch_impl<3, true>(p, items, n_items, segs, status, wait_limit_ns, st);
+  if (nslices == 2) return launch_impl<2, true>(p, items, n_items, segs, status, wait_limit_ns, st);
+  return cudaErrorInvalidValue;
+}
+
+// chi2 and logL per column from the per-row-tile partials (fixed order),
+// for every segment of a grouped launch.
+__global__ void k_tc_finalize(const TcSegDev* __restrict__ segs) {
+  const TcSegDev& sd = segs[blockIdx.y];
+  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < sd.K;
+       col += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int m = 0; m < sd.nm; ++m) s += sd.partials[(int64_t)m * sd.ldp + col];
+    if (sd.chi2) sd.chi2[col] = s;
+    sd.logL[col] = -0.5 * s - 0.5 * sd.logdet - 0.5 * (double)sd.nk * 1.8378770664093454836;
+  }
+}
+
+cudaError_t launch_tc_finalize(const TcSegDev* segs, int nseg, int64_t maxK, cudaStream_t st) {
+  if (nseg <= 0 || maxK <= 0) return cudaSuccess;
+  int gx = (int)ceil_div(maxK, 256);
+  if (gx > 8) gx = 8;
+  k_tc_finalize<<<dim3(gx, nseg), 256, 0, st>>>(segs);
+  return cudaGetLastError();
+}
+
+}  // namespace td

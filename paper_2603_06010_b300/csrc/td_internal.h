@@ -1,0 +1,133 @@
+// Host-side internals of libtd: the segment object, scratch, kernel launchers.
+#pragma once
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/td.h"
+#include "td_common.cuh"
+
+namespace td {
+
+constexpr int FT = 64;          // FP64 tile (factor, FP64 forward substitution)
+constexpr int OP_ROWS = 256;    // operator row tile (tensor-core N)
+constexpr int OP_KB = 32;       // operator k-block (64 B of bf16)
+constexpr int TC_COLS = 128;    // residual columns per tensor-core tile (MMA M)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
+
+// offset (in 256x32 blocks) of operator row tile m in the packed lower triangle
+inline int64_t op_row_offset(int64_t m) { return (OP_ROWS / OP_KB) * m * (m + 1) / 2; }
+
+struct TcItem {      // one tensor-core output tile
+  int seg;           // index into the launch's segment table
+  int m;             // W row tile (256 rows)
+  int c;             // residual column tile (128 columns)
+  int nkb;           // k-blocks of 32 to accumulate
+};
+
+struct TcSegDev {    // per-segment launch data (device-resident)
+  CUtensorMap mapA;  // residual slices  (j: N', k: K, slice: 3)
+  CUtensorMap mapB;  // operator slices  (32, 256, blocks*3)
+  double* partials;  // [n_row_tiles][ldp]
+  int nk;
+  int K;
+  int ldp;
+  int nm;            // operator row tiles
+  double logdet;
+  double* logL;
+  double* chi2;
+  int64_t pad[2];
+};
+static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+
+struct Scratch {
+  int64_t capK = 0;          // columns the buffers hold
+  __nv_bfloat16* rs = nullptr;  // residual slices [3][capK][nkp8]
+  double* partials = nullptr;   // [n_tiles][capK_pad] (tensor path) / [nt64][capK_pad] (fp64)
+  double* w64 = nullptr;        // FP64 W for the plain path [nkp][capK]
+  TcItem* items = nullptr;      // tensor-core work list
+  int n_items = 0;
+  int64_t items_for_K = -1;
+  TcSegDev* segdev = nullptr;   // one device descriptor
+  int64_t segdev_K = -1;
+  const float* segdev_R = nullptr;
+  int64_t segdev_ldr = -1;
+  float* rsf = nullptr;         // streaming-path partial W [units][64][K] (float)
+  int64_t rsf_bytes = 0;
+};
+
+}  // namespace td
+
+struct td_segment {
+  int device = 0;
+  int64_t n = 0;          // samples
+  int64_t nk = 0;         // kept samples N'
+  int64_t nkp = 0;        // N' padded to 256
+  int64_t nkp8 = 0;       // N' padded to 8 (row stride of residual slices)
+  double* acf = nullptr;          // device [n]
+  int32_t* t = nullptr;           // device kept indices [nk]
+  double* L = nullptr;            // device FP64 [nkp x nkp] column-major, lower = factor
+  double* dinv = nullptr;         // device FP64 [nkp/64][64*64] inverse diagonal tiles
+  double* ldpart = nullptr;       // device [nkp/64]
+  __nv_bfloat16* op = nullptr;    // device operator slices, packed 256x32 blocks x 3
+  int64_t op_blocks = 0;
+  td::DevStatus* status = nullptr;  // device
+  bool factored = false;
+  double logdet = 0.0;
+  int64_t pivot = -1;
+  td::Scratch scr;
+  // instrumentation
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;   // start/stop pairs
+  size_t ev_used = 0;
+  int64_t prof_kernels = 0;
+};
+
+namespace td {
+// error plumbing
+td_status fail(td_status code, const std::string& msg);
+td_status cuda_fail(cudaError_t e, const char* what);
+#define TD_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return td::cuda_fail(e_, #call); \
+  } while (0)
+
+// kernel launchers (return cudaError_t of the launch)
+cudaError_t launch_gather(const double* acf, const int32_t* t, int64_t nk, int64_t nkp, double* A,
+                          cudaStream_t st);
+cudaError_t launch_potrf_diag(double* A, int64_t ld, int64_t nk, int j, double* dinv, double* ldpart,
+                              DevStatus* status, cudaStream_t st);
+cudaError_t launch_panel(double* A, int64_t ld, int j, int nt, const double* dinv, cudaStream_t st);
+cudaError_t launch_syrk(double* A, int64_t ld, int j, int nt, cudaStream_t st);
+
+// FP64 forward substitution of block row I: W_I = Dinv_I (RHS_I - sum_J L_IJ W_J)
+//   rhs32 != nullptr: RHS = float32 R (ldr); else identity (computes L^{-1}).
+cudaError_t launch_trsm_f64_row(const double* L, int64_t ld, const double* dinv, int I, const float* rhs32,
+                                int64_t ldr, int64_t nk, int64_t ncols, double* W, int64_t ldw,
+                                double* partials, int64_t ldp, cudaStream_t st);
+cudaError_t launch_finalize(const double* partials, int64_t ldp, int nparts, int64_t K, double logdet,
+                            int64_t nk, double* logL, double* chi2, cudaStream_t st);
+
+cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, __nv_bfloat16* op,
+                             cudaStream_t st);
+cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8,
+                            int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st);
+
+// tensor-core CDO product + chi2 partials over a work list
+cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices,
+                          DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
+cudaError_t launch_tc_finalize(const TcSegDev* segs, int nseg, int64_t maxK, cudaStream_t st);
+
+cudaError_t launch_bounded_wait_probe(DevStatus* status, int64_t limit_ns, cudaStream_t st);
+
+// tensor map encoding (driver API)
+td_status encode_maps(td_segment* s, const __nv_bfloat16* rs, int64_t K, int64_t capK, TcSegDev* host);
+
+}  // namespace td

@@ -1,0 +1,151 @@
+// Plain FP64 blocked forward substitution W = L^{-1} R (Sec. II.A, the
+// whitening operator W = L^{-1}; Sec. III.A, the triangular-solve form of
+// the whitening), the FP64 chi2 / logL reduction, and the bounded-wait probe.
+//
+// One launch per 64-row block row I (the dependency chain of the solve):
+//   W_I = L_II^{-1} (R_I - sum_{J<I} L_IJ W_J)
+// Each CTA owns 32 columns.  With no right-hand side given, R is the
+// identity and the launches build L^{-1} itself (columns right of the
+// diagonal block are zero and skipped).
+#include "td_internal.h"
+
+namespace td {
+
+constexpr double LOG2PI = 1.8378770664093454836;
+
+__global__ void __launch_bounds__(256) k_trsm_f64_row(const double* __restrict__ L, int64_t ld,
+                                                       const double* __restrict__ dinv, int I,
+                                                       const float* __restrict__ rhs32, int64_t ldr, int64_t nk,
+                                                       int64_t ncols, double* __restrict__ W, int64_t ldw,
+                                                       double* __restrict__ partials, int64_t ldp) {
+  __shared__ double Ls[FT * FT];   // Ls[k*64 + r] = L_IJ[r][k]
+  __shared__ double Ws[FT * 32];   // Ws[k*32 + c] = W_J[k][c]; later the reduction scratch
+  const int tid = threadIdx.x;
+  const int r = tid & 63, cg = tid >> 6;   // 4 groups of 8 columns
+  const int64_t col0 = (int64_t)blockIdx.x * 32;
+  const bool ident = (rhs32 == nullptr);
+  int Jstart = 0;
+  if (ident) {
+    if (col0 >= (int64_t)(I + 1) * FT) return;   // strictly upper part of L^{-1}: zero
+    Jstart = (int)(col0 / FT);
+  }
+  const int64_t row = (int64_t)I * FT + r;
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t col = col0 + cg * 8 + q;
+    if (ident)
+      acc[q] = (row == col) ? 1.0 : 0.0;
+    else
+      acc[q] = (row < nk && col < ncols) ? (double)rhs32[row + col * ldr] : 0.0;
+  }
+  for (int J = Jstart; J < I; ++J) {
+    for (int e = tid; e < FT * FT; e += 256) {
+      const int rr = e % FT, k = e / FT;
+      Ls[e] = L[((int64_t)I * FT + rr) + ((int64_t)J * FT + k) * ld];
+    }
+    for (int e = tid; e < FT * 32; e += 256) {
+      const int k = e % FT, c = e / FT;
+      const int64_t col = col0 + c;
+      Ws[k * 32 + c] = (col < ncols) ? W[((int64_t)J * FT + k) + col * ldw] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < FT; ++k) {
+      const double a = Ls[k * FT + r];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc[q] = fma(-a, Ws[k * 32 + cg * 8 + q], acc[q]);
+    }
+    __syncthreads();
+  }
+  // W_I = Dinv_I * T  (T = acc, staged through shared memory)
+#pragma unroll
+  for (int q = 0; q < 8; ++q) Ws[r * 32 + cg * 8 + q] = acc[q];
+  const double* D = dinv + (int64_t)I * FT * FT;   // column-major: D[rr + 64 k] = Dinv[rr][k]
+  for (int e = tid; e < FT * FT; e += 256) Ls[e] = D[e];
+  __syncthreads();
+  double out[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) out[q] = 0.0;
+  for (int k = 0; k <= r; ++k) {
+    const double a = Ls[k * FT + r];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) out[q] = fma(a, Ws[k * 32 + cg * 8 + q], out[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int64_t col = col0 + cg * 8 + q;
+    if (col < ncols) W[row + col * ldw] = out[q];
+  }
+  if (partials != nullptr) {
+    // chi2 share of these 64 rows, per column: fixed shuffle tree, then 2 warps
+    __syncthreads();   // Ws is free again
+    double (*red)[8] = reinterpret_cast<double (*)[8]>(Ws);
+    const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      double v = out[q] * out[q];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][q] = v;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      const int g = tid >> 3, q = tid & 7;
+      const int64_t col = col0 + g * 8 + q;
+      const double s = red[2 * g][q] + red[2 * g + 1][q];
+      if (col < ncols) partials[(int64_t)I * ldp + col] = s;
+    }
+  }
+}
+
+cudaError_t launch_trsm_f64_row(const double* L, int64_t ld, const double* dinv, int I, const float* rhs32,
+                                int64_t ldr, int64_t nk, int64_t ncols, double* W, int64_t ldw,
+                                double* partials, int64_t ldp, cudaStream_t st) {
+  const int64_t grid = ceil_div(ncols, 32);
+  if (grid <= 0) return cudaSuccess;
+  k_trsm_f64_row<<<(unsigned)grid, 256, 0, st>>>(L, ld, dinv, I, rhs32, ldr, nk, ncols, W, ldw, partials,
+                                                  ldp);
+  return cudaGetLastError();
+}
+
+// chi2_k = sum over row blocks of the partials (fixed order), then
+// logL_k = -chi2_k/2 - logdet/2 - (N'/2) log 2 pi   (Eq. eqn:lik with the
+// constant written out).
+__global__ void k_finalize(const double* __restrict__ partials, int64_t ldp, int nparts, int64_t K,
+                           double logdet, int64_t nk, double* __restrict__ logL, double* __restrict__ chi2) {
+  const int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (col >= K) return;
+  double s = 0.0;
+  for (int p = 0; p < nparts; ++p) s += partials[(int64_t)p * ldp + col];
+  if (chi2) chi2[col] = s;
+  logL[col] = -0.5 * s - 0.5 * logdet - 0.5 * (double)nk * LOG2PI;
+}
+
+cudaError_t launch_finalize(const double* partials, int64_t ldp, int nparts, int64_t K, double logdet,
+                            int64_t nk, double* logL, double* chi2, cudaStream_t st) {
+  if (K <= 0) return cudaSuccess;
+  k_finalize<<<(unsigned)ceil_div(K, 256), 256, 0, st>>>(partials, ldp, nparts, K, logdet, nk, logL, chi2);
+  return cudaGetLastError();
+}
+
+// A wait on an mbarrier that nothing arrives at: must give up after limit_ns
+// and report TD_ERR_TIMEOUT, leaving the context usable.
+__global__ void k_wait_probe(DevStatus* status, int64_t limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (!mbar_wait(&bar, 0, (uint64_t)limit_ns)) set_status(status, ST_TIMEOUT, 1);
+  }
+}
+
+cudaError_t launch_bounded_wait_probe(DevStatus* status, int64_t limit_ns, cudaStream_t st) {
+  k_wait_probe<<<1, 32, 0, st>>>(status, limit_ns);
+  return cudaGetLastError();
+}
+
+}  // namespace td

@@ -1,0 +1,193 @@
+"""Thin ctypes binding of libtd (the C ABI in include/td.h).
+
+Argument marshalling only: every step of the likelihood runs in libtd's CUDA
+kernels.  The library is loaded from the package directory; if it is missing
+the import of this module's `lib()` raises -- there is no CPU fallback.
+Device buffers are torch tensors (PyTorch supplies device memory and
+streams); their data pointers are passed through unchanged.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtd.so")
+
+TD_OK, TD_ERR_INVALID, TD_ERR_NOT_PD, TD_ERR_OOM, TD_ERR_CUDA, TD_ERR_TIMEOUT, TD_ERR_NOT_FACTORED, \
+    TD_ERR_UNSUPPORTED = range(8)
+TD_PREC_FP64, TD_PREC_6XBF16, TD_PREC_3XBF16, TD_PREC_AUTO = range(4)
+TD_PATH_AUTO, TD_PATH_TENSOR, TD_PATH_STREAM, TD_PATH_FP64 = range(4)
+
+STATUS_NAMES = {0: "TD_OK", 1: "TD_ERR_INVALID", 2: "TD_ERR_NOT_PD", 3: "TD_ERR_OOM", 4: "TD_ERR_CUDA",
+                5: "TD_ERR_TIMEOUT", 6: "TD_ERR_NOT_FACTORED", 7: "TD_ERR_UNSUPPORTED"}
+
+# every symbol include/td.h declares, with (restype, argtypes)
+_c = ctypes
+_vp = _c.c_void_p
+_i64 = _c.c_int64
+SIGNATURES = {
+    "td_options_default": (None, [_vp]),
+    "td_segment_create": (_c.c_int, [_vp, _i64, _vp, _vp, _c.POINTER(_vp)]),
+    "td_factor": (_c.c_int, [_vp, _vp]),
+    "td_logdet": (_c.c_int, [_vp, _c.POINTER(_c.c_double)]),
+    "td_kept": (_i64, [_vp]),
+    "td_last_pivot": (_i64, [_vp]),
+    "td_loglike_batch": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
+    "td_reserve": (_c.c_int, [_vp, _i64, _vp]),
+    "td_loglike_grouped": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp]),
+    "td_check": (_c.c_int, [_vp, _vp]),
+    "td_segment_destroy": (None, [_vp]),
+    "td_last_error": (_c.c_char_p, []),
+    "td_resident_bytes": (_i64, [_vp]),
+    "td_debug_bounded_wait": (_c.c_int, [_i64, _vp]),
+    "td_profile_enable": (_c.c_int, [_vp, _c.c_int]),
+    "td_profile_read": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.POINTER(_i64), _c.POINTER(_i64)]),
+}
+
+
+class TdOptions(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("path", ctypes.c_int), ("refine", ctypes.c_int),
+                ("reserved0", ctypes.c_int), ("wait_limit_ns", ctypes.c_int64)]
+
+
+class TdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libtd.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libtd.so is not built ({LIB_PATH}); run paper_2603_06010_b300/build.py")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(code: int):
+    if code != TD_OK:
+        raise TdError(code, lib().td_last_error().decode())
+
+
+def options(precision: int = TD_PREC_6XBF16, path: int = TD_PATH_AUTO, refine: int = 0,
+            wait_limit_ns: int = 1_000_000_000) -> TdOptions:
+    o = TdOptions()
+    lib().td_options_default(ctypes.byref(o))
+    o.precision, o.path, o.refine, o.wait_limit_ns = precision, path, refine, wait_limit_ns
+    return o
+
+
+def _stream_ptr(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Segment:
+    """One analysis segment (td_segment): ACF + gap mask, factored on device."""
+
+    def __init__(self, acf, mask=None, stream=None, factor: bool = True):
+        acf = np.ascontiguousarray(acf, dtype=np.float64)
+        self.n = int(acf.shape[0])
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        h = ctypes.c_void_p()
+        st = _stream_ptr(stream)
+        _check(lib().td_segment_create(acf.ctypes.data, self.n, None if m is None else m.ctypes.data,
+                                       st, ctypes.byref(h)))
+        self.handle = h
+        if factor:
+            self.factor(stream)
+
+    def factor(self, stream=None):
+        _check(lib().td_factor(self.handle, _stream_ptr(stream)))
+
+    @property
+    def n_kept(self) -> int:
+        return int(lib().td_kept(self.handle))
+
+    @property
+    def logdet(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().td_logdet(self.handle, ctypes.byref(v)))
+        return v.value
+
+    @property
+    def last_pivot(self) -> int:
+        return int(lib().td_last_pivot(self.handle))
+
+    @property
+    def resident_bytes(self) -> int:
+        return int(lib().td_resident_bytes(self.handle))
+
+    def reserve(self, K: int, opt: TdOptions | None = None):
+        _check(lib().td_reserve(self.handle, int(K), None if opt is None else ctypes.byref(opt)))
+
+    def loglike_into(self, R, logL, opt: TdOptions | None = None, chi2=None, stream=None, ldr=None):
+        """R: CUDA float32 tensor, shape (K, ldr) row-major == N' x K column-major.
+        logL (and chi2): CUDA float64 tensors of K entries."""
+        K = int(R.shape[0])
+        ld = int(R.stride(0)) if ldr is None else int(ldr)
+        _check(lib().td_loglike_batch(self.handle, R.data_ptr(), ld, K, logL.data_ptr(),
+                                      None if opt is None else ctypes.byref(opt),
+                                      None if chi2 is None else chi2.data_ptr(), _stream_ptr(stream)))
+
+    def loglike(self, R, opt: TdOptions | None = None, with_chi2: bool = False, stream=None):
+        import torch
+        K = int(R.shape[0])
+        logL = torch.empty(K, dtype=torch.float64, device=R.device)
+        chi2 = torch.empty(K, dtype=torch.float64, device=R.device) if with_chi2 else None
+        self.loglike_into(R, logL, opt, chi2, stream)
+        return (logL, chi2) if with_chi2 else logL
+
+    def profile(self, enable: bool = True):
+        _check(lib().td_profile_enable(self.handle, 1 if enable else 0))
+
+    def profile_read(self):
+        """(dominant-kernel ms summed, dominant launches, kernels launched)."""
+        ms, nd, nk = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().td_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(nd), ctypes.byref(nk)))
+        return ms.value, nd.value, nk.value
+
+    def check(self, stream=None):
+        _check(lib().td_check(self.handle, _stream_ptr(stream)))
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().td_segment_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def loglike_grouped(segments, Rs, logLs, opt: TdOptions | None = None, stream=None):
+    n = len(segments)
+    H = (ctypes.c_void_p * n)(*[s.handle.value for s in segments])
+    RP = (ctypes.c_void_p * n)(*[r.data_ptr() for r in Rs])
+    LD = (ctypes.c_int64 * n)(*[int(r.stride(0)) for r in Rs])
+    KK = (ctypes.c_int64 * n)(*[int(r.shape[0]) for r in Rs])
+    LP = (ctypes.c_void_p * n)(*[x.data_ptr() for x in logLs])
+    _check(lib().td_loglike_grouped(H, RP, LD, KK, LP, n, None if opt is None else ctypes.byref(opt),
+                                    _stream_ptr(stream)))
+
+
+def debug_bounded_wait(limit_ns: int, stream=None) -> int:
+    """Run the bounded-wait probe; returns the td_status (TD_ERR_TIMEOUT expected)."""
+    return int(lib().td_debug_bounded_wait(int(limit_ns), _stream_ptr(stream)))

@@ -1,0 +1,63 @@
+"""Write tests/golden/full_size.json: oracle logdet / chi2 / logL for sampled
+columns of the full-size workloads (one N=1024 segment; the gap-free N=8192
+batch of K=4096; the gapped three-detector N=16384 batch of K=1024).
+
+Calls only the CPU oracle and the seeded input generators.  Run from the
+repository root:  python tests/golden/make_golden.py
+"""
+import json
+import os
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+sys.path.insert(0, ROOT)
+
+import oracle  # noqa: E402
+from paper_2603_06010_b300 import inputs  # noqa: E402
+
+OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "full_size.json")
+
+
+def sample_cols(K, extra):
+    cols = sorted(set([c for c in extra if c < K]))
+    return cols
+
+
+def one(n, fs, seed, K, rseed, cols, n_gaps=0, gap_len=512, scale=1.0):
+    seg = inputs.make_segment(n, fs, seed, n_gaps=n_gaps, gap_len=gap_len, scale=scale)
+    R = inputs.residual_batch(seg, K, rseed)
+    osg = oracle.OracleSegment(seg.acf, seg.mask)
+    sub = R[cols]
+    chi = osg.chi2(sub)
+    ll = oracle.loglike_from_chi2(chi, osg.logdet, osg.n_kept)
+    return dict(n=n, fs=fs, seed=seed, K=K, rseed=rseed, n_gaps=n_gaps, gap_len=gap_len, scale=scale,
+                n_kept=osg.n_kept, columns=cols, logdet=osg.logdet, chi2=chi.tolist(), logL=ll.tolist(),
+                r_checksum=[float(np.sum(sub[i].astype(np.float64))) for i in range(len(cols))])
+
+
+def main():
+    t0 = time.time()
+    out = {}
+    c1 = inputs.CFG1
+    out["cfg1"] = one(c1["n"], c1["fs"], c1["seed"], 1, c1["seed"] + 1, [0])
+    c2 = inputs.CFG2
+    cols2 = sample_cols(c2["K"], [0, 1, 2, 3, 127, 128, 129, 1000, 2047, 2048, 3001, 4094, 4095])
+    out["cfg2"] = one(c2["n"], c2["fs"], c2["seed"], c2["K"], c2["seed"] + 1, cols2)
+    c3 = inputs.CFG3
+    cols3 = sample_cols(c3["K"], [0, 1, 100, 511, 512, 1022, 1023])
+    dets = []
+    for d, sc in enumerate(c3["scales"]):
+        dets.append(one(c3["n"], c3["fs"], c3["seed"] + 10 * d, c3["K"], c3["seed"] + 10 * d + 1, cols3,
+                        n_gaps=c3["n_gaps"], gap_len=c3["gap_len"], scale=sc))
+    out["cfg3"] = dict(detectors=dets, columns=cols3,
+                       joint_logL=np.sum([d_["logL"] for d_ in dets], axis=0).tolist())
+    with open(OUT, "w") as f:
+        json.dump(out, f, indent=1)
+    print(f"wrote {OUT} in {time.time() - t0:.1f} s")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+"""CUDA path (through the C ABI) against the CPU FP64 oracle.
+
+Tolerances (the bar stated for the method): |delta logL| <= 1e-3 absolute and
+chi2 relative error <= 1e-7 for the split-product tensor-core path; the
+plain FP64 path is held to 1e-11 relative.  The 3xBF16 (two-slice) option
+is checked against the error band its arithmetic gives (~1e-5 relative),
+which is above the bar by design.
+"""
+import json
+import os
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_06010_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+TOL = {  # precision -> (chi2 rel, |dlogL| abs)
+    "fp64": (1e-11, 1e-7),
+    "6xbf16": (1e-7, 1e-3),
+    "3xbf16": (1e-4, 5.0),
+}
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _opt(td, prec):
+    p = {"fp64": td.TD_PREC_FP64, "6xbf16": td.TD_PREC_6XBF16, "3xbf16": td.TD_PREC_3XBF16}[prec]
+    return td.options(precision=p)
+
+
+def _run(torch, td, seg, R_kn, prec):
+    R = torch.from_numpy(np.ascontiguousarray(R_kn)).cuda()
+    logL, chi2 = seg.loglike(R, _opt(td, prec), with_chi2=True)
+    torch.cuda.synchronize()
+    seg.check()
+    return logL.cpu().numpy(), chi2.cpu().numpy()
+
+
+def _compare(prec, got_ll, got_chi, exp_ll, exp_chi, what=""):
+    rel_tol, abs_tol = TOL[prec]
+    rel = np.abs(got_chi - exp_chi) / np.abs(exp_chi)
+    dll = np.abs(got_ll - exp_ll)
+    assert np.all(np.isfinite(got_ll)), what
+    assert rel.max() <= rel_tol, f"{what} {prec}: chi2 rel {rel.max():.3e} > {rel_tol}"
+    assert dll.max() <= abs_tol, f"{what} {prec}: |dlogL| {dll.max():.3e} > {abs_tol}"
+    return rel.max(), dll.max()
+
+
+def _mask(n, spans):
+    m = np.ones(n, np.uint8)
+    for a, b in spans:
+        m[a:b] = 0
+    return m
+
+
+# (name, n, fs, mask spans, K) -- sizes span several 64/256-row tiles, ragged
+# tails, ragged column tiles, gaps at the start/end/adjacent, a single kept
+# sample and the one-sample segment.
+CASES = [
+    ("n1", 1, 1024.0, None, 3),
+    ("n64_k1", 64, 1024.0, None, 1),
+    ("n255_k3", 255, 1024.0, None, 3),
+    ("n257_gaps_k129", 257, 1024.0, [(10, 30), (100, 120)], 129),
+    ("n600_edges_adjacent_k127", 600, 2048.0, [(0, 7), (200, 260), (261, 300), (590, 600)], 127),
+    ("one_kept_k5", 700, 2048.0, [(0, 350), (351, 700)], 5),
+    ("n2048_gaps_k300", 2048, 2048.0, [(500, 1012), (1500, 1600)], 300),
+    ("n1100_k257", 1100, 4096.0, None, 257),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "6xbf16", "3xbf16"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_parity_small(torch_cuda, gpu_lib, case, prec):
+    from paper_2603_06010_b300 import td
+    name, n, fs, spans, K = case
+    mask = None if spans is None else _mask(n, spans)
+    acf = inputs.acf_from_psd(n, fs) if n > 1 else np.array([2.5])
+    seg_o = oracle.OracleSegment(acf, mask)
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    R = inputs.noise_residuals(n, fs, K, 17, mask=mask) if n > 1 else \
+        rng.standard_normal((K, 1)).astype(np.float32)
+    R = (R + 0.5 * rng.standard_normal(R.shape)).astype(np.float32)
+    exp_chi = seg_o.chi2(R)
+    exp_ll = oracle.loglike_from_chi2(exp_chi, seg_o.logdet, seg_o.n_kept)
+    seg = td.Segment(acf, mask)
+    assert seg.n_kept == seg_o.n_kept
+    assert abs(seg.logdet - seg_o.logdet) <= 1e-10 * max(1.0, abs(seg_o.logdet))
+    got_ll, got_chi = _run(torch_cuda, td, seg, R, prec)
+    _compare(prec, got_ll, got_chi, exp_ll, exp_chi, name)
+
+
+def test_white_noise_closed_form(torch_cuda, gpu_lib):
+    """C = s2 I with gaps: logL = -|r|^2/(2 s2) - (N'/2) log(2 pi s2) exactly."""
+    from paper_2603_06010_b300 import td
+    n, s2 = 777, 3.5
+    mask = _mask(n, [(5, 9), (300, 420)])
+    nk = int(mask.sum())
+    R = np.random.default_rng(5).standard_normal((40, nk)).astype(np.float32)
+    R64 = R.astype(np.float64)
+    exp_ll = -np.sum(R64 * R64, 1) / (2 * s2) - 0.5 * nk * np.log(2 * np.pi * s2)
+    seg = td.Segment(inputs.white_acf(n, s2), mask)
+    for prec in ("fp64", "6xbf16"):
+        ll, _ = _run(torch_cuda, td, seg, R, prec)
+        assert np.max(np.abs(ll - exp_ll)) < 1e-6, prec
+
+
+def test_column_alone_equals_in_batch(torch_cuda, gpu_lib):
+    """A column's logL does not depend on the batch it is evaluated in (bitwise)."""
+    from paper_2603_06010_b300 import td
+    n = 1500
+    mask = _mask(n, [(700, 800)])
+    seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
+    R = inputs.noise_residuals(n, 2048.0, 300, 23, mask=mask)
+    for prec in ("fp64", "6xbf16"):
+        full, _ = _run(torch_cuda, td, seg, R, prec)
+        for k in (0, 1, 127, 128, 299):
+            alone, _ = _run(torch_cuda, td, seg, R[k:k + 1], prec)
+            assert alone[0] == full[k], (prec, k, alone[0], full[k])
+        part, _ = _run(torch_cuda, td, seg, R[100:229], prec)
+        assert np.array_equal(part, full[100:229]), prec
+
+
+def test_repeatable_bits(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    n = 1024
+    seg = td.Segment(inputs.acf_from_psd(n, 1024.0))
+    R = inputs.noise_residuals(n, 1024.0, 200, 29)
+    a, _ = _run(torch_cuda, td, seg, R, "6xbf16")
+    b, _ = _run(torch_cuda, td, seg, R, "6xbf16")
+    assert np.array_equal(a, b)
+
+
+def test_not_positive_definite(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    acf = np.zeros(100)
+    acf[0], acf[1] = 1.0, 2.0
+    with pytest.raises(td.TdError) as e:
+        td.Segment(acf)
+    assert e.value.code == td.TD_ERR_NOT_PD
+    seg = td.Segment(acf, factor=False)
+    with pytest.raises(td.TdError):
+        seg.factor()
+    assert seg.last_pivot == 1
+    o = oracle
+    with pytest.raises(o.NotPositiveDefinite) as e2:
+        o.OracleSegment(acf)
+    assert e2.value.pivot == seg.last_pivot
+
+
+def test_not_factored_and_bad_args(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    seg = td.Segment(inputs.acf_from_psd(128, 1024.0), factor=False)
+    R = torch_cuda.zeros((2, 128), dtype=torch_cuda.float32, device="cuda")
+    with pytest.raises(td.TdError) as e:
+        seg.loglike(R)
+    assert e.value.code == td.TD_ERR_NOT_FACTORED
+    seg.factor()
+    with pytest.raises(td.TdError) as e:
+        seg.loglike_into(R, torch_cuda.empty(2, dtype=torch_cuda.float64, device="cuda"), ldr=100)
+    assert e.value.code == td.TD_ERR_INVALID
+
+
+def test_bounded_wait_times_out_and_context_survives(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    assert td.debug_bounded_wait(20_000_000) == td.TD_ERR_TIMEOUT
+    # the context is still usable
+    seg = td.Segment(inputs.white_acf(64, 1.0))
+    R = torch_cuda.ones((3, 64), dtype=torch_cuda.float32, device="cuda")
+    ll = seg.loglike(R).cpu().numpy()
+    assert np.allclose(ll, -32.0 - 32.0 * np.log(2 * np.pi))
+
+
+# ---------------------------------------------------------------------------
+# full-size workloads, sampled columns against stored oracle values
+# ---------------------------------------------------------------------------
+def _golden():
+    with open(os.path.join(HERE, "golden", "full_size.json")) as f:
+        return json.load(f)
+
+
+def _full_case(torch, td, g, prec):
+    seg_in = inputs.make_segment(g["n"], g["fs"], g["seed"], n_gaps=g["n_gaps"], gap_len=g["gap_len"],
+                                 scale=g["scale"])
+    R = inputs.residual_batch(seg_in, g["K"], g["rseed"])
+    cols = g["columns"]
+    chk = [float(np.sum(R[c].astype(np.float64))) for c in cols]
+    assert np.allclose(chk, g["r_checksum"], rtol=1e-6, atol=1e-3), "input generator drifted"
+    seg = td.Segment(seg_in.acf, seg_in.mask)
+    assert abs(seg.logdet - g["logdet"]) <= 1e-9 * abs(g["logdet"])
+    ll, chi = _run(torch, td, seg, R, prec)   # the whole batch, as the benchmark launches it
+    seg.close()
+    return ll[cols], chi[cols]
+
+
+@pytest.mark.parametrize("prec", ["6xbf16", "fp64"])
+def test_full_cfg1(torch_cuda, gpu_lib, prec):
+    from paper_2603_06010_b300 import td
+    g = _golden()["cfg1"]
+    ll, chi = _full_case(torch_cuda, td, g, prec)
+    _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg1")
+
+
+def test_full_cfg2_gapfree_8192(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    g = _golden()["cfg2"]
+    ll, chi = _full_case(torch_cuda, td, g, "6xbf16")
+    _compare("6xbf16", ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg2")
+
+
+def test_full_cfg3_gapped_three_detectors(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    gg = _golden()["cfg3"]
+    joint = None
+    for g in gg["detectors"]:
+        ll, chi = _full_case(torch_cuda, td, g, "6xbf16")
+        _compare("6xbf16", ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg3 detector")
+        joint = ll if joint is None else joint + ll
+    assert np.max(np.abs(joint - np.array(gg["joint_logL"]))) <= 1e-3

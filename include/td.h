@@ -54,9 +54,13 @@ typedef enum {
 
 typedef enum {
   TD_PREC_FP64 = 0,   /* plain FP64 blocked forward substitution (CUDA cores) */
-  TD_PREC_6XBF16 = 1, /* 3 bf16 slices of L^{-1} and of R, 6 tensor-core products,
-                         FP32 accumulation in tensor memory (default) */
-  TD_PREC_3XBF16 = 2, /* 2 slices, 3 products (hi*hi + hi*lo + lo*hi) */
+  TD_PREC_BF16X10 = 1,/* default: L^{-1} and R as 4 bf16 slices each (a fixed-point hi
+                         slice on a per-row / per-column power-of-two quantum, plus
+                         3 floating remainder slices); 10 tensor-core products; the
+                         hi*hi sum accumulates exactly, the rest in a second FP32
+                         accumulator; combined in double-float */
+  TD_PREC_BF16X3 = 2, /* hi and first remainder slice only, 3 products (hi*hi +
+                         hi*r1 + r1*hi): ~1e-5 relative, below the accuracy bar */
   TD_PREC_AUTO = 3    /* library picks by (N', K): tensor-core or small-K streaming */
 } td_precision;
 
@@ -68,14 +72,14 @@ typedef enum {
 } td_path;
 
 typedef struct {
-  int precision;        /* td_precision; default TD_PREC_6XBF16 */
+  int precision;        /* td_precision; default TD_PREC_BF16X10 */
   int path;             /* td_path; default TD_PATH_AUTO */
   int refine;           /* 1: one refinement step s = r - L w (FP64), w += L^{-1} s */
   int reserved0;
   int64_t wait_limit_ns;/* bound on any in-kernel wait; <= 0 -> 1 s */
 } td_options;
 
-/* Fill *opt with the defaults (6xBF16, auto path, no refinement, 1 s waits). */
+/* Fill *opt with the defaults (BF16X10, auto path, no refinement, 1 s waits). */
 void td_options_default(td_options* opt);
 
 /*

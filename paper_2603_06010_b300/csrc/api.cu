@@ -69,10 +69,11 @@ static td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint6
 
 // residual-slice map (A operand) and operator map (B operand) of one segment
 td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, TcSegDev* out) {
-  td_status st = encode_3d(&out->mapA, s->scr.rs, (uint64_t)s->nk, (uint64_t)K, 3, (uint64_t)s->nkp8 * 2,
-                           (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, TC_COLS, (uint32_t)nsl);
+  td_status st = encode_3d(&out->mapA, s->scr.rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES,
+                           (uint64_t)s->nkp8 * 2, (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, TC_COLS,
+                           (uint32_t)nsl);
   if (st != TD_OK) return st;
-  return encode_3d(&out->mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * 3, OP_KB * 2,
+  return encode_3d(&out->mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
                    (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, OP_ROWS, (uint32_t)nsl);
 }
 
@@ -102,7 +103,7 @@ static td_status check_device(const td_segment* s) {
   return TD_OK;
 }
 
-static int nslices_for(int precision) { return precision == TD_PREC_3XBF16 ? 2 : 3; }
+static int nslices_for(int precision) { return precision == TD_PREC_BF16X3 ? 2 : OP_SLICES; }
 
 // Grow the per-segment scratch so batches of K columns fit.
 static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaStream_t st) {
@@ -113,7 +114,7 @@ static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaSt
     dev_free(sc.partials);
     dev_free(sc.w64);
     const int64_t cap = round_up(K, TC_COLS);
-    td_status r = dev_alloc(&sc.rs, (size_t)(3 * cap * s->nkp8), "residual slices");
+    td_status r = dev_alloc(&sc.rs, (size_t)(OP_SLICES * cap * s->nkp8), "residual slices");
     if (r != TD_OK) return r;
     r = dev_alloc(&sc.partials, (size_t)((s->nkp / FT) * cap), "chi2 partials");
     if (r != TD_OK) return r;
@@ -167,7 +168,7 @@ extern "C" {
 void td_options_default(td_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof *opt);
-  opt->precision = TD_PREC_6XBF16;
+  opt->precision = TD_PREC_BF16X10;
   opt->path = TD_PATH_AUTO;
   opt->refine = 0;
   opt->wait_limit_ns = 1000000000LL;
@@ -235,7 +236,7 @@ int64_t td_resident_bytes(const td_segment* s) {
   int64_t b = s->n * 8 + s->nk * 4;
   if (s->L) b += s->nkp * s->nkp * 8;
   if (s->dinv) b += (s->nkp / FT) * FT * FT * 8;
-  if (s->op) b += s->op_blocks * 3 * OP_ROWS * OP_KB * 2;
+  if (s->op) b += s->op_blocks * OP_SLICES * OP_ROWS * OP_KB * 2;
   return b;
 }
 
@@ -279,15 +280,22 @@ td_status td_factor(td_segment* s, void* stream) {
   const int64_t nm = nkp / OP_ROWS;
   s->op_blocks = op_row_offset(nm);
   if (e == cudaSuccess && !s->op) {
-    r = dev_alloc(&s->op, (size_t)(s->op_blocks * 3 * OP_ROWS * OP_KB), "operator slices");
+    r = dev_alloc(&s->op, (size_t)(s->op_blocks * OP_SLICES * OP_ROWS * OP_KB), "operator slices");
     if (r != TD_OK) {
       cudaFree(linv);
       return r;
     }
   }
-  if (e == cudaSuccess) e = launch_op_slices(linv, nkp, s->nk, nkp, s->op, st);
+  double* qrow = nullptr;
+  if (e == cudaSuccess && (r = dev_alloc(&qrow, (size_t)nkp, "row quanta")) != TD_OK) {
+    cudaFree(linv);
+    return r;
+  }
+  if (e == cudaSuccess) e = launch_row_quantum(linv, nkp, s->nk, nkp, qrow, st);
+  if (e == cudaSuccess) e = launch_op_slices(linv, nkp, s->nk, nkp, qrow, s->op, st);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cudaFree(linv);
+  if (qrow) cudaFree(qrow);
   if (e != cudaSuccess) return cuda_fail(e, "td_factor operator build");
   s->logdet = logdet;
   s->factored = true;

@@ -1,77 +1,151 @@
 // bf16 slicing of the whitening operator and of residual batches.
 //
-// Operator: L^{-1} (FP64, computed once per segment) is stored as three
-// bf16 slices x = s0 + s1 + s2 of its lower triangle, packed as 256 x 32
-// blocks: row tile m (256 rows) holds k-blocks kb = 0 .. 8(m+1)-1 of 32
-// columns, at block offset 8 m (m+1) / 2 + kb; each block stores its three
-// slices one after another ([block][slice][256][32], row-major).  This is the
-// tensor-core B operand, read by TMA one k-block (48 KB) at a time.
+// Both operands are held as four bf16 slices x = s0 + s1 + s2 + s3: s0 is a
+// fixed-point "hi" slice, an integer multiple (|.| <= 127) of a power-of-two
+// quantum shared by the whole operator row (resp. residual column), and
+// s1..s3 are floating bf16 slices of the remainder.  The hi*hi products of
+// one output element are then all multiples of one quantum and their FP32
+// tensor-core sum is exact; the remaining products carry the small rest.
 //
-// Residuals: float32 R (N' x K, column-major) -> three bf16 slices laid out
+// Operator: L^{-1} (FP64, computed once per segment), lower triangle packed as
+// 256 x 32 blocks: row tile m (256 rows) holds k-blocks kb = 0 .. 8(m+1)-1 of
+// 32 columns, at block offset 8 m (m+1) / 2 + kb; each block stores its four
+// slices one after another ([block][slice][256][32], row-major) -- the
+// tensor-core B operand, read by TMA one k-block (64 KB) at a time.
+//
+// Residuals: float32 R (N' x K, column-major) -> four bf16 slices laid out
 // [slice][k][j] (j contiguous, row stride nkp8): the tensor-core A operand.
-// Three slices hold a float32 exactly.
+// The four slices hold each float32 exactly.
 #include "td_internal.h"
 
 namespace td {
 
+// Per-row power-of-two quantum q_i of the operator's fixed-point hi slice:
+// the smallest 2^e with max_j |Linv_ij| <= 127 q_i, made coarser if needed so
+// that sum_j |round(Linv_ij / q_i)| <= 2^17.  Any residual column whose hi
+// slice is an integer multiple of its own quantum with magnitude <= 127 then
+// gives hi*hi partial sums that are integer multiples of q_i p_k below 2^24
+// of them: exactly representable in FP32, so the tensor-core accumulation of
+// that product is exact.
+__global__ void k_row_quantum(const double* __restrict__ Linv, int64_t ld, int64_t nk, int64_t nkp,
+                              double* __restrict__ qrow) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nkp; i += (int64_t)gridDim.x * blockDim.x) {
+    double mx = 0.0;
+    const int64_t jmax = (i < nk) ? i : -1;
+    for (int64_t j = 0; j <= jmax; ++j) mx = fmax(mx, fabs(Linv[i + j * ld]));
+    if (!(mx > 0.0)) {
+      qrow[i] = 1.0;
+      continue;
+    }
+    int e = (int)ceil(log2(mx / 127.0));
+    double q = ldexp(1.0, e);
+    if (mx / q > 127.0) q *= 2.0;
+    for (int it = 0; it < 64; ++it) {
+      double l1 = 0.0;
+      for (int64_t j = 0; j <= jmax; ++j) l1 += fabs(rint(Linv[i + j * ld] / q));
+      if (l1 <= 131072.0) break;
+      q *= 2.0;
+    }
+    qrow[i] = q;
+  }
+}
+
+cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, double* qrow,
+                               cudaStream_t st) {
+  k_row_quantum<<<(unsigned)ceil_div(nkp, 128), 128, 0, st>>>(Linv, ld, nk, nkp, qrow);
+  return cudaGetLastError();
+}
+
+// x = q a0 + r,  a0 = rint(x / q) (|a0| <= 127, exact in bf16 as q a0),
+// r = x - q a0 split into three floating bf16 slices.
+__device__ __forceinline__ void split4_fixed_f64(double x, double q, __nv_bfloat16 (&s)[4]) {
+  const double hi = q * rint(x / q);
+  s[0] = __double2bfloat16(hi);
+  split3_f64(x - hi, s[1], s[2], s[3]);
+}
+
 __global__ void __launch_bounds__(256) k_op_slices(const double* __restrict__ Linv, int64_t ld, int64_t nk,
+                                                    const double* __restrict__ qrow,
                                                     __nv_bfloat16* __restrict__ op) {
   const int m = blockIdx.y, kb = blockIdx.x;
   if (kb >= (OP_ROWS / OP_KB) * (m + 1)) return;
   const int r = threadIdx.x;
   const int64_t i = (int64_t)m * OP_ROWS + r;
   const int64_t blk = (OP_ROWS / OP_KB) * (int64_t)m * (m + 1) / 2 + kb;
-  __align__(16) __nv_bfloat16 s0[OP_KB], s1[OP_KB], s2[OP_KB];
+  const double q = qrow[i];
+  __align__(16) __nv_bfloat16 sl[OP_SLICES][OP_KB];
 #pragma unroll 4
   for (int c = 0; c < OP_KB; ++c) {
     const int64_t j = (int64_t)kb * OP_KB + c;
     const double x = (i < nk && j < nk && j <= i) ? Linv[i + j * ld] : 0.0;
-    split3_f64(x, s0[c], s1[c], s2[c]);
-  }
-  __nv_bfloat16* base = op + (blk * 3) * (OP_ROWS * OP_KB) + (int64_t)r * OP_KB;
-  const uint4* v0 = reinterpret_cast<const uint4*>(s0);
-  const uint4* v1 = reinterpret_cast<const uint4*>(s1);
-  const uint4* v2 = reinterpret_cast<const uint4*>(s2);
-  uint4* d0 = reinterpret_cast<uint4*>(base);
-  uint4* d1 = reinterpret_cast<uint4*>(base + OP_ROWS * OP_KB);
-  uint4* d2 = reinterpret_cast<uint4*>(base + 2 * OP_ROWS * OP_KB);
+    __nv_bfloat16 s4[4];
+    split4_fixed_f64(x, q, s4);
 #pragma unroll
-  for (int u = 0; u < OP_KB * 2 / 16; ++u) {
-    d0[u] = v0[u];
-    d1[u] = v1[u];
-    d2[u] = v2[u];
+    for (int u = 0; u < OP_SLICES; ++u) sl[u][c] = s4[u];
+  }
+  __nv_bfloat16* base = op + (blk * OP_SLICES) * (OP_ROWS * OP_KB) + (int64_t)r * OP_KB;
+#pragma unroll
+  for (int u = 0; u < OP_SLICES; ++u) {
+    const uint4* v = reinterpret_cast<const uint4*>(sl[u]);
+    uint4* d = reinterpret_cast<uint4*>(base + (int64_t)u * OP_ROWS * OP_KB);
+#pragma unroll
+    for (int w = 0; w < OP_KB * 2 / 16; ++w) d[w] = v[w];
   }
 }
 
-cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, __nv_bfloat16* op,
-                             cudaStream_t st) {
+cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, const double* qrow,
+                             __nv_bfloat16* op, cudaStream_t st) {
   const int nm = (int)(nkp / OP_ROWS);
   dim3 grid((OP_ROWS / OP_KB) * nm, nm);
-  k_op_slices<<<grid, OP_ROWS, 0, st>>>(Linv, ld, nk, op);
+  k_op_slices<<<grid, OP_ROWS, 0, st>>>(Linv, ld, nk, qrow, op);
   return cudaGetLastError();
 }
 
-__global__ void k_r_slices(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8,
-                           int64_t capK, __nv_bfloat16* __restrict__ rs, int nslices) {
+// Residual slices, one CTA per column: the column's power-of-two quantum
+// p_k (max_j |R_jk| <= 127 p_k), then R = p_k b0 + r with r in three
+// floating bf16 slices (exact: a float32 is held exactly).
+__global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t K,
+                                                   int64_t nkp8, int64_t capK, __nv_bfloat16* __restrict__ rs,
+                                                   int nslices) {
+  __shared__ float red[8];
   const int64_t slice_stride = capK * nkp8;
-  for (int64_t k = blockIdx.y; k < K; k += gridDim.y)
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x) {
-    const float x = R[j + k * ldr];
-    __nv_bfloat16 a, b, c;
-    split3_f32(x, a, b, c);
-    __nv_bfloat16* p = rs + k * nkp8 + j;
-    p[0] = a;
-    p[slice_stride] = b;
-    if (nslices > 2) p[2 * slice_stride] = c;
+  for (int64_t k = blockIdx.x; k < K; k += gridDim.x) {
+    const float* col = R + k * ldr;
+    float mx = 0.f;
+    for (int64_t j = threadIdx.x; j < nk; j += blockDim.x) mx = fmaxf(mx, fabsf(col[j]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+    __syncthreads();
+    float p = 1.f;
+    if (mx > 0.f) {
+      p = exp2f(ceilf(log2f(mx / 127.f)));
+      if (mx / p > 127.f) p *= 2.f;
+    }
+    __nv_bfloat16* dst = rs + k * nkp8;
+    for (int64_t j = threadIdx.x; j < nk; j += blockDim.x) {
+      const float x = col[j];
+      const float hi = p * rintf(x / p);
+      __nv_bfloat16 a, b, c;
+      split3_f32(x - hi, a, b, c);
+      dst[j] = __float2bfloat16_rn(hi);
+      dst[j + slice_stride] = a;
+      if (nslices > 2) {
+        dst[j + 2 * slice_stride] = b;
+        dst[j + 3 * slice_stride] = c;
+      }
+    }
   }
 }
 
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8, int64_t capK,
                             __nv_bfloat16* rs, int nslices, cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  int gx = (int)ceil_div(nk, 256);
-  if (gx > 32) gx = 32;
-  dim3 grid(gx, (unsigned)(K < 65535 ? K : 65535));
+  const int grid = (int)(K < 4096 ? K : 4096);
   k_r_slices<<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
   return cudaGetLastError();
 }

@@ -9,9 +9,15 @@
 //   MMA M = 128 residual columns (A = R^T slices, K-major),
 //   MMA N = 256 rows of W        (B = L^{-1} slices, K-major),
 //   reduction over the kept samples j in k-blocks of 32 (64-byte swizzle).
-// Each operand is split into bf16 slices x = x0 + x1 (+ x2); the accumulator
-// takes the products x_a * y_b with a + b <= NSL - 1 (3 for two slices, 6 for
-// three), all in FP32 in tensor memory.
+// Each operand is held as four bf16 slices x = x0 + x1 + x2 + x3 with x0 a
+// fixed-point hi slice (integer multiple of a per-row / per-column
+// power-of-two quantum) and x1..x3 floating slices of the remainder.  The
+// tensor core accumulates in FP32 with truncation, which biases every sum
+// that is not exactly representable; so the hi*hi products, whose partial sums
+// are exact integer multiples of one quantum, go to their own accumulator
+// (exact), and the nine products x_a * y_b with 1 <= a + b <= 3 go, smallest
+// first, to a second accumulator whose magnitude (and so its truncation
+// error) is small.  The epilogue adds the two in double-float.
 //
 // Work: one output tile = (segment, row tile m, column tile c); the row tile
 // needs k-blocks 0 .. 8(m+1)-1 (the lower triangle).  Tiles are sorted by
@@ -22,8 +28,8 @@
 //   warp 1        : TMEM allocator; lane 0 issues tcgen05.mma
 //   warps 2..5    : epilogue; TMEM -> registers, exact squares, compensated
 //                   sums, one FP64 partial per (row tile, column)
-// Two TMEM accumulators (2 x 256 columns) let the epilogue of one tile
-// overlap the MMAs of the next.  Every wait is bounded (wait_limit_ns).
+// TMEM holds the two accumulators (2 x 256 columns).  Every wait is bounded
+// (wait_limit_ns).
 #include "td_internal.h"
 
 namespace td {
@@ -31,12 +37,12 @@ namespace tc {
 constexpr int BM = TC_COLS;      // 128
 constexpr int BN = OP_ROWS;      // 256
 constexpr int BK = OP_KB;        // 32
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int A_SLICE = BM * BK * 2;   // 8 KB
 constexpr int B_SLICE = BN * BK * 2;   // 16 KB
-constexpr int A_STAGE = 3 * A_SLICE;
-constexpr int B_STAGE = 3 * B_SLICE;
-constexpr int STAGE = A_STAGE + B_STAGE;   // 72 KB
+constexpr int A_STAGE = OP_SLICES * A_SLICE;
+constexpr int B_STAGE = OP_SLICES * B_SLICE;
+constexpr int STAGE = A_STAGE + B_STAGE;   // 96 KB
 constexpr int BAR_BYTES = 256;
 constexpr int SMEM = STAGES * STAGE + BAR_BYTES + 1024;
 constexpr int THREADS = 192;
@@ -60,6 +66,11 @@ __device__ __forceinline__ TcItem single_item(const TcSingle& p, int idx) {
   return it;
 }
 
+// correction products (a, b), smallest first; the hi*hi product (0, 0) is separate
+__device__ constexpr int kCorr10[9][2] = {{3, 0}, {2, 1}, {1, 2}, {0, 3}, {2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}};
+__device__ constexpr int kCorr3[2][2] = {{1, 0}, {0, 1}};
+
+// NSL slices loaded per operand: 4 (10 products) or 2 (3 products)
 template <int NSL, bool GROUPED>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     k_tc_cdo(const __grid_constant__ TcSingle single, const TcItem* __restrict__ items, int n_items,
@@ -81,10 +92,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(&tfull[b], 1);
-      mbar_init(&tempty[b], 4);
-    }
+    mbar_init(&tfull[0], 1);
+    mbar_init(&tempty[0], 4);
     mbar_init(fin, 1);
     *abort_flag = 0;
     fence_mbar_init();
@@ -128,7 +137,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           uint8_t* sb = sa + A_STAGE;
           mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (A_SLICE + B_SLICE)));
           tma_load_3d(sa, &sd->mapA, &full[stage], kb * BK, it.c * BM, 0);
-          tma_load_3d(sb, &sd->mapB, &full[stage], 0, 0, (blk0 + kb) * 3);
+          tma_load_3d(sb, &sd->mapB, &full[stage], 0, 0, (blk0 + kb) * OP_SLICES);
           issued_mask |= 1u << stage;
           issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -153,15 +162,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
         if (idx >= n_total) continue;
         const TcItem it = GROUPED ? items[idx] : single_item(single, idx);
-        const int buf = tl & 1;
-        const uint32_t use = (uint32_t)(tl >> 1);
-        if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, limit_ns)) {
+        if (!mbar_wait(&tempty[0], ((uint32_t)tl & 1u) ^ 1u, limit_ns)) {
           set_status(status, ST_TIMEOUT, 20);
           *abort_flag = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t dt = tmem_base + (uint32_t)(buf * BN);
+        const uint32_t d_hi = tmem_base;              // hi*hi (exact)
+        const uint32_t d_lo = tmem_base + (uint32_t)BN;   // corrections
         bool ok = true;
         for (int kb = 0; kb < it.nkb; ++kb) {
           if (!mbar_wait(&full[stage], phase, limit_ns)) {
@@ -175,16 +183,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           const uint32_t sb = sa + A_STAGE;
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
+            const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+            tc_mma_f16(d_hi, smem_desc_sw64(sa + kk * 32), smem_desc_sw64(sb + kk * 32), idesc, first);
+            constexpr int NC = (NSL == 4) ? 9 : 2;
 #pragma unroll
-            for (int ia = 0; ia < NSL; ++ia) {
-#pragma unroll
-              for (int ib = 0; ib < NSL; ++ib) {
-                if (ia + ib > NSL - 1) continue;
-                const uint64_t ad = smem_desc_sw64(sa + ia * A_SLICE + kk * 32);
-                const uint64_t bd = smem_desc_sw64(sb + ib * B_SLICE + kk * 32);
-                const uint32_t acc = (kb > 0 || kk > 0 || ia > 0 || ib > 0) ? 1u : 0u;
-                tc_mma_f16(dt, ad, bd, idesc, acc);
-              }
+            for (int p = 0; p < NC; ++p) {
+              const int ia = (NSL == 4) ? kCorr10[p][1] : kCorr3[p][1];   // residual slice (A)
+              const int ib = (NSL == 4) ? kCorr10[p][0] : kCorr3[p][0];   // operator slice (B)
+              const uint64_t ad = smem_desc_sw64(sa + ia * A_SLICE + kk * 32);
+              const uint64_t bd = smem_desc_sw64(sb + ib * B_SLICE + kk * 32);
+              tc_mma_f16(d_lo, ad, bd, idesc, (first | (p > 0 ? 1u : 0u)));
             }
           }
           tc_commit(&empty[stage]);   // frees this smem stage once these MMAs retire
@@ -194,7 +202,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           }
         }
         if (!ok) break;
-        tc_commit(&tfull[buf]);       // accumulator ready for the epilogue
+        tc_commit(&tfull[0]);         // accumulators ready for the epilogue
         ++tl;
       }
       tc_commit(fin);                 // all MMAs issued by this thread retired
@@ -209,26 +217,25 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       if (idx >= n_total) continue;
       const TcItem it = GROUPED ? items[idx] : single_item(single, idx);
       const TcSegDev* sd = GROUPED ? &segs[it.seg] : &single.seg;
-      const int buf = tl & 1;
-      const uint32_t use = (uint32_t)(tl >> 1);
-      if (!mbar_wait(&tfull[buf], use & 1u, limit_ns)) {
+      if (!mbar_wait(&tfull[0], (uint32_t)tl & 1u, limit_ns)) {
         if (lane == 0) set_status(status, ST_TIMEOUT, 30);
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
       float hi = 0.f, lo = 0.f;
-      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * BN);
+      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16);
 #pragma unroll 1
       for (int ch = 0; ch < BN / 32; ++ch) {
-        float v[32];
-        tmem_ld32(ta + (uint32_t)(ch * 32), v);
+        float v0[32], v1[32];
+        tmem_ld32(ta + (uint32_t)(ch * 32), v0);
+        tmem_ld32(ta + (uint32_t)(BN + ch * 32), v1);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) ff_add_square(v[i], hi, lo);
+        for (int i = 0; i < 32; ++i) ff_add_square2(v0[i], v1[i], hi, lo);
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[buf]);
+      if (lane == 0) mbar_arrive(&tempty[0]);
       const int col = it.c * BM + q * 32 + lane;
       if (col < sd->K) sd->partials[(int64_t)it.m * sd->ldp + col] = (double)hi + (double)lo;
       ++tl;
@@ -282,7 +289,7 @@ cudaError_t launch_tc_single(const TcSegDev& seg, int nm, int nc, int nkb_max, i
   p.nm = nm;
   p.nc = nc;
   p.nkb_max = nkb_max;
-  if (nslices == 3) return launch_impl<3, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
+  if (nslices == 4) return launch_impl<4, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
   if (nslices == 2) return launch_impl<2, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
   return cudaErrorInvalidValue;
 }
@@ -291,7 +298,7 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
                           DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
   TcSingle p;
   memset(&p, 0, sizeof(p));
-  if (nslices == 3) return launch_impl<3, true>(p, items, n_items, segs, status, wait_limit_ns, st);
+  if (nslices == 4) return launch_impl<4, true>(p, items, n_items, segs, status, wait_limit_ns, st);
   if (nslices == 2) return launch_impl<2, true>(p, items, n_items, segs, status, wait_limit_ns, st);
   return cudaErrorInvalidValue;
 }

@@ -185,4 +185,19 @@ __device__ __forceinline__ void ff_add_square(float w, float& hi, float& lo) {
   lo += err + e;
 }
 
+// (a + b)^2 for an FP32 pair whose sum is the value: two-sum first, then the
+// exact square of the head and the cross term, accumulated into (hi, lo)
+__device__ __forceinline__ void ff_add_square2(float a, float b, float& hi, float& lo) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);   // a + b = s + e exactly
+  float p = s * s;
+  float pe = fmaf(s, s, -p);             // s*s = p + pe exactly
+  float t = hi + p;
+  float bp = t - hi;
+  float err = (hi - (t - bp)) + (p - bp);
+  hi = t;
+  lo += err + pe + 2.f * s * e;
+}
+
 }  // namespace td

@@ -17,6 +17,7 @@ constexpr int FT = 64;          // FP64 tile (factor, FP64 forward substitution)
 constexpr int OP_ROWS = 256;    // operator row tile (tensor-core N)
 constexpr int OP_KB = 32;       // operator k-block (64 B of bf16)
 constexpr int TC_COLS = 128;    // residual columns per tensor-core tile (MMA M)
+constexpr int OP_SLICES = 4;    // bf16 slices per operand element (fixed-point hi + 3 floating)
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
@@ -32,8 +33,8 @@ struct TcItem {      // one tensor-core output tile
 };
 
 struct TcSegDev {    // per-segment launch data (device-resident)
-  CUtensorMap mapA;  // residual slices  (j: N', k: K, slice: 3)
-  CUtensorMap mapB;  // operator slices  (32, 256, blocks*3)
+  CUtensorMap mapA;  // residual slices  (j: N', k: K, slice: 4)
+  CUtensorMap mapB;  // operator slices  (32, 256, blocks*4)
   double* partials;  // [n_row_tiles][ldp]
   int nk;
   int K;
@@ -48,7 +49,7 @@ static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
 
 struct Scratch {
   int64_t capK = 0;          // columns the buffers hold
-  __nv_bfloat16* rs = nullptr;  // residual slices [3][capK][nkp8]
+  __nv_bfloat16* rs = nullptr;  // residual slices [4][capK][nkp8]
   double* partials = nullptr;   // [n_tiles][capK_pad] (tensor path) / [nt64][capK_pad] (fp64)
   double* w64 = nullptr;        // FP64 W for the plain path [nkp][capK]
   TcItem* items = nullptr;      // tensor-core work list
@@ -75,7 +76,7 @@ struct td_segment {
   double* L = nullptr;            // device FP64 [nkp x nkp] column-major, lower = factor
   double* dinv = nullptr;         // device FP64 [nkp/64][64*64] inverse diagonal tiles
   double* ldpart = nullptr;       // device [nkp/64]
-  __nv_bfloat16* op = nullptr;    // device operator slices, packed 256x32 blocks x 3
+  __nv_bfloat16* op = nullptr;    // device operator slices, packed 256x32 blocks x 4
   int64_t op_blocks = 0;
   td::DevStatus* status = nullptr;  // device
   bool factored = false;
@@ -115,8 +116,10 @@ cudaError_t launch_trsm_f64_row(const double* L, int64_t ld, const double* dinv,
 cudaError_t launch_finalize(const double* partials, int64_t ldp, int nparts, int64_t K, double logdet,
                             int64_t nk, double* logL, double* chi2, cudaStream_t st);
 
-cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, __nv_bfloat16* op,
-                             cudaStream_t st);
+cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, double* qrow,
+                               cudaStream_t st);
+cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, const double* qrow,
+                             __nv_bfloat16* op, cudaStream_t st);
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8,
                             int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st);
 

@@ -141,6 +141,32 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
                            double* logL, const td_options* opt, double* chi2,
                            void* stream);
 
+/*
+ * td_loglike_batch_noalloc -- the same evaluation as td_loglike_batch with the
+ * default options, for callers that cannot allocate device memory while they
+ * run: an application whose device memory is all reserved by its own caching
+ * pool, a process under a hard device-memory cap, or a latency-critical loop
+ * that must not enter cudaMalloc (which can synchronise the device).  This call
+ * allocates nothing: its scratch (residual slices and chi2 partials) is one
+ * fixed device array of TD_NOALLOC_SCRATCH_BYTES inside this library, which
+ * every GPU that loads the library holds until the process exits.  The paper
+ * has no counterpart; it is a property of this library's interface.
+ *   Arguments as for td_loglike_batch (R, ldr, K, logL, chi2 caller-owned,
+ *   device memory).  The segment must be factored (td_factor allocates).
+ *   Size limit: 8 K N8 + 8 K ceil(N'/256) bytes must fit (N8 = N' rounded up
+ *   to 8, the slices' row rounded to 256 bytes), e.g. N' = 8192 with K up to 497;
+ *   larger batches return TD_ERR_INVALID before any device work.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with that device current); make that first call before any stream
+ *   capture.  Every call shares the one array, so calls whose kernels overlap
+ *   on the GPU (other streams, other segments at the same time) race on it;
+ *   serialise them.  Nothing in the array needs clearing: a call writes every
+ *   scratch byte it reads.
+ */
+#define TD_NOALLOC_SCRATCH_BYTES (32ll << 20)
+td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int64_t ldr, int64_t K,
+                                   double* logL, double* chi2, void* stream);
+
 /* Pre-size the segment's scratch for batches of up to K columns (allocates). */
 td_status td_reserve(td_segment* s, int64_t K, const td_options* opt);
 

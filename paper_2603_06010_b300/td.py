@@ -43,6 +43,7 @@ SIGNATURES = {
     "td_last_error": (_c.c_char_p, []),
     "td_resident_bytes": (_i64, [_vp]),
     "td_debug_bounded_wait": (_c.c_int, [_i64, _vp]),
+    "td_loglike_batch_noalloc": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "td_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "td_profile_read": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.POINTER(_i64), _c.POINTER(_i64)]),
 }
@@ -152,6 +153,13 @@ class Segment:
         chi2 = torch.empty(K, dtype=torch.float64, device=R.device) if with_chi2 else None
         self.loglike_into(R, logL, opt, chi2, stream)
         return (logL, chi2) if with_chi2 else logL
+
+    def loglike_noalloc_into(self, R, logL, chi2=None, stream=None):
+        """td_loglike_batch_noalloc: default options, scratch in the library's
+        fixed device array (no device allocation by this call)."""
+        _check(lib().td_loglike_batch_noalloc(self.handle, R.data_ptr(), int(R.stride(0)), int(R.shape[0]),
+                                              logL.data_ptr(), None if chi2 is None else chi2.data_ptr(),
+                                              _stream_ptr(stream)))
 
     def profile(self, enable: bool = True):
         _check(lib().td_profile_enable(self.handle, 1 if enable else 0))

@@ -39,7 +39,7 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--precision", default="bf16x10", choices=["bf16x10", "bf16x3", "fp64"])
+    p.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x10", "bf16x3", "fp64"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=5)
@@ -186,7 +186,8 @@ def main():
 
     c, seg_in, R_host = make_workload(rank)
     K, N = R_host.shape[0], R_host.shape[1]
-    prec = {"bf16x10": td.TD_PREC_BF16X10, "bf16x3": td.TD_PREC_BF16X3, "fp64": td.TD_PREC_FP64}[args.precision]
+    prec = {"bf16x6": td.TD_PREC_BF16X6, "bf16x10": td.TD_PREC_BF16X10, "bf16x3": td.TD_PREC_BF16X3,
+            "fp64": td.TD_PREC_FP64}[args.precision]
     opt = td.options(precision=prec)
     stream = torch.cuda.current_stream()
 
@@ -279,7 +280,7 @@ def main():
     pk, basis = peaks()
     flops = float(N) * float(N) * float(K)      # N'^2 K: N'^2/2 multiply-adds per column
     kern_avg_ms = kern_ms / max(kern_n, 1)
-    products = 10 if args.precision == "bf16x10" else (3 if args.precision == "bf16x3" else None)
+    products = {"bf16x6": 6, "bf16x10": 10, "bf16x3": 3}.get(args.precision)
     if products:
         achieved = flops / (kern_avg_ms / 1e3) / 1e12
         peak = pk["bf16_tflops"] / products

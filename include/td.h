@@ -53,15 +53,17 @@ typedef enum {
 } td_status;
 
 typedef enum {
-  TD_PREC_FP64 = 0,   /* plain FP64 blocked forward substitution (CUDA cores) */
-  TD_PREC_BF16X10 = 1,/* default: L^{-1} and R as 4 bf16 slices each (a fixed-point hi
-                         slice on a per-row / per-column power-of-two quantum, plus
-                         3 floating remainder slices); 10 tensor-core products; the
-                         hi*hi sum accumulates exactly, the rest in a second FP32
-                         accumulator; combined in double-float */
-  TD_PREC_BF16X3 = 2, /* hi and first remainder slice only, 3 products (hi*hi +
-                         hi*r1 + r1*hi): ~1e-5 relative, below the accuracy bar */
-  TD_PREC_AUTO = 3    /* library picks by (N', K): tensor-core or small-K streaming */
+  TD_PREC_FP64 = 0,    /* plain FP64 blocked forward substitution (CUDA cores) */
+  TD_PREC_BF16X6 = 1,  /* default: L^{-1} and R as 3 bf16 slices each -- a fixed-point hi
+                          slice (|.| <= 255 times a per-row / per-column power-of-two
+                          quantum) and 2 floating remainder slices; 6 tensor-core
+                          products; the hi*hi sum accumulates exactly in one FP32
+                          accumulator, the 5 others in a second; combined in
+                          double-float.  chi2 ~2e-8 relative to FP64. */
+  TD_PREC_BF16X3 = 2,  /* hi + 1 remainder slice, 3 products: ~1e-5 relative, below
+                          the accuracy bar (kept to show why more products are needed) */
+  TD_PREC_AUTO = 3,    /* library picks by (N', K) */
+  TD_PREC_BF16X10 = 4  /* 4 slices each, the 10 products a+b <= 3: chi2 ~1e-9 relative */
 } td_precision;
 
 typedef enum {
@@ -72,14 +74,14 @@ typedef enum {
 } td_path;
 
 typedef struct {
-  int precision;        /* td_precision; default TD_PREC_BF16X10 */
+  int precision;        /* td_precision; default TD_PREC_BF16X6 */
   int path;             /* td_path; default TD_PATH_AUTO */
   int refine;           /* 1: one refinement step s = r - L w (FP64), w += L^{-1} s */
   int reserved0;
   int64_t wait_limit_ns;/* bound on any in-kernel wait; <= 0 -> 1 s */
 } td_options;
 
-/* Fill *opt with the defaults (BF16X10, auto path, no refinement, 1 s waits). */
+/* Fill *opt with the defaults (BF16X6, auto path, no refinement, 1 s waits). */
 void td_options_default(td_options* opt);
 
 /*

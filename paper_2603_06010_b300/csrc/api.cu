@@ -103,7 +103,9 @@ static td_status check_device(const td_segment* s) {
   return TD_OK;
 }
 
-static int nslices_for(int precision) { return precision == TD_PREC_BF16X3 ? 2 : OP_SLICES; }
+static int nslices_for(int precision) {
+  return precision == TD_PREC_BF16X3 ? 2 : (precision == TD_PREC_BF16X10 ? 4 : 3);
+}
 
 // Grow the per-segment scratch so batches of K columns fit.
 static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaStream_t st) {
@@ -168,7 +170,7 @@ extern "C" {
 void td_options_default(td_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof *opt);
-  opt->precision = TD_PREC_BF16X10;
+  opt->precision = TD_PREC_BF16X6;
   opt->path = TD_PATH_AUTO;
   opt->refine = 0;
   opt->wait_limit_ns = 1000000000LL;

@@ -115,18 +115,18 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
   if ((r = na_encode(&seg.mapA, rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES, (uint64_t)s->nkp8 * 2,
-                     (uint64_t)K * s->nkp8 * 2, OP_KB, TC_COLS, OP_SLICES)) != TD_OK)
+                     (uint64_t)K * s->nkp8 * 2, OP_KB, TC_COLS, 3)) != TD_OK)
     return r;
   if ((r = na_encode(&seg.mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
-                     (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, OP_ROWS, OP_SLICES)) != TD_OK)
+                     (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, OP_ROWS, 3)) != TD_OK)
     return r;
   seg.partials = partials;
   seg.nk = (int)s->nk;
   seg.K = (int)K;
   seg.ldp = (int)K;
   seg.nm = (int)nm;
-  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, K, rs, OP_SLICES, st));
-  TD_CUDA(launch_tc_single(seg, (int)nm, (int)ceil_div(K, TC_COLS), (int)ceil_div(s->nk, OP_KB), OP_SLICES,
+  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, K, rs, 3, st));
+  TD_CUDA(launch_tc_single(seg, (int)nm, (int)ceil_div(K, TC_COLS), (int)ceil_div(s->nk, OP_KB), 3,
                            s->status, 1000000000LL, st));
   TD_CUDA(launch_finalize(partials, K, (int)nm, K, s->logdet, s->nk, logL, chi2, st));
   return TD_OK;

@@ -1,7 +1,7 @@
 // bf16 slicing of the whitening operator and of residual batches.
 //
 // Both operands are held as four bf16 slices x = s0 + s1 + s2 + s3: s0 is a
-// fixed-point "hi" slice, an integer multiple (|.| <= 127) of a power-of-two
+// fixed-point "hi" slice, an integer multiple (|.| <= 255) of a power-of-two
 // quantum shared by the whole operator row (resp. residual column), and
 // s1..s3 are floating bf16 slices of the remainder.  The hi*hi products of
 // one output element are then all multiples of one quantum and their FP32
@@ -21,12 +21,12 @@
 namespace td {
 
 // Per-row power-of-two quantum q_i of the operator's fixed-point hi slice:
-// the smallest 2^e with max_j |Linv_ij| <= 127 q_i, made coarser if needed so
-// that sum_j |round(Linv_ij / q_i)| <= 2^17.  Any residual column whose hi
-// slice is an integer multiple of its own quantum with magnitude <= 127 then
+// the smallest 2^e with max_j |Linv_ij| <= 255 q_i, made coarser if needed so
+// that sum_j |round(Linv_ij / q_i)| <= 2^16.  Any residual column whose hi
+// slice is an integer multiple of its own quantum with magnitude <= 255 then
 // gives hi*hi partial sums that are integer multiples of q_i p_k below 2^24
 // of them: exactly representable in FP32, so the tensor-core accumulation of
-// that product is exact.
+// that product is exact.  (Integers up to 256 are exact in bf16.)
 __global__ void k_row_quantum(const double* __restrict__ Linv, int64_t ld, int64_t nk, int64_t nkp,
                               double* __restrict__ qrow) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nkp; i += (int64_t)gridDim.x * blockDim.x) {
@@ -37,13 +37,13 @@ __global__ void k_row_quantum(const double* __restrict__ Linv, int64_t ld, int64
       qrow[i] = 1.0;
       continue;
     }
-    int e = (int)ceil(log2(mx / 127.0));
+    int e = (int)ceil(log2(mx / 255.0));
     double q = ldexp(1.0, e);
-    if (mx / q > 127.0) q *= 2.0;
+    if (mx / q > 255.0) q *= 2.0;
     for (int it = 0; it < 64; ++it) {
       double l1 = 0.0;
       for (int64_t j = 0; j <= jmax; ++j) l1 += fabs(rint(Linv[i + j * ld] / q));
-      if (l1 <= 131072.0) break;
+      if (l1 <= 65536.0) break;
       q *= 2.0;
     }
     qrow[i] = q;
@@ -56,7 +56,7 @@ cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64
   return cudaGetLastError();
 }
 
-// x = q a0 + r,  a0 = rint(x / q) (|a0| <= 127, exact in bf16 as q a0),
+// x = q a0 + r,  a0 = rint(x / q) (|a0| <= 255, exact in bf16 as q a0),
 // r = x - q a0 split into three floating bf16 slices.
 __device__ __forceinline__ void split4_fixed_f64(double x, double q, __nv_bfloat16 (&s)[4]) {
   const double hi = q * rint(x / q);
@@ -102,8 +102,8 @@ cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t
 }
 
 // Residual slices, one CTA per column: the column's power-of-two quantum
-// p_k (max_j |R_jk| <= 127 p_k), then R = p_k b0 + r with r in three
-// floating bf16 slices (exact: a float32 is held exactly).
+// p_k (max_j |R_jk| <= 255 p_k), then R = p_k b0 + r with r in up to three
+// floating bf16 slices (all four slices hold a float32 exactly).
 __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t K,
                                                    int64_t nkp8, int64_t capK, __nv_bfloat16* __restrict__ rs,
                                                    int nslices) {
@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, i
     __syncthreads();
     float p = 1.f;
     if (mx > 0.f) {
-      p = exp2f(ceilf(log2f(mx / 127.f)));
-      if (mx / p > 127.f) p *= 2.f;
+      p = exp2f(ceilf(log2f(mx / 255.f)));
+      if (mx / p > 255.f) p *= 2.f;
     }
     __nv_bfloat16* dst = rs + k * nkp8;
     for (int64_t j = threadIdx.x; j < nk; j += blockDim.x) {
@@ -134,10 +134,8 @@ __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, i
       split3_f32(x - hi, a, b, c);
       dst[j] = __float2bfloat16_rn(hi);
       dst[j + slice_stride] = a;
-      if (nslices > 2) {
-        dst[j + 2 * slice_stride] = b;
-        dst[j + 3 * slice_stride] = c;
-      }
+      if (nslices > 2) dst[j + 2 * slice_stride] = b;
+      if (nslices > 3) dst[j + 3 * slice_stride] = c;
     }
   }
 }

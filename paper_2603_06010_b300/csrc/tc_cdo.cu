@@ -9,15 +9,16 @@
 //   MMA M = 128 residual columns (A = R^T slices, K-major),
 //   MMA N = 256 rows of W        (B = L^{-1} slices, K-major),
 //   reduction over the kept samples j in k-blocks of 32 (64-byte swizzle).
-// Each operand is held as four bf16 slices x = x0 + x1 + x2 + x3 with x0 a
-// fixed-point hi slice (integer multiple of a per-row / per-column
-// power-of-two quantum) and x1..x3 floating slices of the remainder.  The
+// Each operand is held as bf16 slices x = x0 + x1 + x2 (+ x3) with x0 a
+// fixed-point hi slice (integer multiple, |.| <= 255, of a per-row /
+// per-column power-of-two quantum) and x1.. floating slices of the remainder.  The
 // tensor core accumulates in FP32 with truncation, which biases every sum
 // that is not exactly representable; so the hi*hi products, whose partial sums
 // are exact integer multiples of one quantum, go to their own accumulator
-// (exact), and the nine products x_a * y_b with 1 <= a + b <= 3 go, smallest
-// first, to a second accumulator whose magnitude (and so its truncation
-// error) is small.  The epilogue adds the two in double-float.
+// (exact), and the products x_a * y_b with 1 <= a + b <= NSL - 1 (five for
+// three slices, nine for four) go, smallest first, to a second accumulator
+// whose magnitude (and so its truncation error) is small.  The epilogue adds
+// the two in double-float.
 //
 // Work: one output tile = (segment, row tile m, column tile c); the row tile
 // needs k-blocks 0 .. 8(m+1)-1 (the lower triangle).  Tiles are sorted by
@@ -37,14 +38,17 @@ namespace tc {
 constexpr int BM = TC_COLS;      // 128
 constexpr int BN = OP_ROWS;      // 256
 constexpr int BK = OP_KB;        // 32
-constexpr int STAGES = 2;
 constexpr int A_SLICE = BM * BK * 2;   // 8 KB
 constexpr int B_SLICE = BN * BK * 2;   // 16 KB
-constexpr int A_STAGE = OP_SLICES * A_SLICE;
-constexpr int B_STAGE = OP_SLICES * B_SLICE;
-constexpr int STAGE = A_STAGE + B_STAGE;   // 96 KB
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM = STAGES * STAGE + BAR_BYTES + 1024;
+// per loaded-slice count NSL: stage = NSL x 24 KB, as many stages as fit
+template <int NSL> struct Cfg {
+  static constexpr int A_STAGE = NSL * A_SLICE;
+  static constexpr int B_STAGE = NSL * B_SLICE;
+  static constexpr int STAGE = A_STAGE + B_STAGE;
+  static constexpr int STAGES = (220 * 1024) / STAGE > 4 ? 4 : (220 * 1024) / STAGE;
+  static constexpr int SMEM = STAGES * STAGE + BAR_BYTES + 1024;
+};
 constexpr int THREADS = 192;
 constexpr uint32_t TMEM_COLS = 512;
 }  // namespace tc
@@ -66,16 +70,34 @@ __device__ __forceinline__ TcItem single_item(const TcSingle& p, int idx) {
   return it;
 }
 
-// correction products (a, b), smallest first; the hi*hi product (0, 0) is separate
-__device__ constexpr int kCorr10[9][2] = {{3, 0}, {2, 1}, {1, 2}, {0, 3}, {2, 0}, {1, 1}, {0, 2}, {1, 0}, {0, 1}};
-__device__ constexpr int kCorr3[2][2] = {{1, 0}, {0, 1}};
+// correction products (operator slice, residual slice), smallest first; the
+// hi*hi product (0, 0) is separate.  NSL slices per operand: 4 -> a+b <= 3
+// (10 products), 3 -> a+b <= 2 (6 products), 2 -> a+b <= 1 (3 products).
+template <int NSL> struct Corr;
+template <> struct Corr<4> {   // (3,0) (2,1) (1,2) (0,3) (2,0) (1,1) (0,2) (1,0) (0,1)
+  static constexpr int N = 9;
+  __device__ static constexpr int op(int p) { return p < 4 ? 3 - p : (p < 7 ? 6 - p : 8 - p); }
+  __device__ static constexpr int rs(int p) { return p < 4 ? p : (p < 7 ? p - 4 : p - 7); }
+};
+template <> struct Corr<3> {   // (2,0) (1,1) (0,2) (1,0) (0,1)
+  static constexpr int N = 5;
+  __device__ static constexpr int op(int p) { return p < 3 ? 2 - p : 4 - p; }
+  __device__ static constexpr int rs(int p) { return p < 3 ? p : p - 3; }
+};
+template <> struct Corr<2> {   // (1,0) (0,1)
+  static constexpr int N = 2;
+  __device__ static constexpr int op(int p) { return 1 - p; }
+  __device__ static constexpr int rs(int p) { return p; }
+};
 
-// NSL slices loaded per operand: 4 (10 products) or 2 (3 products)
 template <int NSL, bool GROUPED>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     k_tc_cdo(const __grid_constant__ TcSingle single, const TcItem* __restrict__ items, int n_items,
              const TcSegDev* __restrict__ segs, DevStatus* status, uint64_t limit_ns) {
   using namespace tc;
+  constexpr int A_STAGE = Cfg<NSL>::A_STAGE;
+  constexpr int STAGE = Cfg<NSL>::STAGE;
+  constexpr int STAGES = Cfg<NSL>::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
@@ -185,11 +207,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           for (int kk = 0; kk < 2; ++kk) {
             const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
             tc_mma_f16(d_hi, smem_desc_sw64(sa + kk * 32), smem_desc_sw64(sb + kk * 32), idesc, first);
-            constexpr int NC = (NSL == 4) ? 9 : 2;
 #pragma unroll
-            for (int p = 0; p < NC; ++p) {
-              const int ia = (NSL == 4) ? kCorr10[p][1] : kCorr3[p][1];   // residual slice (A)
-              const int ib = (NSL == 4) ? kCorr10[p][0] : kCorr3[p][0];   // operator slice (B)
+            for (int p = 0; p < Corr<NSL>::N; ++p) {
+              const int ia = Corr<NSL>::rs(p);   // residual slice (A)
+              const int ib = Corr<NSL>::op(p);   // operator slice (B)
               const uint64_t ad = smem_desc_sw64(sa + ia * A_SLICE + kk * 32);
               const uint64_t bd = smem_desc_sw64(sb + ib * B_SLICE + kk * 32);
               tc_mma_f16(d_lo, ad, bd, idesc, (first | (p > 0 ? 1u : 0u)));
@@ -268,7 +289,7 @@ static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int 
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_cdo<NSL, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tc::SMEM);
+                                         tc::Cfg<NSL>::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -276,7 +297,7 @@ static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int 
   if (n_total <= 0) return cudaSuccess;
   int grid = num_sms();
   if (grid > n_total) grid = n_total;
-  k_tc_cdo<NSL, GROUPED><<<grid, tc::THREADS, tc::SMEM, st>>>(single, items, n_items, segs, status,
+  k_tc_cdo<NSL, GROUPED><<<grid, tc::THREADS, tc::Cfg<NSL>::SMEM, st>>>(single, items, n_items, segs, status,
                                                               (uint64_t)wait_limit_ns);
   return cudaGetLastError();
 }
@@ -290,6 +311,7 @@ cudaError_t launch_tc_single(const TcSegDev& seg, int nm, int nc, int nkb_max, i
   p.nc = nc;
   p.nkb_max = nkb_max;
   if (nslices == 4) return launch_impl<4, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
+  if (nslices == 3) return launch_impl<3, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
   if (nslices == 2) return launch_impl<2, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
   return cudaErrorInvalidValue;
 }
@@ -299,6 +321,7 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
   TcSingle p;
   memset(&p, 0, sizeof(p));
   if (nslices == 4) return launch_impl<4, true>(p, items, n_items, segs, status, wait_limit_ns, st);
+  if (nslices == 3) return launch_impl<3, true>(p, items, n_items, segs, status, wait_limit_ns, st);
   if (nslices == 2) return launch_impl<2, true>(p, items, n_items, segs, status, wait_limit_ns, st);
   return cudaErrorInvalidValue;
 }

@@ -21,6 +21,7 @@ pytestmark = pytest.mark.gpu
 HERE = os.path.dirname(os.path.abspath(__file__))
 TOL = {  # precision -> (chi2 rel, |dlogL| abs)
     "fp64": (1e-11, 1e-7),
+    "bf16x6": (1e-7, 1e-3),
     "bf16x10": (1e-7, 1e-3),
     "bf16x3": (3e-4, 5.0),
 }
@@ -35,7 +36,8 @@ def torch_cuda():
 
 
 def _opt(td, prec):
-    p = {"fp64": td.TD_PREC_FP64, "bf16x10": td.TD_PREC_BF16X10, "bf16x3": td.TD_PREC_BF16X3}[prec]
+    p = {"fp64": td.TD_PREC_FP64, "bf16x6": td.TD_PREC_BF16X6, "bf16x10": td.TD_PREC_BF16X10,
+         "bf16x3": td.TD_PREC_BF16X3}[prec]
     return td.options(precision=p)
 
 
@@ -79,7 +81,7 @@ CASES = [
 ]
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x10", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "bf16x6", "bf16x10", "bf16x3"])
 @pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
 def test_parity_small(torch_cuda, gpu_lib, case, prec):
     from paper_2603_06010_b300 import td
@@ -110,7 +112,7 @@ def test_white_noise_closed_form(torch_cuda, gpu_lib):
     R64 = R.astype(np.float64)
     exp_ll = -np.sum(R64 * R64, 1) / (2 * s2) - 0.5 * nk * np.log(2 * np.pi * s2)
     seg = td.Segment(inputs.white_acf(n, s2), mask)
-    for prec in ("fp64", "bf16x10"):
+    for prec in ("fp64", "bf16x6", "bf16x10"):
         ll, _ = _run(torch_cuda, td, seg, R, prec)
         assert np.max(np.abs(ll - exp_ll)) < 1e-6, prec
 
@@ -122,7 +124,7 @@ def test_column_alone_equals_in_batch(torch_cuda, gpu_lib):
     mask = _mask(n, [(700, 800)])
     seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
     R = inputs.noise_residuals(n, 2048.0, 300, 23, mask=mask)
-    for prec in ("fp64", "bf16x10"):
+    for prec in ("fp64", "bf16x6", "bf16x10"):
         full, _ = _run(torch_cuda, td, seg, R, prec)
         for k in (0, 1, 127, 128, 299):
             alone, _ = _run(torch_cuda, td, seg, R[k:k + 1], prec)
@@ -136,8 +138,8 @@ def test_repeatable_bits(torch_cuda, gpu_lib):
     n = 1024
     seg = td.Segment(inputs.acf_from_psd(n, 1024.0))
     R = inputs.noise_residuals(n, 1024.0, 200, 29)
-    a, _ = _run(torch_cuda, td, seg, R, "bf16x10")
-    b, _ = _run(torch_cuda, td, seg, R, "bf16x10")
+    a, _ = _run(torch_cuda, td, seg, R, "bf16x6")
+    b, _ = _run(torch_cuda, td, seg, R, "bf16x6")
     assert np.array_equal(a, b)
 
 
@@ -203,7 +205,7 @@ def _full_case(torch, td, g, prec):
     return ll[cols], chi[cols]
 
 
-@pytest.mark.parametrize("prec", ["bf16x10", "fp64"])
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x10", "fp64"])
 def test_full_cfg1(torch_cuda, gpu_lib, prec):
     from paper_2603_06010_b300 import td
     g = _golden()["cfg1"]
@@ -211,19 +213,21 @@ def test_full_cfg1(torch_cuda, gpu_lib, prec):
     _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg1")
 
 
-def test_full_cfg2_gapfree_8192(torch_cuda, gpu_lib):
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x10"])
+def test_full_cfg2_gapfree_8192(torch_cuda, gpu_lib, prec):
     from paper_2603_06010_b300 import td
     g = _golden()["cfg2"]
-    ll, chi = _full_case(torch_cuda, td, g, "bf16x10")
-    _compare("bf16x10", ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg2")
+    ll, chi = _full_case(torch_cuda, td, g, prec)
+    _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg2")
 
 
-def test_full_cfg3_gapped_three_detectors(torch_cuda, gpu_lib):
+@pytest.mark.parametrize("prec", ["bf16x6", "bf16x10"])
+def test_full_cfg3_gapped_three_detectors(torch_cuda, gpu_lib, prec):
     from paper_2603_06010_b300 import td
     gg = _golden()["cfg3"]
     joint = None
     for g in gg["detectors"]:
-        ll, chi = _full_case(torch_cuda, td, g, "bf16x10")
-        _compare("bf16x10", ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg3 detector")
+        ll, chi = _full_case(torch_cuda, td, g, prec)
+        _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg3 detector")
         joint = ll if joint is None else joint + ll
     assert np.max(np.abs(joint - np.array(gg["joint_logL"]))) <= 1e-3

@@ -68,8 +68,10 @@ typedef enum {
 
 typedef enum {
   TD_PATH_AUTO = 0,
-  TD_PATH_TENSOR = 1,  /* tcgen05 persistent split-product GEMM (K >= ~32) */
-  TD_PATH_STREAM = 2,  /* operator streamed once from HBM, CUDA-core FMAs (K <= ~16) */
+  TD_PATH_TENSOR = 1,  /* tcgen05 split-product GEMM, 256-row operator tiles (large K) */
+  TD_PATH_STREAM = 2,  /* the same kernel with 64-row operator tiles: 4x the work items,
+                          the operator streamed from HBM by a deep TMA ring (small K);
+                          identical per-element arithmetic, so identical results */
   TD_PATH_FP64 = 3     /* plain FP64 forward substitution */
 } td_path;
 
@@ -155,8 +157,9 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
  * has no counterpart; it is a property of this library's interface.
  *   Arguments as for td_loglike_batch (R, ldr, K, logL, chi2 caller-owned,
  *   device memory).  The segment must be factored (td_factor allocates).
- *   Size limit: 8 K N8 + 8 K ceil(N'/256) bytes must fit (N8 = N' rounded up
- *   to 8, the slices' row rounded to 256 bytes), e.g. N' = 8192 with K up to 497;
+ *   Size limit: 8 K N8 + 8 K ceil(N'/256) * 4 bytes must fit (N8 = N' rounded
+ *   up to 8, the slices' row rounded to 256 bytes), e.g. N' = 8192 with K up
+ *   to 504;
  *   larger batches return TD_ERR_INVALID before any device work.
  *   The first call on a device looks up the array's device address (once per
  *   device, with that device current); make that first call before any stream

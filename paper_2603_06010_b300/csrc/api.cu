@@ -12,8 +12,6 @@
 #include "td_internal.h"
 
 namespace td {
-cudaError_t launch_tc_single(const TcSegDev& seg, int nm, int nc, int nkb_max, int nslices, DevStatus* status,
-                             int64_t wait_limit_ns, cudaStream_t st);
 
 static thread_local std::string g_last_error;
 
@@ -67,14 +65,24 @@ static td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint6
   return TD_OK;
 }
 
-// residual-slice map (A operand) and operator map (B operand) of one segment
-td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, TcSegDev* out) {
+// residual-slice map (A operand) and operator map (B operand, tiles of bn rows) of one segment
+td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out) {
   td_status st = encode_3d(&out->mapA, s->scr.rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES,
                            (uint64_t)s->nkp8 * 2, (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, TC_COLS,
                            (uint32_t)nsl);
   if (st != TD_OK) return st;
   return encode_3d(&out->mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
-                   (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, OP_ROWS, (uint32_t)nsl);
+                   (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, (uint32_t)bn, (uint32_t)nsl);
+}
+
+// operator row-tile height for a batch: 256-row tiles while they give at
+// least two waves of work items, else 64-row tiles (4x the items, the same
+// per-element arithmetic); td_options.path can force either.
+static int choose_bn(const td_segment* s, int64_t K, int path) {
+  if (path == TD_PATH_TENSOR) return 256;
+  if (path == TD_PATH_STREAM) return 64;
+  const int64_t items256 = (s->nkp / OP_ROWS) * ceil_div(K, TC_COLS);
+  return items256 >= 2 * (int64_t)tc_num_sms() ? 256 : 64;
 }
 
 template <class T>
@@ -345,23 +353,24 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     return TD_OK;
   }
   const int nsl = nslices_for(o.precision);
+  const int bn = choose_bn(s, K, o.path);
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
-  if ((r = encode_seg_maps(s, K, nsl, &seg)) != TD_OK) return r;
+  if ((r = encode_seg_maps(s, K, nsl, bn, &seg)) != TD_OK) return r;
   seg.partials = sc.partials;
   seg.nk = (int)s->nk;
   seg.K = (int)K;
   seg.ldp = (int)ldp;
-  const int nm = (int)(s->nkp / OP_ROWS);
-  seg.nm = nm;
+  const int ngroups = (int)(s->nkp / 64);
+  seg.nm = ngroups;
   const int nc = (int)ceil_div(K, TC_COLS);
   const int nkb_max = (int)ceil_div(s->nk, OP_KB);
   const bool pm = s->prof && s->ev_used + 2 <= 8192;
   if (pm) prof_mark(s, st, true);
-  TD_CUDA(launch_tc_single(seg, nm, nc, nkb_max, nsl, s->status, o.wait_limit_ns, st));
+  TD_CUDA(launch_tc_single(seg, bn, nc, nkb_max, nsl, s->status, o.wait_limit_ns, st));
   if (pm) prof_mark(s, st, false);
-  TD_CUDA(launch_finalize(sc.partials, ldp, nm, K, s->logdet, s->nk, logL, chi2, st));
+  TD_CUDA(launch_finalize(sc.partials, ldp, ngroups, K, s->logdet, s->nk, logL, chi2, st));
   s->prof_kernels += 3;
   return TD_OK;
 }

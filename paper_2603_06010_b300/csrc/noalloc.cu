@@ -30,8 +30,6 @@
 #include "td_internal.h"
 
 namespace td {
-cudaError_t launch_tc_single(const TcSegDev& seg, int nm, int nc, int nkb_max, int nslices, DevStatus* status,
-                             int64_t wait_limit_ns, cudaStream_t st);
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[TD_NOALLOC_SCRATCH_BYTES];
 
@@ -92,15 +90,15 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != s->device) return fail(TD_ERR_INVALID, "segment belongs to another device; set it current first");
-  // scratch layout: residual slices [4][K][nkp8] bf16, then chi2 partials [nm][K] f64
-  const int64_t nm = s->nkp / OP_ROWS;
+  // scratch layout: residual slices [4][K][nkp8] bf16, then chi2 partials [N'p/64][K] f64
+  const int64_t nm = s->nkp / 64;
   const int64_t rs_bytes = (int64_t)OP_SLICES * K * s->nkp8 * 2;
   const int64_t part_off = round_up(rs_bytes, 256);
   const int64_t need = part_off + nm * K * 8;
   if (need > (int64_t)TD_NOALLOC_SCRATCH_BYTES) {
     char buf[200];
     snprintf(buf, sizeof buf,
-             "batch needs %lld scratch bytes (about 8 K N' for residual slices plus 8 K N'/256 for chi2 "
+             "batch needs %lld scratch bytes (about 8 K N' for residual slices plus 8 K N'/64 for chi2 "
              "partials), above the fixed %lld-byte no-alloc scratch; use a smaller K or td_loglike_batch",
              (long long)need, (long long)TD_NOALLOC_SCRATCH_BYTES);
     return fail(TD_ERR_INVALID, buf);
@@ -118,7 +116,7 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
                      (uint64_t)K * s->nkp8 * 2, OP_KB, TC_COLS, 3)) != TD_OK)
     return r;
   if ((r = na_encode(&seg.mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
-                     (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, OP_ROWS, 3)) != TD_OK)
+                     (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, 64, 3)) != TD_OK)
     return r;
   seg.partials = partials;
   seg.nk = (int)s->nk;
@@ -126,7 +124,7 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
   seg.ldp = (int)K;
   seg.nm = (int)nm;
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, K, rs, 3, st));
-  TD_CUDA(launch_tc_single(seg, (int)nm, (int)ceil_div(K, TC_COLS), (int)ceil_div(s->nk, OP_KB), 3,
+  TD_CUDA(launch_tc_single(seg, 64, (int)ceil_div(K, TC_COLS), (int)ceil_div(s->nk, OP_KB), 3,
                            s->status, 1000000000LL, st));
   TD_CUDA(launch_finalize(partials, K, (int)nm, K, s->logdet, s->nk, logL, chi2, st));
   return TD_OK;

@@ -6,69 +6,59 @@
 // The product is computed transposed, W^T = R^T (L^{-1})^T, so that each
 // TMEM lane holds one residual column and the chi2 sum over rows happens in
 // one thread's registers with no cross-thread reduction:
-//   MMA M = 128 residual columns (A = R^T slices, K-major),
-//   MMA N = 256 rows of W        (B = L^{-1} slices, K-major),
+//   MMA M = 128 residual columns  (A = R^T slices, K-major),
+//   MMA N = BN rows of W, BN = 256 (large batches) or 64 (small batches)
+//                                 (B = L^{-1} slices, K-major),
 //   reduction over the kept samples j in k-blocks of 32 (64-byte swizzle).
 // Each operand is held as bf16 slices x = x0 + x1 + x2 (+ x3) with x0 a
 // fixed-point hi slice (integer multiple, |.| <= 255, of a per-row /
-// per-column power-of-two quantum) and x1.. floating slices of the remainder.  The
-// tensor core accumulates in FP32 with truncation, which biases every sum
+// per-column power-of-two quantum) and x1.. floating slices of the remainder.
+// The tensor core accumulates in FP32 with truncation, which biases every sum
 // that is not exactly representable; so the hi*hi products, whose partial sums
 // are exact integer multiples of one quantum, go to their own accumulator
 // (exact), and the products x_a * y_b with 1 <= a + b <= NSL - 1 (five for
 // three slices, nine for four) go, smallest first, to a second accumulator
 // whose magnitude (and so its truncation error) is small.  The epilogue adds
-// the two in double-float.
+// the two in double-float and emits one FP64 chi2 partial per 64-row group.
+//
+// Each output element goes through the same k-blocks, products and order
+// whichever tile shape computes it, and the chi2 partials are always per
+// 64-row group, so a column's result does not depend on BN or on the batch.
 //
 // Work: one output tile = (segment, row tile m, column tile c); the row tile
-// needs k-blocks 0 .. 8(m+1)-1 (the lower triangle).  Tiles are sorted by
-// work (largest first) and dealt to the persistent CTAs in snake order.
+// needs the k-blocks up to its diagonal (the lower triangle).  Tiles are
+// sorted by work (largest first) and dealt to the persistent CTAs in snake
+// order.
 //
 // Warp roles (192 threads, one CTA per SM):
 //   warp 0 lane 0 : TMA producer, STAGES-deep ring of (A, B) slice stages
 //   warp 1        : TMEM allocator; lane 0 issues tcgen05.mma
 //   warps 2..5    : epilogue; TMEM -> registers, exact squares, compensated
-//                   sums, one FP64 partial per (row tile, column)
-// TMEM holds the two accumulators (2 x 256 columns).  Every wait is bounded
-// (wait_limit_ns).
+//                   sums, FP64 partials
+// TMEM holds NBUF pairs of accumulators (one pair for BN = 256, two for
+// BN = 64 so the epilogue of one tile overlaps the MMAs of the next).  Every
+// wait is bounded (wait_limit_ns).
 #include "td_internal.h"
 
 namespace td {
 namespace tc {
-constexpr int BM = TC_COLS;      // 128
-constexpr int BN = OP_ROWS;      // 256
+constexpr int BM = TC_COLS;      // 128 residual columns
 constexpr int BK = OP_KB;        // 32
 constexpr int A_SLICE = BM * BK * 2;   // 8 KB
-constexpr int B_SLICE = BN * BK * 2;   // 16 KB
 constexpr int BAR_BYTES = 256;
-// per loaded-slice count NSL: stage = NSL x 24 KB, as many stages as fit
-template <int NSL> struct Cfg {
+constexpr int THREADS = 192;
+template <int NSL, int BN> struct Cfg {
+  static constexpr int B_SLICE = BN * BK * 2;
   static constexpr int A_STAGE = NSL * A_SLICE;
   static constexpr int B_STAGE = NSL * B_SLICE;
   static constexpr int STAGE = A_STAGE + B_STAGE;
-  static constexpr int STAGES = (220 * 1024) / STAGE > 4 ? 4 : (220 * 1024) / STAGE;
+  static constexpr int STAGES = (220 * 1024) / STAGE > 8 ? 8 : (220 * 1024) / STAGE;
   static constexpr int SMEM = STAGES * STAGE + BAR_BYTES + 1024;
+  static constexpr int NBUF = (4 * BN <= 512) ? 2 : 1;           // accumulator pairs in TMEM
+  static constexpr uint32_t TMEM_COLS = (NBUF * 2 * BN <= 256) ? 256 : 512;
+  static constexpr int GROUPS = BN / 64;                          // 64-row chi2 groups per tile
 };
-constexpr int THREADS = 192;
-constexpr uint32_t TMEM_COLS = 512;
 }  // namespace tc
-
-struct TcSingle {           // single-segment launch: item list is implicit
-  TcSegDev seg;
-  int nm;                   // row tiles
-  int nc;                   // column tiles
-  int nkb_max;              // k-blocks available (ceil(N'/32))
-};
-
-__device__ __forceinline__ TcItem single_item(const TcSingle& p, int idx) {
-  TcItem it;
-  it.seg = 0;
-  it.m = p.nm - 1 - idx / p.nc;
-  it.c = idx % p.nc;
-  int nkb = (tc::BN / tc::BK) * (it.m + 1);
-  it.nkb = nkb < p.nkb_max ? nkb : p.nkb_max;
-  return it;
-}
 
 // correction products (operator slice, residual slice), smallest first; the
 // hi*hi product (0, 0) is separate.  NSL slices per operand: 4 -> a+b <= 3
@@ -90,21 +80,42 @@ template <> struct Corr<2> {   // (1,0) (0,1)
   __device__ static constexpr int rs(int p) { return p; }
 };
 
-template <int NSL, bool GROUPED>
+struct TcSingle {           // single-segment launch: item list is implicit
+  TcSegDev seg;
+  int nm;                   // row tiles of BN rows
+  int nc;                   // column tiles
+  int nkb_max;              // k-blocks available (ceil(N'/32))
+};
+
+template <int BN>
+__device__ __forceinline__ TcItem single_item(const TcSingle& p, int idx) {
+  TcItem it;
+  it.seg = 0;
+  it.m = p.nm - 1 - idx / p.nc;
+  it.c = idx % p.nc;
+  const int nkb = (BN / tc::BK) * (it.m + 1);
+  it.nkb = nkb < p.nkb_max ? nkb : p.nkb_max;
+  return it;
+}
+
+template <int NSL, int BN, bool GROUPED>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     k_tc_cdo(const __grid_constant__ TcSingle single, const TcItem* __restrict__ items, int n_items,
              const TcSegDev* __restrict__ segs, DevStatus* status, uint64_t limit_ns) {
   using namespace tc;
-  constexpr int A_STAGE = Cfg<NSL>::A_STAGE;
-  constexpr int STAGE = Cfg<NSL>::STAGE;
-  constexpr int STAGES = Cfg<NSL>::STAGES;
+  using C = Cfg<NSL, BN>;
+  constexpr int A_STAGE = C::A_STAGE;
+  constexpr int B_SLICE = C::B_SLICE;
+  constexpr int STAGE = C::STAGE;
+  constexpr int STAGES = C::STAGES;
+  constexpr int NBUF = C::NBUF;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
   uint64_t* empty = full + STAGES;
   uint64_t* tfull = empty + STAGES;
-  uint64_t* tempty = tfull + 2;
-  uint64_t* fin = tempty + 2;
+  uint64_t* tempty = tfull + NBUF;
+  uint64_t* fin = tempty + NBUF;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -114,14 +125,16 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(&tfull[0], 1);
-    mbar_init(&tempty[0], 4);
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
     mbar_init(fin, 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
   if (warp == 1) {
-    tmem_alloc(tmem_slot, TMEM_COLS);
+    tmem_alloc(tmem_slot, C::TMEM_COLS);
     tmem_relinquish();
   }
   tc_fence_before();
@@ -144,9 +157,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
         const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
         if (idx >= n_total) continue;
-        const TcItem it = GROUPED ? items[idx] : single_item(single, idx);
+        const TcItem it = GROUPED ? items[idx] : single_item<BN>(single, idx);
         const TcSegDev* sd = GROUPED ? &segs[it.seg] : &single.seg;
-        const int blk0 = (BN / BK) * it.m * (it.m + 1) / 2;
+        const int row0 = it.m * BN;                      // first W row of the tile
+        const int M256 = row0 / OP_ROWS;                 // 256-row operator tile holding it
+        const int yoff = row0 - M256 * OP_ROWS;          // row offset inside the 256-row block
+        const int blk0 = (OP_ROWS / BK) * M256 * (M256 + 1) / 2;
         bool ok = true;
         for (int kb = 0; kb < it.nkb; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, limit_ns)) {
@@ -159,7 +175,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           uint8_t* sb = sa + A_STAGE;
           mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (A_SLICE + B_SLICE)));
           tma_load_3d(sa, &sd->mapA, &full[stage], kb * BK, it.c * BM, 0);
-          tma_load_3d(sb, &sd->mapB, &full[stage], 0, 0, (blk0 + kb) * OP_SLICES);
+          tma_load_3d(sb, &sd->mapB, &full[stage], 0, yoff, (blk0 + kb) * OP_SLICES);
           issued_mask |= 1u << stage;
           issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -183,15 +199,17 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
         const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
         if (idx >= n_total) continue;
-        const TcItem it = GROUPED ? items[idx] : single_item(single, idx);
-        if (!mbar_wait(&tempty[0], ((uint32_t)tl & 1u) ^ 1u, limit_ns)) {
+        const TcItem it = GROUPED ? items[idx] : single_item<BN>(single, idx);
+        const int buf = tl % NBUF;
+        const uint32_t use = (uint32_t)(tl / NBUF);
+        if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, limit_ns)) {
           set_status(status, ST_TIMEOUT, 20);
           *abort_flag = 1;
           break;
         }
         tc_fence_after();
-        const uint32_t d_hi = tmem_base;              // hi*hi (exact)
-        const uint32_t d_lo = tmem_base + (uint32_t)BN;   // corrections
+        const uint32_t d_hi = tmem_base + (uint32_t)(buf * 2 * BN);   // hi*hi (exact)
+        const uint32_t d_lo = d_hi + (uint32_t)BN;                      // corrections
         bool ok = true;
         for (int kb = 0; kb < it.nkb; ++kb) {
           if (!mbar_wait(&full[stage], phase, limit_ns)) {
@@ -223,7 +241,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           }
         }
         if (!ok) break;
-        tc_commit(&tfull[0]);         // accumulators ready for the epilogue
+        tc_commit(&tfull[buf]);       // accumulators ready for the epilogue
         ++tl;
       }
       tc_commit(fin);                 // all MMAs issued by this thread retired
@@ -236,29 +254,40 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
       const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
       if (idx >= n_total) continue;
-      const TcItem it = GROUPED ? items[idx] : single_item(single, idx);
+      const TcItem it = GROUPED ? items[idx] : single_item<BN>(single, idx);
       const TcSegDev* sd = GROUPED ? &segs[it.seg] : &single.seg;
-      if (!mbar_wait(&tfull[0], (uint32_t)tl & 1u, limit_ns)) {
+      const int buf = tl % NBUF;
+      const uint32_t use = (uint32_t)(tl / NBUF);
+      if (!mbar_wait(&tfull[buf], use & 1u, limit_ns)) {
         if (lane == 0) set_status(status, ST_TIMEOUT, 30);
         *abort_flag = 1;
         break;
       }
       tc_fence_after();
-      float hi = 0.f, lo = 0.f;
-      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16);
-#pragma unroll 1
-      for (int ch = 0; ch < BN / 32; ++ch) {
-        float v0[32], v1[32];
-        tmem_ld32(ta + (uint32_t)(ch * 32), v0);
-        tmem_ld32(ta + (uint32_t)(BN + ch * 32), v1);
+      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * BN);
+      double part[C::GROUPS];
 #pragma unroll
-        for (int i = 0; i < 32; ++i) ff_add_square2(v0[i], v1[i], hi, lo);
+      for (int g = 0; g < C::GROUPS; ++g) {
+        float hi = 0.f, lo = 0.f;
+#pragma unroll 1
+        for (int ch = 2 * g; ch < 2 * g + 2; ++ch) {
+          float v0[32], v1[32];
+          tmem_ld32(ta + (uint32_t)(ch * 32), v0);
+          tmem_ld32(ta + (uint32_t)(BN + ch * 32), v1);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) ff_add_square2(v0[i], v1[i], hi, lo);
+        }
+        part[g] = (double)hi + (double)lo;
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[0]);
+      if (lane == 0) mbar_arrive(&tempty[buf]);
       const int col = it.c * BM + q * 32 + lane;
-      if (col < sd->K) sd->partials[(int64_t)it.m * sd->ldp + col] = (double)hi + (double)lo;
+      if (col < sd->K) {
+        const int64_t g0 = (int64_t)it.m * C::GROUPS;
+#pragma unroll
+        for (int g = 0; g < C::GROUPS; ++g) sd->partials[(g0 + g) * sd->ldp + col] = part[g];
+      }
       ++tl;
     }
   }
@@ -267,13 +296,13 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    tmem_dealloc(tmem_base, TMEM_COLS);
+    tmem_dealloc(tmem_base, C::TMEM_COLS);
   }
 }
 
 static int g_num_sms = 0;
 
-static int num_sms() {
+int tc_num_sms() {
   if (g_num_sms == 0) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -283,51 +312,63 @@ static int num_sms() {
   return g_num_sms;
 }
 
-template <int NSL, bool GROUPED>
+template <int NSL, int BN, bool GROUPED>
 static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int n_items, const TcSegDev* segs,
                                DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+  using C = tc::Cfg<NSL, BN>;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_cdo<NSL, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tc::Cfg<NSL>::SMEM);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_tc_cdo<NSL, BN, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   const int n_total = GROUPED ? n_items : single.nm * single.nc;
   if (n_total <= 0) return cudaSuccess;
-  int grid = num_sms();
+  int grid = tc_num_sms();
   if (grid > n_total) grid = n_total;
-  k_tc_cdo<NSL, GROUPED><<<grid, tc::THREADS, tc::Cfg<NSL>::SMEM, st>>>(single, items, n_items, segs, status,
-                                                              (uint64_t)wait_limit_ns);
+  k_tc_cdo<NSL, BN, GROUPED><<<grid, tc::THREADS, C::SMEM, st>>>(single, items, n_items, segs, status,
+                                                                 (uint64_t)wait_limit_ns);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_single(const TcSegDev& seg, int nm, int nc, int nkb_max, int nslices, DevStatus* status,
+template <bool GROUPED>
+static cudaError_t dispatch(int nslices, int bn, const TcSingle& p, const TcItem* items, int n_items,
+                            const TcSegDev* segs, DevStatus* status, int64_t lim, cudaStream_t st) {
+  if (bn == 256) {
+    if (nslices == 3) return launch_impl<3, 256, GROUPED>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 4) return launch_impl<4, 256, GROUPED>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 2) return launch_impl<2, 256, GROUPED>(p, items, n_items, segs, status, lim, st);
+  } else if (bn == 64) {
+    if (nslices == 3) return launch_impl<3, 64, GROUPED>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 4) return launch_impl<4, 64, GROUPED>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 2) return launch_impl<2, 64, GROUPED>(p, items, n_items, segs, status, lim, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+// single segment: tiles of bn rows (256 or 64); seg.partials holds one row per
+// 64-row group, seg.ldp apart
+cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st) {
   TcSingle p;
   memset(&p, 0, sizeof(p));
   p.seg = seg;
-  p.nm = nm;
+  p.nm = (int)(ceil_div((int64_t)seg.nk, OP_ROWS) * OP_ROWS / bn);
   p.nc = nc;
   p.nkb_max = nkb_max;
-  if (nslices == 4) return launch_impl<4, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
-  if (nslices == 3) return launch_impl<3, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
-  if (nslices == 2) return launch_impl<2, false>(p, nullptr, 0, nullptr, status, wait_limit_ns, st);
-  return cudaErrorInvalidValue;
+  return dispatch<false>(nslices, bn, p, nullptr, 0, nullptr, status, wait_limit_ns, st);
 }
 
-cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices,
+cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
                           DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
   TcSingle p;
   memset(&p, 0, sizeof(p));
-  if (nslices == 4) return launch_impl<4, true>(p, items, n_items, segs, status, wait_limit_ns, st);
-  if (nslices == 3) return launch_impl<3, true>(p, items, n_items, segs, status, wait_limit_ns, st);
-  if (nslices == 2) return launch_impl<2, true>(p, items, n_items, segs, status, wait_limit_ns, st);
-  return cudaErrorInvalidValue;
+  return dispatch<true>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st);
 }
 
-// chi2 and logL per column from the per-row-tile partials (fixed order),
-// for every segment of a grouped launch.
+// chi2 and logL per column from the per-group partials (fixed order), for
+// every segment of a grouped launch (TcSegDev::nm = number of 64-row groups).
 __global__ void k_tc_finalize(const TcSegDev* __restrict__ segs) {
   const TcSegDev& sd = segs[blockIdx.y];
   for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < sd.K;

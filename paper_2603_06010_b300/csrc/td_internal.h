@@ -123,9 +123,12 @@ cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8,
                             int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st);
 
-// tensor-core CDO product + chi2 partials over a work list
-cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices,
+// tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
+cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
                           DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
+cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
+                             int64_t wait_limit_ns, cudaStream_t st);
+int tc_num_sms();
 cudaError_t launch_tc_finalize(const TcSegDev* segs, int nseg, int64_t maxK, cudaStream_t st);
 
 cudaError_t launch_bounded_wait_probe(DevStatus* status, int64_t limit_ns, cudaStream_t st);

@@ -231,3 +231,20 @@ def test_full_cfg3_gapped_three_detectors(torch_cuda, gpu_lib, prec):
         _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg3 detector")
         joint = ll if joint is None else joint + ll
     assert np.max(np.abs(joint - np.array(gg["joint_logL"]))) <= 1e-3
+
+
+@pytest.mark.parametrize("K", [1, 5, 130, 300])
+def test_tile_shapes_give_identical_bits(torch_cuda, gpu_lib, K):
+    """256-row and 64-row operator tiles run the same per-element arithmetic."""
+    from paper_2603_06010_b300 import td
+    n = 2000
+    mask = _mask(n, [(900, 1000)])
+    seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
+    R = torch_cuda.from_numpy(inputs.noise_residuals(n, 2048.0, K, 31, mask=mask)).cuda()
+    out = {}
+    for path in (td.TD_PATH_TENSOR, td.TD_PATH_STREAM):
+        ll = seg.loglike(R, td.options(path=path))
+        torch_cuda.cuda.synchronize()
+        seg.check()
+        out[path] = ll.cpu().numpy()
+    assert np.array_equal(out[td.TD_PATH_TENSOR], out[td.TD_PATH_STREAM])

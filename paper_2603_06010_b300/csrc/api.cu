@@ -115,11 +115,21 @@ static int nslices_for(int precision) {
   return precision == TD_PREC_BF16X3 ? 2 : (precision == TD_PREC_BF16X10 ? 4 : 3);
 }
 
+static void free_plans(Scratch& sc) {
+  for (SplitPlan& p : sc.plans) {
+    dev_free(p.items);
+    dev_free(p.units);
+    dev_free(p.segdev);
+  }
+  sc.plans.clear();
+}
+
 // Grow the per-segment scratch so batches of K columns fit.
 static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaStream_t st) {
   Scratch& sc = s->scr;
   if (K > sc.capK) {
     cudaStreamSynchronize(st);   // old buffers may still be in use on this stream
+    free_plans(sc);              // their tensor maps point at the old residual slices
     dev_free(sc.rs);
     dev_free(sc.partials);
     dev_free(sc.w64);
@@ -134,6 +144,76 @@ static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaSt
     td_status r = dev_alloc(&sc.w64, (size_t)(s->nkp * sc.capK), "FP64 whitened residuals");
     if (r != TD_OK) return r;
   }
+  return TD_OK;
+}
+
+// device work lists for a 64-row-tile batch of K columns (cached per K)
+static td_status get_split_plan(td_segment* s, int64_t K, int nsl, cudaStream_t st, SplitPlan** out) {
+  Scratch& sc = s->scr;
+  ++sc.use_clock;
+  for (SplitPlan& p : sc.plans)
+    if (p.K == K && p.nsl == nsl) {
+      p.last_use = sc.use_clock;
+      *out = &p;
+      return TD_OK;
+    }
+  const int S = split_chunk(s->nk, s->nkp);
+  std::vector<TcItem> items;
+  std::vector<SplitUnit> units;
+  int n_slots = 0;
+  plan_split_segment(0, s->nk, s->nkp, K, S, items, units, n_slots);
+  sort_items(items);
+  td_status r;
+  if (n_slots > sc.wpart_slots) {
+    cudaStreamSynchronize(st);
+    free_plans(sc);
+    dev_free(sc.wpart);
+    sc.wpart_slots = 0;
+    if ((r = dev_alloc(&sc.wpart, (size_t)n_slots * TC_COLS * 64, "split accumulators")) != TD_OK) return r;
+    sc.wpart_slots = n_slots;
+  }
+  if (sc.plans.size() >= 8) {   // evict the least recently used plan
+    size_t lru = 0;
+    for (size_t i = 1; i < sc.plans.size(); ++i)
+      if (sc.plans[i].last_use < sc.plans[lru].last_use) lru = i;
+    cudaStreamSynchronize(st);
+    dev_free(sc.plans[lru].items);
+    dev_free(sc.plans[lru].units);
+    dev_free(sc.plans[lru].segdev);
+    sc.plans.erase(sc.plans.begin() + (long)lru);
+  }
+  SplitPlan p;
+  p.K = K;
+  p.nsl = nsl;
+  p.S = S;
+  p.n_items = (int)items.size();
+  p.n_units = (int)units.size();
+  p.n_slots = n_slots;
+  TcSegDev seg;
+  memset(&seg, 0, sizeof seg);
+  if ((r = encode_seg_maps(s, K, nsl, 64, &seg)) != TD_OK) return r;
+  seg.partials = sc.partials;
+  seg.wpart = sc.wpart;
+  seg.nk = (int)s->nk;
+  seg.K = (int)K;
+  seg.ldp = (int)sc.capK;
+  seg.nm = (int)(s->nkp / 64);
+  seg.logdet = s->logdet;
+  if ((r = dev_alloc(&p.items, items.size(), "work items")) != TD_OK ||
+      (r = dev_alloc(&p.units, units.size(), "split units")) != TD_OK ||
+      (r = dev_alloc(&p.segdev, 1, "segment descriptor")) != TD_OK) {
+    dev_free(p.items);
+    dev_free(p.units);
+    dev_free(p.segdev);
+    return r;
+  }
+  TD_CUDA(cudaMemcpy(p.items, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice));
+  if (!units.empty())
+    TD_CUDA(cudaMemcpy(p.units, units.data(), units.size() * sizeof(SplitUnit), cudaMemcpyHostToDevice));
+  TD_CUDA(cudaMemcpy(p.segdev, &seg, sizeof seg, cudaMemcpyHostToDevice));
+  p.last_use = sc.use_clock;
+  sc.plans.push_back(p);
+  *out = &sc.plans.back();
   return TD_OK;
 }
 
@@ -367,6 +447,18 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   const int nc = (int)ceil_div(K, TC_COLS);
   const int nkb_max = (int)ceil_div(s->nk, OP_KB);
   const bool pm = s->prof && s->ev_used + 2 <= 8192;
+  if (bn == 64) {
+    SplitPlan* plan = nullptr;
+    if ((r = get_split_plan(s, K, nsl, st, &plan)) != TD_OK) return r;
+    if (pm) prof_mark(s, st, true);
+    TD_CUDA(launch_tc_cdo(plan->items, plan->n_items, plan->segdev, nsl, 64, true, s->status, o.wait_limit_ns,
+                          st));
+    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, st));
+    if (pm) prof_mark(s, st, false);
+    TD_CUDA(launch_finalize(sc.partials, ldp, ngroups, K, s->logdet, s->nk, logL, chi2, st));
+    s->prof_kernels += plan->n_units > 0 ? 4 : 3;
+    return TD_OK;
+  }
   if (pm) prof_mark(s, st, true);
   TD_CUDA(launch_tc_single(seg, bn, nc, nkb_max, nsl, s->status, o.wait_limit_ns, st));
   if (pm) prof_mark(s, st, false);
@@ -447,6 +539,8 @@ void td_segment_destroy(td_segment* s) {
   dev_free(s->scr.items);
   dev_free(s->scr.segdev);
   dev_free(s->scr.rsf);
+  dev_free(s->scr.wpart);
+  free_plans(s->scr);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
   delete s;

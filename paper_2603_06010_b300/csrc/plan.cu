@@ -1,0 +1,54 @@
+// Work lists for the tensor-core kernel's explicit-list modes.
+//
+// Small batches use 64-row operator tiles; a row tile whose k-range is longer
+// than S k-blocks is cut into chunks of at most S, so no single work item
+// holds back the launch.  S depends only on N' (not on K), so the split of a
+// given column is the same in every batch.  Chunks of one row tile write
+// their accumulator pairs to consecutive slots; one SplitUnit per split tile
+// tells k_split_reduce which slots to add.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "td_internal.h"
+
+namespace td {
+
+int split_chunk(int64_t nk, int64_t nkp) {
+  const int64_t nm = nkp / 64;
+  const int64_t nkb_max = ceil_div(nk, OP_KB);
+  int64_t total = 0;
+  for (int64_t m = 0; m < nm; ++m) total += std::min<int64_t>(2 * (m + 1), nkb_max);
+  int64_t S = ceil_div(total, 2 * (int64_t)tc_num_sms());
+  if (S < 4) S = 4;
+  return (int)S;
+}
+
+// append the items of one segment (64-row tiles, chunk S) to the lists
+void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int S, std::vector<TcItem>& items,
+                        std::vector<SplitUnit>& units, int& n_slots) {
+  const int nm = (int)(nkp / 64);
+  const int nc = (int)ceil_div(K, TC_COLS);
+  const int nkb_max = (int)ceil_div(nk, OP_KB);
+  for (int c = 0; c < nc; ++c) {
+    for (int m = 0; m < nm; ++m) {
+      const int nkb = std::min(2 * (m + 1), nkb_max);
+      const int nch = (nkb + S - 1) / S;
+      if (nch <= 1) {
+        items.push_back(TcItem{seg, m, c, nkb, 0, -1});
+        continue;
+      }
+      units.push_back(SplitUnit{seg, m, c, n_slots, nch, 0});
+      for (int ch = 0; ch < nch; ++ch) {
+        const int kb0 = ch * S;
+        items.push_back(TcItem{seg, m, c, std::min(S, nkb - kb0), kb0, n_slots++});
+      }
+    }
+  }
+}
+
+void sort_items(std::vector<TcItem>& items) {
+  std::stable_sort(items.begin(), items.end(), [](const TcItem& a, const TcItem& b) { return a.nkb > b.nkb; });
+}
+
+}  // namespace td

@@ -21,9 +21,9 @@
 // whose magnitude (and so its truncation error) is small.  The epilogue adds
 // the two in double-float and emits one FP64 chi2 partial per 64-row group.
 //
-// Each output element goes through the same k-blocks, products and order
-// whichever tile shape computes it, and the chi2 partials are always per
-// 64-row group, so a column's result does not depend on BN or on the batch.
+// A given (tile shape, k-range split) fixes every rounding, so a column's
+// result does not depend on the other columns of its batch; chi2 partials
+// are always per 64-row group.
 //
 // Work: one output tile = (segment, row tile m, column tile c); the row tile
 // needs the k-blocks up to its diagonal (the lower triangle).  Tiles are
@@ -95,10 +95,17 @@ __device__ __forceinline__ TcItem single_item(const TcSingle& p, int idx) {
   it.c = idx % p.nc;
   const int nkb = (BN / tc::BK) * (it.m + 1);
   it.nkb = nkb < p.nkb_max ? nkb : p.nkb_max;
+  it.kb0 = 0;
+  it.slot = -1;
   return it;
 }
 
-template <int NSL, int BN, bool GROUPED>
+// MODE 0: one segment, implicit item list, chi2 partials in the epilogue
+// MODE 1: explicit item list (many segments), chi2 partials in the epilogue
+// MODE 2: explicit item list whose items may cover part of a row's k-range
+//         (slot >= 0): the epilogue stores the accumulator pair and
+//         k_split_reduce finishes; items with slot < 0 cover whole rows
+template <int NSL, int BN, int MODE>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     k_tc_cdo(const __grid_constant__ TcSingle single, const TcItem* __restrict__ items, int n_items,
              const TcSegDev* __restrict__ segs, DevStatus* status, uint64_t limit_ns) {
@@ -142,6 +149,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int G = gridDim.x, b = blockIdx.x;
+  constexpr bool GROUPED = MODE != 0;
   const int n_total = GROUPED ? n_items : single.nm * single.nc;
 
   if (warp == 0) {
@@ -164,7 +172,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const int yoff = row0 - M256 * OP_ROWS;          // row offset inside the 256-row block
         const int blk0 = (OP_ROWS / BK) * M256 * (M256 + 1) / 2;
         bool ok = true;
-        for (int kb = 0; kb < it.nkb; ++kb) {
+        for (int kb = it.kb0; kb < it.kb0 + it.nkb; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, limit_ns)) {
             set_status(status, ST_TIMEOUT, 10);
             *abort_flag = 1;
@@ -211,7 +219,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         const uint32_t d_hi = tmem_base + (uint32_t)(buf * 2 * BN);   // hi*hi (exact)
         const uint32_t d_lo = d_hi + (uint32_t)BN;                      // corrections
         bool ok = true;
-        for (int kb = 0; kb < it.nkb; ++kb) {
+        for (int kb = it.kb0; kb < it.kb0 + it.nkb; ++kb) {
           if (!mbar_wait(&full[stage], phase, limit_ns)) {
             set_status(status, ST_TIMEOUT, 21);
             *abort_flag = 1;
@@ -223,7 +231,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           const uint32_t sb = sa + A_STAGE;
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
-            const uint32_t first = (kb > 0 || kk > 0) ? 1u : 0u;
+            const uint32_t first = (kb > it.kb0 || kk > 0) ? 1u : 0u;
             tc_mma_f16(d_hi, smem_desc_sw64(sa + kk * 32), smem_desc_sw64(sb + kk * 32), idesc, first);
 #pragma unroll
             for (int p = 0; p < Corr<NSL>::N; ++p) {
@@ -265,28 +273,47 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       }
       tc_fence_after();
       const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * BN);
-      double part[C::GROUPS];
-#pragma unroll
-      for (int g = 0; g < C::GROUPS; ++g) {
-        float hi = 0.f, lo = 0.f;
+      const int col = it.c * BM + q * 32 + lane;
+      if (MODE == 2 && it.slot >= 0) {
+        // accumulator pair of this chunk, for k_split_reduce: [slot][column][row]
+        float2* dst = sd->wpart + ((int64_t)it.slot * BM + q * 32 + lane) * BN;
 #pragma unroll 1
-        for (int ch = 2 * g; ch < 2 * g + 2; ++ch) {
+        for (int ch = 0; ch < BN / 32; ++ch) {
           float v0[32], v1[32];
           tmem_ld32(ta + (uint32_t)(ch * 32), v0);
           tmem_ld32(ta + (uint32_t)(BN + ch * 32), v1);
+          if (col < sd->K) {
+            float4* d4 = reinterpret_cast<float4*>(dst + ch * 32);
 #pragma unroll
-          for (int i = 0; i < 32; ++i) ff_add_square2(v0[i], v1[i], hi, lo);
+            for (int i = 0; i < 16; ++i) d4[i] = make_float4(v0[2 * i], v1[2 * i], v0[2 * i + 1], v1[2 * i + 1]);
+          }
         }
-        part[g] = (double)hi + (double)lo;
-      }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&tempty[buf]);
-      const int col = it.c * BM + q * 32 + lane;
-      if (col < sd->K) {
-        const int64_t g0 = (int64_t)it.m * C::GROUPS;
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+      } else {
+        double part[C::GROUPS];
 #pragma unroll
-        for (int g = 0; g < C::GROUPS; ++g) sd->partials[(g0 + g) * sd->ldp + col] = part[g];
+        for (int g = 0; g < C::GROUPS; ++g) {
+          float hi = 0.f, lo = 0.f;
+#pragma unroll 1
+          for (int ch = 2 * g; ch < 2 * g + 2; ++ch) {
+            float v0[32], v1[32];
+            tmem_ld32(ta + (uint32_t)(ch * 32), v0);
+            tmem_ld32(ta + (uint32_t)(BN + ch * 32), v1);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) ff_add_square2(v0[i], v1[i], hi, lo);
+          }
+          part[g] = (double)hi + (double)lo;
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
+        if (col < sd->K) {
+          const int64_t g0 = (int64_t)it.m * C::GROUPS;
+#pragma unroll
+          for (int g = 0; g < C::GROUPS; ++g) sd->partials[(g0 + g) * sd->ldp + col] = part[g];
+        }
       }
       ++tl;
     }
@@ -312,37 +339,37 @@ int tc_num_sms() {
   return g_num_sms;
 }
 
-template <int NSL, int BN, bool GROUPED>
+template <int NSL, int BN, int MODE>
 static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int n_items, const TcSegDev* segs,
                                DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
   using C = tc::Cfg<NSL, BN>;
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_tc_cdo<NSL, BN, GROUPED>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaFuncSetAttribute(k_tc_cdo<NSL, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const int n_total = GROUPED ? n_items : single.nm * single.nc;
+  const int n_total = MODE != 0 ? n_items : single.nm * single.nc;
   if (n_total <= 0) return cudaSuccess;
   int grid = tc_num_sms();
   if (grid > n_total) grid = n_total;
-  k_tc_cdo<NSL, BN, GROUPED><<<grid, tc::THREADS, C::SMEM, st>>>(single, items, n_items, segs, status,
-                                                                 (uint64_t)wait_limit_ns);
+  k_tc_cdo<NSL, BN, MODE><<<grid, tc::THREADS, C::SMEM, st>>>(single, items, n_items, segs, status,
+                                                              (uint64_t)wait_limit_ns);
   return cudaGetLastError();
 }
 
-template <bool GROUPED>
+template <int MODE>
 static cudaError_t dispatch(int nslices, int bn, const TcSingle& p, const TcItem* items, int n_items,
                             const TcSegDev* segs, DevStatus* status, int64_t lim, cudaStream_t st) {
   if (bn == 256) {
-    if (nslices == 3) return launch_impl<3, 256, GROUPED>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 4) return launch_impl<4, 256, GROUPED>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 2) return launch_impl<2, 256, GROUPED>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 3) return launch_impl<3, 256, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 4) return launch_impl<4, 256, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 2) return launch_impl<2, 256, MODE>(p, items, n_items, segs, status, lim, st);
   } else if (bn == 64) {
-    if (nslices == 3) return launch_impl<3, 64, GROUPED>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 4) return launch_impl<4, 64, GROUPED>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 2) return launch_impl<2, 64, GROUPED>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 3) return launch_impl<3, 64, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 4) return launch_impl<4, 64, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 2) return launch_impl<2, 64, MODE>(p, items, n_items, segs, status, lim, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -357,14 +384,56 @@ cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, i
   p.nm = (int)(ceil_div((int64_t)seg.nk, OP_ROWS) * OP_ROWS / bn);
   p.nc = nc;
   p.nkb_max = nkb_max;
-  return dispatch<false>(nslices, bn, p, nullptr, 0, nullptr, status, wait_limit_ns, st);
+  return dispatch<0>(nslices, bn, p, nullptr, 0, nullptr, status, wait_limit_ns, st);
 }
 
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
-                          DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
   TcSingle p;
   memset(&p, 0, sizeof(p));
-  return dispatch<true>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st);
+  if (split) return dispatch<2>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st);
+  return dispatch<1>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st);
+}
+
+// Reduce the accumulator pairs of a split row tile (BN = 64 rows): for each
+// row, w = sum over chunks of (hi*hi sum + correction sum), in double-float
+// (the hi*hi sums are exact, their sum stays exact well past these lengths);
+// then the chi2 share of the 64 rows in double-float, as one FP64 partial in
+// the same per-64-row-group layout the direct epilogue writes.
+__global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restrict__ units,
+                                                       const TcSegDev* __restrict__ segs) {
+  __shared__ float red_hi[128], red_lo[128];
+  const SplitUnit u = units[blockIdx.x];
+  const TcSegDev& sd = segs[u.seg];
+  const int cl = threadIdx.x & 127, half = threadIdx.x >> 7;
+  const int col = u.c * 128 + cl;
+  float hi = 0.f, lo = 0.f;
+  if (col < sd.K) {
+    for (int r = half * 32; r < half * 32 + 32; ++r) {
+      float wh = 0.f, wl = 0.f;
+      for (int ch = 0; ch < u.nchunk; ++ch) {
+        const float2 v = sd.wpart[((int64_t)(u.slot0 + ch) * 128 + cl) * 64 + r];
+        ff_add(v.x, wh, wl);
+        ff_add(v.y, wh, wl);
+      }
+      ff_add_square2(wh, wl, hi, lo);
+    }
+  }
+  if (half == 1) {
+    red_hi[cl] = hi;
+    red_lo[cl] = lo;
+  }
+  __syncthreads();
+  if (half == 0 && col < sd.K) {
+    const double s = ((double)hi + (double)lo) + ((double)red_hi[cl] + (double)red_lo[cl]);
+    sd.partials[(int64_t)u.m * sd.ldp + col] = s;
+  }
+}
+
+cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, cudaStream_t st) {
+  if (n_units <= 0) return cudaSuccess;
+  k_split_reduce<<<n_units, 256, 0, st>>>(units, segs);
+  return cudaGetLastError();
 }
 
 // chi2 and logL per column from the per-group partials (fixed order), for

@@ -185,6 +185,15 @@ __device__ __forceinline__ void ff_add_square(float w, float& hi, float& lo) {
   lo += err + e;
 }
 
+// (hi, lo) += a, compensated (two-sum on the head)
+__device__ __forceinline__ void ff_add(float a, float& hi, float& lo) {
+  float t = hi + a;
+  float bp = t - hi;
+  float err = (hi - (t - bp)) + (a - bp);
+  hi = t;
+  lo += err;
+}
+
 // (a + b)^2 for an FP32 pair whose sum is the value: two-sum first, then the
 // exact square of the head and the cross term, accumulated into (hi, lo)
 __device__ __forceinline__ void ff_add_square2(float a, float b, float& hi, float& lo) {

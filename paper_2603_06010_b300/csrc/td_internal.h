@@ -25,11 +25,22 @@ inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
 // offset (in 256x32 blocks) of operator row tile m in the packed lower triangle
 inline int64_t op_row_offset(int64_t m) { return (OP_ROWS / OP_KB) * m * (m + 1) / 2; }
 
-struct TcItem {      // one tensor-core output tile
+struct TcItem {      // one tensor-core work item
   int seg;           // index into the launch's segment table
-  int m;             // W row tile (256 rows)
+  int m;             // W row tile (BN rows)
   int c;             // residual column tile (128 columns)
   int nkb;           // k-blocks of 32 to accumulate
+  int kb0;           // first k-block
+  int slot;          // split mode: accumulator-pair slot this item writes
+};
+
+struct SplitUnit {   // one (segment, row tile, column tile) whose chunks are reduced together
+  int seg;
+  int m;
+  int c;
+  int slot0;         // first slot; the unit's chunks are slot0 .. slot0 + nchunk - 1
+  int nchunk;
+  int pad;
 };
 
 struct TcSegDev {    // per-segment launch data (device-resident)
@@ -43,9 +54,23 @@ struct TcSegDev {    // per-segment launch data (device-resident)
   double logdet;
   double* logL;
   double* chi2;
-  int64_t pad[2];
+  float2* wpart;     // split mode: accumulator pairs [slot][128 columns][BN rows]
+  int64_t pad;
 };
 static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+
+struct SplitPlan {           // device work lists for one batch width (64-row tiles, split mode)
+  int64_t K = -1;
+  int nsl = 0;
+  int S = 0;
+  TcItem* items = nullptr;
+  int n_items = 0;
+  SplitUnit* units = nullptr;
+  int n_units = 0;
+  int n_slots = 0;
+  TcSegDev* segdev = nullptr;
+  uint64_t last_use = 0;
+};
 
 struct Scratch {
   int64_t capK = 0;          // columns the buffers hold
@@ -59,9 +84,18 @@ struct Scratch {
   int64_t segdev_K = -1;
   const float* segdev_R = nullptr;
   int64_t segdev_ldr = -1;
-  float* rsf = nullptr;         // streaming-path partial W [units][64][K] (float)
+  float* rsf = nullptr;         // unused
   int64_t rsf_bytes = 0;
+  float2* wpart = nullptr;      // split-mode accumulator pairs
+  int64_t wpart_slots = 0;
+  std::vector<SplitPlan> plans;
+  uint64_t use_clock = 0;
 };
+
+int split_chunk(int64_t nk, int64_t nkp);
+void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int S, std::vector<TcItem>& items,
+                        std::vector<SplitUnit>& units, int& n_slots);
+void sort_items(std::vector<TcItem>& items);
 
 }  // namespace td
 
@@ -125,7 +159,8 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
 
 // tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
-                          DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
+                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
+cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, cudaStream_t st);
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st);
 int tc_num_sms();

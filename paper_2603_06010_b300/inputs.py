@@ -227,7 +227,7 @@ def noise_residuals(n: int, fs: float, K: int, seed: int, mask: np.ndarray | Non
     rng = np.random.default_rng(seed)
     x = noise_draw(n, fs, rng, a=a, floor=floor, scale=scale, count=K)
     kept = kept_index(mask, n)
-    return x[:, kept].astype(np.float32)
+    return np.ascontiguousarray(x[:, kept], dtype=np.float32)
 
 
 # ----------------------------------------------------------------------------

@@ -1,6 +1,7 @@
 // C ABI of libtd: segment lifetime, factor, per-evaluation batches.
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstdio>
@@ -65,10 +66,12 @@ static td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint6
   return TD_OK;
 }
 
-// residual-slice map (A operand) and operator map (B operand, tiles of bn rows) of one segment
-td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out) {
+// residual-slice map (A operand: a box of a_rows residual columns) and operator
+// map (B operand, tiles of bn rows) of one segment
+td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out, int a_rows = TC_COLS) {
+  out->a_rows = a_rows;
   td_status st = encode_3d(&out->mapA, s->scr.rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES,
-                           (uint64_t)s->nkp8 * 2, (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, TC_COLS,
+                           (uint64_t)s->nkp8 * 2, (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, (uint32_t)a_rows,
                            (uint32_t)nsl);
   if (st != TD_OK) return st;
   return encode_3d(&out->mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
@@ -191,7 +194,8 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, cudaStream_t 
   p.n_slots = n_slots;
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
-  if ((r = encode_seg_maps(s, K, nsl, 64, &seg)) != TD_OK) return r;
+  const int a_rows = (int)std::min<int64_t>(TC_COLS, round_up(K, 8));
+  if ((r = encode_seg_maps(s, K, nsl, 64, &seg, a_rows)) != TD_OK) return r;
   seg.partials = sc.partials;
   seg.wpart = sc.wpart;
   seg.nk = (int)s->nk;

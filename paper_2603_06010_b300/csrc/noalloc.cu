@@ -119,6 +119,7 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
                      (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, 64, 3)) != TD_OK)
     return r;
   seg.partials = partials;
+  seg.a_rows = TC_COLS;
   seg.nk = (int)s->nk;
   seg.K = (int)K;
   seg.ldp = (int)K;

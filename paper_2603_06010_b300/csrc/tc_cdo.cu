@@ -144,6 +144,15 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     tmem_alloc(tmem_slot, C::TMEM_COLS);
     tmem_relinquish();
   }
+  // residual rows the TMA box does not cover must read as zero in every stage
+  // (a narrow box is only used when every item of the launch has it)
+  if ((MODE != 0 ? segs[0].a_rows : single.seg.a_rows) < BM) {
+    for (int s = 0; s < STAGES; ++s) {
+      uint4* a = reinterpret_cast<uint4*>(smem + s * STAGE);
+      for (int i = threadIdx.x; i < A_STAGE / 16; i += blockDim.x) a[i] = make_uint4(0, 0, 0, 0);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // visible to the tensor core
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -181,7 +190,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           }
           uint8_t* sa = smem + stage * STAGE;
           uint8_t* sb = sa + A_STAGE;
-          mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (A_SLICE + B_SLICE)));
+          mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (sd->a_rows * BK * 2 + B_SLICE)));
           tma_load_3d(sa, &sd->mapA, &full[stage], kb * BK, it.c * BM, 0);
           tma_load_3d(sb, &sd->mapB, &full[stage], 0, yoff, (blk0 + kb) * OP_SLICES);
           issued_mask |= 1u << stage;
@@ -400,33 +409,61 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
 // (the hi*hi sums are exact, their sum stays exact well past these lengths);
 // then the chi2 share of the 64 rows in double-float, as one FP64 partial in
 // the same per-64-row-group layout the direct epilogue writes.
+// Thread (row, column group): rows are contiguous in the slot layout, so a
+// warp's loads are coalesced; the 64-row sum is a fixed shuffle tree.
 __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restrict__ units,
                                                        const TcSegDev* __restrict__ segs) {
-  __shared__ float red_hi[128], red_lo[128];
+  __shared__ float red_hi[4][2][32], red_lo[4][2][32];
   const SplitUnit u = units[blockIdx.x];
   const TcSegDev& sd = segs[u.seg];
-  const int cl = threadIdx.x & 127, half = threadIdx.x >> 7;
-  const int col = u.c * 128 + cl;
-  float hi = 0.f, lo = 0.f;
-  if (col < sd.K) {
-    for (int r = half * 32; r < half * 32 + 32; ++r) {
-      float wh = 0.f, wl = 0.f;
-      for (int ch = 0; ch < u.nchunk; ++ch) {
-        const float2 v = sd.wpart[((int64_t)(u.slot0 + ch) * 128 + cl) * 64 + r];
-        ff_add(v.x, wh, wl);
-        ff_add(v.y, wh, wl);
+  const int row = threadIdx.x & 63, grp = threadIdx.x >> 6;   // 4 column groups of 2 warps
+  const int wig = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
+  const int ncol = min(128, sd.K - u.c * 128);
+  for (int cb = 0; cb < ncol; cb += 4 * 32) {
+    // each group handles up to 32 columns of this block: cl = cb + grp*32 + i
+    float ch_hi[32], ch_lo[32];
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      const int cl = cb + grp * 32 + i;
+      float hi = 0.f, lo = 0.f;
+      if (cl < ncol) {
+        float wh = 0.f, wl = 0.f;
+        for (int ch = 0; ch < u.nchunk; ++ch) {
+          const float2 v = sd.wpart[((int64_t)(u.slot0 + ch) * 128 + cl) * 64 + row];
+          ff_add(v.x, wh, wl);
+          ff_add(v.y, wh, wl);
+        }
+        ff_add_square2(wh, wl, hi, lo);
       }
-      ff_add_square2(wh, wl, hi, lo);
+      // sum over the 32 rows of this warp (fixed tree), compensated
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+        ff_add(oh, hi, lo);
+        lo += ol;
+      }
+      ch_hi[i] = hi;
+      ch_lo[i] = lo;
     }
-  }
-  if (half == 1) {
-    red_hi[cl] = hi;
-    red_lo[cl] = lo;
-  }
-  __syncthreads();
-  if (half == 0 && col < sd.K) {
-    const double s = ((double)hi + (double)lo) + ((double)red_hi[cl] + (double)red_lo[cl]);
-    sd.partials[(int64_t)u.m * sd.ldp + col] = s;
+    if (lane == 0) {
+#pragma unroll 4
+      for (int i = 0; i < 32; ++i) {
+        red_hi[grp][wig][i] = ch_hi[i];
+        red_lo[grp][wig][i] = ch_lo[i];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 128) {
+      const int g = threadIdx.x >> 5, i = threadIdx.x & 31;
+      const int cl = cb + g * 32 + i;
+      if (cl < ncol) {
+        const double s = ((double)red_hi[g][0][i] + (double)red_lo[g][0][i]) +
+                         ((double)red_hi[g][1][i] + (double)red_lo[g][1][i]);
+        sd.partials[(int64_t)u.m * sd.ldp + u.c * 128 + cl] = s;
+      }
+    }
+    __syncthreads();
   }
 }
 

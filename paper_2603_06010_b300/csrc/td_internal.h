@@ -55,7 +55,8 @@ struct TcSegDev {    // per-segment launch data (device-resident)
   double* logL;
   double* chi2;
   float2* wpart;     // split mode: accumulator pairs [slot][128 columns][BN rows]
-  int64_t pad;
+  int a_rows;        // rows of the residual box (<= 128); the rest of each A stage stays zero
+  int pad;
 };
 static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
 

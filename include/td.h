@@ -68,11 +68,13 @@ typedef enum {
 
 typedef enum {
   TD_PATH_AUTO = 0,
-  TD_PATH_TENSOR = 1,  /* tcgen05 split-product GEMM, 256-row operator tiles (large K) */
-  TD_PATH_STREAM = 2,  /* the same kernel with 64-row operator tiles: 4x the work items,
-                          the operator streamed from HBM by a deep TMA ring (small K);
-                          identical per-element arithmetic, so identical results */
-  TD_PATH_FP64 = 3     /* plain FP64 forward substitution */
+  TD_PATH_TENSOR = 1,   /* tcgen05 split-product GEMM, 256-row operator tiles over whole
+                           rows, chi2 in the epilogue (large K) */
+  TD_PATH_STREAM = 2,   /* the same kernel with long rows cut into balanced k-chunks
+                           (more work items; the operator streams from HBM), chunk
+                           results added in double-float by a reduce kernel (small K) */
+  TD_PATH_FP64 = 3,     /* plain FP64 forward substitution */
+  TD_PATH_STREAM64 = 4  /* as TD_PATH_STREAM with 64-row operator tiles */
 } td_path;
 
 typedef struct {

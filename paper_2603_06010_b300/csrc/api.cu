@@ -72,20 +72,26 @@ td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* o
   out->a_rows = a_rows;
   td_status st = encode_3d(&out->mapA, s->scr.rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES,
                            (uint64_t)s->nkp8 * 2, (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, (uint32_t)a_rows,
-                           (uint32_t)nsl);
+                           1);
   if (st != TD_OK) return st;
   return encode_3d(&out->mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
                    (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, (uint32_t)bn, (uint32_t)nsl);
 }
 
-// operator row-tile height for a batch: 256-row tiles while they give at
-// least two waves of work items, else 64-row tiles (4x the items, the same
-// per-element arithmetic); td_options.path can force either.
-static int choose_bn(const td_segment* s, int64_t K, int path) {
-  if (path == TD_PATH_TENSOR) return 256;
-  if (path == TD_PATH_STREAM) return 64;
+// Tile shape and split for a batch: 256-row tiles over whole rows while they
+// give at least two waves of work items; otherwise rows are split into
+// balanced chunks (256-row tiles), and td_options.path can force any shape.
+struct Shape {
+  int bn;
+  bool split;
+};
+static Shape choose_shape(const td_segment* s, int64_t K, int path) {
+  if (path == TD_PATH_TENSOR) return {256, false};
+  if (path == TD_PATH_STREAM) return {256, true};
+  if (path == TD_PATH_STREAM64) return {64, true};
   const int64_t items256 = (s->nkp / OP_ROWS) * ceil_div(K, TC_COLS);
-  return items256 >= 2 * (int64_t)tc_num_sms() ? 256 : 64;
+  if (items256 >= 2 * (int64_t)tc_num_sms()) return {256, false};
+  return {256, true};
 }
 
 template <class T>
@@ -151,29 +157,30 @@ static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaSt
 }
 
 // device work lists for a 64-row-tile batch of K columns (cached per K)
-static td_status get_split_plan(td_segment* s, int64_t K, int nsl, cudaStream_t st, SplitPlan** out) {
+static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaStream_t st, SplitPlan** out) {
   Scratch& sc = s->scr;
   ++sc.use_clock;
   for (SplitPlan& p : sc.plans)
-    if (p.K == K && p.nsl == nsl) {
+    if (p.K == K && p.nsl == nsl && p.bn == bn) {
       p.last_use = sc.use_clock;
       *out = &p;
       return TD_OK;
     }
-  const int S = split_chunk(s->nk, s->nkp);
+  const int S = split_chunk(s->nk, s->nkp, bn);
   std::vector<TcItem> items;
   std::vector<SplitUnit> units;
   int n_slots = 0;
-  plan_split_segment(0, s->nk, s->nkp, K, S, items, units, n_slots);
+  plan_split_segment(0, s->nk, s->nkp, K, bn, S, items, units, n_slots);
+  const int64_t slot_elems = (int64_t)TC_COLS * bn;   // float2 per slot
   sort_items(items);
   td_status r;
-  if (n_slots > sc.wpart_slots) {
+  if (n_slots * slot_elems > sc.wpart_slots) {   // wpart_slots counts float2 elements
     cudaStreamSynchronize(st);
     free_plans(sc);
     dev_free(sc.wpart);
     sc.wpart_slots = 0;
-    if ((r = dev_alloc(&sc.wpart, (size_t)n_slots * TC_COLS * 64, "split accumulators")) != TD_OK) return r;
-    sc.wpart_slots = n_slots;
+    if ((r = dev_alloc(&sc.wpart, (size_t)(n_slots * slot_elems), "split accumulators")) != TD_OK) return r;
+    sc.wpart_slots = n_slots * slot_elems;
   }
   if (sc.plans.size() >= 8) {   // evict the least recently used plan
     size_t lru = 0;
@@ -188,6 +195,7 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, cudaStream_t 
   SplitPlan p;
   p.K = K;
   p.nsl = nsl;
+  p.bn = bn;
   p.S = S;
   p.n_items = (int)items.size();
   p.n_units = (int)units.size();
@@ -195,7 +203,7 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, cudaStream_t 
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
   const int a_rows = (int)std::min<int64_t>(TC_COLS, round_up(K, 8));
-  if ((r = encode_seg_maps(s, K, nsl, 64, &seg, a_rows)) != TD_OK) return r;
+  if ((r = encode_seg_maps(s, K, nsl, bn, &seg, a_rows)) != TD_OK) return r;
   seg.partials = sc.partials;
   seg.wpart = sc.wpart;
   seg.nk = (int)s->nk;
@@ -437,7 +445,8 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     return TD_OK;
   }
   const int nsl = nslices_for(o.precision);
-  const int bn = choose_bn(s, K, o.path);
+  const Shape shape = choose_shape(s, K, o.path);
+  const int bn = shape.bn;
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
@@ -451,13 +460,13 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   const int nc = (int)ceil_div(K, TC_COLS);
   const int nkb_max = (int)ceil_div(s->nk, OP_KB);
   const bool pm = s->prof && s->ev_used + 2 <= 8192;
-  if (bn == 64) {
+  if (shape.split) {
     SplitPlan* plan = nullptr;
-    if ((r = get_split_plan(s, K, nsl, st, &plan)) != TD_OK) return r;
+    if ((r = get_split_plan(s, K, nsl, bn, st, &plan)) != TD_OK) return r;
     if (pm) prof_mark(s, st, true);
-    TD_CUDA(launch_tc_cdo(plan->items, plan->n_items, plan->segdev, nsl, 64, true, s->status, o.wait_limit_ns,
+    TD_CUDA(launch_tc_cdo(plan->items, plan->n_items, plan->segdev, nsl, bn, true, s->status, o.wait_limit_ns,
                           st));
-    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, st));
+    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, bn, st));
     if (pm) prof_mark(s, st, false);
     TD_CUDA(launch_finalize(sc.partials, ldp, ngroups, K, s->logdet, s->nk, logL, chi2, st));
     s->prof_kernels += plan->n_units > 0 ? 4 : 3;

@@ -113,7 +113,7 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
   if ((r = na_encode(&seg.mapA, rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES, (uint64_t)s->nkp8 * 2,
-                     (uint64_t)K * s->nkp8 * 2, OP_KB, TC_COLS, 3)) != TD_OK)
+                     (uint64_t)K * s->nkp8 * 2, OP_KB, TC_COLS, 1)) != TD_OK)
     return r;
   if ((r = na_encode(&seg.mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
                      (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, 64, 3)) != TD_OK)

@@ -1,8 +1,7 @@
 // Work lists for the tensor-core kernel's explicit-list modes.
 //
-// Small batches use 64-row operator tiles; a row tile whose k-range is longer
-// than S k-blocks is cut into chunks of at most S, so no single work item
-// holds back the launch.  S depends only on N' (not on K), so the split of a
+// Small batches cut a row tile whose k-range is longer than S k-blocks into
+// chunks of at most S, so no single work item holds back the launch.  S depends only on N' (not on K), so the split of a
 // given column is the same in every batch.  Chunks of one row tile write
 // their accumulator pairs to consecutive slots; one SplitUnit per split tile
 // tells k_split_reduce which slots to add.
@@ -14,25 +13,27 @@
 
 namespace td {
 
-int split_chunk(int64_t nk, int64_t nkp) {
-  const int64_t nm = nkp / 64;
+int split_chunk(int64_t nk, int64_t nkp, int bn) {
+  const int64_t nm = nkp / bn;
+  const int64_t per = bn / OP_KB;
   const int64_t nkb_max = ceil_div(nk, OP_KB);
   int64_t total = 0;
-  for (int64_t m = 0; m < nm; ++m) total += std::min<int64_t>(2 * (m + 1), nkb_max);
+  for (int64_t m = 0; m < nm; ++m) total += std::min<int64_t>(per * (m + 1), nkb_max);
   int64_t S = ceil_div(total, 2 * (int64_t)tc_num_sms());
   if (S < 4) S = 4;
   return (int)S;
 }
 
-// append the items of one segment (64-row tiles, chunk S) to the lists
-void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int S, std::vector<TcItem>& items,
+// append the items of one segment (bn-row tiles, chunk S) to the lists
+void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
                         std::vector<SplitUnit>& units, int& n_slots) {
-  const int nm = (int)(nkp / 64);
+  const int nm = (int)(nkp / bn);
+  const int per = bn / OP_KB;
   const int nc = (int)ceil_div(K, TC_COLS);
   const int nkb_max = (int)ceil_div(nk, OP_KB);
   for (int c = 0; c < nc; ++c) {
     for (int m = 0; m < nm; ++m) {
-      const int nkb = std::min(2 * (m + 1), nkb_max);
+      const int nkb = std::min(per * (m + 1), nkb_max);
       const int nch = (nkb + S - 1) / S;
       if (nch <= 1) {
         items.push_back(TcItem{seg, m, c, nkb, 0, -1});

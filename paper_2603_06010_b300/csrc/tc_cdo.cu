@@ -191,7 +191,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           uint8_t* sa = smem + stage * STAGE;
           uint8_t* sb = sa + A_STAGE;
           mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (sd->a_rows * BK * 2 + B_SLICE)));
-          tma_load_3d(sa, &sd->mapA, &full[stage], kb * BK, it.c * BM, 0);
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl)   // one box per slice: each slice owns an 8 KB region
+            tma_load_3d(sa + sl * A_SLICE, &sd->mapA, &full[stage], kb * BK, it.c * BM, sl);
           tma_load_3d(sb, &sd->mapB, &full[stage], 0, yoff, (blk0 + kb) * OP_SLICES);
           issued_mask |= 1u << stage;
           issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
@@ -404,7 +406,7 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
   return dispatch<1>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st);
 }
 
-// Reduce the accumulator pairs of a split row tile (BN = 64 rows): for each
+// Reduce the accumulator pairs of a split row tile (one block per 64 rows): for each
 // row, w = sum over chunks of (hi*hi sum + correction sum), in double-float
 // (the hi*hi sums are exact, their sum stays exact well past these lengths);
 // then the chi2 share of the 64 rows in double-float, as one FP64 partial in
@@ -412,9 +414,10 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
 // Thread (row, column group): rows are contiguous in the slot layout, so a
 // warp's loads are coalesced; the 64-row sum is a fixed shuffle tree.
 __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restrict__ units,
-                                                       const TcSegDev* __restrict__ segs) {
+                                                       const TcSegDev* __restrict__ segs, int bn) {
   __shared__ float red_hi[4][2][32], red_lo[4][2][32];
   const SplitUnit u = units[blockIdx.x];
+  const int g64 = blockIdx.y;                   // 64-row group of the bn-row tile
   const TcSegDev& sd = segs[u.seg];
   const int row = threadIdx.x & 63, grp = threadIdx.x >> 6;   // 4 column groups of 2 warps
   const int wig = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
@@ -422,14 +425,15 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
   for (int cb = 0; cb < ncol; cb += 4 * 32) {
     // each group handles up to 32 columns of this block: cl = cb + grp*32 + i
     float ch_hi[32], ch_lo[32];
+    const int nmine = max(0, min(32, ncol - cb - grp * 32));   // valid columns of this group
 #pragma unroll 4
-    for (int i = 0; i < 32; ++i) {
+    for (int i = 0; i < nmine; ++i) {
       const int cl = cb + grp * 32 + i;
       float hi = 0.f, lo = 0.f;
       if (cl < ncol) {
         float wh = 0.f, wl = 0.f;
         for (int ch = 0; ch < u.nchunk; ++ch) {
-          const float2 v = sd.wpart[((int64_t)(u.slot0 + ch) * 128 + cl) * 64 + row];
+          const float2 v = sd.wpart[((int64_t)(u.slot0 + ch) * 128 + cl) * bn + g64 * 64 + row];
           ff_add(v.x, wh, wl);
           ff_add(v.y, wh, wl);
         }
@@ -448,7 +452,7 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
     }
     if (lane == 0) {
 #pragma unroll 4
-      for (int i = 0; i < 32; ++i) {
+      for (int i = 0; i < nmine; ++i) {
         red_hi[grp][wig][i] = ch_hi[i];
         red_lo[grp][wig][i] = ch_lo[i];
       }
@@ -460,36 +464,43 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
       if (cl < ncol) {
         const double s = ((double)red_hi[g][0][i] + (double)red_lo[g][0][i]) +
                          ((double)red_hi[g][1][i] + (double)red_lo[g][1][i]);
-        sd.partials[(int64_t)u.m * sd.ldp + u.c * 128 + cl] = s;
+        sd.partials[((int64_t)u.m * (bn / 64) + g64) * sd.ldp + u.c * 128 + cl] = s;
       }
     }
     __syncthreads();
   }
 }
 
-cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, cudaStream_t st) {
+cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn,
+                                cudaStream_t st) {
   if (n_units <= 0) return cudaSuccess;
-  k_split_reduce<<<n_units, 256, 0, st>>>(units, segs);
+  k_split_reduce<<<dim3(n_units, bn / 64), 256, 0, st>>>(units, segs, bn);
   return cudaGetLastError();
 }
 
-// chi2 and logL per column from the per-group partials (fixed order), for
-// every segment of a grouped launch (TcSegDev::nm = number of 64-row groups).
+// chi2 and logL per column from the per-group partials, for every segment of
+// a grouped launch (TcSegDev::nm = number of 64-row groups); same order as
+// k_finalize: one warp per column, strided sums, fixed shuffle tree.
 __global__ void k_tc_finalize(const TcSegDev* __restrict__ segs) {
   const TcSegDev& sd = segs[blockIdx.y];
-  for (int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; col < sd.K;
-       col += (int64_t)gridDim.x * blockDim.x) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t col = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); col < sd.K;
+       col += (int64_t)gridDim.x * (blockDim.x >> 5)) {
     double s = 0.0;
-    for (int m = 0; m < sd.nm; ++m) s += sd.partials[(int64_t)m * sd.ldp + col];
-    if (sd.chi2) sd.chi2[col] = s;
-    sd.logL[col] = -0.5 * s - 0.5 * sd.logdet - 0.5 * (double)sd.nk * 1.8378770664093454836;
+    for (int m = lane; m < sd.nm; m += 32) s += sd.partials[(int64_t)m * sd.ldp + col];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) {
+      if (sd.chi2) sd.chi2[col] = s;
+      sd.logL[col] = -0.5 * s - 0.5 * sd.logdet - 0.5 * (double)sd.nk * 1.8378770664093454836;
+    }
   }
 }
 
 cudaError_t launch_tc_finalize(const TcSegDev* segs, int nseg, int64_t maxK, cudaStream_t st) {
   if (nseg <= 0 || maxK <= 0) return cudaSuccess;
-  int gx = (int)ceil_div(maxK, 256);
-  if (gx > 8) gx = 8;
+  int gx = (int)ceil_div(maxK, 8);
+  if (gx > 64) gx = 64;
   k_tc_finalize<<<dim3(gx, nseg), 256, 0, st>>>(segs);
   return cudaGetLastError();
 }

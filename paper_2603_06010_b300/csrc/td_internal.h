@@ -60,9 +60,10 @@ struct TcSegDev {    // per-segment launch data (device-resident)
 };
 static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
 
-struct SplitPlan {           // device work lists for one batch width (64-row tiles, split mode)
+struct SplitPlan {           // device work lists for one batch width (split mode)
   int64_t K = -1;
   int nsl = 0;
+  int bn = 0;
   int S = 0;
   TcItem* items = nullptr;
   int n_items = 0;
@@ -93,8 +94,8 @@ struct Scratch {
   uint64_t use_clock = 0;
 };
 
-int split_chunk(int64_t nk, int64_t nkp);
-void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int S, std::vector<TcItem>& items,
+int split_chunk(int64_t nk, int64_t nkp, int bn);
+void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
                         std::vector<SplitUnit>& units, int& n_slots);
 void sort_items(std::vector<TcItem>& items);
 
@@ -161,7 +162,7 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
 // tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
                           bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
-cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, cudaStream_t st);
+cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn, cudaStream_t st);
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st);
 int tc_num_sms();

@@ -109,23 +109,29 @@ cudaError_t launch_trsm_f64_row(const double* L, int64_t ld, const double* dinv,
   return cudaGetLastError();
 }
 
-// chi2_k = sum over row blocks of the partials (fixed order), then
+// chi2_k = sum over row groups of the partials, then
 // logL_k = -chi2_k/2 - logdet/2 - (N'/2) log 2 pi   (Eq. eqn:lik with the
-// constant written out).
+// constant written out).  One warp per column: lane l adds groups l, l+32, ...
+// in order, then a fixed shuffle tree -- the same order for every batch.
 __global__ void k_finalize(const double* __restrict__ partials, int64_t ldp, int nparts, int64_t K,
                            double logdet, int64_t nk, double* __restrict__ logL, double* __restrict__ chi2) {
-  const int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t col = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col >= K) return;
   double s = 0.0;
-  for (int p = 0; p < nparts; ++p) s += partials[(int64_t)p * ldp + col];
-  if (chi2) chi2[col] = s;
-  logL[col] = -0.5 * s - 0.5 * logdet - 0.5 * (double)nk * LOG2PI;
+  for (int p = lane; p < nparts; p += 32) s += partials[(int64_t)p * ldp + col];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) {
+    if (chi2) chi2[col] = s;
+    logL[col] = -0.5 * s - 0.5 * logdet - 0.5 * (double)nk * LOG2PI;
+  }
 }
 
 cudaError_t launch_finalize(const double* partials, int64_t ldp, int nparts, int64_t K, double logdet,
                             int64_t nk, double* logL, double* chi2, cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  k_finalize<<<(unsigned)ceil_div(K, 256), 256, 0, st>>>(partials, ldp, nparts, K, logdet, nk, logL, chi2);
+  k_finalize<<<(unsigned)ceil_div(K, 8), 256, 0, st>>>(partials, ldp, nparts, K, logdet, nk, logL, chi2);
   return cudaGetLastError();
 }
 

@@ -243,7 +243,7 @@ def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
     R = torch_cuda.from_numpy(inputs.noise_residuals(n, 2048.0, K, 31, mask=mask)).cuda()
     out = {}
-    for path in (td.TD_PATH_TENSOR, td.TD_PATH_STREAM):
+    for path in (td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64):
         ll, chi = seg.loglike(R, td.options(path=path), with_chi2=True)
         torch_cuda.cuda.synchronize()
         seg.check()
@@ -253,5 +253,7 @@ def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     exp_ll = oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept)
     for path, (ll, chi) in out.items():
         _compare("bf16x6", ll, chi, exp_ll, exp_chi, f"path {path}")
-    a, b = out[td.TD_PATH_TENSOR][1], out[td.TD_PATH_STREAM][1]
-    assert np.max(np.abs(a - b) / b) <= 1e-7
+    a = out[td.TD_PATH_TENSOR][1]
+    for path in (td.TD_PATH_STREAM, td.TD_PATH_STREAM64):
+        b = out[path][1]
+        assert np.max(np.abs(a - b) / b) <= 1e-7

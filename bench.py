@@ -280,7 +280,10 @@ def main():
         for Ks in (1, 8, 64):
             Rs = R[:Ks].contiguous()
             ls = torch.empty(Ks, dtype=torch.float64, device="cuda")
-            for pname, path in (("stream256", td.TD_PATH_STREAM), ("stream64", td.TD_PATH_STREAM64)):
+            cand = [("stream256", td.TD_PATH_STREAM), ("stream64", td.TD_PATH_STREAM64)]
+            if Ks <= 32:
+                cand = [("smallk", td.TD_PATH_SMALLK)] + cand
+            for pname, path in cand:
                 o2 = td.options(precision=prec, path=path)
                 for _ in range(3):
                     seg.loglike_into(Rs, ls, o2)

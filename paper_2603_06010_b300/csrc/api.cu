@@ -89,6 +89,7 @@ static Shape choose_shape(const td_segment* s, int64_t K, int path) {
   if (path == TD_PATH_TENSOR) return {256, false};
   if (path == TD_PATH_STREAM) return {256, true};
   if (path == TD_PATH_STREAM64) return {64, true};
+  if (path == TD_PATH_SMALLK || (path == TD_PATH_AUTO && K <= 32)) return {0, true};
   const int64_t items256 = (s->nkp / OP_ROWS) * ceil_div(K, TC_COLS);
   if (items256 >= 2 * (int64_t)tc_num_sms()) return {256, false};
   return {256, true};
@@ -157,11 +158,15 @@ static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaSt
 }
 
 // device work lists for a 64-row-tile batch of K columns (cached per K)
-static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaStream_t st, SplitPlan** out) {
+// nc > 0: plan for the small-batch kernel (128-row operator tiles as the MMA
+// M dimension, nc residual columns per tile, chi2 partials per 32 rows).
+static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaStream_t st, SplitPlan** out,
+                                int nc = 0) {
   Scratch& sc = s->scr;
   ++sc.use_clock;
+  const int key_bn = nc > 0 ? -nc : bn;
   for (SplitPlan& p : sc.plans)
-    if (p.K == K && p.nsl == nsl && p.bn == bn) {
+    if (p.K == K && p.nsl == nsl && p.bn == key_bn) {
       p.last_use = sc.use_clock;
       *out = &p;
       return TD_OK;
@@ -195,21 +200,21 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   SplitPlan p;
   p.K = K;
   p.nsl = nsl;
-  p.bn = bn;
+  p.bn = key_bn;
   p.S = S;
   p.n_items = (int)items.size();
   p.n_units = (int)units.size();
   p.n_slots = n_slots;
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
-  const int a_rows = (int)std::min<int64_t>(TC_COLS, round_up(K, 8));
+  const int a_rows = nc > 0 ? nc : (int)std::min<int64_t>(TC_COLS, round_up(K, 8));
   if ((r = encode_seg_maps(s, K, nsl, bn, &seg, a_rows)) != TD_OK) return r;
   seg.partials = sc.partials;
   seg.wpart = sc.wpart;
   seg.nk = (int)s->nk;
   seg.K = (int)K;
-  seg.ldp = (int)sc.capK;
-  seg.nm = (int)(s->nkp / 64);
+  seg.ldp = nc > 0 ? (int)(sc.capK / 2) : (int)sc.capK;     // small: the buffer as [N'p/32][capK/2]
+  seg.nm = nc > 0 ? (int)(s->nkp / 32) : (int)(s->nkp / 64);
   seg.logdet = s->logdet;
   if ((r = dev_alloc(&p.items, items.size(), "work items")) != TD_OK ||
       (r = dev_alloc(&p.units, units.size(), "split units")) != TD_OK ||
@@ -460,6 +465,19 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   const int nc = (int)ceil_div(K, TC_COLS);
   const int nkb_max = (int)ceil_div(s->nk, OP_KB);
   const bool pm = s->prof && s->ev_used + 2 <= 8192;
+  if (bn == 0) {   // small batch: operator rows as the MMA M dimension
+    if (K > 32) return fail(TD_ERR_UNSUPPORTED, "the small-batch path takes K <= 32");
+    const int ncs = K <= 16 ? 16 : 32;
+    SplitPlan* plan = nullptr;
+    if ((r = get_split_plan(s, K, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
+    if (pm) prof_mark(s, st, true);
+    TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, st));
+    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, 128, st, 32));
+    if (pm) prof_mark(s, st, false);
+    TD_CUDA(launch_finalize(sc.partials, sc.capK / 2, (int)(s->nkp / 32), K, s->logdet, s->nk, logL, chi2, st));
+    s->prof_kernels += plan->n_units > 0 ? 4 : 3;
+    return TD_OK;
+  }
   if (shape.split) {
     SplitPlan* plan = nullptr;
     if ((r = get_split_plan(s, K, nsl, bn, st, &plan)) != TD_OK) return r;

@@ -414,7 +414,7 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
 // Thread (row, column group): rows are contiguous in the slot layout, so a
 // warp's loads are coalesced; the 64-row sum is a fixed shuffle tree.
 __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restrict__ units,
-                                                       const TcSegDev* __restrict__ segs, int bn) {
+                                                       const TcSegDev* __restrict__ segs, int bn, int part_rows) {
   __shared__ float red_hi[4][2][32], red_lo[4][2][32];
   const SplitUnit u = units[blockIdx.x];
   const int g64 = blockIdx.y;                   // 64-row group of the bn-row tile
@@ -450,6 +450,16 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
       ch_hi[i] = hi;
       ch_lo[i] = lo;
     }
+    if (part_rows == 32) {   // one partial per 32-row warp group, no combine
+      if (lane == 0) {
+        for (int i = 0; i < nmine; ++i) {
+          const int cl = cb + grp * 32 + i;
+          sd.partials[(((int64_t)u.m * (bn / 64) + g64) * 2 + wig) * sd.ldp + u.c * 128 + cl] =
+              (double)ch_hi[i] + (double)ch_lo[i];
+        }
+      }
+      continue;
+    }
     if (lane == 0) {
 #pragma unroll 4
       for (int i = 0; i < nmine; ++i) {
@@ -472,9 +482,9 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
 }
 
 cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn,
-                                cudaStream_t st) {
+                                cudaStream_t st, int part_rows) {
   if (n_units <= 0) return cudaSuccess;
-  k_split_reduce<<<dim3(n_units, bn / 64), 256, 0, st>>>(units, segs, bn);
+  k_split_reduce<<<dim3(n_units, bn / 64), 256, 0, st>>>(units, segs, bn, part_rows);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,311 @@
+// Tensor-core whitening for small batches (K <= 32 residual columns).
+//
+// Same method and slices as the main kernel (Sec. II.A, W = L^{-1}; Sec.
+// III.A, the cached-operator evaluation), with the operand roles swapped so
+// the MMA is not padded to 128 residual columns:
+//   MMA M = 128 rows of W           (A = L^{-1} slices, K-major),
+//   MMA N = NC residual columns, 16 or 32 (B = R^T slices, K-major),
+// so D[lane i][col n] = W[i][n].  Per 32-column k-block the operator tile is
+// 24 KB (three slices) and the MMA work is tiny, so the kernel streams the
+// packed operator from HBM once.  Long rows are cut into balanced k-chunks;
+// a chunk stores its accumulator pair (exact hi*hi sum, corrections) for
+// k_split_reduce, a whole row reduces chi2 here: w = hi + corrections in
+// double-float, exact squares, a fixed shuffle tree over the 32 rows of a
+// warp -> one FP64 partial per 32-row group (this path's partial layout).
+//
+// Warp roles as in the main kernel: warp 0 lane 0 TMA producer, warp 1
+// TMEM owner and MMA issuer, warps 2..5 epilogue.  Every wait is bounded.
+#include "td_internal.h"
+
+namespace td {
+namespace tsm {
+constexpr int BM = 128;                 // operator rows per tile (MMA M)
+constexpr int BK = OP_KB;               // 32
+constexpr int A_SLICE = BM * BK * 2;    // 8 KB of operator per slice
+constexpr int THREADS = 192;
+template <int NSL, int NC> struct Cfg {
+  static constexpr int B_SLICE = NC * BK * 2;
+  static constexpr int A_STAGE = NSL * A_SLICE;
+  static constexpr int STAGE = A_STAGE + NSL * B_SLICE;
+  static constexpr int STAGES = (216 * 1024) / STAGE > 8 ? 8 : (216 * 1024) / STAGE;
+  static constexpr int NBUF = 4;                         // accumulator pairs in TMEM
+  static constexpr uint32_t TMEM_COLS = (NBUF * 2 * NC <= 128) ? 128 : 256;
+  static constexpr int SMEM = STAGES * STAGE + 256 + 1024;   // stages + barriers + alignment
+};
+}  // namespace tsm
+
+template <int NSL> struct CorrS;
+template <> struct CorrS<4> {   // (operator, residual): (3,0) (2,1) (1,2) (0,3) (2,0) (1,1) (0,2) (1,0) (0,1)
+  static constexpr int N = 9;
+  __device__ static constexpr int op(int p) { return p < 4 ? 3 - p : (p < 7 ? 6 - p : 8 - p); }
+  __device__ static constexpr int rs(int p) { return p < 4 ? p : (p < 7 ? p - 4 : p - 7); }
+};
+template <> struct CorrS<3> {   // (2,0) (1,1) (0,2) (1,0) (0,1)
+  static constexpr int N = 5;
+  __device__ static constexpr int op(int p) { return p < 3 ? 2 - p : 4 - p; }
+  __device__ static constexpr int rs(int p) { return p < 3 ? p : p - 3; }
+};
+template <> struct CorrS<2> {
+  static constexpr int N = 2;
+  __device__ static constexpr int op(int p) { return 1 - p; }
+  __device__ static constexpr int rs(int p) { return p; }
+};
+
+// 32 lanes x 16 consecutive 32-bit columns
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int NSL, int NC>
+__global__ void __launch_bounds__(tsm::THREADS, 1)
+    k_tc_small(const TcItem* __restrict__ items, int n_items, const TcSegDev* __restrict__ segs,
+               DevStatus* status, uint64_t limit_ns) {
+  using namespace tsm;
+  using C = Cfg<NSL, NC>;
+  constexpr int A_STAGE = C::A_STAGE;
+  constexpr int B_SLICE = C::B_SLICE;
+  constexpr int STAGE = C::STAGE;
+  constexpr int STAGES = C::STAGES;
+  constexpr int NBUF = C::NBUF;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
+  uint64_t* empty = full + STAGES;
+  uint64_t* tfull = empty + STAGES;
+  uint64_t* tempty = tfull + NBUF;
+  uint64_t* fin = tempty + NBUF;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], 4);
+    }
+    mbar_init(fin, 1);
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == 1) {
+    tmem_alloc(tmem_slot, C::TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const int G = gridDim.x, b = blockIdx.x;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_mask = 0, issued_phase = 0;
+      for (int r = 0; (int64_t)r * G < n_items && !*abort_flag; ++r) {
+        const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+        if (idx >= n_items) continue;
+        const TcItem it = items[idx];
+        const TcSegDev* sd = &segs[it.seg];
+        const int row0 = it.m * BM;
+        const int M256 = row0 / OP_ROWS;
+        const int yoff = row0 - M256 * OP_ROWS;
+        const int blk0 = (OP_ROWS / BK) * M256 * (M256 + 1) / 2;
+        bool ok = true;
+        for (int kb = it.kb0; kb < it.kb0 + it.nkb; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, limit_ns)) {
+            set_status(status, ST_TIMEOUT, 40);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          uint8_t* sa = smem + stage * STAGE;    // operator slices (A)
+          uint8_t* sb = sa + A_STAGE;            // residual slices (B)
+          mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (A_SLICE + B_SLICE)));
+          tma_load_3d(sa, &sd->mapB, &full[stage], 0, yoff, (blk0 + kb) * OP_SLICES);
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl)
+            tma_load_3d(sb + sl * B_SLICE, &sd->mapA, &full[stage], kb * BK, it.c * NC, sl);
+          issued_mask |= 1u << stage;
+          issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+      }
+      for (int s = 0; s < STAGES; ++s)
+        if (issued_mask & (1u << s)) mbar_wait(&full[s], (issued_phase >> s) & 1u, limit_ns);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16_f32(BM, NC);
+      int stage = 0;
+      uint32_t phase = 0;
+      int tl = 0;
+      for (int r = 0; (int64_t)r * G < n_items && !*abort_flag; ++r) {
+        const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+        if (idx >= n_items) continue;
+        const TcItem it = items[idx];
+        const int buf = tl % NBUF;
+        const uint32_t use = (uint32_t)(tl / NBUF);
+        if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, limit_ns)) {
+          set_status(status, ST_TIMEOUT, 41);
+          *abort_flag = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_hi = tmem_base + (uint32_t)(buf * 2 * NC);
+        const uint32_t d_lo = d_hi + (uint32_t)NC;
+        bool ok = true;
+        for (int kb = it.kb0; kb < it.kb0 + it.nkb; ++kb) {
+          if (!mbar_wait(&full[stage], phase, limit_ns)) {
+            set_status(status, ST_TIMEOUT, 42);
+            *abort_flag = 1;
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t sa = smem_u32(smem + stage * STAGE);
+          const uint32_t sb = sa + A_STAGE;
+#pragma unroll
+          for (int kk = 0; kk < 2; ++kk) {
+            const uint32_t first = (kb > it.kb0 || kk > 0) ? 1u : 0u;
+            tc_mma_f16(d_hi, smem_desc_sw64(sa + kk * 32), smem_desc_sw64(sb + kk * 32), idesc, first);
+#pragma unroll
+            for (int p = 0; p < CorrS<NSL>::N; ++p) {
+              const uint64_t ad = smem_desc_sw64(sa + CorrS<NSL>::op(p) * A_SLICE + kk * 32);
+              const uint64_t bd = smem_desc_sw64(sb + CorrS<NSL>::rs(p) * B_SLICE + kk * 32);
+              tc_mma_f16(d_lo, ad, bd, idesc, (first | (p > 0 ? 1u : 0u)));
+            }
+          }
+          tc_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) break;
+        tc_commit(&tfull[buf]);
+        ++tl;
+      }
+      tc_commit(fin);
+      mbar_wait(fin, 0, limit_ns);
+    }
+  } else {
+    const int q = warp & 3;          // TMEM lane quarter = rows 32q .. 32q+31 of the tile
+    int tl = 0;
+    for (int r = 0; (int64_t)r * G < n_items && !*abort_flag; ++r) {
+      const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+      if (idx >= n_items) continue;
+      const TcItem it = items[idx];
+      const TcSegDev* sd = &segs[it.seg];
+      const int buf = tl % NBUF;
+      const uint32_t use = (uint32_t)(tl / NBUF);
+      if (!mbar_wait(&tfull[buf], use & 1u, limit_ns)) {
+        if (lane == 0) set_status(status, ST_TIMEOUT, 43);
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * NC);
+      float a0[NC], a1[NC];
+#pragma unroll
+      for (int h = 0; h < NC / 16; ++h) {
+        float t0[16], t1[16];
+        tmem_ld16(ta + (uint32_t)(h * 16), t0);
+        tmem_ld16(ta + (uint32_t)(NC + h * 16), t1);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          a0[h * 16 + i] = t0[i];
+          a1[h * 16 + i] = t1[i];
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[buf]);
+      const int row = it.m * BM + q * 32 + lane;
+      const int ncol = min(NC, sd->K - it.c * NC);
+      if (it.slot >= 0) {
+        // accumulator pair for k_split_reduce: [slot][128 columns][128 rows]
+        float2* dst = sd->wpart + (int64_t)it.slot * 128 * BM + q * 32 + lane;
+#pragma unroll
+        for (int n = 0; n < NC; ++n)
+          if (n < ncol) dst[(int64_t)n * BM] = make_float2(a0[n], a1[n]);
+      } else {
+        // chi2 of this warp's 32 rows per column: exact squares, fixed shuffle tree
+#pragma unroll
+        for (int n = 0; n < NC; ++n) {
+          float hi = 0.f, lo = 0.f;
+          ff_add_square2(a0[n], a1[n], hi, lo);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) {
+            const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+            const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+            ff_add(oh, hi, lo);
+            lo += ol;
+          }
+          if (lane == 0 && n < ncol)
+            sd->partials[((int64_t)it.m * 4 + q) * sd->ldp + it.c * NC + n] = (double)hi + (double)lo;
+        }
+      }
+      (void)row;
+      ++tl;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    tmem_dealloc(tmem_base, C::TMEM_COLS);
+  }
+}
+
+template <int NSL, int NC>
+static cudaError_t launch_small_impl(const TcItem* items, int n_items, const TcSegDev* segs, DevStatus* status,
+                                     int64_t lim, cudaStream_t st) {
+  using C = tsm::Cfg<NSL, NC>;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_small<NSL, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  if (n_items <= 0) return cudaSuccess;
+  int grid = tc_num_sms();
+  if (grid > n_items) grid = n_items;
+  k_tc_small<NSL, NC><<<grid, tsm::THREADS, C::SMEM, st>>>(items, n_items, segs, status, (uint64_t)lim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
+                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+  if (nc == 16) {
+    if (nslices == 3) return launch_small_impl<3, 16>(items, n_items, segs, status, wait_limit_ns, st);
+    if (nslices == 4) return launch_small_impl<4, 16>(items, n_items, segs, status, wait_limit_ns, st);
+    if (nslices == 2) return launch_small_impl<2, 16>(items, n_items, segs, status, wait_limit_ns, st);
+  } else if (nc == 32) {
+    if (nslices == 3) return launch_small_impl<3, 32>(items, n_items, segs, status, wait_limit_ns, st);
+    if (nslices == 4) return launch_small_impl<4, 32>(items, n_items, segs, status, wait_limit_ns, st);
+    if (nslices == 2) return launch_small_impl<2, 32>(items, n_items, segs, status, wait_limit_ns, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace td

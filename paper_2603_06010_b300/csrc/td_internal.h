@@ -162,7 +162,11 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
 // tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
                           bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
-cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn, cudaStream_t st);
+// part_rows: 64 (partials per 64-row group) or 32 (per 32-row group, the small-batch layout)
+cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn, cudaStream_t st,
+                                int part_rows = 64);
+cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
+                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st);
 int tc_num_sms();

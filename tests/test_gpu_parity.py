@@ -118,19 +118,33 @@ def test_white_noise_closed_form(torch_cuda, gpu_lib):
 
 
 def test_column_alone_equals_in_batch(torch_cuda, gpu_lib):
-    """A column's logL does not depend on the batch it is evaluated in (bitwise)."""
+    """With the tile shape fixed, a column's logL does not depend on the batch
+    it is evaluated in (bitwise); with automatic shapes (which depend on K) it
+    agrees within the bar."""
     from paper_2603_06010_b300 import td
     n = 1500
     mask = _mask(n, [(700, 800)])
     seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
     R = inputs.noise_residuals(n, 2048.0, 300, 23, mask=mask)
-    for prec in ("fp64", "bf16x6", "bf16x10"):
-        full, _ = _run(torch_cuda, td, seg, R, prec)
-        for k in (0, 1, 127, 128, 299):
-            alone, _ = _run(torch_cuda, td, seg, R[k:k + 1], prec)
-            assert alone[0] == full[k], (prec, k, alone[0], full[k])
-        part, _ = _run(torch_cuda, td, seg, R[100:229], prec)
-        assert np.array_equal(part, full[100:229]), prec
+    Rd = torch_cuda.from_numpy(R).cuda()
+
+    def run(Rsub, opt):
+        ll = seg.loglike(Rsub.contiguous(), opt)
+        torch_cuda.cuda.synchronize()
+        seg.check()
+        return ll.cpu().numpy()
+
+    for prec in (td.TD_PREC_FP64, td.TD_PREC_BF16X6, td.TD_PREC_BF16X10):
+        for path in ((td.TD_PATH_FP64,) if prec == td.TD_PREC_FP64 else
+                     (td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64)):
+            opt = td.options(precision=prec, path=path)
+            full = run(Rd, opt)
+            for k in (0, 1, 127, 128, 299):
+                assert run(Rd[k:k + 1], opt)[0] == full[k], (prec, path, k)
+            assert np.array_equal(run(Rd[100:229], opt), full[100:229]), (prec, path)
+    auto_full = run(Rd, td.options())
+    for k in (0, 5, 299):
+        assert abs(run(Rd[k:k + 1], td.options())[0] - auto_full[k]) <= 1e-3
 
 
 def test_repeatable_bits(torch_cuda, gpu_lib):
@@ -233,7 +247,7 @@ def test_full_cfg3_gapped_three_detectors(torch_cuda, gpu_lib, prec):
     assert np.max(np.abs(joint - np.array(gg["joint_logL"]))) <= 1e-3
 
 
-@pytest.mark.parametrize("K", [1, 5, 130, 300])
+@pytest.mark.parametrize("K", [1, 5, 17, 32, 130, 300])
 def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     """256-row direct tiles and 64-row split tiles agree within the bar (their
     correction sums round differently), and each matches the oracle."""
@@ -243,7 +257,8 @@ def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
     R = torch_cuda.from_numpy(inputs.noise_residuals(n, 2048.0, K, 31, mask=mask)).cuda()
     out = {}
-    for path in (td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64):
+    paths = [td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64] + ([td.TD_PATH_SMALLK] if K <= 32 else [])
+    for path in paths:
         ll, chi = seg.loglike(R, td.options(path=path), with_chi2=True)
         torch_cuda.cuda.synchronize()
         seg.check()
@@ -254,6 +269,6 @@ def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     for path, (ll, chi) in out.items():
         _compare("bf16x6", ll, chi, exp_ll, exp_chi, f"path {path}")
     a = out[td.TD_PATH_TENSOR][1]
-    for path in (td.TD_PATH_STREAM, td.TD_PATH_STREAM64):
+    for path in paths[1:]:
         b = out[path][1]
         assert np.max(np.abs(a - b) / b) <= 1e-7

@@ -453,15 +453,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   const Shape shape = choose_shape(s, K, o.path);
   const int bn = shape.bn;
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
-  TcSegDev seg;
-  memset(&seg, 0, sizeof seg);
-  if ((r = encode_seg_maps(s, K, nsl, bn, &seg)) != TD_OK) return r;
-  seg.partials = sc.partials;
-  seg.nk = (int)s->nk;
-  seg.K = (int)K;
-  seg.ldp = (int)ldp;
   const int ngroups = (int)(s->nkp / 64);
-  seg.nm = ngroups;
   const int nc = (int)ceil_div(K, TC_COLS);
   const int nkb_max = (int)ceil_div(s->nk, OP_KB);
   const bool pm = s->prof && s->ev_used + 2 <= 8192;
@@ -490,6 +482,14 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     s->prof_kernels += plan->n_units > 0 ? 4 : 3;
     return TD_OK;
   }
+  TcSegDev seg;   // whole rows: one segment, implicit item list
+  memset(&seg, 0, sizeof seg);
+  if ((r = encode_seg_maps(s, K, nsl, bn, &seg)) != TD_OK) return r;
+  seg.partials = sc.partials;
+  seg.nk = (int)s->nk;
+  seg.K = (int)K;
+  seg.ldp = (int)ldp;
+  seg.nm = ngroups;
   if (pm) prof_mark(s, st, true);
   TD_CUDA(launch_tc_single(seg, bn, nc, nkb_max, nsl, s->status, o.wait_limit_ns, st));
   if (pm) prof_mark(s, st, false);

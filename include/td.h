@@ -181,11 +181,37 @@ td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int64_t ldr, i
 td_status td_reserve(td_segment* s, int64_t K, const td_options* opt);
 
 /*
- * td_loglike_grouped -- many segments (uneven N', own K each) in one
- * persistent tensor-core launch (block-diagonal C over disjoint segments and
- * detectors, Sec. II.B items 1 and 3).  Arrays have nseg entries; R[i],
- * ldr[i], K[i], logL[i] as for td_loglike_batch on segs[i].  Asynchronous.
+ * Grouped evaluation -- many segments (uneven N', own K each) in one
+ * persistent tensor-core launch (the covariance of disjoint segments and
+ * detectors is block-diagonal, Sec. II.B items 1 and 3).  Arrays have nseg
+ * entries; R[i], ldr[i], K[i], logL[i] as for td_loglike_batch on segs[i];
+ * chi2 may be NULL (or an array of per-segment device pointers, each may be
+ * NULL).  All segments must be factored on the current device.
+ *
+ * td_group_create builds a plan: device work lists, segment descriptors and
+ * scratch (this call allocates and synchronises).  The plan keeps the
+ * pointers it was given: later launches read R[i] and write logL[i] there.
+ * td_group_launch enqueues the evaluation on `stream` (four kernels whatever
+ * nseg; no allocation; capturable in a CUDA graph).  td_group_graph_launch
+ * captures the launch into a CUDA graph on first use and replays it.
+ * td_group_tune times the candidate tile shapes and chunk sizes on the plan's
+ * own inputs, keeps the fastest, and records it for later plans of the same
+ * kind in this process (synchronises; writes logL).  td_group_check reports a
+ * device-side error (bounded-wait timeout).  td_group_shape reports the
+ * chosen operator tile height, chunk multiplier and work-item count.
  */
+typedef struct td_group td_group;
+td_status td_group_create(td_segment* const* segs, const float* const* R, const int64_t* ldr,
+                          const int64_t* K, double* const* logL, double* const* chi2, int nseg,
+                          const td_options* opt, void* stream, td_group** out);
+td_status td_group_launch(td_group* g, void* stream);
+td_status td_group_graph_launch(td_group* g, void* stream);
+td_status td_group_tune(td_group* g, void* stream, double* best_ms);
+td_status td_group_check(td_group* g, void* stream);
+int td_group_shape(const td_group* g, int* bn, int* s_factor, int* n_items);
+void td_group_destroy(td_group* g);
+
+/* One-shot grouped evaluation: create, launch, check, destroy (synchronises). */
 td_status td_loglike_grouped(td_segment* const* segs, const float* const* R,
                              const int64_t* ldr, const int64_t* K, double* const* logL,
                              int nseg, const td_options* opt, void* stream);

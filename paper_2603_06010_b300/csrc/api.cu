@@ -498,16 +498,6 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   return TD_OK;
 }
 
-td_status td_loglike_grouped(td_segment* const* segs, const float* const* R, const int64_t* ldr, const int64_t* K,
-                             double* const* logL, int nseg, const td_options* opt, void* stream) {
-  if (nseg < 0 || (nseg > 0 && (!segs || !R || !ldr || !K || !logL))) return fail(TD_ERR_INVALID, "bad arguments");
-  for (int i = 0; i < nseg; ++i) {
-    td_status r = td_loglike_batch(segs[i], R[i], ldr[i], K[i], logL[i], opt, nullptr, stream);
-    if (r != TD_OK) return r;
-  }
-  return TD_OK;
-}
-
 td_status td_check(td_segment* s, void* stream) {
   if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);

@@ -1,0 +1,461 @@
+// Grouped evaluation: many segments (uneven N', each its own K) in one
+// persistent tensor-core launch.  The joint covariance of disjoint segments
+// and detectors is block-diagonal (Sec. II.B items 1 and 3), so each
+// segment's whitening is independent and the work items of all segments share
+// one launch, sorted by work and dealt to the SMs in snake order.
+//
+// A td_group is a plan: it owns the device work lists, segment descriptors
+// and scratch, so td_group_launch only launches kernels (five per call,
+// whatever the number of segments) and can be captured in a CUDA graph;
+// td_group_graph_launch captures it once and replays the graph.  The
+// autotuner (td_group_tune) times the candidate tile shapes and chunk sizes
+// on the real inputs and keeps the fastest.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "td_internal.h"
+
+namespace td {
+td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out, int a_rows);
+
+static td_status group_alloc(void** p, size_t bytes, const char* what) {
+  *p = nullptr;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(TD_ERR_OOM, std::string("device allocation failed: ") + what);
+  }
+  return TD_OK;
+}
+
+struct RsJob {          // one segment's residual slicing for the grouped slicing kernel
+  const float* R;
+  int64_t ldr;
+  int64_t nk;
+  int64_t K;
+  int64_t nkp8;
+  int64_t capK;
+  __nv_bfloat16* rs;
+  int64_t col0;         // first global column of this segment
+};
+
+// per-column quantum and slices for every segment of the group (as k_r_slices)
+__global__ void __launch_bounds__(256) k_r_slices_grouped(const RsJob* __restrict__ jobs, int njobs,
+                                                           int64_t total_cols, int nslices) {
+  __shared__ float red[8];
+  for (int64_t gc = blockIdx.x; gc < total_cols; gc += gridDim.x) {
+    int lo = 0, hi = njobs - 1;   // last job with col0 <= gc
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (jobs[mid].col0 <= gc) lo = mid; else hi = mid - 1;
+    }
+    const RsJob& jb = jobs[lo];
+    const int64_t k = gc - jb.col0;
+    const float* col = jb.R + k * jb.ldr;
+    float mx = 0.f;
+    for (int64_t j = threadIdx.x; j < jb.nk; j += blockDim.x) mx = fmaxf(mx, fabsf(col[j]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+    __syncthreads();
+    float p = 1.f;
+    if (mx > 0.f) {
+      p = exp2f(ceilf(log2f(mx / 255.f)));
+      if (mx / p > 255.f) p *= 2.f;
+    }
+    const int64_t ss = jb.capK * jb.nkp8;
+    __nv_bfloat16* dst = jb.rs + k * jb.nkp8;
+    for (int64_t j = threadIdx.x; j < jb.nk; j += blockDim.x) {
+      const float x = col[j];
+      const float h = p * rintf(x / p);
+      __nv_bfloat16 a, b, c;
+      split3_f32(x - h, a, b, c);
+      dst[j] = __float2bfloat16_rn(h);
+      dst[j + ss] = a;
+      if (nslices > 2) dst[j + 2 * ss] = b;
+      if (nslices > 3) dst[j + 3 * ss] = c;
+    }
+  }
+}
+
+}  // namespace td
+
+using namespace td;
+
+struct td_group {
+  int device = 0;
+  int nseg = 0;
+  int nsl = 3;
+  int bn = 256;
+  int s_factor = 1;           // chunk size multiplier chosen by the autotuner
+  int64_t wait_limit_ns = 1000000000LL;
+  int64_t total_cols = 0;
+  int64_t maxK = 0;
+  std::vector<td_segment*> segs;
+  std::vector<TcSegDev> host_seg;
+  std::vector<RsJob> host_jobs;
+  // device
+  TcSegDev* d_seg = nullptr;
+  RsJob* d_jobs = nullptr;
+  TcItem* d_items = nullptr;
+  SplitUnit* d_units = nullptr;
+  int n_items = 0, n_units = 0;
+  __nv_bfloat16* rs = nullptr;
+  double* partials = nullptr;
+  float2* wpart = nullptr;
+  DevStatus* status = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  cudaStream_t graph_stream = nullptr;
+};
+
+namespace td {
+
+static void group_free_lists(td_group* g) {
+  if (g->d_items) cudaFree(g->d_items);
+  if (g->d_units) cudaFree(g->d_units);
+  if (g->wpart) cudaFree(g->wpart);
+  g->d_items = nullptr;
+  g->d_units = nullptr;
+  g->wpart = nullptr;
+  g->n_items = g->n_units = 0;
+  if (g->graph) {
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
+}
+
+// build work lists and maps for a tile height and chunk multiplier
+static td_status group_build(td_group* g, int bn, int s_factor) {
+  group_free_lists(g);
+  g->bn = bn;
+  g->s_factor = s_factor;
+  // work per residual-column tile summed over segments; chunk so that the
+  // longest item is about 1/(2 s_factor) of an SM's even share
+  int64_t tiles_work = 0;
+  for (int i = 0; i < g->nseg; ++i) {
+    td_segment* s = g->segs[(size_t)i];
+    const int64_t nm = s->nkp / bn, per = bn / OP_KB, nkb_max = ceil_div(s->nk, OP_KB);
+    int64_t w = 0;
+    for (int64_t m = 0; m < nm; ++m) w += std::min<int64_t>(per * (m + 1), nkb_max);
+    tiles_work += w * ceil_div(g->host_seg[(size_t)i].K, TC_COLS);
+  }
+  int S = (int)ceil_div(tiles_work, 2LL * s_factor * tc_num_sms());
+  if (S < 4) S = 4;
+  std::vector<TcItem> items;
+  std::vector<SplitUnit> units;
+  int n_slots = 0;
+  for (int i = 0; i < g->nseg; ++i) {
+    td_segment* s = g->segs[(size_t)i];
+    plan_split_segment(i, s->nk, s->nkp, g->host_seg[(size_t)i].K, bn, S, items, units, n_slots);
+  }
+  sort_items(items);
+  td_status r;
+  const size_t wbytes = (size_t)n_slots * TC_COLS * bn * sizeof(float2);
+  if ((r = group_alloc((void**)&g->d_items, std::max<size_t>(1, items.size()) * sizeof(TcItem), "items")) != TD_OK ||
+      (r = group_alloc((void**)&g->d_units, std::max<size_t>(1, units.size()) * sizeof(SplitUnit), "units")) !=
+          TD_OK ||
+      (r = group_alloc((void**)&g->wpart, std::max<size_t>(8, wbytes), "split accumulators")) != TD_OK)
+    return r;
+  for (int i = 0; i < g->nseg; ++i) {
+    TcSegDev& sd = g->host_seg[(size_t)i];
+    td_segment* s = g->segs[(size_t)i];
+    // residual map over this segment's slice region of the group buffer
+    const int64_t cap = sd.ldp;
+    td_segment tmp_view;   // only the fields encode_seg_maps reads
+    tmp_view.nk = s->nk;
+    tmp_view.nkp8 = s->nkp8;
+    tmp_view.op = s->op;
+    tmp_view.op_blocks = s->op_blocks;
+    tmp_view.scr.rs = g->host_jobs[(size_t)i].rs;
+    tmp_view.scr.capK = cap;
+    TcSegDev enc;
+    memset(&enc, 0, sizeof enc);
+    if ((r = encode_seg_maps(&tmp_view, sd.K, g->nsl, bn, &enc, TC_COLS)) != TD_OK) {
+      tmp_view.scr.rs = nullptr;
+      tmp_view.op = nullptr;
+      return r;
+    }
+    tmp_view.scr.rs = nullptr;   // not owned
+    tmp_view.op = nullptr;
+    sd.mapA = enc.mapA;
+    sd.mapB = enc.mapB;
+    sd.a_rows = TC_COLS;
+    sd.wpart = g->wpart;
+  }
+  if (cudaMemcpy(g->d_seg, g->host_seg.data(), g->host_seg.size() * sizeof(TcSegDev), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      (!items.empty() &&
+       cudaMemcpy(g->d_items, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (!units.empty() &&
+       cudaMemcpy(g->d_units, units.data(), units.size() * sizeof(SplitUnit), cudaMemcpyHostToDevice) != cudaSuccess))
+    return fail(TD_ERR_CUDA, "upload of group work lists failed");
+  g->n_items = (int)items.size();
+  g->n_units = (int)units.size();
+  return TD_OK;
+}
+
+static td_status group_launch_impl(td_group* g, cudaStream_t st) {
+  int gx = (int)std::min<int64_t>(g->total_cols, 8192);
+  if (gx > 0) {
+    k_r_slices_grouped<<<gx, 256, 0, st>>>(g->d_jobs, g->nseg, g->total_cols, g->nsl);
+    TD_CUDA(cudaGetLastError());
+  }
+  TD_CUDA(launch_tc_cdo(g->d_items, g->n_items, g->d_seg, g->nsl, g->bn, true, g->status, g->wait_limit_ns, st));
+  TD_CUDA(launch_split_reduce(g->d_units, g->n_units, g->d_seg, g->bn, st));
+  TD_CUDA(launch_tc_finalize(g->d_seg, g->nseg, g->maxK, st));
+  return TD_OK;
+}
+
+// process-wide autotuner decisions: signature -> (bn, s_factor)
+struct TuneEntry {
+  std::string key;
+  int bn;
+  int s_factor;
+  double ms;
+};
+static std::mutex g_tune_mu;
+static std::vector<TuneEntry> g_tune;
+
+static std::string group_signature(const td_group* g) {
+  // device name + bucketed shape of the work: log2 of total N'^2 K and of the segment count
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, g->device);
+  double work = 0.0;
+  for (int i = 0; i < g->nseg; ++i) {
+    const double n = (double)g->segs[(size_t)i]->nk;
+    work += n * n * (double)g->host_seg[(size_t)i].K;
+  }
+  char buf[256];
+  snprintf(buf, sizeof buf, "%s|nsl%d|w%d|s%d", prop.name, g->nsl, (int)std::log2(std::max(1.0, work)),
+           (int)std::log2((double)std::max(1, g->nseg)));
+  return buf;
+}
+
+}  // namespace td
+
+extern "C" {
+
+td_status td_group_create(td_segment* const* segs, const float* const* R, const int64_t* ldr, const int64_t* K,
+                          double* const* logL, double* const* chi2, int nseg, const td_options* opt, void* stream,
+                          td_group** out) {
+  if (!out) return fail(TD_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (nseg <= 0 || !segs || !R || !ldr || !K || !logL) return fail(TD_ERR_INVALID, "bad arguments");
+  td_options o;
+  td_options_default(&o);
+  if (opt) o = *opt;
+  if (o.precision == TD_PREC_FP64) return fail(TD_ERR_UNSUPPORTED, "grouped launches use the tensor-core path");
+  td_group* g = new td_group();
+  cudaGetDevice(&g->device);
+  g->nseg = nseg;
+  g->nsl = o.precision == TD_PREC_BF16X3 ? 2 : (o.precision == TD_PREC_BF16X10 ? 4 : 3);
+  g->wait_limit_ns = o.wait_limit_ns > 0 ? o.wait_limit_ns : 1000000000LL;
+  int64_t rs_elems = 0, part_elems = 0;
+  for (int i = 0; i < nseg; ++i) {
+    td_segment* s = segs[i];
+    if (!s || !s->factored) {
+      delete g;
+      return fail(!s ? TD_ERR_INVALID : TD_ERR_NOT_FACTORED, "segment missing or not factored");
+    }
+    if (s->device != g->device || K[i] < 0 || (K[i] > 0 && (!R[i] || !logL[i])) || ldr[i] < s->nk) {
+      delete g;
+      return fail(TD_ERR_INVALID, "bad segment arguments");
+    }
+    g->segs.push_back(s);
+    const int64_t cap = round_up(std::max<int64_t>(K[i], 1), TC_COLS);
+    rs_elems += OP_SLICES * cap * s->nkp8;
+    part_elems += (s->nkp / 64) * cap;
+  }
+  td_status r;
+  if ((r = group_alloc((void**)&g->rs, (size_t)rs_elems * 2, "group residual slices")) != TD_OK ||
+      (r = group_alloc((void**)&g->partials, (size_t)part_elems * 8, "group partials")) != TD_OK ||
+      (r = group_alloc((void**)&g->d_seg, (size_t)nseg * sizeof(TcSegDev), "segment descriptors")) != TD_OK ||
+      (r = group_alloc((void**)&g->d_jobs, (size_t)nseg * sizeof(RsJob), "slicing jobs")) != TD_OK ||
+      (r = group_alloc((void**)&g->status, sizeof(DevStatus), "status")) != TD_OK) {
+    td_group_destroy(g);
+    return r;
+  }
+  int64_t rs_off = 0, part_off = 0, col0 = 0;
+  for (int i = 0; i < nseg; ++i) {
+    td_segment* s = segs[i];
+    const int64_t cap = round_up(std::max<int64_t>(K[i], 1), TC_COLS);
+    TcSegDev sd;
+    memset(&sd, 0, sizeof sd);
+    sd.partials = g->partials + part_off;
+    sd.nk = (int)s->nk;
+    sd.K = (int)K[i];
+    sd.ldp = (int)cap;
+    sd.nm = (int)(s->nkp / 64);
+    sd.logdet = s->logdet;
+    sd.logL = logL[i];
+    sd.chi2 = chi2 ? chi2[i] : nullptr;
+    g->host_seg.push_back(sd);
+    RsJob jb{R[i], ldr[i], s->nk, K[i], s->nkp8, cap, g->rs + rs_off, col0};
+    g->host_jobs.push_back(jb);
+    rs_off += OP_SLICES * cap * s->nkp8;
+    part_off += (s->nkp / 64) * cap;
+    col0 += K[i];
+    g->maxK = std::max(g->maxK, K[i]);
+  }
+  g->total_cols = col0;
+  DevStatus hs{0, 0, 0};
+  if (cudaMemcpy(g->d_jobs, g->host_jobs.data(), (size_t)nseg * sizeof(RsJob), cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(g->status, &hs, sizeof hs, cudaMemcpyHostToDevice) != cudaSuccess) {
+    td_group_destroy(g);
+    return fail(TD_ERR_CUDA, "group upload failed");
+  }
+  // tile shape: a decision the autotuner made for this kind of group, else 256-row tiles
+  int bn = 256, sf = 1;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const std::string key = group_signature(g);
+    for (const TuneEntry& e : g_tune)
+      if (e.key == key) {
+        bn = e.bn;
+        sf = e.s_factor;
+      }
+  }
+  if (o.path == TD_PATH_STREAM64) bn = 64;
+  if (o.path == TD_PATH_STREAM) bn = 256;
+  if ((r = group_build(g, bn, sf)) != TD_OK) {
+    td_group_destroy(g);
+    return r;
+  }
+  (void)stream;
+  *out = g;
+  return TD_OK;
+}
+
+td_status td_group_launch(td_group* g, void* stream) {
+  if (!g) return fail(TD_ERR_INVALID, "group is NULL");
+  return group_launch_impl(g, reinterpret_cast<cudaStream_t>(stream));
+}
+
+td_status td_group_graph_launch(td_group* g, void* stream) {
+  if (!g) return fail(TD_ERR_INVALID, "group is NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (!g->graph) {
+    cudaStream_t cap;
+    TD_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    td_status r = TD_OK;
+    if (e == cudaSuccess) r = group_launch_impl(g, cap);
+    cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (e != cudaSuccess || e2 != cudaSuccess || r != TD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return r != TD_OK ? r : cuda_fail(e != cudaSuccess ? e : e2, "graph capture of the grouped launch");
+    }
+    e = cudaGraphInstantiate(&g->graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+  }
+  TD_CUDA(cudaGraphLaunch(g->graph, st));
+  return TD_OK;
+}
+
+td_status td_group_tune(td_group* g, void* stream, double* best_ms) {
+  if (!g) return fail(TD_ERR_INVALID, "group is NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  const int cand[][2] = {{256, 1}, {256, 2}, {256, 4}, {64, 1}, {64, 2}};
+  double best = 1e300;
+  int bb = g->bn, bs = g->s_factor;
+  cudaEvent_t a, b;
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+  for (const auto& c : cand) {
+    td_status r = group_build(g, c[0], c[1]);
+    if (r != TD_OK) continue;
+    for (int w = 0; w < 2; ++w) group_launch_impl(g, st);
+    cudaEventRecord(a, st);
+    for (int it = 0; it < 5; ++it) group_launch_impl(g, st);
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    const double per = ms / 5.0;
+    if (per < best) {
+      best = per;
+      bb = c[0];
+      bs = c[1];
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  td_status r = group_build(g, bb, bs);
+  if (r != TD_OK) return r;
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    const std::string key = group_signature(g);
+    bool found = false;
+    for (TuneEntry& e : g_tune)
+      if (e.key == key) {
+        e.bn = bb;
+        e.s_factor = bs;
+        e.ms = best;
+        found = true;
+      }
+    if (!found) g_tune.push_back(TuneEntry{key, bb, bs, best});
+  }
+  if (best_ms) *best_ms = best;
+  return TD_OK;
+}
+
+td_status td_group_check(td_group* g, void* stream) {
+  if (!g) return fail(TD_ERR_INVALID, "group is NULL");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  DevStatus hs;
+  TD_CUDA(cudaMemcpyAsync(&hs, g->status, sizeof hs, cudaMemcpyDeviceToHost, st));
+  TD_CUDA(cudaStreamSynchronize(st));
+  if (hs.code != 0) {
+    DevStatus z{0, 0, 0};
+    cudaMemcpy(g->status, &z, sizeof z, cudaMemcpyHostToDevice);
+    return fail(hs.code == ST_TIMEOUT ? TD_ERR_TIMEOUT : (td_status)hs.code, "device reported an error");
+  }
+  return TD_OK;
+}
+
+int td_group_shape(const td_group* g, int* bn, int* s_factor, int* n_items) {
+  if (!g) return -1;
+  if (bn) *bn = g->bn;
+  if (s_factor) *s_factor = g->s_factor;
+  if (n_items) *n_items = g->n_items;
+  return 0;
+}
+
+void td_group_destroy(td_group* g) {
+  if (!g) return;
+  cudaDeviceSynchronize();
+  group_free_lists(g);
+  if (g->rs) cudaFree(g->rs);
+  if (g->partials) cudaFree(g->partials);
+  if (g->d_seg) cudaFree(g->d_seg);
+  if (g->d_jobs) cudaFree(g->d_jobs);
+  if (g->status) cudaFree(g->status);
+  delete g;
+}
+
+td_status td_loglike_grouped(td_segment* const* segs, const float* const* R, const int64_t* ldr, const int64_t* K,
+                             double* const* logL, int nseg, const td_options* opt, void* stream) {
+  td_group* g = nullptr;
+  td_status r = td_group_create(segs, R, ldr, K, logL, nullptr, nseg, opt, stream, &g);
+  if (r != TD_OK) return r;
+  r = td_group_launch(g, stream);
+  if (r == TD_OK) r = td_group_check(g, stream);
+  td_group_destroy(g);
+  return r;
+}
+
+}  // extern "C"

@@ -44,6 +44,13 @@ SIGNATURES = {
     "td_resident_bytes": (_i64, [_vp]),
     "td_debug_bounded_wait": (_c.c_int, [_i64, _vp]),
     "td_loglike_batch_noalloc": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
+    "td_group_create": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp, _c.POINTER(_vp)]),
+    "td_group_launch": (_c.c_int, [_vp, _vp]),
+    "td_group_graph_launch": (_c.c_int, [_vp, _vp]),
+    "td_group_tune": (_c.c_int, [_vp, _vp, _c.POINTER(_c.c_double)]),
+    "td_group_check": (_c.c_int, [_vp, _vp]),
+    "td_group_shape": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
+    "td_group_destroy": (None, [_vp]),
     "td_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "td_profile_read": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.POINTER(_i64), _c.POINTER(_i64)]),
 }
@@ -194,6 +201,54 @@ def loglike_grouped(segments, Rs, logLs, opt: TdOptions | None = None, stream=No
     LP = (ctypes.c_void_p * n)(*[x.data_ptr() for x in logLs])
     _check(lib().td_loglike_grouped(H, RP, LD, KK, LP, n, None if opt is None else ctypes.byref(opt),
                                     _stream_ptr(stream)))
+
+
+class Group:
+    """A grouped-evaluation plan (td_group): many segments, one launch."""
+
+    def __init__(self, segments, Rs, logLs, chi2s=None, opt: TdOptions | None = None, stream=None):
+        n = len(segments)
+        self._keep = (list(segments), list(Rs), list(logLs), list(chi2s) if chi2s else None)
+        H = (ctypes.c_void_p * n)(*[s.handle.value for s in segments])
+        RP = (ctypes.c_void_p * n)(*[r.data_ptr() for r in Rs])
+        LD = (ctypes.c_int64 * n)(*[int(r.stride(0)) for r in Rs])
+        KK = (ctypes.c_int64 * n)(*[int(r.shape[0]) for r in Rs])
+        LP = (ctypes.c_void_p * n)(*[x.data_ptr() for x in logLs])
+        CP = None if not chi2s else (ctypes.c_void_p * n)(*[x.data_ptr() for x in chi2s])
+        h = ctypes.c_void_p()
+        _check(lib().td_group_create(H, RP, LD, KK, LP, CP, n, None if opt is None else ctypes.byref(opt),
+                                     _stream_ptr(stream), ctypes.byref(h)))
+        self.handle = h
+
+    def launch(self, stream=None):
+        _check(lib().td_group_launch(self.handle, _stream_ptr(stream)))
+
+    def graph_launch(self, stream=None):
+        _check(lib().td_group_graph_launch(self.handle, _stream_ptr(stream)))
+
+    def tune(self, stream=None) -> float:
+        ms = ctypes.c_double()
+        _check(lib().td_group_tune(self.handle, _stream_ptr(stream), ctypes.byref(ms)))
+        return ms.value
+
+    def check(self, stream=None):
+        _check(lib().td_group_check(self.handle, _stream_ptr(stream)))
+
+    def shape(self):
+        bn, sf, ni = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        lib().td_group_shape(self.handle, ctypes.byref(bn), ctypes.byref(sf), ctypes.byref(ni))
+        return bn.value, sf.value, ni.value
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().td_group_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def debug_bounded_wait(limit_ns: int, stream=None) -> int:

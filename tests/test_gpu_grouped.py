@@ -1,0 +1,106 @@
+"""Grouped launches (many uneven segments, one persistent launch) against the
+CPU oracle; CUDA-graph replay and autotuned shapes give the same results."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_06010_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+CHI2_REL, DLOGL_ABS = 1e-7, 1e-3
+
+SEGS = [  # (n, fs, a, floor, gaps, K)
+    (300, 4096.0, -4.2, 1.5, [], 16),
+    (777, 4096.0, -3.6, 2.8, [(100, 140)], 33),
+    (1024, 4096.0, -4.0, 2.0, [], 130),
+    (1500, 4096.0, -4.4, 1.1, [(200, 300), (900, 950)], 257),
+    (2048, 4096.0, -3.9, 2.4, [(0, 64)], 1),
+    (640, 4096.0, -4.0, 2.0, [], 0),
+]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _build(torch, td):
+    segs, Rs, outs, chis, exp_ll, exp_chi = [], [], [], [], [], []
+    for i, (n, fs, a, fl, gaps, K) in enumerate(SEGS):
+        mask = None
+        if gaps:
+            mask = np.ones(n, np.uint8)
+            for s0, s1 in gaps:
+                mask[s0:s1] = 0
+        acf = inputs.acf_from_psd(n, fs, a=a, floor=fl)
+        seg = td.Segment(acf, mask)
+        R = inputs.noise_residuals(n, fs, max(K, 1), 100 + i, mask=mask, a=a, floor=fl)[:K]
+        o = oracle.OracleSegment(acf, mask)
+        c = o.chi2(R) if K else np.zeros(0)
+        exp_chi.append(c)
+        exp_ll.append(oracle.loglike_from_chi2(c, o.logdet, o.n_kept) if K else np.zeros(0))
+        segs.append(seg)
+        Rs.append(torch.from_numpy(np.ascontiguousarray(R)).cuda() if K else
+                  torch.zeros((0, o.n_kept), dtype=torch.float32, device="cuda"))
+        outs.append(torch.full((K,), np.nan, dtype=torch.float64, device="cuda"))
+        chis.append(torch.full((K,), np.nan, dtype=torch.float64, device="cuda"))
+    return segs, Rs, outs, chis, exp_ll, exp_chi
+
+
+def _check_all(outs, chis, exp_ll, exp_chi):
+    for ll, ch, el, ec in zip(outs, chis, exp_ll, exp_chi):
+        ll = ll.cpu().numpy()
+        ch = ch.cpu().numpy()
+        if el.size == 0:
+            continue
+        assert np.max(np.abs(ch - ec) / ec) <= CHI2_REL
+        assert np.max(np.abs(ll - el)) <= DLOGL_ABS
+
+
+def test_grouped_plan_graph_and_tune(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    segs, Rs, outs, chis, exp_ll, exp_chi = _build(torch_cuda, td)
+    g = td.Group(segs, Rs, outs, chis)
+    g.launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    _check_all(outs, chis, exp_ll, exp_chi)
+    first = [x.cpu().numpy().copy() for x in outs]
+    # graph replay: same kernels, same plan -> same bits
+    for x in outs:
+        x.fill_(np.nan)
+    g.graph_launch()
+    g.graph_launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    for a, b in zip(first, outs):
+        assert np.array_equal(a, b.cpu().numpy())
+    # autotuned shape: still within the bar
+    ms = g.tune()
+    assert ms > 0
+    bn, sf, ni = g.shape()
+    assert bn in (64, 256) and sf >= 1 and ni > 0
+    for x in outs:
+        x.fill_(np.nan)
+    g.launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    _check_all(outs, chis, exp_ll, exp_chi)
+    g.close()
+
+
+def test_grouped_one_shot_matches_per_segment(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    segs, Rs, outs, chis, exp_ll, exp_chi = _build(torch_cuda, td)
+    td.loglike_grouped(segs, Rs, outs)
+    torch_cuda.cuda.synchronize()
+    for seg, R, out in zip(segs, Rs, outs):
+        if R.shape[0] == 0:
+            continue
+        single = seg.loglike(R)
+        torch_cuda.cuda.synchronize()
+        assert np.max(np.abs(single.cpu().numpy() - out.cpu().numpy())) <= DLOGL_ABS

@@ -169,6 +169,9 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
   for (int i = 0; i < g->nseg; ++i) {
     TcSegDev& sd = g->host_seg[(size_t)i];
     td_segment* s = g->segs[(size_t)i];
+    sd.a_rows = TC_COLS;
+    sd.wpart = g->wpart;
+    if (sd.K == 0) continue;   // no work item refers to an empty segment
     // residual map over this segment's slice region of the group buffer
     const int64_t cap = sd.ldp;
     td_segment tmp_view;   // only the fields encode_seg_maps reads

@@ -49,7 +49,8 @@ typedef enum {
   TD_ERR_CUDA = 4,          /* a CUDA runtime/driver call failed */
   TD_ERR_TIMEOUT = 5,       /* a bounded in-kernel wait ran out */
   TD_ERR_NOT_FACTORED = 6,  /* td_factor has not succeeded on this segment */
-  TD_ERR_UNSUPPORTED = 7    /* precision/size combination not built */
+  TD_ERR_UNSUPPORTED = 7,   /* precision/size combination not built */
+  TD_ERR_BUSY = 8           /* server admission refused (capacity) or request already running */
 } td_status;
 
 typedef enum {
@@ -118,6 +119,14 @@ td_status td_segment_create(const double* acf, int64_t n, const uint8_t* mask,
  * then gives the 0-based kept-sample index of the first failing pivot.
  */
 td_status td_factor(td_segment* s, void* stream);
+
+/*
+ * Free the segment's FP64 factor (L and its diagonal-tile inverses), keeping
+ * the whitening operator slices and log det: the tensor-core paths keep
+ * working, the FP64 path then returns TD_ERR_UNSUPPORTED.  Saves 8 N'^2
+ * bytes of device memory.  Synchronises the device.
+ */
+td_status td_segment_release_fp64(td_segment* s);
 
 /* log det C_kept (host scalar).  Requires a successful td_factor. */
 td_status td_logdet(const td_segment* s, double* out);
@@ -238,6 +247,67 @@ td_status td_profile_read(td_segment* s, double* ms_total, int64_t* dominant_lau
 
 /* Release a segment and all device memory it owns (synchronises its work). */
 void td_segment_destroy(td_segment* s);
+
+/*
+ * Serving runtime -- many concurrent likelihood requests on many resident
+ * segments (the paper's pool of concurrent proposal evaluations, Sec. III.B
+ * "CPU acceleration", as requests).  A scheduler thread packs the pending
+ * columns of one segment into one batch whenever one of n_streams streams is
+ * free (continuous batching: requests arriving while other batches run join
+ * the next batch of their segment); batches of different segments run
+ * concurrently.  Whitening operators stay resident in HBM under
+ * resident_bytes_budget with LRU eviction; an evicted operator is kept in
+ * pinned host memory and copied back on its next use.  All calls are
+ * thread-safe.  Results of a request are within the library's accuracy bar of
+ * the same request evaluated alone (the batch's tile shape depends on its
+ * width).
+ *   add_segment: host acf/mask as td_segment_create; the factor is computed on
+ *     first use or by td_server_prefetch (synchronous; also reserves scratch
+ *     for max_batch_cols).  The FP64 factor is released after factoring.
+ *   submit: R (device, float32, N' x K column-major, leading dimension ldr) and
+ *     logL (device, float64[K]) are caller-owned and must stay valid until the
+ *     request completes; 1 <= K <= max_batch_cols.  Returns TD_ERR_BUSY when
+ *     the pending-column capacity would be exceeded (admission refused).
+ *   poll: state 0 pending, 1 running, 2 done, 3 cancelled, 4 failed.
+ *   wait: blocks up to timeout_us (TD_ERR_TIMEOUT after).
+ *   cancel: only before the request is batched (TD_ERR_BUSY after).
+ *   pause: stops batching new work (for tests and draining).
+ *   replay: submits n requests at t_submit_s[i] seconds after the call
+ *     (open-loop load from a native thread); tickets[i] = -1 if refused.
+ *   get_stats: latency percentiles from submission to completion, evaluations per
+ *     second between the first submission and the last completion, LRU
+ *     counters; reset != 0 clears them.
+ */
+typedef struct td_server td_server;
+typedef struct {
+  int64_t max_batch_cols;        /* widest batch the scheduler packs (and largest request) */
+  int64_t max_pending_cols;      /* admission capacity: queued + running columns */
+  int64_t resident_bytes_budget; /* HBM budget for resident operators; 0 = unlimited */
+  int n_streams;                 /* concurrent batches, 1..16 */
+  int precision;                 /* td_precision of the tensor-core path */
+  int64_t max_kept;              /* largest N' a segment may have (sizes batch buffers) */
+} td_server_config;
+typedef struct {
+  double p50_us, p99_us, max_us, evals_per_s;
+  int64_t requests_done, evals, batches, hits, misses, evictions, refused, failed, resident_bytes;
+} td_server_stats;
+void td_server_config_default(td_server_config* c);
+td_status td_server_create(const td_server_config* cfg, td_server** out);
+td_status td_server_add_segment(td_server* srv, const double* acf, int64_t n, const uint8_t* mask,
+                                int64_t* seg_id);
+td_status td_server_prefetch(td_server* srv, int64_t seg_id);
+td_status td_server_submit(td_server* srv, int64_t seg_id, const float* R, int64_t ldr, int64_t K,
+                           double* logL, int64_t* ticket);
+td_status td_server_poll(td_server* srv, int64_t ticket, int* state);
+td_status td_server_wait(td_server* srv, int64_t ticket, int64_t timeout_us);
+td_status td_server_cancel(td_server* srv, int64_t ticket);
+td_status td_server_pause(td_server* srv, int paused);
+td_status td_server_drain(td_server* srv, int64_t timeout_us);
+td_status td_server_replay(td_server* srv, const double* t_submit_s, const int64_t* seg,
+                           const float* const* R, const int64_t* ldr, const int64_t* K,
+                           double* const* logL, int64_t n, int64_t* tickets);
+td_status td_server_get_stats(td_server* srv, td_server_stats* out, int reset);
+void td_server_destroy(td_server* srv);
 
 /* Thread-local message for the last failing call on this thread ("" if none). */
 const char* td_last_error(void);

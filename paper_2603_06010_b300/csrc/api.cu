@@ -434,6 +434,8 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   if (o.refine) return fail(TD_ERR_UNSUPPORTED, "refinement is not built in this version");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const bool fp64 = (o.precision == TD_PREC_FP64) || (o.path == TD_PATH_FP64);
+  if (fp64 && !s->L) return fail(TD_ERR_UNSUPPORTED, "the FP64 factor of this segment was released");
+  if (!fp64 && !s->op) return fail(TD_ERR_NOT_FACTORED, "the operator of this segment is not resident");
   if ((r = ensure_scratch(s, K, fp64, st)) != TD_OK) return r;
   Scratch& sc = s->scr;
   const int64_t ldp = sc.capK;
@@ -495,6 +497,15 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   if (pm) prof_mark(s, st, false);
   TD_CUDA(launch_finalize(sc.partials, ldp, ngroups, K, s->logdet, s->nk, logL, chi2, st));
   s->prof_kernels += 3;
+  return TD_OK;
+}
+
+td_status td_segment_release_fp64(td_segment* s) {
+  if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
+  cudaDeviceSynchronize();
+  dev_free(s->L);
+  dev_free(s->dinv);
+  dev_free(s->scr.w64);
   return TD_OK;
 }
 

@@ -17,12 +17,12 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libtd.so")
 
 TD_OK, TD_ERR_INVALID, TD_ERR_NOT_PD, TD_ERR_OOM, TD_ERR_CUDA, TD_ERR_TIMEOUT, TD_ERR_NOT_FACTORED, \
-    TD_ERR_UNSUPPORTED = range(8)
+    TD_ERR_UNSUPPORTED, TD_ERR_BUSY = range(9)
 TD_PREC_FP64, TD_PREC_BF16X6, TD_PREC_BF16X3, TD_PREC_AUTO, TD_PREC_BF16X10 = range(5)
 TD_PATH_AUTO, TD_PATH_TENSOR, TD_PATH_STREAM, TD_PATH_FP64, TD_PATH_STREAM64, TD_PATH_SMALLK = range(6)
 
 STATUS_NAMES = {0: "TD_OK", 1: "TD_ERR_INVALID", 2: "TD_ERR_NOT_PD", 3: "TD_ERR_OOM", 4: "TD_ERR_CUDA",
-                5: "TD_ERR_TIMEOUT", 6: "TD_ERR_NOT_FACTORED", 7: "TD_ERR_UNSUPPORTED"}
+                5: "TD_ERR_TIMEOUT", 6: "TD_ERR_NOT_FACTORED", 7: "TD_ERR_UNSUPPORTED", 8: "TD_ERR_BUSY"}
 
 # every symbol include/td.h declares, with (restype, argtypes)
 _c = ctypes
@@ -51,9 +51,37 @@ SIGNATURES = {
     "td_group_check": (_c.c_int, [_vp, _vp]),
     "td_group_shape": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "td_group_destroy": (None, [_vp]),
+    "td_segment_release_fp64": (_c.c_int, [_vp]),
+    "td_server_config_default": (None, [_vp]),
+    "td_server_create": (_c.c_int, [_vp, _c.POINTER(_vp)]),
+    "td_server_add_segment": (_c.c_int, [_vp, _vp, _i64, _vp, _c.POINTER(_i64)]),
+    "td_server_prefetch": (_c.c_int, [_vp, _i64]),
+    "td_server_submit": (_c.c_int, [_vp, _i64, _vp, _i64, _i64, _vp, _c.POINTER(_i64)]),
+    "td_server_poll": (_c.c_int, [_vp, _i64, _c.POINTER(_c.c_int)]),
+    "td_server_wait": (_c.c_int, [_vp, _i64, _i64]),
+    "td_server_cancel": (_c.c_int, [_vp, _i64]),
+    "td_server_pause": (_c.c_int, [_vp, _c.c_int]),
+    "td_server_drain": (_c.c_int, [_vp, _i64]),
+    "td_server_replay": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i64, _vp]),
+    "td_server_get_stats": (_c.c_int, [_vp, _vp, _c.c_int]),
+    "td_server_destroy": (None, [_vp]),
     "td_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "td_profile_read": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.POINTER(_i64), _c.POINTER(_i64)]),
 }
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("max_batch_cols", ctypes.c_int64), ("max_pending_cols", ctypes.c_int64),
+                ("resident_bytes_budget", ctypes.c_int64), ("n_streams", ctypes.c_int), ("precision", ctypes.c_int),
+                ("max_kept", ctypes.c_int64)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("p50_us", ctypes.c_double), ("p99_us", ctypes.c_double), ("max_us", ctypes.c_double),
+                ("evals_per_s", ctypes.c_double), ("requests_done", ctypes.c_int64), ("evals", ctypes.c_int64),
+                ("batches", ctypes.c_int64), ("hits", ctypes.c_int64), ("misses", ctypes.c_int64),
+                ("evictions", ctypes.c_int64), ("refused", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("resident_bytes", ctypes.c_int64)]
 
 
 class TdOptions(ctypes.Structure):
@@ -140,6 +168,9 @@ class Segment:
     @property
     def resident_bytes(self) -> int:
         return int(lib().td_resident_bytes(self.handle))
+
+    def release_fp64(self):
+        _check(lib().td_segment_release_fp64(self.handle))
 
     def reserve(self, K: int, opt: TdOptions | None = None):
         _check(lib().td_reserve(self.handle, int(K), None if opt is None else ctypes.byref(opt)))
@@ -242,6 +273,87 @@ class Group:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             lib().td_group_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """td_server: continuous-batching likelihood server (see include/td.h)."""
+
+    PENDING, RUNNING, DONE, CANCELLED, FAILED = range(5)
+
+    def __init__(self, max_batch_cols=4096, max_pending_cols=1 << 20, resident_bytes_budget=0, n_streams=4,
+                 precision=TD_PREC_BF16X6, max_kept=32768):
+        c = ServerConfig()
+        lib().td_server_config_default(ctypes.byref(c))
+        c.max_batch_cols, c.max_pending_cols = max_batch_cols, max_pending_cols
+        c.resident_bytes_budget, c.n_streams, c.precision, c.max_kept = (resident_bytes_budget, n_streams,
+                                                                         precision, max_kept)
+        h = ctypes.c_void_p()
+        _check(lib().td_server_create(ctypes.byref(c), ctypes.byref(h)))
+        self.handle = h
+
+    def add_segment(self, acf, mask=None) -> int:
+        acf = np.ascontiguousarray(acf, dtype=np.float64)
+        m = None if mask is None else np.ascontiguousarray(mask, dtype=np.uint8)
+        sid = ctypes.c_int64()
+        _check(lib().td_server_add_segment(self.handle, acf.ctypes.data, int(acf.shape[0]),
+                                           None if m is None else m.ctypes.data, ctypes.byref(sid)))
+        return sid.value
+
+    def prefetch(self, seg_id: int):
+        _check(lib().td_server_prefetch(self.handle, int(seg_id)))
+
+    def submit(self, seg_id: int, R, logL) -> int:
+        """R: CUDA float32 (K, ldr); logL: CUDA float64 (K,).  Raises TdError(TD_ERR_BUSY) if refused."""
+        t = ctypes.c_int64()
+        _check(lib().td_server_submit(self.handle, int(seg_id), R.data_ptr(), int(R.stride(0)), int(R.shape[0]),
+                                      logL.data_ptr(), ctypes.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int) -> int:
+        st = ctypes.c_int()
+        _check(lib().td_server_poll(self.handle, int(ticket), ctypes.byref(st)))
+        return st.value
+
+    def wait(self, ticket: int, timeout_us: int = 60_000_000):
+        _check(lib().td_server_wait(self.handle, int(ticket), int(timeout_us)))
+
+    def cancel(self, ticket: int):
+        _check(lib().td_server_cancel(self.handle, int(ticket)))
+
+    def pause(self, paused: bool = True):
+        _check(lib().td_server_pause(self.handle, 1 if paused else 0))
+
+    def drain(self, timeout_us: int = 120_000_000):
+        _check(lib().td_server_drain(self.handle, int(timeout_us)))
+
+    def replay(self, t_submit_s, seg_ids, Rs, logLs):
+        n = len(t_submit_s)
+        T = np.ascontiguousarray(t_submit_s, dtype=np.float64)
+        S = np.ascontiguousarray(seg_ids, dtype=np.int64)
+        RP = np.array([r.data_ptr() for r in Rs], dtype=np.uint64)
+        LD = np.array([int(r.stride(0)) for r in Rs], dtype=np.int64)
+        KK = np.array([int(r.shape[0]) for r in Rs], dtype=np.int64)
+        LP = np.array([x.data_ptr() for x in logLs], dtype=np.uint64)
+        tickets = np.zeros(n, dtype=np.int64)
+        _check(lib().td_server_replay(self.handle, T.ctypes.data, S.ctypes.data, RP.ctypes.data, LD.ctypes.data,
+                                      KK.ctypes.data, LP.ctypes.data, n, tickets.ctypes.data))
+        return tickets
+
+    def stats(self, reset: bool = False) -> dict:
+        s = ServerStats()
+        _check(lib().td_server_get_stats(self.handle, ctypes.byref(s), 1 if reset else 0))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().td_server_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):

@@ -115,6 +115,7 @@ static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st) 
   }
   srv->misses++;
   const int64_t budget = srv->cfg.resident_bytes_budget;
+  // e.op_bytes is known from N' before the first factor
   while (budget > 0 && (int64_t)(srv->resident_bytes + e.op_bytes) > budget) {
     int64_t victim = -1;
     for (size_t i = 0; i < srv->segs.size(); ++i) {
@@ -129,7 +130,6 @@ static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st) 
     td_status r = td_factor(e.s, st);
     if (r != TD_OK) return r;
     td_segment_release_fp64(e.s);
-    e.op_bytes = (size_t)e.s->op_blocks * OP_SLICES * OP_ROWS * OP_KB * 2;
   } else {
     void* p = nullptr;
     if (cudaMalloc(&p, e.op_bytes) != cudaSuccess) {
@@ -333,6 +333,7 @@ td_status td_server_add_segment(td_server* srv, const double* acf, int64_t n, co
   std::lock_guard<std::mutex> lk(srv->mu);
   SegEntry e;
   e.s = s;
+  e.op_bytes = (size_t)op_row_offset(s->nkp / OP_ROWS) * OP_SLICES * OP_ROWS * OP_KB * 2;
   srv->segs.push_back(e);
   *seg_id = (int64_t)srv->segs.size() - 1;
   return TD_OK;

@@ -43,6 +43,9 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-compare", action="store_true")
     p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--no-grouped", action="store_true")
+    p.add_argument("--no-serving", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=3.0)
     return p.parse_args()
 
 
@@ -138,6 +141,112 @@ def cpu_baseline(seg, R, budget_s=12.0):
                       f"repeated for >= {budget_s:.0f} s"}
 
 
+def grouped_extra(td, torch):
+    """A config-4-like mix in one grouped launch (reduced N range, see note)."""
+    from paper_2603_06010_b300 import inputs
+    specs = inputs.cfg4_segments(count=64)
+    rng = np.random.default_rng(4040)
+    segs, Rs, outs = [], [], []
+    t0 = time.perf_counter()
+    for sp in specs:
+        n = int(min(sp["n"], 8192))
+        acf = inputs.acf_from_psd(n, sp["fs"], a=sp["a"], floor=sp["floor"])
+        segs.append(td.Segment(acf))
+        R = (rng.standard_normal((sp["K"], n)) * np.sqrt(acf[0])).astype(np.float32)
+        Rs.append(torch.from_numpy(R).cuda())
+        outs.append(torch.empty(sp["K"], dtype=torch.float64, device="cuda"))
+    factor_s = time.perf_counter() - t0
+    g = td.Group(segs, Rs, outs)
+    tuned_ms = g.tune()
+    bn, sf, ni = g.shape()
+    for _ in range(3):
+        g.graph_launch()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    a.record()
+    for _ in range(reps):
+        g.graph_launch()
+    b.record()
+    torch.cuda.synchronize()
+    g.check()
+    ms = a.elapsed_time(b) / reps
+    cols = sum(int(r.shape[0]) for r in Rs)
+    flops = sum(float(s.n_kept) ** 2 * int(r.shape[0]) for s, r in zip(segs, Rs))
+    g.close()
+    return {"note": "64 segments, N log-uniform in [512, 32768] capped at 8192 (B300 FP64 factor time), "
+                    "K uniform in [16, 512], own PSD each; one captured-graph grouped launch",
+            "segments": len(segs), "columns": cols, "ms_per_launch": ms, "evals_per_s": cols / (ms / 1e3),
+            "algorithmic_tflops": flops / (ms / 1e3) / 1e12, "tile_rows": bn, "chunk_factor": sf,
+            "work_items": ni, "autotune_best_ms": tuned_ms, "factor_s": factor_s}
+
+
+def serving_extra(td, torch, seconds):
+    """Open-loop Poisson serving on a fleet of resident segments (reduced size)."""
+    from paper_2603_06010_b300 import inputs
+    rng = np.random.default_rng(5050)
+    nseg = 24
+    srv = td.Server(max_batch_cols=2048, n_streams=4, max_kept=8192, max_pending_cols=1 << 22)
+    ids, pools, nks = [], [], []
+    t0 = time.perf_counter()
+    for i in range(nseg):
+        n = int(rng.choice([4096, 8192]))
+        g = int(rng.integers(0, 4))
+        mask = inputs.gap_mask(n, g, 512, rng) if g else None
+        acf = inputs.acf_from_psd(n, 2048.0)
+        sid = srv.add_segment(acf, mask)
+        srv.prefetch(sid)
+        nk = int(n if mask is None else mask.sum())
+        pool = (rng.standard_normal((512, nk)) * np.sqrt(acf[0])).astype(np.float32)
+        ids.append(sid)
+        pools.append(torch.from_numpy(pool).cuda())
+        nks.append(nk)
+    factor_s = time.perf_counter() - t0
+    lam = 2000.0
+    nreq = int(lam * (seconds + 0.5))
+    t = np.cumsum(rng.exponential(1.0 / lam, nreq))
+    segs = rng.integers(0, nseg, nreq)
+    Ks = rng.choice([1, 8, 64, 512], nreq)
+    Rs = [pools[s][:k] for s, k in zip(segs, Ks)]
+    outs = [torch.empty(int(k), dtype=torch.float64, device="cuda") for k in Ks]
+    torch.cuda.synchronize()
+    warm = int(np.searchsorted(t, 0.5))
+    srv.replay(t[:warm], segs[:warm], Rs[:warm], outs[:warm])
+    srv.drain()
+    srv.stats(reset=True)
+    t2 = t[warm:] - t[warm]
+    tickets = srv.replay(t2, segs[warm:], Rs[warm:], outs[warm:])
+    srv.drain()
+    st = srv.stats()
+    srv.close()
+    # the plain per-request FP64 solve on one of these segments, for comparison
+    acf = inputs.acf_from_psd(8192, 2048.0)
+    s64 = td.Segment(acf)
+    o64 = td.options(precision=td.TD_PREC_FP64)
+    per = {}
+    for k in (1, 64):
+        Rk = torch.from_numpy((rng.standard_normal((k, 8192)) * np.sqrt(acf[0])).astype(np.float32)).cuda()
+        out = torch.empty(k, dtype=torch.float64, device="cuda")
+        s64.loglike_into(Rk, out, o64)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        s64.loglike_into(Rk, out, o64)
+        b.record()
+        torch.cuda.synchronize()
+        per[k] = a.elapsed_time(b)
+    s64.close()
+    mean_k = float(np.mean(Ks[warm:]))
+    fp64_evals_per_s = 1.0 / (np.mean([per[1], per[64]]) / 1e3) * mean_k
+    return {"note": f"{nseg} segments, N in {{4096, 8192}} (capped from up to 32768: B300 FP64 factor time), "
+                    "0-3 gaps of 512, Poisson 2000 req/s open loop (native replay), K in {1, 8, 64, 512}",
+            "seconds": seconds, "requests": int(st["requests_done"]), "refused": int(st["refused"]),
+            "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3, "evals_per_s": st["evals_per_s"],
+            "batches": int(st["batches"]), "fp64_per_request_ms": {"K=1": per[1], "K=64": per[64]},
+            "fp64_per_request_evals_per_s_est": fp64_evals_per_s, "factor_s": factor_s,
+            "submitted": int(np.sum(tickets >= 0))}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -226,12 +335,10 @@ def main():
     seg.profile(False)
     seg.check()
     step_ms = np.array([a.elapsed_time(b) for a, b in ev])
-    tot_ms = float(step_ms.sum())
-    if world > 1:
-        t = torch.tensor([tot_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-    value = world * K * args.steps / (tot_ms / 1e3)
+    from paper_2603_06010_b300 import dist as tddist
+    tot_s, all_evals = tddist.aggregate(float(step_ms.sum()) / 1e3, K * args.steps, device="cuda")
+    tot_ms = tot_s * 1e3
+    value = all_evals / tot_s
 
     # end to end through the C ABI with host buffers (pinned), copies timed
     R_pin = torch.from_numpy(R_host).pin_memory()
@@ -249,12 +356,8 @@ def main():
         torch.cuda.synchronize()
         if i > 0:
             e2e_ms.append(a.elapsed_time(b))
-    e2e_tot = float(np.sum(e2e_ms))
-    if world > 1:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_value = world * K * len(e2e_ms) / (e2e_tot / 1e3)
+    e2e_s, e2e_evals = tddist.aggregate(float(np.sum(e2e_ms)) / 1e3, K * len(e2e_ms), device="cuda")
+    e2e_value = e2e_evals / e2e_s
 
     # plain FP64 GPU solve on the same batch (the baseline the split path must beat)
     fp64 = None
@@ -351,6 +454,10 @@ def main():
                           "runs": small},
         "clocks": clk,
     }
+    if world == 1 and not args.no_grouped:
+        line["grouped"] = grouped_extra(td, torch)
+    if world == 1 and not args.no_serving:
+        line["serving"] = serving_extra(td, torch, args.serve_seconds)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(seg_in, R_host)
     print(json.dumps(line), flush=True)

@@ -459,7 +459,10 @@ def main():
     if world == 1 and not args.no_serving:
         line["serving"] = serving_extra(td, torch, args.serve_seconds)
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(seg_in, R_host)
+        try:
+            line["cpu_baseline"] = cpu_baseline(seg_in, R_host)
+        except Exception as ex:   # report, do not lose the measured line
+            line["cpu_baseline"] = {"error": repr(ex)}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

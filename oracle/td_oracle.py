@@ -168,9 +168,15 @@ def time_per_eval_path(seg: OracleSegment, R_kn, threads: int | None = None,
                        min_seconds: float = 0.0):
     """Time whiten + chi2 + logL for the columns of R_kn on `threads` BLAS
     threads (default: all host cores).  Returns (seconds, threads_used)."""
-    from threadpoolctl import threadpool_limits
+    import contextlib
     threads = threads or (os.cpu_count() or 1)
-    with threadpool_limits(limits=threads):
+    try:
+        from threadpoolctl import threadpool_limits
+        ctx = threadpool_limits(limits=threads)
+    except ImportError:          # BLAS then uses its default: all host cores
+        ctx = contextlib.nullcontext()
+        threads = os.cpu_count() or 1
+    with ctx:
         reps = 0
         t0 = time.perf_counter()
         while True:

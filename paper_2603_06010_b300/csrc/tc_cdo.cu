@@ -409,75 +409,54 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
 // Reduce the accumulator pairs of a split row tile (one block per 64 rows): for each
 // row, w = sum over chunks of (hi*hi sum + correction sum), in double-float
 // (the hi*hi sums are exact, their sum stays exact well past these lengths);
-// then the chi2 share of the 64 rows in double-float, as one FP64 partial in
-// the same per-64-row-group layout the direct epilogue writes.
+// then the chi2 share of the rows in double-float, as FP64 partials per
+// 64-row group (part_rows = 64) or per 32-row warp group (part_rows = 32).
 // Thread (row, column group): rows are contiguous in the slot layout, so a
-// warp's loads are coalesced; the 64-row sum is a fixed shuffle tree.
+// warp's loads are coalesced; columns are dealt round-robin to the four
+// column groups so every warp works even for a few columns; the sum over a
+// warp's 32 rows is a fixed shuffle tree, the two warps of a group are added
+// in a fixed order.
 __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restrict__ units,
                                                        const TcSegDev* __restrict__ segs, int bn, int part_rows) {
-  __shared__ float red_hi[4][2][32], red_lo[4][2][32];
+  __shared__ float red_hi[128][2], red_lo[128][2];
   const SplitUnit u = units[blockIdx.x];
   const int g64 = blockIdx.y;                   // 64-row group of the bn-row tile
   const TcSegDev& sd = segs[u.seg];
   const int row = threadIdx.x & 63, grp = threadIdx.x >> 6;   // 4 column groups of 2 warps
   const int wig = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
   const int ncol = min(128, sd.K - u.c * 128);
-  for (int cb = 0; cb < ncol; cb += 4 * 32) {
-    // each group handles up to 32 columns of this block: cl = cb + grp*32 + i
-    float ch_hi[32], ch_lo[32];
-    const int nmine = max(0, min(32, ncol - cb - grp * 32));   // valid columns of this group
-#pragma unroll 4
-    for (int i = 0; i < nmine; ++i) {
-      const int cl = cb + grp * 32 + i;
-      float hi = 0.f, lo = 0.f;
-      if (cl < ncol) {
-        float wh = 0.f, wl = 0.f;
-        for (int ch = 0; ch < u.nchunk; ++ch) {
-          const float2 v = sd.wpart[((int64_t)(u.slot0 + ch) * 128 + cl) * bn + g64 * 64 + row];
-          ff_add(v.x, wh, wl);
-          ff_add(v.y, wh, wl);
-        }
-        ff_add_square2(wh, wl, hi, lo);
-      }
-      // sum over the 32 rows of this warp (fixed tree), compensated
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float oh = __shfl_down_sync(0xffffffffu, hi, off);
-        const float ol = __shfl_down_sync(0xffffffffu, lo, off);
-        ff_add(oh, hi, lo);
-        lo += ol;
-      }
-      ch_hi[i] = hi;
-      ch_lo[i] = lo;
+  const float2* base = sd.wpart + (int64_t)u.slot0 * 128 * bn + g64 * 64 + row;
+  for (int cl = grp; cl < ncol; cl += 4) {
+    float wh = 0.f, wl = 0.f;
+    for (int ch = 0; ch < u.nchunk; ++ch) {
+      const float2 v = base[((int64_t)ch * 128 + cl) * bn];
+      ff_add(v.x, wh, wl);
+      ff_add(v.y, wh, wl);
     }
-    if (part_rows == 32) {   // one partial per 32-row warp group, no combine
-      if (lane == 0) {
-        for (int i = 0; i < nmine; ++i) {
-          const int cl = cb + grp * 32 + i;
-          sd.partials[(((int64_t)u.m * (bn / 64) + g64) * 2 + wig) * sd.ldp + u.c * 128 + cl] =
-              (double)ch_hi[i] + (double)ch_lo[i];
-        }
-      }
-      continue;
+    float hi = 0.f, lo = 0.f;
+    ff_add_square2(wh, wl, hi, lo);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+      const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+      ff_add(oh, hi, lo);
+      lo += ol;
     }
     if (lane == 0) {
-#pragma unroll 4
-      for (int i = 0; i < nmine; ++i) {
-        red_hi[grp][wig][i] = ch_hi[i];
-        red_lo[grp][wig][i] = ch_lo[i];
+      if (part_rows == 32) {
+        sd.partials[(((int64_t)u.m * (bn / 64) + g64) * 2 + wig) * sd.ldp + u.c * 128 + cl] =
+            (double)hi + (double)lo;
+      } else {
+        red_hi[cl][wig] = hi;
+        red_lo[cl][wig] = lo;
       }
     }
-    __syncthreads();
-    if (threadIdx.x < 128) {
-      const int g = threadIdx.x >> 5, i = threadIdx.x & 31;
-      const int cl = cb + g * 32 + i;
-      if (cl < ncol) {
-        const double s = ((double)red_hi[g][0][i] + (double)red_lo[g][0][i]) +
-                         ((double)red_hi[g][1][i] + (double)red_lo[g][1][i]);
-        sd.partials[((int64_t)u.m * (bn / 64) + g64) * sd.ldp + u.c * 128 + cl] = s;
-      }
-    }
-    __syncthreads();
+  }
+  if (part_rows == 32) return;
+  __syncthreads();
+  for (int cl = threadIdx.x; cl < ncol; cl += blockDim.x) {
+    const double s = ((double)red_hi[cl][0] + (double)red_lo[cl][0]) + ((double)red_hi[cl][1] + (double)red_lo[cl][1]);
+    sd.partials[((int64_t)u.m * (bn / 64) + g64) * sd.ldp + u.c * 128 + cl] = s;
   }
 }
 

@@ -454,8 +454,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   const int nsl = nslices_for(o.precision);
   const Shape shape = choose_shape(s, K, o.path);
   const int bn = shape.bn;
-  if (!sc.colmax && (r = dev_alloc(&sc.colmax, 64, "column maxima")) != TD_OK) return r;
-  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st, sc.colmax));
+  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   const int ngroups = (int)(s->nkp / 64);
   const int nc = (int)ceil_div(K, TC_COLS);
   const int nkb_max = (int)ceil_div(s->nk, OP_KB);
@@ -573,7 +572,6 @@ void td_segment_destroy(td_segment* s) {
   dev_free(s->scr.segdev);
   dev_free(s->scr.rsf);
   dev_free(s->scr.wpart);
-  dev_free(s->scr.colmax);
   free_plans(s->scr);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (prev >= 0 && prev != s->device) cudaSetDevice(prev);

@@ -19,8 +19,7 @@ int split_chunk(int64_t nk, int64_t nkp, int bn) {
   const int64_t nkb_max = ceil_div(nk, OP_KB);
   int64_t total = 0;
   for (int64_t m = 0; m < nm; ++m) total += std::min<int64_t>(per * (m + 1), nkb_max);
-  // about six work items per SM: the last items leave little idle time
-  int64_t S = ceil_div(total, 6 * (int64_t)tc_num_sms());
+  int64_t S = ceil_div(total, 2 * (int64_t)tc_num_sms());
   if (S < 4) S = 4;
   return (int)S;
 }

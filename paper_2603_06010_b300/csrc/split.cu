@@ -140,63 +140,9 @@ __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, i
   }
 }
 
-// Small batches: many blocks per column.  Pass 1 takes each column's max |R|
-// (atomicMax on the bits of a non-negative float orders like the float);
-// pass 2 slices with the column's quantum.  Same slices as k_r_slices.
-__global__ void k_col_absmax(const float* __restrict__ R, int64_t ldr, int64_t nk, unsigned* __restrict__ colmax) {
-  __shared__ float red[8];
-  const int64_t k = blockIdx.y;
-  const float* col = R + k * ldr;
-  float mx = 0.f;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x)
-    mx = fmaxf(mx, fabsf(col[j]));
-#pragma unroll
-  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
-    mx = fmaxf(mx, red[0]);
-    atomicMax(colmax + k, __float_as_uint(mx));
-  }
-}
-
-__global__ void k_r_slices_cols(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t nkp8, int64_t capK,
-                                const unsigned* __restrict__ colmax, __nv_bfloat16* __restrict__ rs, int nslices) {
-  const int64_t k = blockIdx.y;
-  const float mx = __uint_as_float(colmax[k]);
-  float p = 1.f;
-  if (mx > 0.f) {
-    p = exp2f(ceilf(log2f(mx / 255.f)));
-    if (mx / p > 255.f) p *= 2.f;
-  }
-  const int64_t ss = capK * nkp8;
-  const float* col = R + k * ldr;
-  __nv_bfloat16* dst = rs + k * nkp8;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nk; j += (int64_t)gridDim.x * blockDim.x) {
-    const float x = col[j];
-    const float hi = p * rintf(x / p);
-    __nv_bfloat16 a, b, c;
-    split3_f32(x - hi, a, b, c);
-    dst[j] = __float2bfloat16_rn(hi);
-    dst[j + ss] = a;
-    if (nslices > 2) dst[j + 2 * ss] = b;
-    if (nslices > 3) dst[j + 3 * ss] = c;
-  }
-}
-
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8, int64_t capK,
-                            __nv_bfloat16* rs, int nslices, cudaStream_t st, unsigned* colmax) {
+                            __nv_bfloat16* rs, int nslices, cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  if (colmax != nullptr && K <= 64) {
-    int gx = (int)ceil_div(nk, 1024);
-    if (gx > 64) gx = 64;
-    cudaError_t e = cudaMemsetAsync(colmax, 0, (size_t)K * sizeof(unsigned), st);
-    if (e != cudaSuccess) return e;
-    k_col_absmax<<<dim3(gx, (unsigned)K), 256, 0, st>>>(R, ldr, nk, colmax);
-    k_r_slices_cols<<<dim3(gx, (unsigned)K), 256, 0, st>>>(R, ldr, nk, nkp8, capK, colmax, rs, nslices);
-    return cudaGetLastError();
-  }
   const int grid = (int)(K < 4096 ? K : 4096);
   k_r_slices<<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
   return cudaGetLastError();

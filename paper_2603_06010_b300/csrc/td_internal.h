@@ -89,7 +89,6 @@ struct Scratch {
   float* rsf = nullptr;         // unused
   int64_t rsf_bytes = 0;
   float2* wpart = nullptr;      // split-mode accumulator pairs
-  unsigned* colmax = nullptr;   // per-column max |R| for small batches (64 entries)
   int64_t wpart_slots = 0;
   std::vector<SplitPlan> plans;
   uint64_t use_clock = 0;
@@ -157,10 +156,8 @@ cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64
                                cudaStream_t st);
 cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, const double* qrow,
                              __nv_bfloat16* op, cudaStream_t st);
-// colmax (device, >= 64 unsigned) enables the many-blocks-per-column version for K <= 64
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8,
-                            int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st,
-                            unsigned* colmax = nullptr);
+                            int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st);
 
 // tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,

@@ -128,6 +128,20 @@ td_status td_factor(td_segment* s, void* stream);
  */
 td_status td_segment_release_fp64(td_segment* s);
 
+/*
+ * td_factor_many -- factor several segments.  flags = 0: td_factor on each.
+ * flags = TD_FACTOR_NO_FP64: keep only what the tensor-core paths need; every
+ * gap-free segment then gets its whitening operator in O(N^2) by the
+ * Levinson-Durbin recursion (rows of L^{-1} are the normalised
+ * prediction-error filters; Sec. II.B item 6 names Levinson and Durbin),
+ * one CTA per segment, all in one launch, and log det C = sum log v_t;
+ * segments with gaps use td_factor and then release their FP64 factor.
+ * The FP64 path of such segments returns TD_ERR_UNSUPPORTED.  Synchronises
+ * `stream`; TD_ERR_NOT_PD as td_factor (td_last_pivot gives the order).
+ */
+#define TD_FACTOR_NO_FP64 1
+td_status td_factor_many(td_segment* const* segs, int nseg, int flags, void* stream);
+
 /* log det C_kept (host scalar).  Requires a successful td_factor. */
 td_status td_logdet(const td_segment* s, double* out);
 

@@ -165,6 +165,14 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   Scratch& sc = s->scr;
   ++sc.use_clock;
   const int key_bn = nc > 0 ? -nc : bn;
+  // an operator that was freed and rebuilt or reloaded (re-factor, eviction)
+  // sits at a new address: plans encoded for the old one are dropped
+  for (const SplitPlan& p : sc.plans)
+    if (p.op != (const void*)s->op || p.logdet != s->logdet) {
+      cudaStreamSynchronize(st);
+      free_plans(sc);
+      break;
+    }
   for (SplitPlan& p : sc.plans)
     if (p.K == K && p.nsl == nsl && p.bn == key_bn) {
       p.last_use = sc.use_clock;
@@ -205,6 +213,8 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   p.n_items = (int)items.size();
   p.n_units = (int)units.size();
   p.n_slots = n_slots;
+  p.op = s->op;
+  p.logdet = s->logdet;
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
   const int a_rows = nc > 0 ? nc : (int)std::min<int64_t>(TC_COLS, round_up(K, 8));

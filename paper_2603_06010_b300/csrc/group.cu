@@ -102,6 +102,7 @@ struct td_group {
   int64_t total_cols = 0;
   int64_t maxK = 0;
   std::vector<td_segment*> segs;
+  std::vector<const void*> ops;   // each segment's operator when the tensor maps were encoded
   std::vector<TcSegDev> host_seg;
   std::vector<RsJob> host_jobs;
   // device
@@ -204,6 +205,17 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
     return fail(TD_ERR_CUDA, "upload of group work lists failed");
   g->n_items = (int)items.size();
   g->n_units = (int)units.size();
+  g->ops.clear();
+  for (td_segment* sp : g->segs) g->ops.push_back(sp->op);
+  return TD_OK;
+}
+
+// The tensor maps hold operator addresses: a segment re-factored (or its
+// operator freed and rebuilt) after the group was built makes the group stale.
+static td_status group_check_current(const td_group* g) {
+  for (size_t i = 0; i < g->segs.size(); ++i)
+    if (i >= g->ops.size() || g->segs[i]->op != g->ops[i] || !g->segs[i]->factored)
+      return fail(TD_ERR_INVALID, "a segment of the group was re-factored since the group was built");
   return TD_OK;
 }
 
@@ -342,11 +354,14 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
 
 td_status td_group_launch(td_group* g, void* stream) {
   if (!g) return fail(TD_ERR_INVALID, "group is NULL");
+  td_status r = group_check_current(g);
+  if (r != TD_OK) return r;
   return group_launch_impl(g, reinterpret_cast<cudaStream_t>(stream));
 }
 
 td_status td_group_graph_launch(td_group* g, void* stream) {
   if (!g) return fail(TD_ERR_INVALID, "group is NULL");
+  if (td_status rc = group_check_current(g); rc != TD_OK) return rc;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   if (!g->graph) {
     cudaStream_t cap;

@@ -240,14 +240,26 @@ static void completion_loop(td_server* srv) {
     for (size_t k = 0; k < srv->inflight_order.size();) {
       const int slot = srv->inflight_order[k];
       Slot& sl = srv->slots[(size_t)slot];
-      if (cudaEventQuery(sl.done) != cudaSuccess) {
+      const cudaError_t q = cudaEventQuery(sl.done);
+      if (q == cudaErrorNotReady) {
         ++k;
         continue;
+      }
+      // any other error: the batch is lost and its requests fail (no waiter is left hanging)
+      const bool ok = (q == cudaSuccess);
+      if (!ok) {
+        srv->failed += (int64_t)sl.tickets.size();
+        srv->last_err = cuda_fail(q, "server batch");
       }
       const Clock::time_point now = Clock::now();
       int64_t cols = 0;
       for (int64_t t : sl.tickets) {
         Request& r = srv->reqs[t];
+        if (!ok) {
+          r.state = 4;
+          cols += r.K;
+          continue;
+        }
         r.state = 2;
         cols += r.K;
         srv->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r.t_submit).count());
@@ -256,8 +268,10 @@ static void completion_loop(td_server* srv) {
           srv->any_done = true;
         }
       }
-      srv->t_last = now;
-      srv->evals += cols;
+      if (ok) {
+        srv->t_last = now;
+        srv->evals += cols;
+      }
       srv->pending_cols -= cols;
       srv->segs[(size_t)sl.seg].inflight--;
       sl.busy = false;

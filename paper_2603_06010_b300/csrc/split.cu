@@ -50,9 +50,45 @@ __global__ void k_row_quantum(const double* __restrict__ Linv, int64_t ld, int64
   }
 }
 
+// The same quantum for an operator stored row-major (row i at Linv + i ld):
+// one warp per row, lanes on consecutive columns.  The maximum and the sum of
+// integers are exact in any order, so both layouts give the same q_i.
+__global__ void k_row_quantum_rm(const double* __restrict__ Linv, int64_t ld, int64_t nk, int64_t nkp,
+                                 double* __restrict__ qrow) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < nkp; i += nw) {
+    const double* row = Linv + i * ld;
+    const int64_t jmax = (i < nk) ? i : -1;
+    double mx = 0.0;
+    for (int64_t j = lane; j <= jmax; j += 32) mx = fmax(mx, fabs(row[j]));
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    double q = 1.0;
+    if (mx > 0.0) {
+      q = ldexp(1.0, (int)ceil(log2(mx / 255.0)));
+      if (mx / q > 255.0) q *= 2.0;
+      for (int it = 0; it < 64; ++it) {
+        double l1 = 0.0;
+        for (int64_t j = lane; j <= jmax; j += 32) l1 += fabs(rint(row[j] / q));
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
+        if (l1 <= 65536.0) break;
+        q *= 2.0;
+      }
+    }
+    if (lane == 0) qrow[i] = q;
+  }
+}
+
 cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, double* qrow,
-                               cudaStream_t st) {
-  k_row_quantum<<<(unsigned)ceil_div(nkp, 128), 128, 0, st>>>(Linv, ld, nk, nkp, qrow);
+                               cudaStream_t st, bool row_major) {
+  if (row_major) {
+    const int64_t blocks = ceil_div(nkp, 8);
+    k_row_quantum_rm<<<(unsigned)(blocks < 65535 * 4 ? blocks : 65535 * 4), 256, 0, st>>>(Linv, ld, nk, nkp, qrow);
+  } else {
+    k_row_quantum<<<(unsigned)ceil_div(nkp, 128), 128, 0, st>>>(Linv, ld, nk, nkp, qrow);
+  }
   return cudaGetLastError();
 }
 
@@ -64,6 +100,7 @@ __device__ __forceinline__ void split4_fixed_f64(double x, double q, __nv_bfloat
   split3_f64(x - hi, s[1], s[2], s[3]);
 }
 
+template <bool RM>
 __global__ void __launch_bounds__(256) k_op_slices(const double* __restrict__ Linv, int64_t ld, int64_t nk,
                                                     const double* __restrict__ qrow,
                                                     __nv_bfloat16* __restrict__ op) {
@@ -77,7 +114,7 @@ __global__ void __launch_bounds__(256) k_op_slices(const double* __restrict__ Li
 #pragma unroll 4
   for (int c = 0; c < OP_KB; ++c) {
     const int64_t j = (int64_t)kb * OP_KB + c;
-    const double x = (i < nk && j < nk && j <= i) ? Linv[i + j * ld] : 0.0;
+    const double x = (i < nk && j < nk && j <= i) ? Linv[RM ? i * ld + j : i + j * ld] : 0.0;
     __nv_bfloat16 s4[4];
     split4_fixed_f64(x, q, s4);
 #pragma unroll
@@ -94,10 +131,13 @@ __global__ void __launch_bounds__(256) k_op_slices(const double* __restrict__ Li
 }
 
 cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, const double* qrow,
-                             __nv_bfloat16* op, cudaStream_t st) {
+                             __nv_bfloat16* op, cudaStream_t st, bool row_major) {
   const int nm = (int)(nkp / OP_ROWS);
   dim3 grid((OP_ROWS / OP_KB) * nm, nm);
-  k_op_slices<<<grid, OP_ROWS, 0, st>>>(Linv, ld, nk, qrow, op);
+  if (row_major)
+    k_op_slices<true><<<grid, OP_ROWS, 0, st>>>(Linv, ld, nk, qrow, op);
+  else
+    k_op_slices<false><<<grid, OP_ROWS, 0, st>>>(Linv, ld, nk, qrow, op);
   return cudaGetLastError();
 }
 

@@ -71,6 +71,8 @@ struct SplitPlan {           // device work lists for one batch width (split mod
   int n_units = 0;
   int n_slots = 0;
   TcSegDev* segdev = nullptr;
+  const void* op = nullptr;   // operator the tensor maps in segdev were encoded for
+  double logdet = 0.0;        // and the log det copied into it
   uint64_t last_use = 0;
 };
 
@@ -152,10 +154,11 @@ cudaError_t launch_trsm_f64_row(const double* L, int64_t ld, const double* dinv,
 cudaError_t launch_finalize(const double* partials, int64_t ldp, int nparts, int64_t K, double logdet,
                             int64_t nk, double* logL, double* chi2, cudaStream_t st);
 
+// Linv element (i, j) at Linv[i + j ld] (column-major) or Linv[i ld + j] (row_major)
 cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, double* qrow,
-                               cudaStream_t st);
+                               cudaStream_t st, bool row_major = false);
 cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, const double* qrow,
-                             __nv_bfloat16* op, cudaStream_t st);
+                             __nv_bfloat16* op, cudaStream_t st, bool row_major = false);
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8,
                             int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st);
 

@@ -52,6 +52,7 @@ SIGNATURES = {
     "td_group_shape": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "td_group_destroy": (None, [_vp]),
     "td_segment_release_fp64": (_c.c_int, [_vp]),
+    "td_factor_many": (_c.c_int, [_vp, _c.c_int, _c.c_int, _vp]),
     "td_server_config_default": (None, [_vp]),
     "td_server_create": (_c.c_int, [_vp, _c.POINTER(_vp)]),
     "td_server_add_segment": (_c.c_int, [_vp, _vp, _i64, _vp, _c.POINTER(_i64)]),
@@ -221,6 +222,17 @@ class Segment:
             self.close()
         except Exception:
             pass
+
+
+TD_FACTOR_NO_FP64 = 1
+
+
+def factor_many(segments, flags: int = TD_FACTOR_NO_FP64, stream=None):
+    """td_factor_many: factor segments created with factor=False (gap-free ones
+    by the O(N^2) Levinson-Durbin operator build when flags has NO_FP64)."""
+    n = len(segments)
+    H = (ctypes.c_void_p * n)(*[s.handle.value for s in segments])
+    _check(lib().td_factor_many(H, n, int(flags), _stream_ptr(stream)))
 
 
 def loglike_grouped(segments, Rs, logLs, opt: TdOptions | None = None, stream=None):

@@ -1,9 +1,13 @@
 """Write tests/golden/full_size.json: oracle logdet / chi2 / logL for sampled
 columns of the full-size workloads (one N=1024 segment; the gap-free N=8192
-batch of K=4096; the gapped three-detector N=16384 batch of K=1024).
+batch of K=4096; the gapped three-detector N=16384 batch of K=1024; the
+longest segment, N=32257, of the 64-segment mix).
 
 Calls only the CPU oracle and the seeded input generators.  Run from the
-repository root:  python tests/golden/make_golden.py
+repository root:  python tests/golden/make_golden.py [key ...]
+(with keys, only those entries are recomputed and the others kept).
+The N=32257 entry was written with OPENBLAS_NUM_THREADS=1: the threaded
+OpenBLAS Cholesky of this host crashed at that size (about 4 min single-threaded).
 """
 import json
 import os
@@ -38,22 +42,50 @@ def one(n, fs, seed, K, rseed, cols, n_gaps=0, gap_len=512, scale=1.0):
                 r_checksum=[float(np.sum(sub[i].astype(np.float64))) for i in range(len(cols))])
 
 
+def cfg4_largest():
+    """Longest segment of the 64-segment mix, coloured-noise residuals of its own PSD."""
+    specs = inputs.cfg4_segments()
+    i = max(range(len(specs)), key=lambda j: specs[j]["n"])
+    sp = specs[i]
+    rseed = sp["seed"] + 7
+    acf = inputs.acf_from_psd(sp["n"], sp["fs"], a=sp["a"], floor=sp["floor"])
+    R = inputs.noise_residuals(sp["n"], sp["fs"], sp["K"], rseed, a=sp["a"], floor=sp["floor"])
+    cols = sample_cols(sp["K"], [0, 1, 2, 100, sp["K"] // 2, sp["K"] - 1])
+    osg = oracle.OracleSegment(acf)
+    sub = R[cols]
+    chi = osg.chi2(sub)
+    ll = oracle.loglike_from_chi2(chi, osg.logdet, osg.n_kept)
+    return dict(index=i, n=sp["n"], fs=sp["fs"], a=sp["a"], floor=sp["floor"], K=sp["K"], rseed=rseed,
+                columns=cols, logdet=osg.logdet, chi2=chi.tolist(), logL=ll.tolist(),
+                r_checksum=[float(np.sum(sub[j].astype(np.float64))) for j in range(len(cols))])
+
+
 def main():
     t0 = time.time()
+    keys = sys.argv[1:]
     out = {}
-    c1 = inputs.CFG1
-    out["cfg1"] = one(c1["n"], c1["fs"], c1["seed"], 1, c1["seed"] + 1, [0])
-    c2 = inputs.CFG2
-    cols2 = sample_cols(c2["K"], [0, 1, 2, 3, 127, 128, 129, 1000, 2047, 2048, 3001, 4094, 4095])
-    out["cfg2"] = one(c2["n"], c2["fs"], c2["seed"], c2["K"], c2["seed"] + 1, cols2)
-    c3 = inputs.CFG3
-    cols3 = sample_cols(c3["K"], [0, 1, 100, 511, 512, 1022, 1023])
-    dets = []
-    for d, sc in enumerate(c3["scales"]):
-        dets.append(one(c3["n"], c3["fs"], c3["seed"] + 10 * d, c3["K"], c3["seed"] + 10 * d + 1, cols3,
-                        n_gaps=c3["n_gaps"], gap_len=c3["gap_len"], scale=sc))
-    out["cfg3"] = dict(detectors=dets, columns=cols3,
-                       joint_logL=np.sum([d_["logL"] for d_ in dets], axis=0).tolist())
+    if keys and os.path.exists(OUT):
+        with open(OUT) as f:
+            out = json.load(f)
+    want = (lambda k: not keys or k in keys)
+    if want("cfg1"):
+        c1 = inputs.CFG1
+        out["cfg1"] = one(c1["n"], c1["fs"], c1["seed"], 1, c1["seed"] + 1, [0])
+    if want("cfg2"):
+        c2 = inputs.CFG2
+        cols2 = sample_cols(c2["K"], [0, 1, 2, 3, 127, 128, 129, 1000, 2047, 2048, 3001, 4094, 4095])
+        out["cfg2"] = one(c2["n"], c2["fs"], c2["seed"], c2["K"], c2["seed"] + 1, cols2)
+    if want("cfg3"):
+        c3 = inputs.CFG3
+        cols3 = sample_cols(c3["K"], [0, 1, 100, 511, 512, 1022, 1023])
+        dets = []
+        for d, sc in enumerate(c3["scales"]):
+            dets.append(one(c3["n"], c3["fs"], c3["seed"] + 10 * d, c3["K"], c3["seed"] + 10 * d + 1, cols3,
+                            n_gaps=c3["n_gaps"], gap_len=c3["gap_len"], scale=sc))
+        out["cfg3"] = dict(detectors=dets, columns=cols3,
+                           joint_logL=np.sum([d_["logL"] for d_ in dets], axis=0).tolist())
+    if want("cfg4_largest"):
+        out["cfg4_largest"] = cfg4_largest()
     with open(OUT, "w") as f:
         json.dump(out, f, indent=1)
     print(f"wrote {OUT} in {time.time() - t0:.1f} s")

@@ -157,7 +157,19 @@ static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaSt
   return TD_OK;
 }
 
-// device work lists for a 64-row-tile batch of K columns (cached per K)
+// Width of the cached plan that serves a batch of K columns: plans are keyed
+// by width, not by K, so a server whose batch sizes vary does not rebuild
+// them.  Columns in [K, width) are computed on stale slice rows and dropped
+// (the residual slices and partials hold capK >= width columns); a column's
+// own arithmetic does not depend on the width.
+static int64_t plan_width(int64_t K) {
+  if (K > TC_COLS) return round_up(K, TC_COLS);
+  int64_t w = 8;
+  while (w < K) w <<= 1;
+  return w;
+}
+
+// device work lists for a 64-row-tile batch of K columns (cached per width)
 // nc > 0: plan for the small-batch kernel (128-row operator tiles as the MMA
 // M dimension, nc residual columns per tile, chi2 partials per 32 rows).
 static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaStream_t st, SplitPlan** out,
@@ -195,7 +207,7 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
     if ((r = dev_alloc(&sc.wpart, (size_t)(n_slots * slot_elems), "split accumulators")) != TD_OK) return r;
     sc.wpart_slots = n_slots * slot_elems;
   }
-  if (sc.plans.size() >= 8) {   // evict the least recently used plan
+  if (sc.plans.size() >= 24) {   // evict the least recently used plan
     size_t lru = 0;
     for (size_t i = 1; i < sc.plans.size(); ++i)
       if (sc.plans[i].last_use < sc.plans[lru].last_use) lru = i;
@@ -473,7 +485,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     if (K > 32) return fail(TD_ERR_UNSUPPORTED, "the small-batch path takes K <= 32");
     const int ncs = K <= 16 ? 16 : 32;
     SplitPlan* plan = nullptr;
-    if ((r = get_split_plan(s, K, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
+    if ((r = get_split_plan(s, ncs, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
     if (pm) prof_mark(s, st, true);
     TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, st));
     TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, 128, st, 32));
@@ -484,7 +496,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   }
   if (shape.split) {
     SplitPlan* plan = nullptr;
-    if ((r = get_split_plan(s, K, nsl, bn, st, &plan)) != TD_OK) return r;
+    if ((r = get_split_plan(s, plan_width(K), nsl, bn, st, &plan)) != TD_OK) return r;
     if (pm) prof_mark(s, st, true);
     TD_CUDA(launch_tc_cdo(plan->items, plan->n_items, plan->segdev, nsl, bn, true, s->status, o.wait_limit_ns,
                           st));

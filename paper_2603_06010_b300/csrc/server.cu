@@ -127,9 +127,10 @@ static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st) 
     seg_evict(srv, srv->segs[(size_t)victim]);
   }
   if (!e.s->factored) {
-    td_status r = td_factor(e.s, st);
+    // gap-free: O(N^2) Levinson-Durbin operator; gapped: Cholesky, FP64 factor then released
+    td_segment* one = e.s;
+    td_status r = td_factor_many(&one, 1, TD_FACTOR_NO_FP64, st);
     if (r != TD_OK) return r;
-    td_segment_release_fp64(e.s);
   } else {
     void* p = nullptr;
     if (cudaMalloc(&p, e.op_bytes) != cudaSuccess) {
@@ -139,6 +140,9 @@ static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st) 
     e.s->op = reinterpret_cast<__nv_bfloat16*>(p);
     TD_CUDA(cudaMemcpyAsync(e.s->op, e.host_op, e.op_bytes, cudaMemcpyHostToDevice, st));
   }
+  // scratch for the widest batch up front: no regrowth (and plan rebuild) while serving
+  td_status rr = td_reserve(e.s, srv->cfg.max_batch_cols, nullptr);
+  if (rr != TD_OK) return rr;
   e.resident = true;
   srv->resident_bytes += e.op_bytes;
   return TD_OK;

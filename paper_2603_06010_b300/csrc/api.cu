@@ -130,6 +130,7 @@ static void free_plans(Scratch& sc) {
     dev_free(p.items);
     dev_free(p.units);
     dev_free(p.segdev);
+    dev_free(p.counters);
   }
   sc.plans.clear();
 }
@@ -215,6 +216,7 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
     dev_free(sc.plans[lru].items);
     dev_free(sc.plans[lru].units);
     dev_free(sc.plans[lru].segdev);
+    dev_free(sc.plans[lru].counters);
     sc.plans.erase(sc.plans.begin() + (long)lru);
   }
   SplitPlan p;
@@ -235,17 +237,20 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   seg.wpart = sc.wpart;
   seg.nk = (int)s->nk;
   seg.K = (int)K;
-  seg.ldp = nc > 0 ? (int)(sc.capK / 2) : (int)sc.capK;     // small: the buffer as [N'p/32][capK/2]
-  seg.nm = nc > 0 ? (int)(s->nkp / 32) : (int)(s->nkp / 64);
+  seg.ldp = nc > 0 ? (int)(sc.capK / 2) : (int)sc.capK;     // small: the buffer as [N'p/128][capK/2]
+  seg.nm = nc > 0 ? (int)(s->nkp / 128) : (int)(s->nkp / 64);   // partials: per 128-row tile (small) or 64 rows
   seg.logdet = s->logdet;
   if ((r = dev_alloc(&p.items, items.size(), "work items")) != TD_OK ||
-      (r = dev_alloc(&p.units, units.size(), "split units")) != TD_OK ||
-      (r = dev_alloc(&p.segdev, 1, "segment descriptor")) != TD_OK) {
+      (r = dev_alloc(&p.units, std::max<size_t>(1, units.size()), "split units")) != TD_OK ||
+      (r = dev_alloc(&p.segdev, 1, "segment descriptor")) != TD_OK ||
+      (nc > 0 && (r = dev_alloc(&p.counters, units.size() + 1, "completion counters")) != TD_OK)) {
     dev_free(p.items);
     dev_free(p.units);
     dev_free(p.segdev);
+    dev_free(p.counters);
     return r;
   }
+  if (p.counters) TD_CUDA(cudaMemset(p.counters, 0, (units.size() + 1) * sizeof(int)));
   TD_CUDA(cudaMemcpy(p.items, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice));
   if (!units.empty())
     TD_CUDA(cudaMemcpy(p.units, units.data(), units.size() * sizeof(SplitUnit), cudaMemcpyHostToDevice));
@@ -476,7 +481,6 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   const int nsl = nslices_for(o.precision);
   const Shape shape = choose_shape(s, K, o.path);
   const int bn = shape.bn;
-  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   const int ngroups = (int)(s->nkp / 64);
   const int nc = (int)ceil_div(K, TC_COLS);
   const int nkb_max = (int)ceil_div(s->nk, OP_KB);
@@ -486,14 +490,17 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     const int ncs = K <= 16 ? 16 : 32;
     SplitPlan* plan = nullptr;
     if ((r = get_split_plan(s, ncs, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
+    // two launches: the slicing (which also clears the plan's counters) and the
+    // product with the chunk reduction and logL fused in
+    TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st, plan->counters, plan->n_units + 1));
     if (pm) prof_mark(s, st, true);
-    TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, st));
-    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, 128, st, 32));
+    const SmallFinal fin{plan->units, plan->counters, plan->n_units, (int)K, logL, chi2};
+    TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, fin, st));
     if (pm) prof_mark(s, st, false);
-    TD_CUDA(launch_finalize(sc.partials, sc.capK / 2, (int)(s->nkp / 32), K, s->logdet, s->nk, logL, chi2, st));
-    s->prof_kernels += plan->n_units > 0 ? 4 : 3;
+    s->prof_kernels += 2;
     return TD_OK;
   }
+  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   if (shape.split) {
     SplitPlan* plan = nullptr;
     if ((r = get_split_plan(s, plan_width(K), nsl, bn, st, &plan)) != TD_OK) return r;

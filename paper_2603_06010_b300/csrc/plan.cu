@@ -36,13 +36,16 @@ void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int
       const int nkb = std::min(per * (m + 1), nkb_max);
       const int nch = (nkb + S - 1) / S;
       if (nch <= 1) {
-        items.push_back(TcItem{seg, m, c, nkb, 0, -1});
+        items.push_back(TcItem{seg, m, c, nkb, 0, -1, -1});
         continue;
       }
+      // chunks of exactly S k-blocks and one shorter remainder: the remainders
+      // fill the gaps of the longest-first schedule
+      const int unit = (int)units.size();
       units.push_back(SplitUnit{seg, m, c, n_slots, nch, 0});
       for (int ch = 0; ch < nch; ++ch) {
         const int kb0 = ch * S;
-        items.push_back(TcItem{seg, m, c, std::min(S, nkb - kb0), kb0, n_slots++});
+        items.push_back(TcItem{seg, m, c, std::min(S, nkb - kb0), kb0, n_slots++, unit});
       }
     }
   }

@@ -16,7 +16,11 @@
 // Residuals: float32 R (N' x K, column-major) -> four bf16 slices laid out
 // [slice][k][j] (j contiguous, row stride nkp8): the tensor-core A operand.
 // The four slices hold each float32 exactly.
+#include <cooperative_groups.h>
+
 #include "td_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace td {
 
@@ -141,50 +145,107 @@ cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t
   return cudaGetLastError();
 }
 
-// Residual slices, one CTA per column: the column's power-of-two quantum
-// p_k (max_j |R_jk| <= 255 p_k), then R = p_k b0 + r with r in up to three
+// Residual slices: the column's power-of-two quantum p_k
+// (max_j |R_jk| <= 255 p_k), then R = p_k b0 + r with r in up to three
 // floating bf16 slices (all four slices hold a float32 exactly).
+__device__ __forceinline__ float r_quantum(float mx) {
+  float p = 1.f;
+  if (mx > 0.f) {
+    p = exp2f(ceilf(log2f(mx / 255.f)));
+    if (mx / p > 255.f) p *= 2.f;
+  }
+  return p;
+}
+
+__device__ __forceinline__ void r_slice_rows(const float* __restrict__ col, int64_t j0, int64_t j1, float p,
+                                             __nv_bfloat16* __restrict__ dst, int64_t slice_stride, int nslices) {
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+    const float x = col[j];
+    const float hi = p * rintf(x / p);
+    __nv_bfloat16 a, b, c;
+    split3_f32(x - hi, a, b, c);
+    dst[j] = __float2bfloat16_rn(hi);
+    dst[j + slice_stride] = a;
+    if (nslices > 2) dst[j + 2 * slice_stride] = b;
+    if (nslices > 3) dst[j + 3 * slice_stride] = c;
+  }
+}
+
+__device__ __forceinline__ float block_max256(float mx, float* red) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = red[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
+  __syncthreads();
+  return mx;
+}
+
+// The dependent kernel (the tensor-core product) may start streaming the
+// operator while this one runs; it waits for this grid before reading rs.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// one CTA per column (large batches)
 __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t K,
                                                    int64_t nkp8, int64_t capK, __nv_bfloat16* __restrict__ rs,
-                                                   int nslices) {
+                                                   int nslices, int* __restrict__ zero, int nzero) {
   __shared__ float red[8];
+  pdl_launch_dependents();
+  if (zero && blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0;
   const int64_t slice_stride = capK * nkp8;
   for (int64_t k = blockIdx.x; k < K; k += gridDim.x) {
     const float* col = R + k * ldr;
     float mx = 0.f;
     for (int64_t j = threadIdx.x; j < nk; j += blockDim.x) mx = fmaxf(mx, fabsf(col[j]));
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    mx = red[0];
-#pragma unroll
-    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
-    __syncthreads();
-    float p = 1.f;
-    if (mx > 0.f) {
-      p = exp2f(ceilf(log2f(mx / 255.f)));
-      if (mx / p > 255.f) p *= 2.f;
-    }
-    __nv_bfloat16* dst = rs + k * nkp8;
-    for (int64_t j = threadIdx.x; j < nk; j += blockDim.x) {
-      const float x = col[j];
-      const float hi = p * rintf(x / p);
-      __nv_bfloat16 a, b, c;
-      split3_f32(x - hi, a, b, c);
-      dst[j] = __float2bfloat16_rn(hi);
-      dst[j + slice_stride] = a;
-      if (nslices > 2) dst[j + 2 * slice_stride] = b;
-      if (nslices > 3) dst[j + 3 * slice_stride] = c;
-    }
+    const float p = r_quantum(block_max256(mx, red));
+    r_slice_rows(col, 0, nk, p, rs + k * nkp8, slice_stride, nslices);
   }
 }
 
+// a cluster of RS_CL CTAs per column (small batches: more SMs on the few
+// columns); the column maximum is combined through distributed shared memory.
+// The maximum is exact in any order, so p_k equals the one-CTA kernel's.
+constexpr int RS_CL = 8;
+__global__ void __cluster_dims__(RS_CL, 1, 1) __launch_bounds__(256)
+    k_r_slices_cl(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8, int64_t capK,
+                  __nv_bfloat16* __restrict__ rs, int nslices, int* __restrict__ zero, int nzero) {
+  __shared__ float red[8];
+  __shared__ float cmax;
+  pdl_launch_dependents();
+  if (zero && blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0;
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const int64_t k = blockIdx.x / RS_CL;
+  const int64_t per = (nk + RS_CL - 1) / RS_CL;
+  const int64_t j0 = rank * per, j1 = (j0 + per < nk) ? j0 + per : nk;
+  const float* col = R + k * ldr;
+  float mx = 0.f;
+  for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) mx = fmaxf(mx, fabsf(col[j]));
+  mx = block_max256(mx, red);
+  if (threadIdx.x == 0) cmax = mx;
+  cl.sync();
+  float g = 0.f;
+#pragma unroll
+  for (int r = 0; r < RS_CL; ++r) g = fmaxf(g, *cl.map_shared_rank(&cmax, r));
+  cl.sync();   // every CTA has read its peers' maxima before any of them exits
+  r_slice_rows(col, j0, j1, r_quantum(g), rs + k * nkp8, capK * nkp8, nslices);
+}
+
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8, int64_t capK,
-                            __nv_bfloat16* rs, int nslices, cudaStream_t st) {
+                            __nv_bfloat16* rs, int nslices, cudaStream_t st, int* zero, int nzero) {
   if (K <= 0) return cudaSuccess;
-  const int grid = (int)(K < 4096 ? K : 4096);
-  k_r_slices<<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
+  if (K <= 256) {
+    k_r_slices_cl<<<(unsigned)(K * RS_CL), 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
+  } else {
+    const int grid = (int)(K < 4096 ? K : 4096);
+    k_r_slices<<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
+  }
   return cudaGetLastError();
 }
 

@@ -481,7 +481,7 @@ __global__ void k_tc_finalize(const TcSegDev* __restrict__ segs) {
     for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
     if (lane == 0) {
       if (sd.chi2) sd.chi2[col] = s;
-      sd.logL[col] = -0.5 * s - 0.5 * sd.logdet - 0.5 * (double)sd.nk * 1.8378770664093454836;
+      sd.logL[col] = -0.5 * s - 0.5 * sd.logdet - 0.5 * (double)sd.nk * LOG2PI;
     }
   }
 }

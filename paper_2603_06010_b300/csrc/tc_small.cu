@@ -9,12 +9,20 @@
 // 24 KB (three slices) and the MMA work is tiny, so the kernel streams the
 // packed operator from HBM once.  Long rows are cut into balanced k-chunks;
 // a chunk stores its accumulator pair (exact hi*hi sum, corrections) for
-// k_split_reduce, a whole row reduces chi2 here: w = hi + corrections in
+// k_small_reduce; a whole row reduces chi2 directly: w = hi + corrections in
 // double-float, exact squares, a fixed shuffle tree over the 32 rows of a
-// warp -> one FP64 partial per 32-row group (this path's partial layout).
+// warp, then the four warps in a fixed order -> one FP64 partial per
+// 128-row tile and column.
+//
+// Three launches per call, chained as programmatic dependents so no launch
+// gap is exposed: the residual slicing; this kernel, whose producer streams
+// the first operator stages before it waits for the slices; k_small_reduce,
+// which adds the chunks of each split row tile (chunk order fixed) and whose
+// last CTA sums each column's partials in a fixed order into chi2 and logL.
 //
 // Warp roles as in the main kernel: warp 0 lane 0 TMA producer, warp 1
-// TMEM owner and MMA issuer, warps 2..5 epilogue.  Every wait is bounded.
+// TMEM owner and MMA issuer, warps 2..5 epilogue.  Every wait is bounded;
+// the completion counter is an arrival count only (no thread waits on it).
 #include "td_internal.h"
 
 namespace td {
@@ -66,6 +74,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }   // warps 2..5
+
 template <int NSL, int NC>
 __global__ void __launch_bounds__(tsm::THREADS, 1)
     k_tc_small(const TcItem* __restrict__ items, int n_items, const TcSegDev* __restrict__ segs,
@@ -86,8 +98,11 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
   uint64_t* fin = tempty + NBUF;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  __shared__ int sh_ok[4];
+  __shared__ double sh_part[4][NC];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  pdl_trigger();   // the reduction kernel may be scheduled now; it waits for this grid
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -116,6 +131,24 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       uint32_t issued_mask = 0, issued_phase = 0;
+      // the operator does not depend on the preceding launch: the first stages
+      // stream it while the residual slices are still being written
+      bool dep = false;
+      int pend_n = 0;
+      int pend_stage[STAGES], pend_kb[STAGES], pend_c[STAGES];
+      const TcSegDev* pend_sd[STAGES];
+      auto flush = [&]() {
+        pdl_wait();
+        dep = true;
+        for (int i = 0; i < pend_n; ++i) {
+          uint8_t* sb = smem + pend_stage[i] * STAGE + A_STAGE;
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl)
+            tma_load_3d(sb + sl * B_SLICE, &pend_sd[i]->mapA, &full[pend_stage[i]], pend_kb[i] * BK,
+                        pend_c[i] * NC, sl);
+        }
+        pend_n = 0;
+      };
       for (int r = 0; (int64_t)r * G < n_items && !*abort_flag; ++r) {
         const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
         if (idx >= n_items) continue;
@@ -137,9 +170,17 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
           uint8_t* sb = sa + A_STAGE;            // residual slices (B)
           mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (A_SLICE + B_SLICE)));
           tma_load_3d(sa, &sd->mapB, &full[stage], 0, yoff, (blk0 + kb) * OP_SLICES);
+          if (dep) {
 #pragma unroll
-          for (int sl = 0; sl < NSL; ++sl)
-            tma_load_3d(sb + sl * B_SLICE, &sd->mapA, &full[stage], kb * BK, it.c * NC, sl);
+            for (int sl = 0; sl < NSL; ++sl)
+              tma_load_3d(sb + sl * B_SLICE, &sd->mapA, &full[stage], kb * BK, it.c * NC, sl);
+          } else {
+            pend_stage[pend_n] = stage;
+            pend_kb[pend_n] = kb;
+            pend_c[pend_n] = it.c;
+            pend_sd[pend_n] = sd;
+            if (++pend_n == STAGES) flush();   // every stage is in use: nothing more can be issued first
+          }
           issued_mask |= 1u << stage;
           issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -149,6 +190,7 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
         }
         if (!ok) break;
       }
+      if (!dep) flush();
       for (int s = 0; s < STAGES; ++s)
         if (issued_mask & (1u << s)) mbar_wait(&full[s], (issued_phase >> s) & 1u, limit_ns);
     }
@@ -210,15 +252,21 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
   } else {
     const int q = warp & 3;          // TMEM lane quarter = rows 32q .. 32q+31 of the tile
     int tl = 0;
-    for (int r = 0; (int64_t)r * G < n_items && !*abort_flag; ++r) {
+    for (int r = 0; (int64_t)r * G < n_items; ++r) {
       const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
       if (idx >= n_items) continue;
       const TcItem it = items[idx];
       const TcSegDev* sd = &segs[it.seg];
       const int buf = tl % NBUF;
       const uint32_t use = (uint32_t)(tl / NBUF);
-      if (!mbar_wait(&tfull[buf], use & 1u, limit_ns)) {
-        if (lane == 0) set_status(status, ST_TIMEOUT, 43);
+      // all four warps take the same decision (they meet at named barriers below)
+      const bool got = mbar_wait(&tfull[buf], use & 1u, limit_ns);
+      if (lane == 0) sh_ok[q] = got ? 1 : 0;
+      epi_bar();
+      const bool all_ok = sh_ok[0] && sh_ok[1] && sh_ok[2] && sh_ok[3];
+      epi_bar();
+      if (!all_ok) {
+        if (lane == 0 && !got) set_status(status, ST_TIMEOUT, 43);
         *abort_flag = 1;
         break;
       }
@@ -239,10 +287,9 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
-      const int row = it.m * BM + q * 32 + lane;
       const int ncol = min(NC, sd->K - it.c * NC);
       if (it.slot >= 0) {
-        // accumulator pair for k_split_reduce: [slot][128 columns][128 rows]
+        // accumulator pair of this chunk: [slot][128 columns][128 rows]
         float2* dst = sd->wpart + (int64_t)it.slot * 128 * BM + q * 32 + lane;
 #pragma unroll
         for (int n = 0; n < NC; ++n)
@@ -260,11 +307,15 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
             ff_add(oh, hi, lo);
             lo += ol;
           }
-          if (lane == 0 && n < ncol)
-            sd->partials[((int64_t)it.m * 4 + q) * sd->ldp + it.c * NC + n] = (double)hi + (double)lo;
+          if (lane == 0) sh_part[q][n] = (double)hi + (double)lo;
         }
+        // the tile's four 32-row groups in a fixed order
+        epi_bar();
+        if (q == 0 && lane < ncol)
+          sd->partials[(int64_t)it.m * sd->ldp + it.c * NC + lane] =
+              ((sh_part[0][lane] + sh_part[1][lane]) + sh_part[2][lane]) + sh_part[3][lane];
+        epi_bar();
       }
-      (void)row;
       ++tl;
     }
   }
@@ -277,9 +328,110 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
   }
 }
 
+// Chunk reduction + chi2 / logL for the small-batch kernel.  Grid: (split
+// units, column groups of 4); 128 threads, one per row of the 128-row tile.
+// A thread adds its row's chunk pairs in chunk order (double-float, loads
+// issued 8 chunks x 4 columns ahead), squares exactly; a fixed shuffle tree
+// per 32 rows and the four groups in order give the tile's partial.  The
+// last CTA to finish sums each column's tile partials in a fixed order (one
+// lane per column, tiles in order within each quarter, quarters in order)
+// into chi2 and logL.
+__global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict__ segs, const SmallFinal fin) {
+  __shared__ int sh_last;
+  __shared__ double sh[4][32];
+  pdl_wait();   // the product kernel's pairs and partials are complete and visible
+  const TcSegDev* sd = &segs[0];
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  if (fin.n_units > 0) {
+    const SplitUnit u = fin.units[blockIdx.x];
+    const int n0 = blockIdx.y * 4;
+    const float2* base = sd->wpart + (int64_t)u.slot0 * 128 * 128 + threadIdx.x;
+    constexpr int CB = 4, CH = 8;
+    float wh[CB], wl[CB];
+#pragma unroll
+    for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
+    for (int ch0 = 0; ch0 < u.nchunk; ch0 += CH) {
+      float2 v[CH][CB];
+      // unconditional loads from clamped (in-range) addresses, selected after:
+      // all of them are in flight at once
+#pragma unroll
+      for (int i = 0; i < CH; ++i)
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          const int ch = min(ch0 + i, u.nchunk - 1), n = min(n0 + c, fin.K - 1);
+          v[i][c] = __ldcg(base + ((int64_t)ch * 128 + n) * 128);
+        }
+#pragma unroll
+      for (int i = 0; i < CH; ++i)
+        if (ch0 + i < u.nchunk) {
+#pragma unroll
+          for (int c = 0; c < CB; ++c) {
+            ff_add(v[i][c].x, wh[c], wl[c]);
+            ff_add(v[i][c].y, wh[c], wl[c]);
+          }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      float hi = 0.f, lo = 0.f;
+      ff_add_square2(wh[c], wl[c], hi, lo);
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+        ff_add(oh, hi, lo);
+        lo += ol;
+      }
+      if (lane == 0) sh[q][c] = (double)hi + (double)lo;
+    }
+    __syncthreads();
+    // the tile's four 32-row groups in a fixed order
+    if (threadIdx.x < CB && n0 + threadIdx.x < fin.K) {
+      const int c = threadIdx.x;
+      sd->partials[(int64_t)u.m * sd->ldp + u.c * 128 + n0 + c] = ((sh[0][c] + sh[1][c]) + sh[2][c]) + sh[3][c];
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) sh_last = (atomicAdd(&fin.counters[fin.n_units], 1) == (int)(gridDim.x * gridDim.y) - 1);
+    __syncthreads();
+    if (!sh_last) return;
+    __threadfence();
+  }
+  // chi2 and logL: lane = column (K <= 32, coalesced rows of partials); warp q
+  // adds the tiles of its quarter in order, then the four quarters in order
+  const int nparts = sd->nm;
+  const int per = (nparts + 3) / 4;
+  const int p0 = q * per, p1 = min(nparts, p0 + per);
+  const int col = min(lane, fin.K - 1);
+  double s = 0.0;
+#pragma unroll 8
+  for (int p = p0; p < p1; ++p) s += __ldcg(&sd->partials[(int64_t)p * sd->ldp + col]);
+  sh[q][lane] = s;
+  __syncthreads();
+  if (q == 0 && lane < fin.K) {
+    const double t = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
+    if (fin.chi2) fin.chi2[lane] = t;
+    fin.logL[lane] = -0.5 * t - 0.5 * sd->logdet - 0.5 * (double)sd->nk * LOG2PI;
+  }
+}
+
+static cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void** args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
 template <int NSL, int NC>
 static cudaError_t launch_small_impl(const TcItem* items, int n_items, const TcSegDev* segs, DevStatus* status,
-                                     int64_t lim, cudaStream_t st) {
+                                     int64_t lim, const SmallFinal& fin, cudaStream_t st) {
   using C = tsm::Cfg<NSL, NC>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -290,20 +442,25 @@ static cudaError_t launch_small_impl(const TcItem* items, int n_items, const TcS
   if (n_items <= 0) return cudaSuccess;
   int grid = tc_num_sms();
   if (grid > n_items) grid = n_items;
-  k_tc_small<NSL, NC><<<grid, tsm::THREADS, C::SMEM, st>>>(items, n_items, segs, status, (uint64_t)lim);
-  return cudaGetLastError();
+  uint64_t lim64 = (uint64_t)lim;
+  void* a1[] = {(void*)&items, (void*)&n_items, (void*)&segs, (void*)&status, (void*)&lim64};
+  cudaError_t e = launch_pdl((const void*)k_tc_small<NSL, NC>, dim3((unsigned)grid), dim3(tsm::THREADS), C::SMEM, st, a1);
+  if (e != cudaSuccess) return e;
+  const dim3 rgrid(fin.n_units > 0 ? (unsigned)fin.n_units : 1u, fin.n_units > 0 ? (unsigned)((fin.K + 3) / 4) : 1u);
+  void* a2[] = {(void*)&segs, (void*)&fin};
+  return launch_pdl((const void*)k_small_reduce, rgrid, dim3(128), 0, st, a2);
 }
 
 cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
-                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+                            DevStatus* status, int64_t wait_limit_ns, const SmallFinal& fin, cudaStream_t st) {
   if (nc == 16) {
-    if (nslices == 3) return launch_small_impl<3, 16>(items, n_items, segs, status, wait_limit_ns, st);
-    if (nslices == 4) return launch_small_impl<4, 16>(items, n_items, segs, status, wait_limit_ns, st);
-    if (nslices == 2) return launch_small_impl<2, 16>(items, n_items, segs, status, wait_limit_ns, st);
+    if (nslices == 3) return launch_small_impl<3, 16>(items, n_items, segs, status, wait_limit_ns, fin, st);
+    if (nslices == 4) return launch_small_impl<4, 16>(items, n_items, segs, status, wait_limit_ns, fin, st);
+    if (nslices == 2) return launch_small_impl<2, 16>(items, n_items, segs, status, wait_limit_ns, fin, st);
   } else if (nc == 32) {
-    if (nslices == 3) return launch_small_impl<3, 32>(items, n_items, segs, status, wait_limit_ns, st);
-    if (nslices == 4) return launch_small_impl<4, 32>(items, n_items, segs, status, wait_limit_ns, st);
-    if (nslices == 2) return launch_small_impl<2, 32>(items, n_items, segs, status, wait_limit_ns, st);
+    if (nslices == 3) return launch_small_impl<3, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
+    if (nslices == 4) return launch_small_impl<4, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
+    if (nslices == 2) return launch_small_impl<2, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
   }
   return cudaErrorInvalidValue;
 }

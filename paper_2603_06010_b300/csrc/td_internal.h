@@ -18,6 +18,7 @@ constexpr int OP_ROWS = 256;    // operator row tile (tensor-core N)
 constexpr int OP_KB = 32;       // operator k-block (64 B of bf16)
 constexpr int TC_COLS = 128;    // residual columns per tensor-core tile (MMA M)
 constexpr int OP_SLICES = 4;    // bf16 slices per operand element (fixed-point hi + 3 floating)
+constexpr double LOG2PI = 1.8378770664093454836;   // log(2 pi), the constant of logL
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }
@@ -32,6 +33,7 @@ struct TcItem {      // one tensor-core work item
   int nkb;           // k-blocks of 32 to accumulate
   int kb0;           // first k-block
   int slot;          // split mode: accumulator-pair slot this item writes
+  int unit;          // split mode: index of the SplitUnit the chunk belongs to
 };
 
 struct SplitUnit {   // one (segment, row tile, column tile) whose chunks are reduced together
@@ -71,6 +73,7 @@ struct SplitPlan {           // device work lists for one batch width (split mod
   int n_units = 0;
   int n_slots = 0;
   TcSegDev* segdev = nullptr;
+  int* counters = nullptr;    // small-batch plans: [n_units] chunk arrivals + 1 finished-CTA count
   const void* op = nullptr;   // operator the tensor maps in segdev were encoded for
   double logdet = 0.0;        // and the log det copied into it
   uint64_t last_use = 0;
@@ -159,8 +162,11 @@ cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64
                                cudaStream_t st, bool row_major = false);
 cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, const double* qrow,
                              __nv_bfloat16* op, cudaStream_t st, bool row_major = false);
+// zero / nzero: ints the launch clears first (the next small-batch kernel's counters).
+// The kernel lets a programmatic dependent launch start early.
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8,
-                            int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st);
+                            int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st, int* zero = nullptr,
+                            int nzero = 0);
 
 // tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
@@ -168,8 +174,19 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
 // part_rows: 64 (partials per 64-row group) or 32 (per 32-row group, the small-batch layout)
 cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn, cudaStream_t st,
                                 int part_rows = 64);
+// Small batches, one segment: the chunk reduction and the final chi2 / logL
+// run inside the kernel (the last chunk of a row tile, then the last CTA);
+// launched as a programmatic dependent of the residual slicing.
+struct SmallFinal {
+  const SplitUnit* units;
+  int* counters;     // [n_units] chunk arrivals, [n_units] finished CTAs; zero at launch
+  int n_units;
+  int K;             // columns of this call (the plan may be wider)
+  double* logL;
+  double* chi2;      // optional
+};
 cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
-                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
+                            DevStatus* status, int64_t wait_limit_ns, const SmallFinal& fin, cudaStream_t st);
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st);
 int tc_num_sms();

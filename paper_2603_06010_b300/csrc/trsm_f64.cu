@@ -11,7 +11,6 @@
 
 namespace td {
 
-constexpr double LOG2PI = 1.8378770664093454836;
 
 __global__ void __launch_bounds__(256) k_trsm_f64_row(const double* __restrict__ L, int64_t ld,
                                                        const double* __restrict__ dinv, int I,

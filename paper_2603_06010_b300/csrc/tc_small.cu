@@ -331,7 +331,7 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
 // Chunk reduction + chi2 / logL for the small-batch kernel.  Grid: (split
 // units, column groups of 4); 128 threads, one per row of the 128-row tile.
 // A thread adds its row's chunk pairs in chunk order (double-float, loads
-// issued 8 chunks x 4 columns ahead), squares exactly; a fixed shuffle tree
+// issued 16 chunks x 4 columns ahead), squares exactly; a fixed shuffle tree
 // per 32 rows and the four groups in order give the tile's partial.  The
 // last CTA to finish sums each column's tile partials in a fixed order (one
 // lane per column, tiles in order within each quarter, quarters in order)
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict
     const SplitUnit u = fin.units[blockIdx.x];
     const int n0 = blockIdx.y * 4;
     const float2* base = sd->wpart + (int64_t)u.slot0 * 128 * 128 + threadIdx.x;
-    constexpr int CB = 4, CH = 8;
+    constexpr int CB = 4, CH = 16;
     float wh[CB], wl[CB];
 #pragma unroll
     for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
@@ -404,8 +404,14 @@ __global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict
   const int p0 = q * per, p1 = min(nparts, p0 + per);
   const int col = min(lane, fin.K - 1);
   double s = 0.0;
-#pragma unroll 8
-  for (int p = p0; p < p1; ++p) s += __ldcg(&sd->partials[(int64_t)p * sd->ldp + col]);
+  for (int pb = p0; pb < p1; pb += 8) {
+    double v[8];   // eight loads in flight (clamped addresses), then the additions in order
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __ldcg(&sd->partials[(int64_t)min(pb + i, p1 - 1) * sd->ldp + col]);
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (pb + i < p1) s += v[i];
+  }
   sh[q][lane] = s;
   __syncthreads();
   if (q == 0 && lane < fin.K) {

@@ -174,6 +174,28 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
                            void* stream);
 
 /*
+ * td_loglike_batch_host -- the same evaluation with HOST buffers (the
+ * batched evaluation of Sec. III.A fed from CPU memory).
+ *   R    : host, float32, column-major N' x K, leading dimension ldr >= N'.
+ *          Pinned memory (cudaHostAlloc / cudaHostRegister) lets the copies
+ *          overlap the evaluation; pageable memory works, serialised.
+ *   logL : host, float64[K], overwritten.  chi2: optional host float64[K].
+ *   opt  : as for td_loglike_batch.
+ *   stream: the evaluation runs on it; the host -> device copies run on a
+ *          stream of the segment.  The call returns after the results are in
+ *          host memory (it synchronises `stream`).
+ * The batch is cut into chunks of 512 columns, double-buffered: chunk j+1 is
+ * copied while chunk j is evaluated.  The segment keeps two staging buffers
+ * of 512 N' floats and K-entry result buffers (allocated on first use, grown
+ * when a larger K arrives, freed by td_segment_destroy).  Each chunk goes
+ * through td_loglike_batch, so the results equal that call's bit for bit.
+ * Not for use during stream capture.
+ */
+td_status td_loglike_batch_host(td_segment* s, const float* R, int64_t ldr, int64_t K,
+                                double* logL, const td_options* opt, double* chi2,
+                                void* stream);
+
+/*
  * td_loglike_batch_noalloc -- the same evaluation as td_loglike_batch with the
  * default options, for callers that cannot allocate device memory while they
  * run: an application whose device memory is all reserved by its own caching

@@ -106,6 +106,16 @@ void sort_items(std::vector<TcItem>& items);
 
 }  // namespace td
 
+struct HostStage {            // td_loglike_batch_host: device copies of host column chunks
+  float* buf[2] = {nullptr, nullptr};   // double buffer, [cols][nk] each
+  int64_t cols = 0;
+  double* logL = nullptr;      // device results [cap]
+  double* chi2 = nullptr;
+  int64_t cap = 0;
+  cudaStream_t copy = nullptr;  // host->device copies run here
+  cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+};
+
 struct td_segment {
   int device = 0;
   int64_t n = 0;          // samples
@@ -124,6 +134,7 @@ struct td_segment {
   double logdet = 0.0;
   int64_t pivot = -1;
   td::Scratch scr;
+  HostStage hst;
   // instrumentation
   bool prof = false;
   std::vector<cudaEvent_t> ev;   // start/stop pairs
@@ -132,6 +143,7 @@ struct td_segment {
 };
 
 namespace td {
+void free_host_stage(HostStage& h);
 // error plumbing
 td_status fail(td_status code, const std::string& msg);
 td_status cuda_fail(cudaError_t e, const char* what);

@@ -44,6 +44,7 @@ SIGNATURES = {
     "td_resident_bytes": (_i64, [_vp]),
     "td_debug_bounded_wait": (_c.c_int, [_i64, _vp]),
     "td_loglike_batch_noalloc": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
+    "td_loglike_batch_host": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
     "td_group_create": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp, _c.POINTER(_vp)]),
     "td_group_launch": (_c.c_int, [_vp, _vp]),
     "td_group_graph_launch": (_c.c_int, [_vp, _vp]),
@@ -199,6 +200,17 @@ class Segment:
         _check(lib().td_loglike_batch_noalloc(self.handle, R.data_ptr(), int(R.stride(0)), int(R.shape[0]),
                                               logL.data_ptr(), None if chi2 is None else chi2.data_ptr(),
                                               _stream_ptr(stream)))
+
+    def loglike_host_into(self, R, logL, opt: TdOptions | None = None, chi2=None, stream=None):
+        """td_loglike_batch_host: R a host float32 array/tensor (K, ldr) (row-major
+        == N' x K column-major), logL (and chi2) host float64 of K entries.
+        Pinned torch tensors let the copies overlap the evaluation."""
+        def ptr(x):
+            return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
+        K, ldr = int(R.shape[0]), int(R.stride(0) if hasattr(R, "data_ptr") else R.strides[0] // 4)
+        _check(lib().td_loglike_batch_host(self.handle, ptr(R), ldr, K, ptr(logL),
+                                           None if opt is None else ctypes.byref(opt),
+                                           None if chi2 is None else ptr(chi2), _stream_ptr(stream)))
 
     def profile(self, enable: bool = True):
         _check(lib().td_profile_enable(self.handle, 1 if enable else 0))

@@ -272,3 +272,31 @@ def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     for path in paths[1:]:
         b = out[path][1]
         assert np.max(np.abs(a - b) / b) <= 1e-7
+
+
+def test_host_buffers_match_device_path(torch_cuda, gpu_lib):
+    """td_loglike_batch_host (chunked, double-buffered copies) gives the device
+    path's bits, for pinned and pageable host memory and a ragged last chunk."""
+    from paper_2603_06010_b300 import td
+    n = 1500
+    mask = _mask(n, [(200, 260)])
+    seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
+    K = 1300
+    R = inputs.noise_residuals(n, 2048.0, K, 77, mask=mask)
+    Rd = torch_cuda.from_numpy(R).cuda()
+    opt = td.options(path=td.TD_PATH_STREAM)    # one fixed path: bits comparable across batch sizes
+    ll_d, chi_d = seg.loglike(Rd, opt, with_chi2=True)
+    torch_cuda.cuda.synchronize()
+    for pinned in (True, False):
+        Rh = torch_cuda.from_numpy(R)
+        ll = torch_cuda.empty(K, dtype=torch_cuda.float64)
+        chi = torch_cuda.empty(K, dtype=torch_cuda.float64)
+        if pinned:
+            Rh, ll, chi = Rh.pin_memory(), ll.pin_memory(), chi.pin_memory()
+        seg.loglike_host_into(Rh, ll, opt, chi2=chi)
+        assert np.array_equal(ll.numpy(), ll_d.cpu().numpy()), pinned
+        assert np.array_equal(chi.numpy(), chi_d.cpu().numpy()), pinned
+    o = oracle.OracleSegment(inputs.acf_from_psd(n, 2048.0), mask)
+    exp = oracle.loglike_from_chi2(o.chi2(R[:64]), o.logdet, o.n_kept)
+    assert np.max(np.abs(ll.numpy()[:64] - exp)) <= 1e-3
+    seg.close()

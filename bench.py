@@ -141,6 +141,36 @@ def cpu_baseline(seg, R, budget_s=12.0):
                       f"repeated for >= {budget_s:.0f} s"}
 
 
+def template_extra(td, torch, seg, seg_in, K):
+    """Template-input form on the benchmark segment: data vector fixed, K templates per
+    call; logL alone, then logL with <h,h>, <d,h>, rho_mf and rho_eff^2."""
+    from paper_2603_06010_b300 import inputs
+    d = seg_in.d[seg_in.kept]
+    t0 = time.perf_counter()
+    seg.set_data(d)
+    set_ms = (time.perf_counter() - t0) * 1e3
+    H = torch.from_numpy(inputs.template_batch(seg_in, K, 7070)).cuda()
+    outs = {k: torch.empty(K, dtype=torch.float64, device="cuda") for k in ("logL", "hh", "dh", "rho_mf", "rho_eff2")}
+    res = {}
+    for name, kw in (("logL_only", {}), ("with_snr", {k: outs[k] for k in ("hh", "dh", "rho_mf", "rho_eff2")})):
+        for _ in range(3):
+            seg.template_into(H, outs["logL"], **kw)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(10):
+            seg.template_into(H, outs["logL"], **kw)
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / 10
+        res[name] = {"ms_per_call": ms, "templates_per_s": K / (ms / 1e3)}
+    rho = outs["rho_mf"].cpu().numpy()
+    res.update({"note": f"K={K} chirp templates per call on the gap-free N=8192 segment; <d,d> once "
+                        "(td_set_data); SNR outputs whiten the templates in the same batch (2K columns)",
+                "set_data_ms": set_ms, "rho_mf_max": float(np.max(rho))})
+    return res
+
+
 def grouped_extra(td, torch):
     """The 64-segment uneven mix (N log-uniform in [512, 32768]) in one grouped launch."""
     from paper_2603_06010_b300 import inputs
@@ -487,6 +517,8 @@ def main():
                           "runs": small},
         "clocks": clk,
     }
+    if world == 1:
+        line["template_form"] = template_extra(td, torch, seg, seg_in, K)
     if world == 1 and not args.no_grouped:
         line["grouped"] = grouped_extra(td, torch)
     if world == 1 and not args.no_serving:

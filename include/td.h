@@ -196,6 +196,39 @@ td_status td_loglike_batch_host(td_segment* s, const float* R, int64_t ldr, int6
                                 void* stream);
 
 /*
+ * Template-input form (Sec. III.A: the data vector is fixed and whitened
+ * once, every evaluation brings a template h) and the SNRs of Sec. II.B
+ * item 7, with <a, b> = a^T C^{-1} b (Eq. eqn:ip):
+ *   chi2 = <d - h, d - h>,  logL as td_loglike_batch,
+ *   rho_mf = <d, h> / sqrt(<h, h>),  rho_eff^2 = <d, d> - <d - h, d - h>.
+ *
+ * td_set_data -- store the data vector d (float64, N' kept samples, host or
+ *   device memory: copied) and compute <d, d> (d rounded once to float32 and
+ *   whitened with `opt`).  Synchronises `stream`.  Requires a factored segment.
+ * td_data_inner -- <d, d> of the stored data vector (host scalar).
+ * td_template_batch -- K templates H (device, float32, column-major N' x K,
+ *   leading dimension ldh >= N'): r_k = fl32(d - h_k) goes through
+ *   td_loglike_batch; when out->hh, out->dh or out->rho_mf is requested the
+ *   templates are whitened in the same batch (2K columns) and
+ *   <d, h> = (<d, d> + <h, h> - chi2) / 2.  Outputs (device float64[K], NULL
+ *   = not written; logL required) in td_template_out.  Asynchronous on
+ *   `stream`; the segment's template buffers grow on first use (they may
+ *   allocate).  K <= 65535 per call.  TD_ERR_INVALID without td_set_data.
+ */
+typedef struct td_template_out {
+  double* logL;      /* required */
+  double* chi2;      /* <d - h, d - h> */
+  double* hh;        /* <h, h> */
+  double* dh;        /* <d, h> */
+  double* rho_mf;    /* <d, h> / sqrt(<h, h>) (0 when <h, h> = 0) */
+  double* rho_eff2;  /* <d, d> - chi2 */
+} td_template_out;
+td_status td_set_data(td_segment* s, const double* d, const td_options* opt, void* stream);
+td_status td_data_inner(const td_segment* s, double* dd);
+td_status td_template_batch(td_segment* s, const float* H, int64_t ldh, int64_t K,
+                            const td_template_out* out, const td_options* opt, void* stream);
+
+/*
  * td_loglike_batch_noalloc -- the same evaluation as td_loglike_batch with the
  * default options, for callers that cannot allocate device memory while they
  * run: an application whose device memory is all reserved by its own caching

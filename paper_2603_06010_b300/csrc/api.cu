@@ -603,6 +603,7 @@ void td_segment_destroy(td_segment* s) {
   dev_free(s->scr.wpart);
   free_plans(s->scr);
   free_host_stage(s->hst);
+  free_template_state(s->tpl);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
   delete s;

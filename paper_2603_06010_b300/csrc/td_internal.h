@@ -116,6 +116,17 @@ struct HostStage {            // td_loglike_batch_host: device copies of host co
   cudaEvent_t copied[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
 };
 
+struct TemplateState {        // td_set_data / td_template_batch
+  double* d = nullptr;         // device data vector, N' kept samples
+  size_t d_cap = 0;
+  float* R = nullptr;          // device [d - h_k | h_k] columns of a batch
+  size_t R_cap = 0;
+  double* res = nullptr;       // device logL and chi2 of a batch
+  size_t res_cap = 0;
+  double dd = 0.0;             // <d, d>
+  bool has_data = false;
+};
+
 struct td_segment {
   int device = 0;
   int64_t n = 0;          // samples
@@ -135,6 +146,7 @@ struct td_segment {
   int64_t pivot = -1;
   td::Scratch scr;
   HostStage hst;
+  TemplateState tpl;
   // instrumentation
   bool prof = false;
   std::vector<cudaEvent_t> ev;   // start/stop pairs
@@ -144,6 +156,7 @@ struct td_segment {
 
 namespace td {
 void free_host_stage(HostStage& h);
+void free_template_state(TemplateState& T);
 // error plumbing
 td_status fail(td_status code, const std::string& msg);
 td_status cuda_fail(cudaError_t e, const char* what);

@@ -221,6 +221,18 @@ def residual_batch(seg: Segment, K: int, seed: int) -> np.ndarray:
     return R
 
 
+def template_batch(seg: Segment, K: int, seed: int) -> np.ndarray:
+    """H (K, n') float32, row k = kept samples of the template h(theta_k), theta_k
+    from the chirp priors, with the segment's injection amplitude."""
+    rng = np.random.default_rng(seed)
+    T = seg.n / seg.fs
+    th = draw_theta(rng, T, K)
+    H = np.empty((K, seg.n_kept), dtype=np.float32)
+    for k in range(K):
+        H[k] = chirp(seg.n, seg.fs, th[k, 0], th[k, 1], th[k, 2], amp=seg.amp)[seg.kept].astype(np.float32)
+    return H
+
+
 def noise_residuals(n: int, fs: float, K: int, seed: int, mask: np.ndarray | None = None,
                     a: float = -4.0, floor: float = 2.0, scale: float = 1.0) -> np.ndarray:
     """K pure-noise residuals on the kept samples, float32 (K, n')."""

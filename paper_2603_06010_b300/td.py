@@ -45,6 +45,9 @@ SIGNATURES = {
     "td_debug_bounded_wait": (_c.c_int, [_i64, _vp]),
     "td_loglike_batch_noalloc": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "td_loglike_batch_host": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
+    "td_set_data": (_c.c_int, [_vp, _vp, _vp, _vp]),
+    "td_data_inner": (_c.c_int, [_vp, _c.POINTER(_c.c_double)]),
+    "td_template_batch": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "td_group_create": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp, _c.POINTER(_vp)]),
     "td_group_launch": (_c.c_int, [_vp, _vp]),
     "td_group_graph_launch": (_c.c_int, [_vp, _vp]),
@@ -84,6 +87,11 @@ class ServerStats(ctypes.Structure):
                 ("batches", ctypes.c_int64), ("hits", ctypes.c_int64), ("misses", ctypes.c_int64),
                 ("evictions", ctypes.c_int64), ("refused", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("resident_bytes", ctypes.c_int64)]
+
+
+class TemplateOut(ctypes.Structure):
+    _fields_ = [("logL", ctypes.c_void_p), ("chi2", ctypes.c_void_p), ("hh", ctypes.c_void_p),
+                ("dh", ctypes.c_void_p), ("rho_mf", ctypes.c_void_p), ("rho_eff2", ctypes.c_void_p)]
 
 
 class TdOptions(ctypes.Structure):
@@ -211,6 +219,30 @@ class Segment:
         _check(lib().td_loglike_batch_host(self.handle, ptr(R), ldr, K, ptr(logL),
                                            None if opt is None else ctypes.byref(opt),
                                            None if chi2 is None else ptr(chi2), _stream_ptr(stream)))
+
+    def set_data(self, d, opt: TdOptions | None = None, stream=None):
+        """td_set_data: the data vector (float64, N' kept samples; numpy or torch)."""
+        if hasattr(d, "data_ptr"):
+            ptr, keep = d.data_ptr(), d
+        else:
+            keep = np.ascontiguousarray(d, dtype=np.float64)
+            ptr = keep.ctypes.data
+        _check(lib().td_set_data(self.handle, ptr, None if opt is None else ctypes.byref(opt), _stream_ptr(stream)))
+
+    @property
+    def data_inner(self) -> float:
+        v = ctypes.c_double()
+        _check(lib().td_data_inner(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def template_into(self, H, logL, chi2=None, hh=None, dh=None, rho_mf=None, rho_eff2=None,
+                      opt: TdOptions | None = None, stream=None):
+        """td_template_batch: H CUDA float32 (K, ldh); outputs CUDA float64 (K,) or None."""
+        p = (lambda x: None if x is None else x.data_ptr())
+        out = TemplateOut(p(logL), p(chi2), p(hh), p(dh), p(rho_mf), p(rho_eff2))
+        _check(lib().td_template_batch(self.handle, H.data_ptr(), int(H.stride(0)), int(H.shape[0]),
+                                       ctypes.byref(out), None if opt is None else ctypes.byref(opt),
+                                       _stream_ptr(stream)))
 
     def profile(self, enable: bool = True):
         _check(lib().td_profile_enable(self.handle, 1 if enable else 0))

@@ -436,12 +436,13 @@ def main():
     if args.precision in ("bf16x6", "bf16x10"):
         nsl = 3 if args.precision == "bf16x6" else 4
         op_bytes = (N // 256) * ((N // 256) + 1) // 2 * 8 * nsl * 256 * 32 * 2   # operator slices read once
-        for Ks in (1, 8, 64):
+        for Ks in (1, 8, 64, 256):
             Rs = R[:Ks].contiguous()
             ls = torch.empty(Ks, dtype=torch.float64, device="cuda")
-            cand = [("stream256", td.TD_PATH_STREAM), ("stream64", td.TD_PATH_STREAM64)]
-            if Ks <= 32:
-                cand = [("smallk", td.TD_PATH_SMALLK)] + cand
+            cand = [("auto", td.TD_PATH_AUTO), ("stream256", td.TD_PATH_STREAM),
+                    ("stream128", td.TD_PATH_STREAM128)]
+            if Ks >= 64:
+                cand.append(("tensor128", td.TD_PATH_TENSOR128))
             for pname, path in cand:
                 o2 = td.options(precision=prec, path=path)
                 for _ in range(3):

@@ -89,10 +89,20 @@ static Shape choose_shape(const td_segment* s, int64_t K, int path) {
   if (path == TD_PATH_TENSOR) return {256, false};
   if (path == TD_PATH_STREAM) return {256, true};
   if (path == TD_PATH_STREAM64) return {64, true};
+  if (path == TD_PATH_TENSOR128) return {128, false};
+  if (path == TD_PATH_STREAM128) return {128, true};
   if (path == TD_PATH_SMALLK || (path == TD_PATH_AUTO && K <= 32)) return {0, true};
-  const int64_t items256 = (s->nkp / OP_ROWS) * ceil_div(K, TC_COLS);
+  // measured on B300 (N' = 8192): 256-row whole rows win from K ~ 1024 up;
+  // for mid-size batches 128-row whole rows (two TMEM accumulator pairs, so
+  // epilogues overlap MMAs) win once there is about one tile per SM; below
+  // that, 128-row tiles with k-chunks (K = 64: 100 us vs 120 us for 256-row
+  // chunks; K = 256: 163 us whole 128-row vs 280 us 256-row chunks)
+  const int64_t nc = ceil_div(K, TC_COLS);
+  const int64_t items256 = (s->nkp / OP_ROWS) * nc;
+  const int64_t items128 = (s->nkp / 128) * nc;
   if (items256 >= 2 * (int64_t)tc_num_sms()) return {256, false};
-  return {256, true};
+  if (4 * items128 >= 3 * (int64_t)tc_num_sms()) return {128, false};
+  return {128, true};
 }
 
 template <class T>

@@ -387,7 +387,7 @@ td_status td_group_graph_launch(td_group* g, void* stream) {
 td_status td_group_tune(td_group* g, void* stream, double* best_ms) {
   if (!g) return fail(TD_ERR_INVALID, "group is NULL");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int cand[][2] = {{256, 1}, {256, 2}, {256, 4}, {64, 1}, {64, 2}};
+  const int cand[][2] = {{256, 1}, {256, 2}, {128, 1}, {128, 2}, {128, 4}, {64, 1}, {64, 2}};
   double best = 1e300;
   int bb = g->bn, bs = g->s_factor;
   cudaEvent_t a, b;

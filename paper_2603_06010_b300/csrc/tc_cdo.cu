@@ -7,7 +7,7 @@
 // TMEM lane holds one residual column and the chi2 sum over rows happens in
 // one thread's registers with no cross-thread reduction:
 //   MMA M = 128 residual columns  (A = R^T slices, K-major),
-//   MMA N = BN rows of W, BN = 256 (large batches) or 64 (small batches)
+//   MMA N = BN rows of W, BN = 256, 128 or 64
 //                                 (B = L^{-1} slices, K-major),
 //   reduction over the kept samples j in k-blocks of 32 (64-byte swizzle).
 // Each operand is held as bf16 slices x = x0 + x1 + x2 (+ x3) with x0 a
@@ -36,7 +36,7 @@
 //   warps 2..5    : epilogue; TMEM -> registers, exact squares, compensated
 //                   sums, FP64 partials
 // TMEM holds NBUF pairs of accumulators (one pair for BN = 256, two for
-// BN = 64 so the epilogue of one tile overlaps the MMAs of the next).  Every
+// BN = 128 and 64 so the epilogue of one tile overlaps the MMAs of the next).  Every
 // wait is bounded (wait_limit_ns).
 #include "td_internal.h"
 
@@ -377,6 +377,10 @@ static cudaError_t dispatch(int nslices, int bn, const TcSingle& p, const TcItem
     if (nslices == 3) return launch_impl<3, 256, MODE>(p, items, n_items, segs, status, lim, st);
     if (nslices == 4) return launch_impl<4, 256, MODE>(p, items, n_items, segs, status, lim, st);
     if (nslices == 2) return launch_impl<2, 256, MODE>(p, items, n_items, segs, status, lim, st);
+  } else if (bn == 128) {
+    if (nslices == 3) return launch_impl<3, 128, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 4) return launch_impl<4, 128, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 2) return launch_impl<2, 128, MODE>(p, items, n_items, segs, status, lim, st);
   } else if (bn == 64) {
     if (nslices == 3) return launch_impl<3, 64, MODE>(p, items, n_items, segs, status, lim, st);
     if (nslices == 4) return launch_impl<4, 64, MODE>(p, items, n_items, segs, status, lim, st);
@@ -385,7 +389,7 @@ static cudaError_t dispatch(int nslices, int bn, const TcSingle& p, const TcItem
   return cudaErrorInvalidValue;
 }
 
-// single segment: tiles of bn rows (256 or 64); seg.partials holds one row per
+// single segment: tiles of bn rows (256, 128 or 64); seg.partials holds one row per
 // 64-row group, seg.ldp apart
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st) {

@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libtd.so")
 TD_OK, TD_ERR_INVALID, TD_ERR_NOT_PD, TD_ERR_OOM, TD_ERR_CUDA, TD_ERR_TIMEOUT, TD_ERR_NOT_FACTORED, \
     TD_ERR_UNSUPPORTED, TD_ERR_BUSY = range(9)
 TD_PREC_FP64, TD_PREC_BF16X6, TD_PREC_BF16X3, TD_PREC_AUTO, TD_PREC_BF16X10 = range(5)
-TD_PATH_AUTO, TD_PATH_TENSOR, TD_PATH_STREAM, TD_PATH_FP64, TD_PATH_STREAM64, TD_PATH_SMALLK = range(6)
+(TD_PATH_AUTO, TD_PATH_TENSOR, TD_PATH_STREAM, TD_PATH_FP64, TD_PATH_STREAM64, TD_PATH_SMALLK,
+ TD_PATH_TENSOR128, TD_PATH_STREAM128) = range(8)
 
 STATUS_NAMES = {0: "TD_OK", 1: "TD_ERR_INVALID", 2: "TD_ERR_NOT_PD", 3: "TD_ERR_OOM", 4: "TD_ERR_CUDA",
                 5: "TD_ERR_TIMEOUT", 6: "TD_ERR_NOT_FACTORED", 7: "TD_ERR_UNSUPPORTED", 8: "TD_ERR_BUSY"}

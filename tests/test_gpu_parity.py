@@ -249,15 +249,17 @@ def test_full_cfg3_gapped_three_detectors(torch_cuda, gpu_lib, prec):
 
 @pytest.mark.parametrize("K", [1, 5, 17, 32, 130, 300])
 def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
-    """256-row direct tiles and 64-row split tiles agree within the bar (their
-    correction sums round differently), and each matches the oracle."""
+    """256- and 128-row whole-row tiles, 256/128/64-row split tiles and the
+    small-batch kernel agree within the bar (their correction sums round
+    differently), and each matches the oracle."""
     from paper_2603_06010_b300 import td
     n = 2000
     mask = _mask(n, [(900, 1000)])
     seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
     R = torch_cuda.from_numpy(inputs.noise_residuals(n, 2048.0, K, 31, mask=mask)).cuda()
     out = {}
-    paths = [td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64] + ([td.TD_PATH_SMALLK] if K <= 32 else [])
+    paths = [td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64, td.TD_PATH_TENSOR128,
+             td.TD_PATH_STREAM128] + ([td.TD_PATH_SMALLK] if K <= 32 else [])
     for path in paths:
         ll, chi = seg.loglike(R, td.options(path=path), with_chi2=True)
         torch_cuda.cuda.synchronize()

@@ -207,6 +207,55 @@ __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, i
   }
 }
 
+// one CTA per column, the column held in registers (one read of R): THREADS
+// threads x V float4 each cover up to 4 V THREADS rows; 16-byte loads, 8-byte
+// stores of four bf16 per slice.  Needs ldr, N' multiples of 4 and R 16-byte
+// aligned (the launcher checks).
+template <int THREADS, int V>
+__global__ void __launch_bounds__(THREADS) k_r_slices_reg(const float* __restrict__ R, int64_t ldr, int64_t nk,
+                                                          int64_t K, int64_t nkp8, int64_t capK,
+                                                          __nv_bfloat16* __restrict__ rs, int nslices) {
+  __shared__ float red[THREADS / 32];
+  pdl_launch_dependents();
+  const int64_t k = blockIdx.x;
+  const float4* col = reinterpret_cast<const float4*>(R + k * ldr);
+  const int64_t nv = nk / 4;
+  float4 x[V];
+  float mx = 0.f;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int64_t i = threadIdx.x + (int64_t)v * THREADS;
+    x[v] = i < nv ? col[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(x[v].x), fabsf(x[v].y)), fmaxf(fabsf(x[v].z), fabsf(x[v].w))));
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = red[0];
+#pragma unroll
+  for (int w = 1; w < THREADS / 32; ++w) mx = fmaxf(mx, red[w]);
+  const float p = r_quantum(mx);
+  const int64_t slice_stride = capK * nkp8;
+  __nv_bfloat16* dst = rs + k * nkp8;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const int64_t i = threadIdx.x + (int64_t)v * THREADS;
+    if (i >= nv) break;
+    const float xs[4] = {x[v].x, x[v].y, x[v].z, x[v].w};
+    __align__(8) __nv_bfloat16 o[4][4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float hi = p * rintf(xs[e] / p);
+      o[0][e] = __float2bfloat16_rn(hi);
+      split3_f32(xs[e] - hi, o[1][e], o[2][e], o[3][e]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (u < nslices) *reinterpret_cast<uint2*>(dst + u * slice_stride + 4 * i) = *reinterpret_cast<const uint2*>(o[u]);
+  }
+}
+
 // a cluster of RS_CL CTAs per column (small batches: more SMs on the few
 // columns); the column maximum is combined through distributed shared memory.
 // The maximum is exact in any order, so p_k equals the one-CTA kernel's.
@@ -242,6 +291,16 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
   if (K <= 0) return cudaSuccess;
   if (K <= 256) {
     k_r_slices_cl<<<(unsigned)(K * RS_CL), 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
+  } else if (!zero && K <= 2147483647LL && ldr % 4 == 0 && nk % 4 == 0 && (reinterpret_cast<uintptr_t>(R) & 15) == 0 &&
+             nk <= 4 * 8 * 1024) {
+    // column in registers: 8 float4 per thread
+    const unsigned grid = (unsigned)K;
+    if (nk <= 4 * 8 * 256)
+      k_r_slices_reg<256, 8><<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
+    else if (nk <= 4 * 8 * 512)
+      k_r_slices_reg<512, 8><<<grid, 512, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
+    else
+      k_r_slices_reg<1024, 8><<<grid, 1024, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
   } else {
     const int grid = (int)(K < 4096 ? K : 4096);
     k_r_slices<<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);

@@ -302,3 +302,27 @@ def test_host_buffers_match_device_path(torch_cuda, gpu_lib):
     exp = oracle.loglike_from_chi2(o.chi2(R[:64]), o.logdet, o.n_kept)
     assert np.max(np.abs(ll.numpy()[:64] - exp)) <= 1e-3
     seg.close()
+
+
+@pytest.mark.parametrize("n,K", [(1, 1000), (40, 70000), (2000, 33), (2000, 129), (2000, 257), (2000, 513)])
+def test_extreme_and_transition_shapes(torch_cuda, gpu_lib, n, K):
+    """Very wide batches on tiny segments and the batch sizes where the automatic
+    tile shape changes: every column finite, sampled columns against the oracle."""
+    from paper_2603_06010_b300 import td
+    mask = _mask(n, [(700, 780)]) if n > 1000 else None
+    acf = inputs.acf_from_psd(n, 2048.0) if n > 1 else np.array([1.7])
+    seg = td.Segment(acf, mask)
+    nk = seg.n_kept
+    rng = np.random.default_rng(K + n)
+    R = (rng.standard_normal((K, nk)) * np.sqrt(acf[0])).astype(np.float32)
+    ll, chi = seg.loglike(torch_cuda.from_numpy(R).cuda(), td.options(), with_chi2=True)
+    torch_cuda.cuda.synchronize()
+    seg.check()
+    ll, chi = ll.cpu().numpy(), chi.cpu().numpy()
+    assert np.all(np.isfinite(ll))
+    cols = np.unique(np.r_[0, K - 1, rng.integers(0, K, 40)])
+    o = oracle.OracleSegment(acf, mask)
+    exp_chi = o.chi2(R[cols])
+    _compare("bf16x6", ll[cols], chi[cols], oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept), exp_chi,
+             f"n={n} K={K}")
+    seg.close()

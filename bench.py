@@ -117,6 +117,17 @@ def make_workload(rank: int):
     return c, seg, R
 
 
+def profile_traffic(name):
+    """DRAM bytes per launch from a committed ncu summary under profiles/ (None if absent)."""
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", name)) as f:
+            m = re.search(r"DRAM traffic per launch: ([0-9.]+) MB", f.read())
+        return float(m.group(1)) * 1e6 if m else None
+    except OSError:
+        return None
+
+
 def golden_dlogl(logL_host):
     """max |dlogL| on the stored oracle columns (rank 0's batch only)."""
     try:
@@ -481,8 +492,12 @@ def main():
     if products:
         achieved = flops / (kern_avg_ms / 1e3) / 1e12
         peak = pk["bf16_tflops"] / products
+        # DRAM bytes of this kernel and workload from the committed ncu capture (BF16X6 only)
+        traffic = profile_traffic("k_tc_cdo_gapfree_n8192_k4096.md") if args.precision == "bf16x6" else None
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": "k_tc_cdo",
+                "frac": achieved / peak, "traffic": traffic, "kernel": "k_tc_cdo",
+                "traffic_source": "profiles/k_tc_cdo_gapfree_n8192_k4096.md (ncu dram__bytes_read.sum + "
+                                  "dram__bytes_write.sum, one launch)" if traffic else None,
                 "kernel_ms": kern_avg_ms,
                 "peak_basis": f"{basis} bf16 dense burst {pk['bf16_tflops']} TF/s / {products} split products",
                 "algorithmic": "N'^2 K flops per launch (N'^2/2 multiply-adds per residual column)"}

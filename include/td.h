@@ -292,6 +292,16 @@ td_status td_group_check(td_group* g, void* stream);
 int td_group_shape(const td_group* g, int* bn, int* s_factor, int* n_items);
 void td_group_destroy(td_group* g);
 
+/*
+ * td_group_set_joint -- multi-detector likelihood (Sec. II.B item 3: the
+ * detectors' log-likelihoods add): every later launch of the group also
+ * writes joint[k] = sum over the group's segments (in their order) of
+ * logL_i[k].  All segments must have the same K; joint is device float64[K],
+ * caller-owned; NULL turns the sum off.  Drops a captured graph (the next
+ * td_group_graph_launch captures again).
+ */
+td_status td_group_set_joint(td_group* g, double* joint);
+
 /* One-shot grouped evaluation: create, launch, check, destroy (synchronises). */
 td_status td_loglike_grouped(td_segment* const* segs, const float* const* R,
                              const int64_t* ldr, const int64_t* K, double* const* logL,

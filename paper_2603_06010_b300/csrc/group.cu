@@ -117,6 +117,8 @@ struct td_group {
   DevStatus* status = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
+  double* joint = nullptr;    // optional: sum over the segments of logL (all with joint_K columns)
+  int64_t joint_K = 0;
 };
 
 namespace td {
@@ -219,6 +221,16 @@ static td_status group_check_current(const td_group* g) {
   return TD_OK;
 }
 
+// joint logL over the segments of a group (Sec. II.B item 3: detectors'
+// log-likelihoods add), segment order fixed
+__global__ void k_joint_sum(const TcSegDev* __restrict__ segs, int nseg, int64_t K, double* __restrict__ out) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= K) return;
+  double s = 0.0;
+  for (int i = 0; i < nseg; ++i) s += segs[i].logL[k];
+  out[k] = s;
+}
+
 static td_status group_launch_impl(td_group* g, cudaStream_t st) {
   int gx = (int)std::min<int64_t>(g->total_cols, 8192);
   if (gx > 0) {
@@ -228,6 +240,10 @@ static td_status group_launch_impl(td_group* g, cudaStream_t st) {
   TD_CUDA(launch_tc_cdo(g->d_items, g->n_items, g->d_seg, g->nsl, g->bn, true, g->status, g->wait_limit_ns, st));
   TD_CUDA(launch_split_reduce(g->d_units, g->n_units, g->d_seg, g->bn, st));
   TD_CUDA(launch_tc_finalize(g->d_seg, g->nseg, g->maxK, st));
+  if (g->joint && g->joint_K > 0) {
+    k_joint_sum<<<(unsigned)ceil_div(g->joint_K, 256), 256, 0, st>>>(g->d_seg, g->nseg, g->joint_K, g->joint);
+    TD_CUDA(cudaGetLastError());
+  }
   return TD_OK;
 }
 
@@ -349,6 +365,24 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
   }
   (void)stream;
   *out = g;
+  return TD_OK;
+}
+
+td_status td_group_set_joint(td_group* g, double* joint) {
+  if (!g) return fail(TD_ERR_INVALID, "group is NULL");
+  int64_t K = -1;
+  for (const TcSegDev& sd : g->host_seg) {
+    if (K >= 0 && sd.K != K) return fail(TD_ERR_INVALID, "a joint logL needs the same K in every segment");
+    K = sd.K;
+  }
+  if (joint && !g->host_seg.empty() && !g->host_seg[0].logL)
+    return fail(TD_ERR_INVALID, "segment outputs are missing");
+  if (g->graph) {   // the captured launch does not contain the sum (or contains a stale one)
+    cudaGraphExecDestroy(g->graph);
+    g->graph = nullptr;
+  }
+  g->joint = joint;
+  g->joint_K = joint ? std::max<int64_t>(K, 0) : 0;
   return TD_OK;
 }
 

@@ -50,6 +50,7 @@ SIGNATURES = {
     "td_data_inner": (_c.c_int, [_vp, _c.POINTER(_c.c_double)]),
     "td_template_batch": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "td_group_create": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp, _c.POINTER(_vp)]),
+    "td_group_set_joint": (_c.c_int, [_vp, _vp]),
     "td_group_launch": (_c.c_int, [_vp, _vp]),
     "td_group_graph_launch": (_c.c_int, [_vp, _vp]),
     "td_group_tune": (_c.c_int, [_vp, _vp, _c.POINTER(_c.c_double)]),
@@ -307,6 +308,11 @@ class Group:
         _check(lib().td_group_create(H, RP, LD, KK, LP, CP, n, None if opt is None else ctypes.byref(opt),
                                      _stream_ptr(stream), ctypes.byref(h)))
         self.handle = h
+
+    def set_joint(self, joint):
+        """td_group_set_joint: joint = CUDA float64 (K,) summed logL over the segments, or None."""
+        self._joint = joint
+        _check(lib().td_group_set_joint(self.handle, None if joint is None else joint.data_ptr()))
 
     def launch(self, stream=None):
         _check(lib().td_group_launch(self.handle, _stream_ptr(stream)))

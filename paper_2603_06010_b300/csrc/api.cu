@@ -607,9 +607,6 @@ void td_segment_destroy(td_segment* s) {
   dev_free(s->scr.rs);
   dev_free(s->scr.partials);
   dev_free(s->scr.w64);
-  dev_free(s->scr.items);
-  dev_free(s->scr.segdev);
-  dev_free(s->scr.rsf);
   dev_free(s->scr.wpart);
   free_plans(s->scr);
   free_host_stage(s->hst);

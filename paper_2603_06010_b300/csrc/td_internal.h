@@ -82,17 +82,8 @@ struct SplitPlan {           // device work lists for one batch width (split mod
 struct Scratch {
   int64_t capK = 0;          // columns the buffers hold
   __nv_bfloat16* rs = nullptr;  // residual slices [4][capK][nkp8]
-  double* partials = nullptr;   // [n_tiles][capK_pad] (tensor path) / [nt64][capK_pad] (fp64)
+  double* partials = nullptr;   // chi2 partials [row groups][capK] (layout per path)
   double* w64 = nullptr;        // FP64 W for the plain path [nkp][capK]
-  TcItem* items = nullptr;      // tensor-core work list
-  int n_items = 0;
-  int64_t items_for_K = -1;
-  TcSegDev* segdev = nullptr;   // one device descriptor
-  int64_t segdev_K = -1;
-  const float* segdev_R = nullptr;
-  int64_t segdev_ldr = -1;
-  float* rsf = nullptr;         // unused
-  int64_t rsf_bytes = 0;
   float2* wpart = nullptr;      // split-mode accumulator pairs
   int64_t wpart_slots = 0;
   std::vector<SplitPlan> plans;

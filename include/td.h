@@ -76,8 +76,8 @@ typedef enum {
                            results added in double-float by a reduce kernel (small K) */
   TD_PATH_FP64 = 3,     /* plain FP64 forward substitution */
   TD_PATH_STREAM64 = 4, /* as TD_PATH_STREAM with 64-row operator tiles */
-  TD_PATH_SMALLK = 5,   /* K <= 32: operator rows as the MMA M dimension and the residual
-                           columns as N (16 or 32), so the MMA is not padded to 128
+  TD_PATH_SMALLK = 5,   /* K <= 64: operator rows as the MMA M dimension and the residual
+                           columns as N (16, 32 or 64), so the MMA is not padded to 128
                            columns; the packed operator streams once (default for K <= 32) */
   TD_PATH_TENSOR128 = 6, /* as TD_PATH_TENSOR with 128-row operator tiles (two accumulator
                             pairs in TMEM: a tile's epilogue overlaps the next tile's MMAs) */

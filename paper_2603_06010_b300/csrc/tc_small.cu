@@ -1,10 +1,10 @@
-// Tensor-core whitening for small batches (K <= 32 residual columns).
+// Tensor-core whitening for small batches (K <= 64 residual columns).
 //
 // Same method and slices as the main kernel (Sec. II.A, W = L^{-1}; Sec.
 // III.A, the cached-operator evaluation), with the operand roles swapped so
 // the MMA is not padded to 128 residual columns:
 //   MMA M = 128 rows of W           (A = L^{-1} slices, K-major),
-//   MMA N = NC residual columns, 16 or 32 (B = R^T slices, K-major),
+//   MMA N = NC residual columns, 16, 32 or 64 (B = R^T slices, K-major),
 // so D[lane i][col n] = W[i][n].  Per 32-column k-block the operator tile is
 // 24 KB (three slices) and the MMA work is tiny, so the kernel streams the
 // packed operator from HBM once.  Long rows are cut into balanced k-chunks;
@@ -37,7 +37,7 @@ template <int NSL, int NC> struct Cfg {
   static constexpr int STAGE = A_STAGE + NSL * B_SLICE;
   static constexpr int STAGES = (216 * 1024) / STAGE > 8 ? 8 : (216 * 1024) / STAGE;
   static constexpr int NBUF = 4;                         // accumulator pairs in TMEM
-  static constexpr uint32_t TMEM_COLS = (NBUF * 2 * NC <= 128) ? 128 : 256;
+  static constexpr uint32_t TMEM_COLS = (NBUF * 2 * NC <= 128) ? 128 : ((NBUF * 2 * NC <= 256) ? 256 : 512);
   static constexpr int SMEM = STAGES * STAGE + 256 + 1024;   // stages + barriers + alignment
 };
 }  // namespace tsm
@@ -311,9 +311,10 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
         }
         // the tile's four 32-row groups in a fixed order
         epi_bar();
-        if (q == 0 && lane < ncol)
-          sd->partials[(int64_t)it.m * sd->ldp + it.c * NC + lane] =
-              ((sh_part[0][lane] + sh_part[1][lane]) + sh_part[2][lane]) + sh_part[3][lane];
+        if (q == 0)
+          for (int n = lane; n < ncol; n += 32)
+            sd->partials[(int64_t)it.m * sd->ldp + it.c * NC + n] =
+                ((sh_part[0][n] + sh_part[1][n]) + sh_part[2][n]) + sh_part[3][n];
         epi_bar();
       }
       ++tl;
@@ -397,27 +398,31 @@ __global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict
     if (!sh_last) return;
     __threadfence();
   }
-  // chi2 and logL: lane = column (K <= 32, coalesced rows of partials); warp q
-  // adds the tiles of its quarter in order, then the four quarters in order
+  // chi2 and logL: lane = column (32 columns per pass, coalesced rows of
+  // partials); warp q adds the tiles of its quarter in order, then the four
+  // quarters in order
   const int nparts = sd->nm;
   const int per = (nparts + 3) / 4;
   const int p0 = q * per, p1 = min(nparts, p0 + per);
-  const int col = min(lane, fin.K - 1);
-  double s = 0.0;
-  for (int pb = p0; pb < p1; pb += 8) {
-    double v[8];   // eight loads in flight (clamped addresses), then the additions in order
+  for (int c0 = 0; c0 < fin.K; c0 += 32) {
+    const int col = min(c0 + lane, fin.K - 1);
+    double s = 0.0;
+    for (int pb = p0; pb < p1; pb += 8) {
+      double v[8];   // eight loads in flight (clamped addresses), then the additions in order
 #pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __ldcg(&sd->partials[(int64_t)min(pb + i, p1 - 1) * sd->ldp + col]);
+      for (int i = 0; i < 8; ++i) v[i] = __ldcg(&sd->partials[(int64_t)min(pb + i, p1 - 1) * sd->ldp + col]);
 #pragma unroll
-    for (int i = 0; i < 8; ++i)
-      if (pb + i < p1) s += v[i];
-  }
-  sh[q][lane] = s;
-  __syncthreads();
-  if (q == 0 && lane < fin.K) {
-    const double t = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
-    if (fin.chi2) fin.chi2[lane] = t;
-    fin.logL[lane] = -0.5 * t - 0.5 * sd->logdet - 0.5 * (double)sd->nk * LOG2PI;
+      for (int i = 0; i < 8; ++i)
+        if (pb + i < p1) s += v[i];
+    }
+    __syncthreads();   // sh is free (previous pass read it)
+    sh[q][lane] = s;
+    __syncthreads();
+    if (q == 0 && c0 + lane < fin.K) {
+      const double t = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
+      if (fin.chi2) fin.chi2[c0 + lane] = t;
+      fin.logL[c0 + lane] = -0.5 * t - 0.5 * sd->logdet - 0.5 * (double)sd->nk * LOG2PI;
+    }
   }
 }
 
@@ -467,6 +472,10 @@ cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* se
     if (nslices == 3) return launch_small_impl<3, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
     if (nslices == 4) return launch_small_impl<4, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
     if (nslices == 2) return launch_small_impl<2, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
+  } else if (nc == 64) {
+    if (nslices == 3) return launch_small_impl<3, 64>(items, n_items, segs, status, wait_limit_ns, fin, st);
+    if (nslices == 4) return launch_small_impl<4, 64>(items, n_items, segs, status, wait_limit_ns, fin, st);
+    if (nslices == 2) return launch_small_impl<2, 64>(items, n_items, segs, status, wait_limit_ns, fin, st);
   }
   return cudaErrorInvalidValue;
 }

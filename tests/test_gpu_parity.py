@@ -247,7 +247,7 @@ def test_full_cfg3_gapped_three_detectors(torch_cuda, gpu_lib, prec):
     assert np.max(np.abs(joint - np.array(gg["joint_logL"]))) <= 1e-3
 
 
-@pytest.mark.parametrize("K", [1, 5, 17, 32, 130, 300])
+@pytest.mark.parametrize("K", [1, 5, 17, 32, 48, 64, 130, 300])
 def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     """256- and 128-row whole-row tiles, 256/128/64-row split tiles and the
     small-batch kernel agree within the bar (their correction sums round
@@ -259,7 +259,7 @@ def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     R = torch_cuda.from_numpy(inputs.noise_residuals(n, 2048.0, K, 31, mask=mask)).cuda()
     out = {}
     paths = [td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64, td.TD_PATH_TENSOR128,
-             td.TD_PATH_STREAM128] + ([td.TD_PATH_SMALLK] if K <= 32 else [])
+             td.TD_PATH_STREAM128] + ([td.TD_PATH_SMALLK] if K <= 64 else [])
     for path in paths:
         ll, chi = seg.loglike(R, td.options(path=path), with_chi2=True)
         torch_cuda.cuda.synchronize()

@@ -127,6 +127,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the kernels after this one may be scheduled now; they wait for this grid
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -171,6 +173,24 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         prefetch_tmap(&single.seg.mapA);
         prefetch_tmap(&single.seg.mapB);
       }
+      // launched as a programmatic dependent of the residual slicing: the first
+      // STAGES operator tiles are requested before the wait for the slices
+      bool dep = false;
+      int pend_n = 0;
+      int pend_stage[STAGES], pend_kb[STAGES], pend_c[STAGES];
+      const TcSegDev* pend_sd[STAGES];
+      auto flush = [&]() {
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        dep = true;
+        for (int i = 0; i < pend_n; ++i) {
+          uint8_t* sa = smem + pend_stage[i] * STAGE;
+#pragma unroll
+          for (int sl = 0; sl < NSL; ++sl)
+            tma_load_3d(sa + sl * A_SLICE, &pend_sd[i]->mapA, &full[pend_stage[i]], pend_kb[i] * BK,
+                        pend_c[i] * BM, sl);
+        }
+        pend_n = 0;
+      };
       for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
         const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
         if (idx >= n_total) continue;
@@ -191,10 +211,18 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           uint8_t* sa = smem + stage * STAGE;
           uint8_t* sb = sa + A_STAGE;
           mbar_arrive_expect_tx(&full[stage], (uint32_t)(NSL * (sd->a_rows * BK * 2 + B_SLICE)));
-#pragma unroll
-          for (int sl = 0; sl < NSL; ++sl)   // one box per slice: each slice owns an 8 KB region
-            tma_load_3d(sa + sl * A_SLICE, &sd->mapA, &full[stage], kb * BK, it.c * BM, sl);
           tma_load_3d(sb, &sd->mapB, &full[stage], 0, yoff, (blk0 + kb) * OP_SLICES);
+          if (dep) {
+#pragma unroll
+            for (int sl = 0; sl < NSL; ++sl)   // one box per slice: each slice owns an 8 KB region
+              tma_load_3d(sa + sl * A_SLICE, &sd->mapA, &full[stage], kb * BK, it.c * BM, sl);
+          } else {
+            pend_stage[pend_n] = stage;
+            pend_kb[pend_n] = kb;
+            pend_c[pend_n] = it.c;
+            pend_sd[pend_n] = sd;
+            if (++pend_n == STAGES) flush();   // every stage is in use: nothing more can be issued first
+          }
           issued_mask |= 1u << stage;
           issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
           if (++stage == STAGES) {
@@ -204,6 +232,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
         if (!ok) break;
       }
+      if (!dep) flush();
       // every issued copy must land before the CTA may exit
       for (int s = 0; s < STAGES; ++s)
         if (issued_mask & (1u << s)) mbar_wait(&full[s], (issued_phase >> s) & 1u, limit_ns);
@@ -365,9 +394,19 @@ static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int 
   if (n_total <= 0) return cudaSuccess;
   int grid = tc_num_sms();
   if (grid > n_total) grid = n_total;
-  k_tc_cdo<NSL, BN, MODE><<<grid, tc::THREADS, C::SMEM, st>>>(single, items, n_items, segs, status,
-                                                              (uint64_t)wait_limit_ns);
-  return cudaGetLastError();
+  // programmatic dependent of the residual slicing (see the producer)
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3(tc::THREADS);
+  cfg.dynamicSmemBytes = C::SMEM;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_tc_cdo<NSL, BN, MODE>, single, items, n_items, segs, status,
+                            (uint64_t)wait_limit_ns);
 }
 
 template <int MODE>

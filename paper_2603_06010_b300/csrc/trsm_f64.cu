@@ -114,6 +114,9 @@ cudaError_t launch_trsm_f64_row(const double* L, int64_t ld, const double* dinv,
 // in order, then a fixed shuffle tree -- the same order for every batch.
 __global__ void k_finalize(const double* __restrict__ partials, int64_t ldp, int nparts, int64_t K,
                            double logdet, int64_t nk, double* __restrict__ logL, double* __restrict__ chi2) {
+  // launched as a programmatic dependent: the partials are complete once the
+  // producing grid is
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   const int lane = threadIdx.x & 31;
   const int64_t col = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col >= K) return;
@@ -130,8 +133,16 @@ __global__ void k_finalize(const double* __restrict__ partials, int64_t ldp, int
 cudaError_t launch_finalize(const double* partials, int64_t ldp, int nparts, int64_t K, double logdet,
                             int64_t nk, double* logL, double* chi2, cudaStream_t st) {
   if (K <= 0) return cudaSuccess;
-  k_finalize<<<(unsigned)ceil_div(K, 8), 256, 0, st>>>(partials, ldp, nparts, K, logdet, nk, logL, chi2);
-  return cudaGetLastError();
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)ceil_div(K, 8));
+  cfg.blockDim = dim3(256);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_finalize, partials, ldp, nparts, K, logdet, nk, logL, chi2);
 }
 
 // A wait on an mbarrier that nothing arrives at: must give up after limit_ns

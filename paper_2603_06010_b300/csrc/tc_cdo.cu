@@ -381,7 +381,7 @@ int tc_num_sms() {
 
 template <int NSL, int BN, int MODE>
 static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int n_items, const TcSegDev* segs,
-                               DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+                               DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl) {
   using C = tc::Cfg<NSL, BN>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -394,7 +394,7 @@ static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int 
   if (n_total <= 0) return cudaSuccess;
   int grid = tc_num_sms();
   if (grid > n_total) grid = n_total;
-  // programmatic dependent of the residual slicing (see the producer)
+  // programmatic dependent of the residual slicing when pdl (see the producer)
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid);
   cfg.blockDim = dim3(tc::THREADS);
@@ -404,26 +404,26 @@ static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int 
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, k_tc_cdo<NSL, BN, MODE>, single, items, n_items, segs, status,
                             (uint64_t)wait_limit_ns);
 }
 
 template <int MODE>
 static cudaError_t dispatch(int nslices, int bn, const TcSingle& p, const TcItem* items, int n_items,
-                            const TcSegDev* segs, DevStatus* status, int64_t lim, cudaStream_t st) {
+                            const TcSegDev* segs, DevStatus* status, int64_t lim, cudaStream_t st, bool pdl) {
   if (bn == 256) {
-    if (nslices == 3) return launch_impl<3, 256, MODE>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 4) return launch_impl<4, 256, MODE>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 2) return launch_impl<2, 256, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 3) return launch_impl<3, 256, MODE>(p, items, n_items, segs, status, lim, st, pdl);
+    if (nslices == 4) return launch_impl<4, 256, MODE>(p, items, n_items, segs, status, lim, st, pdl);
+    if (nslices == 2) return launch_impl<2, 256, MODE>(p, items, n_items, segs, status, lim, st, pdl);
   } else if (bn == 128) {
-    if (nslices == 3) return launch_impl<3, 128, MODE>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 4) return launch_impl<4, 128, MODE>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 2) return launch_impl<2, 128, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 3) return launch_impl<3, 128, MODE>(p, items, n_items, segs, status, lim, st, pdl);
+    if (nslices == 4) return launch_impl<4, 128, MODE>(p, items, n_items, segs, status, lim, st, pdl);
+    if (nslices == 2) return launch_impl<2, 128, MODE>(p, items, n_items, segs, status, lim, st, pdl);
   } else if (bn == 64) {
-    if (nslices == 3) return launch_impl<3, 64, MODE>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 4) return launch_impl<4, 64, MODE>(p, items, n_items, segs, status, lim, st);
-    if (nslices == 2) return launch_impl<2, 64, MODE>(p, items, n_items, segs, status, lim, st);
+    if (nslices == 3) return launch_impl<3, 64, MODE>(p, items, n_items, segs, status, lim, st, pdl);
+    if (nslices == 4) return launch_impl<4, 64, MODE>(p, items, n_items, segs, status, lim, st, pdl);
+    if (nslices == 2) return launch_impl<2, 64, MODE>(p, items, n_items, segs, status, lim, st, pdl);
   }
   return cudaErrorInvalidValue;
 }
@@ -438,15 +438,15 @@ cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, i
   p.nm = (int)(ceil_div((int64_t)seg.nk, OP_ROWS) * OP_ROWS / bn);
   p.nc = nc;
   p.nkb_max = nkb_max;
-  return dispatch<0>(nslices, bn, p, nullptr, 0, nullptr, status, wait_limit_ns, st);
+  return dispatch<0>(nslices, bn, p, nullptr, 0, nullptr, status, wait_limit_ns, st, true);
 }
 
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
-                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl) {
   TcSingle p;
   memset(&p, 0, sizeof(p));
-  if (split) return dispatch<2>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st);
-  return dispatch<1>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st);
+  if (split) return dispatch<2>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st, pdl);
+  return dispatch<1>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st, pdl);
 }
 
 // Reduce the accumulator pairs of a split row tile (one block per 64 rows): for each

@@ -185,8 +185,10 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
                             int nzero = 0);
 
 // tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
+// pdl: launch as a programmatic dependent of the preceding kernel (which
+// must trigger early); off for the grouped path, where it measured slower
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
-                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
+                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl = true);
 // part_rows: 64 (partials per 64-row group) or 32 (per 32-row group, the small-batch layout)
 cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn, cudaStream_t st,
                                 int part_rows = 64);

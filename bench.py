@@ -270,11 +270,26 @@ def grouped_extra(td, torch):
     cols = sum(int(r.shape[0]) for r in Rs)
     flops = sum(float(s.n_kept) ** 2 * int(r.shape[0]) for s, r in zip(segs, Rs))
     g.close()
+    dlogl = None
+    try:   # the four shortest segments against the CPU oracle
+        import oracle
+        worst = 0.0
+        for i in sorted(range(len(specs)), key=lambda j: specs[j]["n"])[:4]:
+            sp = specs[i]
+            acf = inputs.acf_from_psd(int(sp["n"]), sp["fs"], a=sp["a"], floor=sp["floor"])
+            o = oracle.OracleSegment(acf)
+            R = Rs[i].cpu().numpy()
+            exp = oracle.loglike_from_chi2(o.chi2(R), o.logdet, o.n_kept)
+            worst = max(worst, float(np.max(np.abs(outs[i].cpu().numpy() - exp))))
+        dlogl = worst
+    except Exception as ex:
+        dlogl = repr(ex)
     return {"note": "64 segments, N log-uniform in [512, 32768], K uniform in [16, 512], own PSD each "
                     "(operators by the Levinson-Durbin build); one captured-graph grouped launch",
             "segments": len(segs), "columns": cols, "ms_per_launch": ms, "evals_per_s": cols / (ms / 1e3),
             "algorithmic_tflops": flops / (ms / 1e3) / 1e12, "tile_rows": bn, "chunk_factor": sf,
-            "work_items": ni, "autotune_best_ms": tuned_ms, "factor_s": factor_s}
+            "work_items": ni, "autotune_best_ms": tuned_ms, "factor_s": factor_s,
+            "max_abs_dlogL_vs_oracle_4_shortest": dlogl}
 
 
 def serving_extra(td, torch, seconds):
@@ -285,7 +300,7 @@ def serving_extra(td, torch, seconds):
     # 8 segments each of N = 4096, 8192, 16384 with 0..3 gaps of 512; 4 gap-free N = 32768
     fleet = [(n, i % 4) for n in (4096, 8192, 16384) for i in range(8)] + [(32768, 0)] * 4
     srv = td.Server(max_batch_cols=2048, n_streams=4, max_kept=32768, max_pending_cols=1 << 22)
-    ids, pools, info = [], [], []
+    ids, pools, info, models = [], [], [], []
     t0 = time.perf_counter()
     for n, g in fleet:
         mask = inputs.gap_mask(n, g, 512, rng) if g else None
@@ -297,6 +312,7 @@ def serving_extra(td, torch, seconds):
         ids.append(sid)
         pools.append(torch.from_numpy(pool).cuda())
         info.append((n, g))
+        models.append((acf, mask, pool))
     factor_s = time.perf_counter() - t0
     lam = 2000.0
 
@@ -315,16 +331,37 @@ def serving_extra(td, torch, seconds):
         tickets = srv.replay(t[warm:] - t[warm], [ids[s] for s in segs[warm:]], Rs[warm:], outs[warm:])
         srv.drain()
         st = srv.stats()
+        served.append((segs[warm:], Ks[warm:], outs[warm:]))
         return {"seconds": secs, "requests": int(st["requests_done"]), "refused": int(st["refused"]),
                 "failed": int(st["failed"]), "p50_ms": st["p50_us"] / 1e3, "p99_ms": st["p99_us"] / 1e3,
                 "evals_per_s": st["evals_per_s"], "batches": int(st["batches"]),
                 "submitted": int(np.sum(tickets >= 0)), "mean_K": float(np.mean(Ks[warm:]))}
 
+    served = []
     everyone = list(range(len(fleet)))
     mix = phase(everyone, seconds)
     g8 = phase([i for i, (n, g) in enumerate(info) if n == 8192 and g > 0], max(1.0, seconds / 2))
     g16 = phase([i for i, (n, g) in enumerate(info) if n == 16384 and g > 0], max(1.0, seconds / 2))
     srv.close()
+    # accuracy of served results: requests on the gapped N=4096 segments against the CPU oracle
+    dlogl = None
+    try:
+        import oracle
+        cache, worst = {}, 0.0
+        for segs_p, Ks_p, outs_p in served:
+            picked = [i for i, sg in enumerate(segs_p) if info[sg][0] == 4096 and info[sg][1] > 0][:12]
+            for i in picked:
+                sg, k = int(segs_p[i]), int(Ks_p[i])
+                if sg not in cache:
+                    acf, mask, pool = models[sg]
+                    cache[sg] = oracle.OracleSegment(acf, mask)
+                o = cache[sg]
+                R = models[sg][2][:k]
+                exp = oracle.loglike_from_chi2(o.chi2(R), o.logdet, o.n_kept)
+                worst = max(worst, float(np.max(np.abs(outs_p[i].cpu().numpy() - exp))))
+        dlogl = worst
+    except Exception as ex:   # report, do not lose the measured line
+        dlogl = repr(ex)
     # the plain per-request FP64 solve on a gap-free N=8192 segment, for comparison
     acf = inputs.acf_from_psd(8192, 2048.0)
     s64 = td.Segment(acf)
@@ -348,6 +385,8 @@ def serving_extra(td, torch, seconds):
                    "open loop (native replay), K in {1, 8, 64, 512}; phases: whole fleet, gapped N=8192 only, "
                    "gapped N=16384 only",
            "fleet": mix, "gapped_n8192": g8, "gapped_n16384": g16,
+           "max_abs_dlogL_vs_oracle_sampled": dlogl,
+           "dlogL_sample": "served requests on the gapped N=4096 segments (up to 12 per phase), CPU FP64 oracle",
            "fp64_per_request_ms": {"K=1": per[1], "K=64": per[64]},
            "fp64_per_request_evals_per_s_est": fp64_evals_per_s, "factor_s": factor_s}
     # flat keys of the whole-fleet phase (read by earlier tooling)

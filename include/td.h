@@ -63,7 +63,7 @@ typedef enum {
                           double-float.  chi2 ~2e-8 relative to FP64. */
   TD_PREC_BF16X3 = 2,  /* hi + 1 remainder slice, 3 products: ~1e-5 relative, below
                           the accuracy bar (kept to show why more products are needed) */
-  TD_PREC_AUTO = 3,    /* library picks by (N', K) */
+  TD_PREC_AUTO = 3,    /* the library's choice; currently TD_PREC_BF16X6 */
   TD_PREC_BF16X10 = 4  /* 4 slices each, the 10 products a+b <= 3: chi2 ~1e-9 relative */
 } td_precision;
 
@@ -71,9 +71,9 @@ typedef enum {
   TD_PATH_AUTO = 0,
   TD_PATH_TENSOR = 1,   /* tcgen05 split-product GEMM, 256-row operator tiles over whole
                            rows, chi2 in the epilogue (large K) */
-  TD_PATH_STREAM = 2,   /* the same kernel with long rows cut into balanced k-chunks
-                           (more work items; the operator streams from HBM), chunk
-                           results added in double-float by a reduce kernel (small K) */
+  TD_PATH_STREAM = 2,   /* the same kernel with long rows cut into k-chunks of a length
+                           fixed by N' (more work items; the operator streams from HBM),
+                           chunk results added in double-float by a reduce kernel */
   TD_PATH_FP64 = 3,     /* plain FP64 forward substitution */
   TD_PATH_STREAM64 = 4, /* as TD_PATH_STREAM with 64-row operator tiles */
   TD_PATH_SMALLK = 5,   /* K <= 64: operator rows as the MMA M dimension and the residual
@@ -87,7 +87,9 @@ typedef enum {
 typedef struct {
   int precision;        /* td_precision; default TD_PREC_BF16X6 */
   int path;             /* td_path; default TD_PATH_AUTO */
-  int refine;           /* 1: one refinement step s = r - L w (FP64), w += L^{-1} s */
+  int refine;           /* refinement (s = r - L w, w += L^{-1} s) is not built: nonzero
+                           returns TD_ERR_UNSUPPORTED; the split products reach the
+                           accuracy bar in one pass */
   int reserved0;
   int64_t wait_limit_ns;/* bound on any in-kernel wait; <= 0 -> 1 s */
 } td_options;
@@ -136,9 +138,12 @@ td_status td_segment_release_fp64(td_segment* s);
  * flags = TD_FACTOR_NO_FP64: keep only what the tensor-core paths need; every
  * gap-free segment then gets its whitening operator in O(N^2) by the
  * Levinson-Durbin recursion (rows of L^{-1} are the normalised
- * prediction-error filters; Sec. II.B item 6 names Levinson and Durbin),
- * one CTA per segment, all in one launch, and log det C = sum log v_t;
- * segments with gaps use td_factor and then release their FP64 factor.
+ * prediction-error filters; Sec. II.B item 6 names Levinson and Durbin):
+ * one CTA per segment runs the recursion in FP64 and writes the rows, many
+ * segments per launch (batched so their temporary N'^2 FP64 rows fit a
+ * share of free memory), and log det C = sum log v_t; segments with gaps use
+ * td_factor and then release their FP64 factor.  Segments longer than 2^20
+ * samples also take td_factor.
  * The FP64 path of such segments returns TD_ERR_UNSUPPORTED.  Synchronises
  * `stream`; TD_ERR_NOT_PD as td_factor (td_last_pivot gives the order).
  */
@@ -168,9 +173,11 @@ int64_t td_last_pivot(const td_segment* s);
  *   stream: CUDA stream; asynchronous.  The segment's scratch space grows on
  *          first use for a given K (that call may allocate); later calls with
  *          K no larger do not allocate (call td_reserve before graph capture).
- * The results for one column do not depend on the other columns of the batch
- * (fixed reduction order), so a column evaluated alone or in any batch gives
- * the same bits.
+ * With a fixed path (opt->path other than TD_PATH_AUTO) the results for one
+ * column do not depend on the other columns of the batch (fixed reduction
+ * order), so a column evaluated alone or in any batch gives the same bits.
+ * TD_PATH_AUTO picks the tile shape by (N', K), so a different K may change
+ * the last bits (within the accuracy bar, never beyond it).
  */
 td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K,
                            double* logL, const td_options* opt, double* chi2,
@@ -273,7 +280,7 @@ td_status td_reserve(td_segment* s, int64_t K, const td_options* opt);
  * scratch (this call allocates and synchronises).  The plan keeps the
  * pointers it was given: later launches read R[i] and write logL[i] there.
  * td_group_launch enqueues the evaluation on `stream` (four kernels whatever
- * nseg; no allocation; capturable in a CUDA graph).  td_group_graph_launch
+ * nseg, five with a joint sum; no allocation; capturable in a CUDA graph).  td_group_graph_launch
  * captures the launch into a CUDA graph on first use and replays it.
  * td_group_tune times the candidate tile shapes and chunk sizes on the plan's
  * own inputs, keeps the fastest, and records it for later plans of the same

@@ -195,3 +195,52 @@ def test_full_cfg4_largest_segment(torch_cuda, gpu_lib):
     ll, chi = _ll(torch_cuda, td, seg, R)
     _cmp(ll[cols], chi[cols], np.array(g["logL"]), np.array(g["chi2"]), "cfg4 largest")
     seg.close()
+
+
+def test_factor_many_mixed_batch_with_a_bad_segment(torch_cuda, gpu_lib):
+    """One non positive definite ACF among good ones: the good ones are factored
+    and evaluate correctly, the call reports TD_ERR_NOT_PD with the bad pivot."""
+    from paper_2603_06010_b300 import td
+    good = [inputs.acf_from_psd(n, 2048.0) for n in (300, 777)]
+    bad = np.zeros(50)
+    bad[0], bad[1] = 1.0, 0.8
+    segs = [td.Segment(good[0], factor=False), td.Segment(bad, factor=False), td.Segment(good[1], factor=False)]
+    with pytest.raises(td.TdError) as e:
+        td.factor_many(segs)
+    assert e.value.code == td.TD_ERR_NOT_PD
+    assert segs[1].last_pivot == 2
+    for seg, acf in ((segs[0], good[0]), (segs[2], good[1])):
+        o = oracle.OracleSegment(acf)
+        R = inputs.noise_residuals(acf.shape[0], 2048.0, 7, 3)
+        exp_chi = o.chi2(R)
+        ll, chi = _ll(torch_cuda, td, seg, R)
+        _cmp(ll, chi, oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept), exp_chi, "good segment")
+    for s in segs:
+        s.close()
+
+
+def test_grouped_launch_over_levinson_segments(torch_cuda, gpu_lib):
+    """The grouped launch on operators built by the recursion (the 64-segment
+    mix's route), segments of uneven N and K, against the oracle."""
+    from paper_2603_06010_b300 import td
+    specs = [(520, 17), (1900, 140), (3000, 64), (700, 300)]
+    segs, Rs, outs, exp = [], [], [], []
+    for i, (n, K) in enumerate(specs):
+        acf = inputs.acf_from_psd(n, 4096.0, a=-4.2 + 0.1 * i, floor=1.5 + 0.3 * i)
+        R = inputs.noise_residuals(n, 4096.0, K, 40 + i, a=-4.2 + 0.1 * i, floor=1.5 + 0.3 * i)
+        o = oracle.OracleSegment(acf)
+        chi = o.chi2(R)
+        exp.append((oracle.loglike_from_chi2(chi, o.logdet, o.n_kept), chi))
+        segs.append(td.Segment(acf, factor=False))
+        Rs.append(torch_cuda.from_numpy(R).cuda())
+        outs.append(torch_cuda.empty(K, dtype=torch_cuda.float64, device="cuda"))
+    td.factor_many(segs)
+    g = td.Group(segs, Rs, outs)
+    g.graph_launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    for out, (el, ec) in zip(outs, exp):
+        assert np.max(np.abs(out.cpu().numpy() - el)) <= LL_ABS
+    g.close()
+    for s in segs:
+        s.close()

@@ -570,7 +570,8 @@ def main():
                 gbs = op_bytes / (kavg / 1e3) / 1e9
                 small.append({"K": Ks, "path": pname, "kernel_ms": kavg, "call_ms": tot / 20,
                               "evals_per_s": Ks / (tot / 20 / 1e3),
-                              "operator_GBps": gbs, "hbm_frac": gbs / peaks()[0]["hbm_gbs"]})
+                              "operator_GBps": gbs, "hbm_frac": gbs / peaks()[0]["hbm_gbs"],
+                              "call_hbm_frac": op_bytes / (tot / 20 / 1e3) / 1e9 / peaks()[0]["hbm_gbs"]})
 
     if rank != 0:
         if world > 1:
@@ -617,11 +618,12 @@ def main():
                 "note": "bound by the host-to-device copy of the FP32 residuals"},
         "setup": {"factor_s": factor_s, "operator_bytes": seg.resident_bytes},
         "fp64_gpu_baseline": fp64,
-        "small_batches": {"note": "kernel_ms = split-product kernel + chunk reduce (CUDA events around them); "
-                                  "call_ms = whole td_loglike_batch, 20 calls back to back; no L2 flush (the "
-                                  "operator read by each call is larger than L2); algorithmic bytes = operator "
-                                  "slices read once (3 x 2 B per packed lower-triangle element); HBM peak of "
-                                  "measured",
+        "small_batches": {"note": "kernel_ms = the tensor-core product kernel alone (CUDA events around it); "
+                                  "call_ms = whole td_loglike_batch (slicing, product, chunk reduction, logL), "
+                                  "20 calls back to back; no L2 flush (the operator read by each call is larger "
+                                  "than L2); algorithmic bytes = operator slices read once (3 x 2 B per packed "
+                                  "lower-triangle element); hbm_frac = of the kernel, call_hbm_frac = of the "
+                                  "whole call, both of measured HBM bandwidth",
                           "runs": small},
         "clocks": clk,
     }

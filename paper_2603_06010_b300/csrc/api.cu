@@ -94,15 +94,15 @@ static Shape choose_shape(const td_segment* s, int64_t K, int path) {
   // small-batch kernel: K <= 32 automatically (measured at N' = 8192: K = 64 takes
   // 97 us there against 91 us as 128-row chunks); up to 64 when asked for
   if (path == TD_PATH_SMALLK || (path == TD_PATH_AUTO && K <= 32)) return {0, true};
-  // measured on B300 (N' = 8192): 256-row whole rows win from K ~ 1024 up;
-  // for mid-size batches 128-row whole rows (two TMEM accumulator pairs, so
-  // epilogues overlap MMAs) win once there is about one tile per SM; below
-  // that, 128-row tiles with k-chunks (K = 64: 100 us vs 120 us for 256-row
-  // chunks; K = 256: 163 us whole 128-row vs 280 us 256-row chunks)
+  // measured on B300 (N' = 8192, one call after an L2 flush): 256-row whole
+  // rows win from K = 1024 (250 us vs 275 us for 128-row); 128-row whole rows
+  // (two TMEM accumulator pairs, so epilogues overlap MMAs) at K = 384..512
+  // (155 us vs 238 us for 256-row); 128-row tiles with k-chunks below that
+  // (K = 128: 91 us vs 149 us whole rows; K = 256: a tie at 155 us)
   const int64_t nc = ceil_div(K, TC_COLS);
   const int64_t items256 = (s->nkp / OP_ROWS) * nc;
   const int64_t items128 = (s->nkp / 128) * nc;
-  if (items256 >= 2 * (int64_t)tc_num_sms()) return {256, false};
+  if (2 * items256 >= 3 * (int64_t)tc_num_sms()) return {256, false};
   if (4 * items128 >= 3 * (int64_t)tc_num_sms()) return {128, false};
   return {128, true};
 }
@@ -502,25 +502,27 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     const int ncs = K <= 16 ? 16 : (K <= 32 ? 32 : 64);
     SplitPlan* plan = nullptr;
     if ((r = get_split_plan(s, ncs, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
-    // two launches: the slicing (which also clears the plan's counters) and the
-    // product with the chunk reduction and logL fused in
+    // three launches chained as programmatic dependents: the slicing (which also
+    // clears the plan's completion counter), the product, the chunk reduction
+    // with chi2 and logL
     TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st, plan->counters, plan->n_units + 1));
-    if (pm) prof_mark(s, st, true);
-    const SmallFinal fin{plan->units, plan->counters, plan->n_units, (int)K, logL, chi2};
-    TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, fin, st));
+    if (pm) prof_mark(s, st, true);   // the events bracket the product kernel alone
+    TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, st));
     if (pm) prof_mark(s, st, false);
-    s->prof_kernels += 2;
+    const SmallFinal fin{plan->units, plan->counters, plan->n_units, (int)K, logL, chi2};
+    TD_CUDA(launch_small_reduce(plan->segdev, fin, st));
+    s->prof_kernels += 3;
     return TD_OK;
   }
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   if (shape.split) {
     SplitPlan* plan = nullptr;
     if ((r = get_split_plan(s, plan_width(K), nsl, bn, st, &plan)) != TD_OK) return r;
-    if (pm) prof_mark(s, st, true);
+    if (pm) prof_mark(s, st, true);   // the events bracket the product kernel alone
     TD_CUDA(launch_tc_cdo(plan->items, plan->n_items, plan->segdev, nsl, bn, true, s->status, o.wait_limit_ns,
                           st));
-    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, bn, st));
     if (pm) prof_mark(s, st, false);
+    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, bn, st, 64, plan->K));
     TD_CUDA(launch_finalize(sc.partials, ldp, ngroups, K, s->logdet, s->nk, logL, chi2, st));
     s->prof_kernels += plan->n_units > 0 ? 4 : 3;
     return TD_OK;

@@ -38,6 +38,8 @@
 // TMEM holds NBUF pairs of accumulators (one pair for BN = 256, two for
 // BN = 128 and 64 so the epilogue of one tile overlaps the MMAs of the next).  Every
 // wait is bounded (wait_limit_ns).
+#include <algorithm>
+
 #include "td_internal.h"
 
 namespace td {
@@ -461,23 +463,46 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
 // in a fixed order.
 __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restrict__ units,
                                                        const TcSegDev* __restrict__ segs, int bn, int part_rows) {
-  __shared__ float red_hi[128][2], red_lo[128][2];
+  __shared__ float red_hi[16][2], red_lo[16][2];
   const SplitUnit u = units[blockIdx.x];
   const int g64 = blockIdx.y;                   // 64-row group of the bn-row tile
+  const int c16 = blockIdx.z * 16;              // 16-column slice of the 128-column tile
   const TcSegDev& sd = segs[u.seg];
   const int row = threadIdx.x & 63, grp = threadIdx.x >> 6;   // 4 column groups of 2 warps
   const int wig = (threadIdx.x >> 5) & 1, lane = threadIdx.x & 31;
   const int ncol = min(128, sd.K - u.c * 128);
+  if (c16 >= ncol) return;
   const float2* base = sd.wpart + (int64_t)u.slot0 * 128 * bn + g64 * 64 + row;
-  for (int cl = grp; cl < ncol; cl += 4) {
-    float wh = 0.f, wl = 0.f;
-    for (int ch = 0; ch < u.nchunk; ++ch) {
-      const float2 v = base[((int64_t)ch * 128 + cl) * bn];
-      ff_add(v.x, wh, wl);
-      ff_add(v.y, wh, wl);
-    }
+  // this thread's four columns c16 + grp + 4 c: the chunk pairs are loaded eight
+  // chunks deep from clamped (in-range) addresses, then added in chunk order
+  constexpr int CB = 4, CH = 8;
+  float wh[CB], wl[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
+  for (int ch0 = 0; ch0 < u.nchunk; ch0 += CH) {
+    float2 v[CH][CB];
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const int ch = min(ch0 + i, u.nchunk - 1), cl = min(c16 + grp + 4 * c, ncol - 1);
+        v[i][c] = __ldcg(base + ((int64_t)ch * 128 + cl) * bn);
+      }
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (ch0 + i < u.nchunk) {
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          ff_add(v[i][c].x, wh[c], wl[c]);
+          ff_add(v[i][c].y, wh[c], wl[c]);
+        }
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < CB; ++c) {
+    const int cl = c16 + grp + 4 * c;
     float hi = 0.f, lo = 0.f;
-    ff_add_square2(wh, wl, hi, lo);
+    ff_add_square2(wh[c], wl[c], hi, lo);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
       const float oh = __shfl_down_sync(0xffffffffu, hi, off);
@@ -485,28 +510,30 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
       ff_add(oh, hi, lo);
       lo += ol;
     }
-    if (lane == 0) {
+    if (lane == 0 && cl < ncol) {
       if (part_rows == 32) {
         sd.partials[(((int64_t)u.m * (bn / 64) + g64) * 2 + wig) * sd.ldp + u.c * 128 + cl] =
             (double)hi + (double)lo;
       } else {
-        red_hi[cl][wig] = hi;
-        red_lo[cl][wig] = lo;
+        red_hi[cl - c16][wig] = hi;
+        red_lo[cl - c16][wig] = lo;
       }
     }
   }
   if (part_rows == 32) return;
   __syncthreads();
-  for (int cl = threadIdx.x; cl < ncol; cl += blockDim.x) {
+  if (threadIdx.x < 16 && c16 + (int)threadIdx.x < ncol) {
+    const int cl = threadIdx.x;
     const double s = ((double)red_hi[cl][0] + (double)red_lo[cl][0]) + ((double)red_hi[cl][1] + (double)red_lo[cl][1]);
-    sd.partials[((int64_t)u.m * (bn / 64) + g64) * sd.ldp + u.c * 128 + cl] = s;
+    sd.partials[((int64_t)u.m * (bn / 64) + g64) * sd.ldp + u.c * 128 + c16 + cl] = s;
   }
 }
 
 cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn,
-                                cudaStream_t st, int part_rows) {
+                                cudaStream_t st, int part_rows, int64_t max_cols) {
   if (n_units <= 0) return cudaSuccess;
-  k_split_reduce<<<dim3(n_units, bn / 64), 256, 0, st>>>(units, segs, bn, part_rows);
+  const unsigned nz = (unsigned)ceil_div(std::min<int64_t>(std::max<int64_t>(max_cols, 1), 128), 16);
+  k_split_reduce<<<dim3(n_units, bn / 64, nz), 256, 0, st>>>(units, segs, bn, part_rows);
   return cudaGetLastError();
 }
 

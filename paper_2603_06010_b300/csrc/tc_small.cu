@@ -442,7 +442,7 @@ static cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, size_t smem
 
 template <int NSL, int NC>
 static cudaError_t launch_small_impl(const TcItem* items, int n_items, const TcSegDev* segs, DevStatus* status,
-                                     int64_t lim, const SmallFinal& fin, cudaStream_t st) {
+                                     int64_t lim, cudaStream_t st) {
   using C = tsm::Cfg<NSL, NC>;
   static bool attr_set = false;
   if (!attr_set) {
@@ -455,29 +455,25 @@ static cudaError_t launch_small_impl(const TcItem* items, int n_items, const TcS
   if (grid > n_items) grid = n_items;
   uint64_t lim64 = (uint64_t)lim;
   void* a1[] = {(void*)&items, (void*)&n_items, (void*)&segs, (void*)&status, (void*)&lim64};
-  cudaError_t e = launch_pdl((const void*)k_tc_small<NSL, NC>, dim3((unsigned)grid), dim3(tsm::THREADS), C::SMEM, st, a1);
-  if (e != cudaSuccess) return e;
-  const dim3 rgrid(fin.n_units > 0 ? (unsigned)fin.n_units : 1u, fin.n_units > 0 ? (unsigned)((fin.K + 3) / 4) : 1u);
-  void* a2[] = {(void*)&segs, (void*)&fin};
-  return launch_pdl((const void*)k_small_reduce, rgrid, dim3(128), 0, st, a2);
+  return launch_pdl((const void*)k_tc_small<NSL, NC>, dim3((unsigned)grid), dim3(tsm::THREADS), C::SMEM, st, a1);
 }
 
 cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
-                            DevStatus* status, int64_t wait_limit_ns, const SmallFinal& fin, cudaStream_t st) {
-  if (nc == 16) {
-    if (nslices == 3) return launch_small_impl<3, 16>(items, n_items, segs, status, wait_limit_ns, fin, st);
-    if (nslices == 4) return launch_small_impl<4, 16>(items, n_items, segs, status, wait_limit_ns, fin, st);
-    if (nslices == 2) return launch_small_impl<2, 16>(items, n_items, segs, status, wait_limit_ns, fin, st);
-  } else if (nc == 32) {
-    if (nslices == 3) return launch_small_impl<3, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
-    if (nslices == 4) return launch_small_impl<4, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
-    if (nslices == 2) return launch_small_impl<2, 32>(items, n_items, segs, status, wait_limit_ns, fin, st);
-  } else if (nc == 64) {
-    if (nslices == 3) return launch_small_impl<3, 64>(items, n_items, segs, status, wait_limit_ns, fin, st);
-    if (nslices == 4) return launch_small_impl<4, 64>(items, n_items, segs, status, wait_limit_ns, fin, st);
-    if (nslices == 2) return launch_small_impl<2, 64>(items, n_items, segs, status, wait_limit_ns, fin, st);
-  }
+                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+#define TD_SMALL_CASE(NSL_, NC_) \
+  if (nslices == NSL_ && nc == NC_) return launch_small_impl<NSL_, NC_>(items, n_items, segs, status, wait_limit_ns, st);
+  TD_SMALL_CASE(3, 16) TD_SMALL_CASE(4, 16) TD_SMALL_CASE(2, 16)
+  TD_SMALL_CASE(3, 32) TD_SMALL_CASE(4, 32) TD_SMALL_CASE(2, 32)
+  TD_SMALL_CASE(3, 64) TD_SMALL_CASE(4, 64) TD_SMALL_CASE(2, 64)
+#undef TD_SMALL_CASE
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_small_reduce(const TcSegDev* segs, const SmallFinal& fin, cudaStream_t st) {
+  const dim3 rgrid(fin.n_units > 0 ? (unsigned)fin.n_units : 1u, fin.n_units > 0 ? (unsigned)((fin.K + 3) / 4) : 1u);
+  SmallFinal f = fin;
+  void* a2[] = {(void*)&segs, (void*)&f};
+  return launch_pdl((const void*)k_small_reduce, rgrid, dim3(128), 0, st, a2);
 }
 
 }  // namespace td

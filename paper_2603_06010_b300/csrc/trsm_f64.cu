@@ -121,7 +121,14 @@ __global__ void k_finalize(const double* __restrict__ partials, int64_t ldp, int
   const int64_t col = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col >= K) return;
   double s = 0.0;
-  for (int p = lane; p < nparts; p += 32) s += partials[(int64_t)p * ldp + col];
+  for (int p0 = lane; p0 < nparts; p0 += 32 * 8) {
+    double v[8];   // eight loads in flight (clamped addresses), then the additions in order
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = partials[(int64_t)min(p0 + 32 * i, nparts - 1) * ldp + col];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (p0 + 32 * i < nparts) s += v[i];
+  }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   if (lane == 0) {

@@ -244,3 +244,18 @@ def test_grouped_launch_over_levinson_segments(torch_cuda, gpu_lib):
     g.close()
     for s in segs:
         s.close()
+
+
+def test_auto_precision_switches_above_32768(torch_cuda, gpu_lib):
+    """TD_PREC_AUTO: six products up to N' = 32768, ten beyond (same bits as the
+    explicit choice)."""
+    from paper_2603_06010_b300 import td
+    for n, expect in ((2000, td.TD_PREC_BF16X6), (33000, td.TD_PREC_BF16X10)):
+        acf = inputs.acf_from_psd(n, 4096.0)
+        seg = td.Segment(acf, factor=False)
+        td.factor_many([seg])
+        R = np.random.default_rng(n).standard_normal((8, n)).astype(np.float32) * np.float32(np.sqrt(acf[0]))
+        la, ca = _ll(torch_cuda, td, seg, R, td.TD_PREC_AUTO)
+        le, ce = _ll(torch_cuda, td, seg, R, expect)
+        assert np.array_equal(la, le) and np.array_equal(ca, ce), n
+        seg.close()

@@ -111,7 +111,7 @@ class Clocks:
 
 def make_workload(rank: int):
     from paper_2603_06010_b300 import inputs
-    c = inputs.CFG2
+    c = inputs.GAPFREE_N8192_K4096
     seg = inputs.make_segment(c["n"], c["fs"], c["seed"])
     R = inputs.residual_batch(seg, c["K"], c["seed"] + 1 + 7919 * rank)
     return c, seg, R
@@ -132,7 +132,7 @@ def golden_dlogl(logL_host):
     """max |dlogL| on the stored oracle columns (rank 0's batch only)."""
     try:
         with open(os.path.join(ROOT, "tests", "golden", "full_size.json")) as f:
-            g = json.load(f)["cfg2"]
+            g = json.load(f)["gapfree_n8192_k4096"]
         cols = g["columns"]
         return float(np.max(np.abs(logL_host[cols] - np.array(g["logL"]))))
     except Exception:
@@ -187,7 +187,7 @@ def gapped_joint_extra(td, torch):
     (N'=14848) per detector, PSD scales 1.0/1.3/2.1, K=1024 residuals each, the
     joint logL summed over detectors in the same captured launch."""
     from paper_2603_06010_b300 import inputs
-    c = inputs.CFG3
+    c = inputs.GAPPED_N16384_3DET
     t0 = time.perf_counter()
     segs, Rs, outs, gold = [], [], [], None
     for d, sc in enumerate(c["scales"]):
@@ -218,7 +218,7 @@ def gapped_joint_extra(td, torch):
     dlogl = None
     try:
         with open(os.path.join(ROOT, "tests", "golden", "full_size.json")) as f:
-            gg = json.load(f)["cfg3"]
+            gg = json.load(f)["gapped_n16384_3det"]
         jl = joint.cpu().numpy()
         dlogl = float(np.max(np.abs(jl[gg["columns"]] - np.array(gg["joint_logL"]))))
     except (OSError, KeyError):
@@ -238,7 +238,7 @@ def gapped_joint_extra(td, torch):
 def grouped_extra(td, torch):
     """The 64-segment uneven mix (N log-uniform in [512, 32768]) in one grouped launch."""
     from paper_2603_06010_b300 import inputs
-    specs = inputs.cfg4_segments(count=64)
+    specs = inputs.mix64_segments(count=64)
     rng = np.random.default_rng(4040)
     segs, Rs, outs = [], [], []
     t0 = time.perf_counter()

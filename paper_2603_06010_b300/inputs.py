@@ -245,13 +245,13 @@ def noise_residuals(n: int, fs: float, K: int, seed: int, mask: np.ndarray | Non
 # ----------------------------------------------------------------------------
 # the configurations of the benchmark suite (shapes of the paper's segments)
 # ----------------------------------------------------------------------------
-CFG1 = dict(name="single_n1024", n=1024, fs=1024.0, K=1, n_gaps=0, seed=1001)
-CFG2 = dict(name="gapfree_n8192_k4096", n=8192, fs=2048.0, K=4096, n_gaps=0, seed=2002)
-CFG3 = dict(name="gapped_n16384_3det_k1024", n=16384, fs=2048.0, K=1024, n_gaps=3,
+SINGLE_N1024 = dict(name="single_n1024", n=1024, fs=1024.0, K=1, n_gaps=0, seed=1001)
+GAPFREE_N8192_K4096 = dict(name="gapfree_n8192_k4096", n=8192, fs=2048.0, K=4096, n_gaps=0, seed=2002)
+GAPPED_N16384_3DET = dict(name="gapped_n16384_3det_k1024", n=16384, fs=2048.0, K=1024, n_gaps=3,
             gap_len=512, scales=(1.0, 1.3, 2.1), seed=3003)
 
 
-def cfg4_segments(seed: int = 4004, count: int = 64) -> list[dict]:
+def mix64_segments(seed: int = 4004, count: int = 64) -> list[dict]:
     """64 disjoint segments: N log-uniform in [512, 32768] at 4096 Hz, K uniform
     in [16, 512], PSD exponent -4 +- 0.5 and floor 2 +- 1."""
     rng = np.random.default_rng(seed)

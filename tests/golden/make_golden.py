@@ -42,9 +42,9 @@ def one(n, fs, seed, K, rseed, cols, n_gaps=0, gap_len=512, scale=1.0):
                 r_checksum=[float(np.sum(sub[i].astype(np.float64))) for i in range(len(cols))])
 
 
-def cfg4_largest():
+def mix64_longest():
     """Longest segment of the 64-segment mix, coloured-noise residuals of its own PSD."""
-    specs = inputs.cfg4_segments()
+    specs = inputs.mix64_segments()
     i = max(range(len(specs)), key=lambda j: specs[j]["n"])
     sp = specs[i]
     rseed = sp["seed"] + 7
@@ -68,24 +68,24 @@ def main():
         with open(OUT) as f:
             out = json.load(f)
     want = (lambda k: not keys or k in keys)
-    if want("cfg1"):
-        c1 = inputs.CFG1
-        out["cfg1"] = one(c1["n"], c1["fs"], c1["seed"], 1, c1["seed"] + 1, [0])
-    if want("cfg2"):
-        c2 = inputs.CFG2
+    if want("single_n1024"):
+        c1 = inputs.SINGLE_N1024
+        out["single_n1024"] = one(c1["n"], c1["fs"], c1["seed"], 1, c1["seed"] + 1, [0])
+    if want("gapfree_n8192_k4096"):
+        c2 = inputs.GAPFREE_N8192_K4096
         cols2 = sample_cols(c2["K"], [0, 1, 2, 3, 127, 128, 129, 1000, 2047, 2048, 3001, 4094, 4095])
-        out["cfg2"] = one(c2["n"], c2["fs"], c2["seed"], c2["K"], c2["seed"] + 1, cols2)
-    if want("cfg3"):
-        c3 = inputs.CFG3
+        out["gapfree_n8192_k4096"] = one(c2["n"], c2["fs"], c2["seed"], c2["K"], c2["seed"] + 1, cols2)
+    if want("gapped_n16384_3det"):
+        c3 = inputs.GAPPED_N16384_3DET
         cols3 = sample_cols(c3["K"], [0, 1, 100, 511, 512, 1022, 1023])
         dets = []
         for d, sc in enumerate(c3["scales"]):
             dets.append(one(c3["n"], c3["fs"], c3["seed"] + 10 * d, c3["K"], c3["seed"] + 10 * d + 1, cols3,
                             n_gaps=c3["n_gaps"], gap_len=c3["gap_len"], scale=sc))
-        out["cfg3"] = dict(detectors=dets, columns=cols3,
+        out["gapped_n16384_3det"] = dict(detectors=dets, columns=cols3,
                            joint_logL=np.sum([d_["logL"] for d_ in dets], axis=0).tolist())
-    if want("cfg4_largest"):
-        out["cfg4_largest"] = cfg4_largest()
+    if want("mix64_longest"):
+        out["mix64_longest"] = mix64_longest()
     with open(OUT, "w") as f:
         json.dump(out, f, indent=1)
     print(f"wrote {OUT} in {time.time() - t0:.1f} s")

@@ -162,10 +162,10 @@ def _golden():
         return json.load(f)
 
 
-def test_full_cfg2_via_levinson(torch_cuda, gpu_lib):
+def test_full_gapfree_n8192_via_levinson(torch_cuda, gpu_lib):
     """The gap-free N=8192, K=4096 batch with the operator built in O(N^2)."""
     from paper_2603_06010_b300 import td
-    g = _golden()["cfg2"]
+    g = _golden()["gapfree_n8192_k4096"]
     seg_in = inputs.make_segment(g["n"], g["fs"], g["seed"], n_gaps=g["n_gaps"], gap_len=g["gap_len"],
                                  scale=g["scale"])
     R = inputs.residual_batch(seg_in, g["K"], g["rseed"])
@@ -174,14 +174,14 @@ def test_full_cfg2_via_levinson(torch_cuda, gpu_lib):
     assert abs(seg.logdet - g["logdet"]) <= 1e-9 * abs(g["logdet"])
     ll, chi = _ll(torch_cuda, td, seg, R)
     cols = g["columns"]
-    _cmp(ll[cols], chi[cols], np.array(g["logL"]), np.array(g["chi2"]), "cfg2 Levinson")
+    _cmp(ll[cols], chi[cols], np.array(g["logL"]), np.array(g["chi2"]), "gap-free N=8192 Levinson")
     seg.close()
 
 
-def test_full_cfg4_largest_segment(torch_cuda, gpu_lib):
+def test_full_mix64_longest_segment(torch_cuda, gpu_lib):
     """The longest segment of the 64-segment mix (N=32257) against stored oracle values."""
     from paper_2603_06010_b300 import td
-    g = _golden().get("cfg4_largest")
+    g = _golden().get("mix64_longest")
     if g is None:
         pytest.skip("no stored values")
     acf = inputs.acf_from_psd(g["n"], g["fs"], a=g["a"], floor=g["floor"])
@@ -193,7 +193,7 @@ def test_full_cfg4_largest_segment(torch_cuda, gpu_lib):
     td.factor_many([seg])
     assert abs(seg.logdet - g["logdet"]) <= 1e-9 * abs(g["logdet"])
     ll, chi = _ll(torch_cuda, td, seg, R)
-    _cmp(ll[cols], chi[cols], np.array(g["logL"]), np.array(g["chi2"]), "cfg4 largest")
+    _cmp(ll[cols], chi[cols], np.array(g["logL"]), np.array(g["chi2"]), "mix64 longest")
     seg.close()
 
 

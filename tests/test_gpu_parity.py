@@ -220,29 +220,29 @@ def _full_case(torch, td, g, prec):
 
 
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x10", "fp64"])
-def test_full_cfg1(torch_cuda, gpu_lib, prec):
+def test_full_single_n1024(torch_cuda, gpu_lib, prec):
     from paper_2603_06010_b300 import td
-    g = _golden()["cfg1"]
+    g = _golden()["single_n1024"]
     ll, chi = _full_case(torch_cuda, td, g, prec)
-    _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg1")
+    _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "single_n1024")
 
 
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x10"])
-def test_full_cfg2_gapfree_8192(torch_cuda, gpu_lib, prec):
+def test_full_gapfree_n8192_k4096(torch_cuda, gpu_lib, prec):
     from paper_2603_06010_b300 import td
-    g = _golden()["cfg2"]
+    g = _golden()["gapfree_n8192_k4096"]
     ll, chi = _full_case(torch_cuda, td, g, prec)
-    _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg2")
+    _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "gapfree_n8192_k4096")
 
 
 @pytest.mark.parametrize("prec", ["bf16x6", "bf16x10"])
-def test_full_cfg3_gapped_three_detectors(torch_cuda, gpu_lib, prec):
+def test_full_gapped_n16384_three_detectors(torch_cuda, gpu_lib, prec):
     from paper_2603_06010_b300 import td
-    gg = _golden()["cfg3"]
+    gg = _golden()["gapped_n16384_3det"]
     joint = None
     for g in gg["detectors"]:
         ll, chi = _full_case(torch_cuda, td, g, prec)
-        _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "cfg3 detector")
+        _compare(prec, ll, chi, np.array(g["logL"]), np.array(g["chi2"]), "gapped N=16384 detector")
         joint = ll if joint is None else joint + ll
     assert np.max(np.abs(joint - np.array(gg["joint_logL"]))) <= 1e-3
 

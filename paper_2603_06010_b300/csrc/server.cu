@@ -52,11 +52,18 @@ struct SegEntry {
   std::deque<int64_t> queue;  // pending tickets
 };
 
+struct ColRef {               // one column of a batch: where it comes from, where its logL goes
+  const float* src;
+  double* dst;
+};
+
 struct Slot {                 // one stream and its batch buffers
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
   float* Rb = nullptr;        // N'max x max_cols batch residuals
   double* Lb = nullptr;       // max_cols batch logL
+  ColRef* refs_h = nullptr;   // pinned host, max_cols: the batch's column map
+  ColRef* refs_d = nullptr;   // device copy of it
   bool busy = false;
   int64_t seg = -1;
   std::vector<int64_t> tickets;
@@ -90,6 +97,20 @@ struct td_server {
 };
 
 namespace td {
+
+// a batch's columns, gathered from the requests' buffers into one N' x cols
+// block (one CTA per column) and its logL scattered back: two launches per
+// batch instead of two copies per request
+__global__ void k_gather_cols(const ColRef* __restrict__ refs, int64_t nk, float* __restrict__ Rb) {
+  const float* src = refs[blockIdx.x].src;
+  float* dst = Rb + (int64_t)blockIdx.x * nk;
+  for (int64_t j = threadIdx.x; j < nk; j += blockDim.x) dst[j] = src[j];
+}
+
+__global__ void k_scatter_logl(const ColRef* __restrict__ refs, int64_t cols, const double* __restrict__ Lb) {
+  const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k < cols) *refs[k].dst = Lb[k];
+}
 
 static void seg_evict(td_server* srv, SegEntry& e) {
   if (!e.resident) return;
@@ -197,20 +218,25 @@ static void scheduler_loop(td_server* srv) {
     td_status st = seg_make_resident(srv, pick, sl.st);
     const int64_t nk = e.s->nk;
     if (st == TD_OK) {
-      // pack the columns, evaluate, scatter logL
+      // the batch's column map (the slot's previous batch has completed, so the
+      // pinned map is free), gather, evaluate, scatter logL
       int64_t off = 0;
       for (int64_t t : sl.tickets) {
         const Request& r = srv->reqs[t];
-        cudaMemcpy2DAsync(sl.Rb + off * nk, (size_t)nk * 4, r.R, (size_t)r.ldr * 4, (size_t)nk * 4, (size_t)r.K,
-                          cudaMemcpyDeviceToDevice, sl.st);
+        for (int64_t k = 0; k < r.K; ++k) sl.refs_h[off + k] = ColRef{r.R + k * r.ldr, r.logL + k};
         off += r.K;
       }
-      st = td_loglike_batch(e.s, sl.Rb, nk, cols, sl.Lb, &opt, nullptr, sl.st);
-      off = 0;
-      for (int64_t t : sl.tickets) {
-        const Request& r = srv->reqs[t];
-        cudaMemcpyAsync(r.logL, sl.Lb + off, (size_t)r.K * 8, cudaMemcpyDeviceToDevice, sl.st);
-        off += r.K;
+      cudaError_t ce = cudaMemcpyAsync(sl.refs_d, sl.refs_h, (size_t)cols * sizeof(ColRef), cudaMemcpyHostToDevice,
+                                       sl.st);
+      if (ce == cudaSuccess) {
+        k_gather_cols<<<(unsigned)cols, 256, 0, sl.st>>>(sl.refs_d, nk, sl.Rb);
+        ce = cudaGetLastError();
+      }
+      st = ce == cudaSuccess ? td_loglike_batch(e.s, sl.Rb, nk, cols, sl.Lb, &opt, nullptr, sl.st)
+                             : cuda_fail(ce, "server batch gather");
+      if (st == TD_OK) {
+        k_scatter_logl<<<(unsigned)ceil_div(cols, 256), 256, 0, sl.st>>>(sl.refs_d, cols, sl.Lb);
+        if ((ce = cudaGetLastError()) != cudaSuccess) st = cuda_fail(ce, "server batch scatter");
       }
     }
     if (st != TD_OK) {
@@ -287,8 +313,10 @@ static void completion_loop(td_server* srv) {
       srv->cv_done.notify_all();
       srv->cv_sched.notify_all();
     } else {
+      // batches in flight: poll again at once (a sleep here costs tens of
+      // microseconds of latency per request); this thread spins a core
       lk.unlock();
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      std::this_thread::yield();
       lk.lock();
     }
   }
@@ -327,7 +355,9 @@ td_status td_server_create(const td_server_config* cfg, td_server** out) {
     if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&sl.Rb, (size_t)srv->cfg.max_kept * srv->cfg.max_batch_cols * 4) != cudaSuccess ||
-        cudaMalloc(&sl.Lb, (size_t)srv->cfg.max_batch_cols * 8) != cudaSuccess) {
+        cudaMalloc(&sl.Lb, (size_t)srv->cfg.max_batch_cols * 8) != cudaSuccess ||
+        cudaMallocHost(&sl.refs_h, (size_t)srv->cfg.max_batch_cols * sizeof(ColRef)) != cudaSuccess ||
+        cudaMalloc(&sl.refs_d, (size_t)srv->cfg.max_batch_cols * sizeof(ColRef)) != cudaSuccess) {
       cudaGetLastError();
       td_server_destroy(srv);
       return fail(TD_ERR_OOM, "server stream buffers");
@@ -512,6 +542,8 @@ void td_server_destroy(td_server* srv) {
   for (Slot& sl : srv->slots) {
     if (sl.Rb) cudaFree(sl.Rb);
     if (sl.Lb) cudaFree(sl.Lb);
+    if (sl.refs_h) cudaFreeHost(sl.refs_h);
+    if (sl.refs_d) cudaFree(sl.refs_d);
     if (sl.done) cudaEventDestroy(sl.done);
     if (sl.st) cudaStreamDestroy(sl.st);
   }

@@ -175,6 +175,7 @@ static void scheduler_loop(td_server* srv) {
   td_options_default(&opt);
   opt.precision = srv->cfg.precision;
   std::unique_lock<std::mutex> lk(srv->mu);
+  Clock::time_point last_batch = Clock::now();
   while (!srv->stop) {
     // a free slot and a segment with pending columns that has no batch in flight
     int slot = -1;
@@ -197,9 +198,18 @@ static void scheduler_loop(td_server* srv) {
       }
     }
     if (slot < 0 || pick < 0) {
-      srv->cv_sched.wait_for(lk, std::chrono::milliseconds(5));
+      // idle: spin for up to a millisecond after the last batch (a condition
+      // variable wake-up costs tens of microseconds per request), then sleep
+      if (Clock::now() - last_batch < std::chrono::milliseconds(1)) {
+        lk.unlock();
+        std::this_thread::yield();
+        lk.lock();
+      } else {
+        srv->cv_sched.wait_for(lk, std::chrono::milliseconds(5));
+      }
       continue;
     }
+    last_batch = Clock::now();
     Slot& sl = srv->slots[(size_t)slot];
     SegEntry& e = srv->segs[(size_t)pick];
     // gather whole requests up to the batch width (oldest first)
@@ -217,7 +227,11 @@ static void scheduler_loop(td_server* srv) {
     if (sl.tickets.empty()) continue;
     td_status st = seg_make_resident(srv, pick, sl.st);
     const int64_t nk = e.s->nk;
-    if (st == TD_OK) {
+    if (st == TD_OK && sl.tickets.size() == 1) {
+      // one request: evaluate it in place (its R and logL are device buffers)
+      const Request& r = srv->reqs[sl.tickets[0]];
+      st = td_loglike_batch(e.s, r.R, r.ldr, r.K, r.logL, &opt, nullptr, sl.st);
+    } else if (st == TD_OK) {
       // the batch's column map (the slot's previous batch has completed, so the
       // pinned map is free), gather, evaluate, scatter logL
       int64_t off = 0;

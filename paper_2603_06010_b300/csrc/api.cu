@@ -526,7 +526,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     TD_CUDA(launch_tc_cdo(plan->items, plan->n_items, plan->segdev, nsl, bn, true, s->status, o.wait_limit_ns,
                           st));
     if (pm) prof_mark(s, st, false);
-    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, bn, st, 64, plan->K));
+    TD_CUDA(launch_split_reduce(plan->units, plan->n_units, plan->segdev, bn, st, plan->K));
     TD_CUDA(launch_finalize(sc.partials, ldp, ngroups, K, s->logdet, s->nk, logL, chi2, st));
     s->prof_kernels += plan->n_units > 0 ? 4 : 3;
     return TD_OK;

@@ -239,7 +239,7 @@ static td_status group_launch_impl(td_group* g, cudaStream_t st) {
   }
   TD_CUDA(launch_tc_cdo(g->d_items, g->n_items, g->d_seg, g->nsl, g->bn, true, g->status, g->wait_limit_ns, st,
                         false));
-  TD_CUDA(launch_split_reduce(g->d_units, g->n_units, g->d_seg, g->bn, st, 64, g->maxK));
+  TD_CUDA(launch_split_reduce(g->d_units, g->n_units, g->d_seg, g->bn, st, g->maxK));
   TD_CUDA(launch_tc_finalize(g->d_seg, g->nseg, g->maxK, st));
   if (g->joint && g->joint_K > 0) {
     k_joint_sum<<<(unsigned)ceil_div(g->joint_K, 256), 256, 0, st>>>(g->d_seg, g->nseg, g->joint_K, g->joint);

@@ -451,18 +451,16 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
   return dispatch<1>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st, pdl);
 }
 
-// Reduce the accumulator pairs of a split row tile (one block per 64 rows): for each
-// row, w = sum over chunks of (hi*hi sum + correction sum), in double-float
-// (the hi*hi sums are exact, their sum stays exact well past these lengths);
-// then the chi2 share of the rows in double-float, as FP64 partials per
-// 64-row group (part_rows = 64) or per 32-row warp group (part_rows = 32).
-// Thread (row, column group): rows are contiguous in the slot layout, so a
-// warp's loads are coalesced; columns are dealt round-robin to the four
-// column groups so every warp works even for a few columns; the sum over a
-// warp's 32 rows is a fixed shuffle tree, the two warps of a group are added
-// in a fixed order.
+// Reduce the accumulator pairs of a split row tile (one block per 64 rows and
+// 16 columns): for each row, w = sum over chunks of (hi*hi sum + correction
+// sum), in double-float (the hi*hi sums are exact, their sum stays exact well
+// past these lengths); then the chi2 share of the rows in double-float, as
+// FP64 partials per 64-row group.  Thread (row, column group): rows are
+// contiguous in the slot layout, so a warp's loads are coalesced; the four
+// column groups take columns round-robin; the sum over a warp's 32 rows is a
+// fixed shuffle tree, the two warps of a group are added in a fixed order.
 __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restrict__ units,
-                                                       const TcSegDev* __restrict__ segs, int bn, int part_rows) {
+                                                       const TcSegDev* __restrict__ segs, int bn) {
   __shared__ float red_hi[16][2], red_lo[16][2];
   const SplitUnit u = units[blockIdx.x];
   const int g64 = blockIdx.y;                   // 64-row group of the bn-row tile
@@ -511,16 +509,10 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
       lo += ol;
     }
     if (lane == 0 && cl < ncol) {
-      if (part_rows == 32) {
-        sd.partials[(((int64_t)u.m * (bn / 64) + g64) * 2 + wig) * sd.ldp + u.c * 128 + cl] =
-            (double)hi + (double)lo;
-      } else {
-        red_hi[cl - c16][wig] = hi;
-        red_lo[cl - c16][wig] = lo;
-      }
+      red_hi[cl - c16][wig] = hi;
+      red_lo[cl - c16][wig] = lo;
     }
   }
-  if (part_rows == 32) return;
   __syncthreads();
   if (threadIdx.x < 16 && c16 + (int)threadIdx.x < ncol) {
     const int cl = threadIdx.x;
@@ -530,10 +522,10 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
 }
 
 cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn,
-                                cudaStream_t st, int part_rows, int64_t max_cols) {
+                                cudaStream_t st, int64_t max_cols) {
   if (n_units <= 0) return cudaSuccess;
   const unsigned nz = (unsigned)ceil_div(std::min<int64_t>(std::max<int64_t>(max_cols, 1), 128), 16);
-  k_split_reduce<<<dim3(n_units, bn / 64, nz), 256, 0, st>>>(units, segs, bn, part_rows);
+  k_split_reduce<<<dim3(n_units, bn / 64, nz), 256, 0, st>>>(units, segs, bn);
   return cudaGetLastError();
 }
 

@@ -189,10 +189,10 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
 // must trigger early); off for the grouped path, where it measured slower
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
                           bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl = true);
-// part_rows: 64 (partials per 64-row group) or 32 (per 32-row group); max_cols: the
-// widest column tile of the units (one CTA per 64 rows and 16 columns)
+// partials per 64-row group; max_cols: the widest column tile of the units
+// (one CTA per 64 rows and 16 columns)
 cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn, cudaStream_t st,
-                                int part_rows = 64, int64_t max_cols = 128);
+                                int64_t max_cols = 128);
 // Small batches, one segment: the chunk reduction and the final chi2 / logL
 // run inside the kernel (the last chunk of a row tile, then the last CTA);
 // launched as a programmatic dependent of the residual slicing.

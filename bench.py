@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=3.0)
+    p.add_argument("--only", default=None, choices=["grouped", "serving", "gapped3"],
+                   help="run one extra workload alone and print its JSON object (profiling; not the bench line)")
     return p.parse_args()
 
 
@@ -430,6 +432,16 @@ def main():
         return run_reference(args)
     import torch
     import torch.distributed as dist
+
+    if args.only:
+        from paper_2603_06010_b300 import build as tdbuild
+        tdbuild.build()
+        from paper_2603_06010_b300 import td
+        torch.cuda.set_device(0)
+        fn = {"grouped": lambda: grouped_extra(td, torch), "serving": lambda: serving_extra(td, torch, args.serve_seconds),
+              "gapped3": lambda: gapped_joint_extra(td, torch)}[args.only]
+        print(json.dumps({"only": args.only, "result": fn()}), flush=True)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -12,10 +12,11 @@
 // O(t) per order, O(N^2) in all, instead of the O(N^3) Cholesky plus
 // inverse.  It runs in FP64.
 //
-// k_levinson_rows: one CTA per segment (1024 threads).  The orders form a
-// chain; the O(t) work of an order (one dot product, one predictor update,
-// one row of L^{-1}) is spread over the threads, the predictor lives in
-// global memory (L2-resident), and each row is stored in FP64, row-major.
+// k_levinson_rows: one cluster of up to 8 CTAs x 1024 threads per segment.  The
+// orders form a chain; the O(t) work of an order (one dot product, one
+// predictor update, one row of L^{-1}) is spread over the cluster, the
+// predictor lives in global memory (L2-resident), and each row is stored in
+// FP64, row-major.
 // FP64 is a slow pipe on this part, so the chain does only these three
 // multiply-adds per element; the per-row quantum and the bf16 slicing then
 // run over all SMs in the same kernels the Cholesky route uses.  Segments
@@ -25,7 +26,11 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "td_internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace td {
 
@@ -59,64 +64,135 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return red[32];
 }
 
+// One thread-block cluster of CL CTAs per segment (CL = 1: one CTA): the
+// O(t) work of an order is spread over CL x 1024 threads (element j to
+// cluster thread (j - 1) mod CL*1024, so warps stay coalesced, the mirrored
+// index too).  One barrier per order: order t's dot product reads only the
+// predictor elements this thread itself wrote at order t-1 (the newest one,
+// k_{t-1}, from a register), so it needs no barrier; after the barrier every
+// thread adds the CL partials in rank order (all CTAs get the same bits, so
+// the same k_t, v_t and decisions), writes its share of row t-1 of L^{-1}
+// (a_{t-1} is complete everywhere now) and updates its share of the
+// predictor.  The cluster size is a launch attribute, chosen per batch.
+template <int CL>
 __global__ void __launch_bounds__(LEV_THREADS, 1) k_levinson_rows(const LevJob* __restrict__ jobs) {
   __shared__ double red[40];
-  __shared__ double sh_v;
-  __shared__ int sh_bad;
-  const LevJob jb = jobs[blockIdx.x];
+  // partials double-buffered by order parity: with one barrier per order a
+  // CTA may publish order t+1's partial while a peer still reads order t's
+  __shared__ double sh_part[2];
+  const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
+  const LevJob jb = jobs[blockIdx.x / CL];
   const int64_t n = jb.n;
   const int tid = threadIdx.x;
+  const int64_t g = (int64_t)rank * LEV_THREADS + tid;   // this thread's place in the cluster
+  constexpr int64_t STRIDE = (int64_t)CL * LEV_THREADS;
+  const bool lead = (g == 0);
   double* a = jb.a0;      // a_{t-1}[1..t-1]
   double* an = jb.a1;     // a_t
   double logdet = 0.0;
-  if (tid == 0) {
-    sh_v = jb.acf[0];
-    sh_bad = !(sh_v > 0.0) || !isfinite(sh_v);
-    if (sh_bad) {
-      atomicMin((unsigned long long*)&jb.status->pivot, 0ull);
-      atomicCAS(&jb.status->code, 0, ST_NOT_PD);
-    }
+  double v = jb.acf[0];   // v_{t-1}, the same in every thread
+  double kp = 0.0;        // k_{t-1} = a_{t-1}[t-1]
+  bool bad = !(v > 0.0) || !isfinite(v);
+  if (bad && lead) {
+    atomicMin((unsigned long long*)&jb.status->pivot, 0ull);
+    atomicCAS(&jb.status->code, 0, ST_NOT_PD);
   }
-  __syncthreads();
-  for (int64_t t = 0; t < n && !sh_bad; ++t) {
-    if (t > 0) {
+  for (int64_t t = 1; t <= n && !bad; ++t) {
+    double k = 0.0, vn = v;
+    if (t < n) {
       // k_t = (acf[t] - sum_{j=1}^{t-1} a_{t-1,j} acf[t-j]) / v_{t-1}
       double part = 0.0;
-      for (int64_t j = 1 + tid; j < t; j += LEV_THREADS) part = fma(a[j], jb.acf[t - j], part);
-      const double dot = block_sum(part, red);   // ends in a barrier: sh_v is settled
-      const double vprev = sh_v;
-      const double k = (jb.acf[t] - dot) / vprev;
-      const double v = vprev * (1.0 - k * k);
-      if (!(v > 0.0) || !isfinite(v)) {
-        if (tid == 0) {
-          atomicMin((unsigned long long*)&jb.status->pivot, (unsigned long long)t);
-          atomicCAS(&jb.status->code, 0, ST_NOT_PD);
-        }
-        break;   // every thread computed the same v
-      }
-      for (int64_t j = 1 + tid; j < t; j += LEV_THREADS) an[j] = fma(-k, a[t - j], a[j]);
-      if (tid == 0) an[t] = k;
-      __syncthreads();   // a_t complete; everyone has read v_{t-1}
-      if (tid == 0) sh_v = v;
-      double* tmp = a;   // a <- a_t
-      a = an;
-      an = tmp;
+      for (int64_t j = 1 + g; j < t; j += STRIDE) part = fma(j == t - 1 ? kp : a[j], jb.acf[t - j], part);
+      part = block_sum(part, red);
+      if (tid == 0) sh_part[t & 1] = part;
     }
-    __syncthreads();
-    const double vt = sh_v;
-    if (tid == 0) logdet += log(vt);
-    // row t of L^{-1}: column c < t holds -a_{t, t-c} / sqrt(v_t), column t holds 1 / sqrt(v_t)
-    const double inv = 1.0 / sqrt(vt);
-    double* row = jb.linv + t * jb.ld;
-    for (int64_t c = tid; c < t; c += LEV_THREADS) row[c] = -a[t - c] * inv;
-    if (tid == 0) row[t] = inv;
+    if constexpr (CL > 1)
+      cg::this_cluster().sync();   // partials published; a_{t-1} complete in every share
+    else
+      __syncthreads();
+    if (t < n) {
+      double dot = 0.0;
+      if constexpr (CL > 1) {
+#pragma unroll
+        for (int r = 0; r < CL; ++r) dot += *cg::this_cluster().map_shared_rank(&sh_part[t & 1], r);
+      } else {
+        dot = sh_part[t & 1];
+      }
+      k = (jb.acf[t] - dot) / v;
+      vn = v * (1.0 - k * k);
+    }
+    // row t-1 of L^{-1}: column c < t-1 holds -a_{t-1, t-1-c} / sqrt(v_{t-1}), column t-1 holds 1 / sqrt(v_{t-1})
+    if (lead) logdet += log(v);
+    const double inv = 1.0 / sqrt(v);
+    double* row = jb.linv + (t - 1) * jb.ld;
+    for (int64_t c = g; c < t - 1; c += STRIDE) row[c] = -a[t - 1 - c] * inv;
+    if (lead) row[t - 1] = inv;
+    if (t == n) break;
+    if (!(vn > 0.0) || !isfinite(vn)) {
+      if (lead) {
+        atomicMin((unsigned long long*)&jb.status->pivot, (unsigned long long)t);
+        atomicCAS(&jb.status->code, 0, ST_NOT_PD);
+      }
+      bad = true;   // every thread of the cluster computed the same vn
+      break;
+    }
+    for (int64_t j = 1 + g; j < t; j += STRIDE) an[j] = fma(-k, a[t - j], a[j]);
+    if (lead) an[t] = k;
+    v = vn;
+    kp = k;
+    double* tmp = a;   // a <- a_t
+    a = an;
+    an = tmp;
   }
-  if (tid == 0) *jb.logdet = logdet;
+  if (lead) *jb.logdet = logdet;
+  if constexpr (CL > 1) cg::this_cluster().sync();   // no CTA leaves while a peer may still read its partial
 }
 
+template <int CL>
+cudaLaunchConfig_t lev_config(int njobs, cudaStream_t st, cudaLaunchAttribute* attr) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)njobs * CL);
+  cfg.blockDim = dim3(LEV_THREADS);
+  cfg.stream = st;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = CL;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Clusters of CL CTAs that can be resident at once (0 if the query fails).
+template <int CL>
+int lev_max_clusters(int njobs, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = lev_config<CL>(njobs, st, attr);
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_levinson_rows<CL>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <int CL>
+cudaError_t lev_launch(const LevJob* jobs, int njobs, cudaStream_t st) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = lev_config<CL>(njobs, st, attr);
+  return cudaLaunchKernelEx(&cfg, k_levinson_rows<CL>, jobs);
+}
+
+// The chains of a batch run side by side, each on the largest cluster that
+// still lets every chain be resident at once (a chain's time is set by its
+// order count, so a second wave would double the batch's time): 8 CTAs for
+// a few long segments, one CTA each for many.
 cudaError_t launch_levinson_rows(const LevJob* jobs, int njobs, cudaStream_t st) {
   if (njobs <= 0) return cudaSuccess;
-  k_levinson_rows<<<njobs, LEV_THREADS, 0, st>>>(jobs);
+  if (njobs <= lev_max_clusters<8>(njobs, st)) return lev_launch<8>(jobs, njobs, st);
+  if (njobs <= lev_max_clusters<4>(njobs, st)) return lev_launch<4>(jobs, njobs, st);
+  if (njobs <= lev_max_clusters<2>(njobs, st)) return lev_launch<2>(jobs, njobs, st);
+  k_levinson_rows<1><<<(unsigned)njobs, LEV_THREADS, 0, st>>>(jobs);
   return cudaGetLastError();
 }
 

@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=3.0)
-    p.add_argument("--only", default=None, choices=["grouped", "serving", "gapped3"],
+    p.add_argument("--only", default=None, choices=["grouped", "serving", "gapped3", "refine"],
                    help="run one extra workload alone and print its JSON object (profiling; not the bench line)")
     return p.parse_args()
 
@@ -294,6 +294,35 @@ def grouped_extra(td, torch):
             "max_abs_dlogL_vs_oracle_4_shortest": dlogl}
 
 
+def refine_extra(td, torch, seg, R, K):
+    """The refinement step on the benchmark batch: per first-pass precision, one pass
+    against one pass + refinement (time per call, max |dlogL| on the stored oracle columns)."""
+    stream = torch.cuda.current_stream()
+    logL = torch.empty(K, dtype=torch.float64, device="cuda")
+    runs = []
+    for pname, prec, refine in (("bf16x3", td.TD_PREC_BF16X3, 0), ("bf16x3", td.TD_PREC_BF16X3, 1),
+                                ("bf16x6", td.TD_PREC_BF16X6, 0), ("bf16x6", td.TD_PREC_BF16X6, 1),
+                                ("bf16x10", td.TD_PREC_BF16X10, 0)):
+        o = td.options(precision=prec, refine=refine)
+        for _ in range(3):
+            seg.loglike_into(R, logL, o)
+        torch.cuda.synchronize()
+        seg.check()
+        dll = golden_dlogl(logL.cpu().numpy())
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(5):
+            seg.loglike_into(R, logL, o)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        ms = ea.elapsed_time(eb) / 5
+        runs.append({"precision": pname, "refine": refine, "call_ms": ms, "evals_per_s": K / (ms / 1e3),
+                     "max_abs_dlogL_vs_oracle": dll})
+    return {"note": "one pass vs one pass + refinement (w~ at the precision, s = r - L w~ by ten split "
+                    "products of L's own slices, delta = L^{-1} s at the precision); calls back to back, "
+                    "inputs (134 MB) and the operator larger than L2", "runs": runs}
+
+
 def serving_extra(td, torch, seconds):
     """Open-loop Poisson serving on a fleet of resident segments: the whole fleet,
     then the gapped N=8192 and gapped N=16384 segments alone (per-size latency)."""
@@ -438,8 +467,12 @@ def main():
         tdbuild.build()
         from paper_2603_06010_b300 import td
         torch.cuda.set_device(0)
+        def only_refine():
+            c, seg_in, R_host = make_workload(0)
+            seg = td.Segment(seg_in.acf, seg_in.mask)
+            return refine_extra(td, torch, seg, torch.from_numpy(R_host).cuda(), R_host.shape[0])
         fn = {"grouped": lambda: grouped_extra(td, torch), "serving": lambda: serving_extra(td, torch, args.serve_seconds),
-              "gapped3": lambda: gapped_joint_extra(td, torch)}[args.only]
+              "gapped3": lambda: gapped_joint_extra(td, torch), "refine": only_refine}[args.only]
         print(json.dumps({"only": args.only, "result": fn()}), flush=True)
         return
 
@@ -641,6 +674,7 @@ def main():
     }
     if world == 1:
         line["template_form"] = template_extra(td, torch, seg, seg_in, K)
+        line["refinement"] = refine_extra(td, torch, seg, R, K)
     if world == 1 and not args.no_grouped:
         line["gapped_n16384_3det"] = gapped_joint_extra(td, torch)
         line["grouped"] = grouped_extra(td, torch)

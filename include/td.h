@@ -89,9 +89,19 @@ typedef enum {
 typedef struct {
   int precision;        /* td_precision; default TD_PREC_BF16X6 */
   int path;             /* td_path; default TD_PATH_AUTO */
-  int refine;           /* refinement (s = r - L w, w += L^{-1} s) is not built: nonzero
-                           returns TD_ERR_UNSUPPORTED; the split products reach the
-                           accuracy bar in one pass */
+  int refine;           /* nonzero: one refinement step (Sec. III.C precision scheme).
+                           w~ = L^{-1} r at `precision`; s = r - L w~ from bf16 slices of
+                           L with ten products (exact hi*hi, ~1e-9 of |L||w~|); delta =
+                           L^{-1} s at `precision`; chi2 = |w~ + delta|^2.  The result
+                           reaches about the ten-product accuracy from any precision
+                           (BF16X3 included) at about three passes' cost; `path` is
+                           ignored (128-row tiles, every row tile through the chunk
+                           reduction).  Needs the FP64 factor L: TD_ERR_UNSUPPORTED on
+                           segments built by td_factor_many(TD_FACTOR_NO_FP64) or after
+                           td_segment_release_fp64; TD_ERR_INVALID with TD_PREC_FP64 or
+                           TD_PATH_FP64; grouped launches: TD_ERR_UNSUPPORTED.  The
+                           slices of L (as large as the operator's) are made on the
+                           first refined call, with two FP32 N'p x K buffers. */
   int reserved0;
   int64_t wait_limit_ns;/* bound on any in-kernel wait; <= 0 -> 1 s */
 } td_options;

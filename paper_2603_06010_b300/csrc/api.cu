@@ -68,13 +68,14 @@ static td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint6
 
 // residual-slice map (A operand: a box of a_rows residual columns) and operator
 // map (B operand, tiles of bn rows) of one segment
-td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out, int a_rows = TC_COLS) {
+td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out, int a_rows,
+                          const __nv_bfloat16* op) {
   out->a_rows = a_rows;
   td_status st = encode_3d(&out->mapA, s->scr.rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES,
                            (uint64_t)s->nkp8 * 2, (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, (uint32_t)a_rows,
                            1);
   if (st != TD_OK) return st;
-  return encode_3d(&out->mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
+  return encode_3d(&out->mapB, op ? op : s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
                    (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, (uint32_t)bn, (uint32_t)nsl);
 }
 
@@ -397,6 +398,7 @@ td_status td_factor(td_segment* s, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   s->factored = false;
   s->pivot = -1;
+  free_refine_state(s);   // slices of the old L
   const int64_t nkp = s->nkp;
   const int nt = (int)(nkp / FT);
   if (!s->L && (r = dev_alloc(&s->L, (size_t)(nkp * nkp), "factor L")) != TD_OK) return r;
@@ -474,9 +476,9 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   td_options_default(&o);
   if (opt) o = *opt;
   if (o.wait_limit_ns <= 0) o.wait_limit_ns = 1000000000LL;
-  if (o.refine) return fail(TD_ERR_UNSUPPORTED, "refinement is not built in this version");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const bool fp64 = (o.precision == TD_PREC_FP64) || (o.path == TD_PATH_FP64);
+  if (fp64 && o.refine) return fail(TD_ERR_INVALID, "refinement applies to the split-product paths, not to FP64");
   if (fp64 && !s->L) return fail(TD_ERR_UNSUPPORTED, "the FP64 factor of this segment was released");
   if (!fp64 && !s->op) return fail(TD_ERR_NOT_FACTORED, "the operator of this segment is not resident");
   if ((r = ensure_scratch(s, K, fp64, st)) != TD_OK) return r;
@@ -495,6 +497,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     return TD_OK;
   }
   const int nsl = nslices_for(o.precision, s->nk);
+  if (o.refine) return refine_batch(s, R, ldr, K, logL, chi2, nsl, o.wait_limit_ns, st);
   const Shape shape = choose_shape(s, K, o.path);
   const int bn = shape.bn;
   const int ngroups = (int)(s->nkp / 64);
@@ -619,6 +622,7 @@ void td_segment_destroy(td_segment* s) {
   free_plans(s->scr);
   free_host_stage(s->hst);
   free_template_state(s->tpl);
+  free_refine_state(s);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
   delete s;

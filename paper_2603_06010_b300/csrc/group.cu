@@ -21,7 +21,6 @@
 #include "td_internal.h"
 
 namespace td {
-td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out, int a_rows);
 
 static td_status group_alloc(void** p, size_t bytes, const char* what) {
   *p = nullptr;
@@ -287,6 +286,7 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
   td_options_default(&o);
   if (opt) o = *opt;
   if (o.precision == TD_PREC_FP64) return fail(TD_ERR_UNSUPPORTED, "grouped launches use the tensor-core path");
+  if (o.refine) return fail(TD_ERR_UNSUPPORTED, "refinement runs on single-segment batches");
   td_group* g = new td_group();
   cudaGetDevice(&g->device);
   g->nseg = nseg;

@@ -315,6 +315,7 @@ extern "C" td_status td_factor_many(td_segment* const* segs, int nseg, int flags
     s->factored = false;
     s->pivot = -1;
     td_segment_release_fp64(s);   // a factor from an earlier td_factor would be stale
+    free_refine_state(s);
     s->op_blocks = op_row_offset(s->nkp / OP_ROWS);
     lev.push_back(s);
   }

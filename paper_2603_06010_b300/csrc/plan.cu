@@ -1,10 +1,12 @@
 // Work lists for the tensor-core kernel's explicit-list modes.
 //
 // Small batches cut a row tile whose k-range is longer than S k-blocks into
-// chunks of at most S, so no single work item holds back the launch.  S depends only on N' (not on K), so the split of a
-// given column is the same in every batch.  Chunks of one row tile write
-// their accumulator pairs to consecutive slots; one SplitUnit per split tile
-// tells k_split_reduce which slots to add.
+// chunks of at most S, so no single work item holds back the launch.  S
+// depends only on N' (not on K), so the split of a given column is the same
+// in every batch.  Chunks of one row tile write their accumulator pairs to
+// consecutive slots; one SplitUnit per split tile tells k_split_reduce which
+// slots to add.  With all_slots every row tile, split or not, leaves its
+// accumulators to the reduction (the refinement step reads W itself).
 #include <algorithm>
 #include <cstring>
 #include <vector>
@@ -26,7 +28,7 @@ int split_chunk(int64_t nk, int64_t nkp, int bn) {
 
 // append the items of one segment (bn-row tiles, chunk S) to the lists
 void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
-                        std::vector<SplitUnit>& units, int& n_slots) {
+                        std::vector<SplitUnit>& units, int& n_slots, bool all_slots) {
   const int nm = (int)(nkp / bn);
   const int per = bn / OP_KB;
   const int nc = (int)ceil_div(K, TC_COLS);
@@ -35,7 +37,7 @@ void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int
     for (int m = 0; m < nm; ++m) {
       const int nkb = std::min(per * (m + 1), nkb_max);
       const int nch = (nkb + S - 1) / S;
-      if (nch <= 1) {
+      if (nch <= 1 && !all_slots) {
         items.push_back(TcItem{seg, m, c, nkb, 0, -1, -1});
         continue;
       }

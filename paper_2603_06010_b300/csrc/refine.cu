@@ -1,0 +1,201 @@
+// One step of iterative refinement of the whitening solve W = L^{-1} R
+// (Sec. III.C: the operator is evaluated in reduced precision; the accuracy
+// that loses is won back by a residual formed more accurately than the solve):
+//   w~    = L^{-1} r          split product at the caller's precision
+//   s     = r - L w~          split product with bf16 slices of L itself,
+//                             ten products (exact hi*hi accumulator)
+//   delta = L^{-1} s          caller's precision
+//   w     = w~ + delta,  chi2 = |w|^2,  then logL as for one pass.
+// w~ is rounded to FP32 before the residual is formed, so s is the exact
+// residual of the iterate that gets corrected.  s is about as small as the
+// first pass's error, and the residual product's own error (about 1e-9 of
+// |L| |w~|) is what the corrected w keeps: the result lands near the
+// ten-product accuracy whatever the first pass's precision was.
+//
+// All three products run in the split-k tensor-core kernel with every row
+// tile leaving its accumulator pairs to the chunk reduction (128-row operator
+// tiles, chunks of at least 64 k-blocks, a length fixed by N' alone, so a
+// column's result does not depend on its batch).  The reduction's modes do the
+// element-wise parts: write w~, form s from r, add w~ and square.
+//
+// Needs the FP64 factor L to slice (once per factor); segments whose L was
+// released, or whose operator came from the Levinson-Durbin route, return
+// TD_ERR_UNSUPPORTED.
+#include <algorithm>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "td_internal.h"
+
+namespace td {
+
+template <class T>
+static td_status ref_alloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return TD_OK;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(TD_ERR_OOM, std::string("device allocation failed: ") + what);
+  }
+  return TD_OK;
+}
+
+template <class T>
+static void ref_free(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+static void drop_plan(RefineState& f) {
+  ref_free(f.items);
+  ref_free(f.units);
+  ref_free(f.seg_op);
+  f.n_items = f.n_units = 0;
+  f.K = -1;
+  f.nsl = 0;
+  f.rs = f.op = nullptr;
+}
+
+void free_refine_state(td_segment* s) {
+  RefineState& f = s->ref;
+  drop_plan(f);
+  ref_free(f.lop);
+  ref_free(f.w32);
+  ref_free(f.s32);
+  ref_free(f.wpart);
+  f.cap = 0;
+  f.wpart_elems = 0;
+}
+
+// bf16 slices of L (same packing and per-row quanta as the whitening operator)
+static td_status build_lop(td_segment* s, cudaStream_t st) {
+  if (!s->L)
+    return fail(TD_ERR_UNSUPPORTED,
+                "refinement needs the FP64 factor L, which this segment released or never formed "
+                "(Levinson-Durbin route)");
+  RefineState& f = s->ref;
+  td_status r = ref_alloc(&f.lop, (size_t)(s->op_blocks * OP_SLICES * OP_ROWS * OP_KB), "slices of L");
+  if (r != TD_OK) return r;
+  double* qrow = nullptr;
+  if ((r = ref_alloc(&qrow, (size_t)s->nkp, "row quanta of L")) != TD_OK) {
+    ref_free(f.lop);
+    return r;
+  }
+  cudaError_t e = launch_row_quantum(s->L, s->nkp, s->nk, s->nkp, qrow, st);
+  if (e == cudaSuccess) e = launch_op_slices(s->L, s->nkp, s->nk, s->nkp, qrow, f.lop, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(qrow);
+  if (e != cudaSuccess) {
+    ref_free(f.lop);
+    return cuda_fail(e, "slicing L");
+  }
+  return TD_OK;
+}
+
+constexpr int REF_BN = 128;      // operator rows per tile
+constexpr int REF_MIN_CHUNK = 64;   // k-blocks
+
+static td_status refine_plan(td_segment* s, int64_t K, int nsl, cudaStream_t st) {
+  RefineState& f = s->ref;
+  const Scratch& sc = s->scr;
+  if (f.K == K && f.nsl == nsl && f.rs == sc.rs && f.op == s->op) return TD_OK;
+  cudaStreamSynchronize(st);   // the old lists may still be read on this stream
+  drop_plan(f);
+  const int S = std::max(split_chunk(s->nk, s->nkp, REF_BN), REF_MIN_CHUNK);
+  std::vector<TcItem> items;
+  std::vector<SplitUnit> units;
+  int n_slots = 0;
+  plan_split_segment(0, s->nk, s->nkp, K, REF_BN, S, items, units, n_slots, true);
+  sort_items(items);
+  td_status r;
+  const int64_t need = (int64_t)n_slots * TC_COLS * REF_BN;
+  if (need > f.wpart_elems) {
+    ref_free(f.wpart);
+    f.wpart_elems = 0;
+    if ((r = ref_alloc(&f.wpart, (size_t)need, "refinement accumulators")) != TD_OK) return r;
+    f.wpart_elems = need;
+  }
+  TcSegDev seg[2];
+  memset(seg, 0, sizeof seg);
+  const int a_rows = (int)std::min<int64_t>(TC_COLS, round_up(K, 8));
+  for (int w = 0; w < 2; ++w) {
+    if ((r = encode_seg_maps(s, K, w == 0 ? nsl : OP_SLICES, REF_BN, &seg[w], a_rows, w == 0 ? s->op : f.lop)) !=
+        TD_OK)
+      return r;
+    seg[w].partials = sc.partials;
+    seg[w].wpart = f.wpart;
+    seg[w].nk = (int)s->nk;
+    seg[w].K = (int)K;
+    seg[w].ldp = (int)sc.capK;
+    seg[w].nm = (int)(s->nkp / 64);
+    seg[w].logdet = s->logdet;
+  }
+  if ((r = ref_alloc(&f.items, items.size(), "refinement work items")) != TD_OK ||
+      (r = ref_alloc(&f.units, units.size(), "refinement units")) != TD_OK ||
+      (r = ref_alloc(&f.seg_op, 2, "refinement descriptors")) != TD_OK) {
+    drop_plan(f);
+    return r;
+  }
+  TD_CUDA(cudaMemcpy(f.items, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice));
+  TD_CUDA(cudaMemcpy(f.units, units.data(), units.size() * sizeof(SplitUnit), cudaMemcpyHostToDevice));
+  TD_CUDA(cudaMemcpy(f.seg_op, seg, sizeof seg, cudaMemcpyHostToDevice));
+  f.n_items = (int)items.size();
+  f.n_units = (int)units.size();
+  f.K = K;
+  f.nsl = nsl;
+  f.rs = sc.rs;
+  f.op = s->op;
+  return TD_OK;
+}
+
+td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl,
+                       int64_t wait_limit_ns, cudaStream_t st) {
+  RefineState& f = s->ref;
+  Scratch& sc = s->scr;
+  td_status r;
+  if (!f.lop && (r = build_lop(s, st)) != TD_OK) return r;
+  if (sc.capK > f.cap) {
+    cudaStreamSynchronize(st);
+    ref_free(f.w32);
+    ref_free(f.s32);
+    f.cap = 0;
+    if ((r = ref_alloc(&f.w32, (size_t)(sc.capK * s->nkp), "first iterate")) != TD_OK ||
+        (r = ref_alloc(&f.s32, (size_t)(sc.capK * s->nkp), "refinement residual")) != TD_OK)
+      return r;
+    f.cap = sc.capK;
+  }
+  if ((r = refine_plan(s, K, nsl, st)) != TD_OK) return r;
+  const TcSegDev* seg_linv = f.seg_op;
+  const TcSegDev* seg_l = f.seg_op + 1;
+  const int64_t ld = s->nkp;
+  // w~ = L^{-1} r, rounded to FP32
+  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
+  TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_linv, nsl, REF_BN, true, s->status, wait_limit_ns, st));
+  RefineIO io;
+  io.out = f.w32;
+  io.ldo = ld;
+  TD_CUDA(launch_split_reduce(f.units, f.n_units, seg_linv, REF_BN, st, K, RED_WRITE, io));
+  // s = r - L w~
+  TD_CUDA(launch_r_slices(f.w32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, OP_SLICES, st));
+  TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_l, OP_SLICES, REF_BN, true, s->status, wait_limit_ns, st));
+  io = RefineIO();
+  io.in = R;
+  io.ldi = ldr;
+  io.out = f.s32;
+  io.ldo = ld;
+  TD_CUDA(launch_split_reduce(f.units, f.n_units, seg_l, REF_BN, st, K, RED_RESID, io));
+  // delta = L^{-1} s; chi2 of w~ + delta
+  TD_CUDA(launch_r_slices(f.s32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
+  TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_linv, nsl, REF_BN, true, s->status, wait_limit_ns, st));
+  io = RefineIO();
+  io.in = f.w32;
+  io.ldi = ld;
+  TD_CUDA(launch_split_reduce(f.units, f.n_units, seg_linv, REF_BN, st, K, RED_FINAL, io));
+  TD_CUDA(launch_finalize(sc.partials, sc.capK, (int)(s->nkp / 64), K, s->logdet, s->nk, logL, chi2, st));
+  s->prof_kernels += 10;
+  return TD_OK;
+}
+
+}  // namespace td

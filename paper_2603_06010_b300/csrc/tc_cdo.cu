@@ -459,8 +459,17 @@ cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs
 // contiguous in the slot layout, so a warp's loads are coalesced; the four
 // column groups take columns round-robin; the sum over a warp's 32 rows is a
 // fixed shuffle tree, the two warps of a group are added in a fixed order.
+//
+// RM selects what is done with w (the refinement step of td_options.refine):
+//   RED_CHI2   chi2 partials of w (above)
+//   RED_WRITE  out = fl32(w)                        (the first iterate w~)
+//   RED_RESID  out = fl32(in - w), in = r           (s = r - L w~)
+//   RED_FINAL  chi2 partials of in + w, in = w~     (w = w~ + L^{-1} s)
+// Element (row i, column k) of in / out sits at [i + k ld]; rows at or past
+// N' read as zero.
+template <int RM>
 __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restrict__ units,
-                                                       const TcSegDev* __restrict__ segs, int bn) {
+                                                       const TcSegDev* __restrict__ segs, int bn, RefineIO io) {
   __shared__ float red_hi[16][2], red_lo[16][2];
   const SplitUnit u = units[blockIdx.x];
   const int g64 = blockIdx.y;                   // 64-row group of the bn-row tile
@@ -496,6 +505,30 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
         }
       }
   }
+  const int64_t i = (int64_t)u.m * bn + g64 * 64 + row;   // row of W
+  if constexpr (RM == RED_WRITE || RM == RED_RESID) {
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      const int cl = c16 + grp + 4 * c;
+      if (cl >= ncol) continue;
+      const int64_t k = (int64_t)u.c * 128 + cl;
+      if constexpr (RM == RED_WRITE) {
+        io.out[i + k * io.ldo] = wh[c] + wl[c];
+      } else {
+        const float r = i < sd.nk ? io.in[i + k * io.ldi] : 0.f;
+        io.out[i + k * io.ldo] = (r - wh[c]) - wl[c];   // r - wh is exact while they are within a factor 2
+      }
+    }
+    return;
+  }
+  if constexpr (RM == RED_FINAL) {
+#pragma unroll
+    for (int c = 0; c < CB; ++c) {
+      const int cl = min(c16 + grp + 4 * c, ncol - 1);
+      const float x = i < sd.nk ? io.in[i + ((int64_t)u.c * 128 + cl) * io.ldi] : 0.f;
+      ff_add(x, wh[c], wl[c]);
+    }
+  }
 #pragma unroll
   for (int c = 0; c < CB; ++c) {
     const int cl = c16 + grp + 4 * c;
@@ -522,10 +555,17 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
 }
 
 cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn,
-                                cudaStream_t st, int64_t max_cols) {
+                                cudaStream_t st, int64_t max_cols, int mode, const RefineIO& io) {
   if (n_units <= 0) return cudaSuccess;
   const unsigned nz = (unsigned)ceil_div(std::min<int64_t>(std::max<int64_t>(max_cols, 1), 128), 16);
-  k_split_reduce<<<dim3(n_units, bn / 64, nz), 256, 0, st>>>(units, segs, bn);
+  const dim3 grid(n_units, bn / 64, nz);
+  switch (mode) {
+    case RED_CHI2: k_split_reduce<RED_CHI2><<<grid, 256, 0, st>>>(units, segs, bn, io); break;
+    case RED_WRITE: k_split_reduce<RED_WRITE><<<grid, 256, 0, st>>>(units, segs, bn, io); break;
+    case RED_RESID: k_split_reduce<RED_RESID><<<grid, 256, 0, st>>>(units, segs, bn, io); break;
+    case RED_FINAL: k_split_reduce<RED_FINAL><<<grid, 256, 0, st>>>(units, segs, bn, io); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 

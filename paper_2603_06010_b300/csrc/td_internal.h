@@ -92,7 +92,7 @@ struct Scratch {
 
 int split_chunk(int64_t nk, int64_t nkp, int bn);
 void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
-                        std::vector<SplitUnit>& units, int& n_slots);
+                        std::vector<SplitUnit>& units, int& n_slots, bool all_slots = false);
 void sort_items(std::vector<TcItem>& items);
 
 }  // namespace td
@@ -118,6 +118,25 @@ struct TemplateState {        // td_set_data / td_template_batch
   bool has_data = false;
 };
 
+struct RefineState {          // td_options.refine
+  __nv_bfloat16* lop = nullptr;     // bf16 slices of L, packed like the operator
+  float* w32 = nullptr;             // first iterate w~ rounded to FP32, [cap][N'p]
+  float* s32 = nullptr;             // residual s = r - L w~ in FP32, [cap][N'p]
+  int64_t cap = 0;
+  float2* wpart = nullptr;          // accumulator pairs of every row tile
+  int64_t wpart_elems = 0;
+  // the cached work list (one batch width)
+  int64_t K = -1;
+  int nsl = 0;
+  const void* rs = nullptr;         // residual slices and operator the maps were encoded for
+  const void* op = nullptr;
+  td::TcItem* items = nullptr;
+  int n_items = 0;
+  td::SplitUnit* units = nullptr;
+  int n_units = 0;
+  td::TcSegDev* seg_op = nullptr;   // [0]: L^{-1} slices (nsl), [1]: L slices (4)
+};
+
 struct td_segment {
   int device = 0;
   int64_t n = 0;          // samples
@@ -138,6 +157,7 @@ struct td_segment {
   td::Scratch scr;
   HostStage hst;
   TemplateState tpl;
+  RefineState ref;
   // instrumentation
   bool prof = false;
   std::vector<cudaEvent_t> ev;   // start/stop pairs
@@ -190,9 +210,17 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
                           bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl = true);
 // partials per 64-row group; max_cols: the widest column tile of the units
-// (one CTA per 64 rows and 16 columns)
+// (one CTA per 64 rows and 16 columns).  mode: RED_CHI2, or one of the
+// refinement modes (element-wise output or chi2 of in + w, through io).
+enum { RED_CHI2 = 0, RED_WRITE = 1, RED_RESID = 2, RED_FINAL = 3 };
+struct RefineIO {
+  const float* in = nullptr;   // RED_RESID: r; RED_FINAL: w~   ([i + k ldi])
+  int64_t ldi = 0;
+  float* out = nullptr;        // RED_WRITE, RED_RESID           ([i + k ldo], rows < N'p)
+  int64_t ldo = 0;
+};
 cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSegDev* segs, int bn, cudaStream_t st,
-                                int64_t max_cols = 128);
+                                int64_t max_cols = 128, int mode = RED_CHI2, const RefineIO& io = RefineIO());
 // Small batches, one segment: the chunk reduction and the final chi2 / logL
 // run inside the kernel (the last chunk of a row tile, then the last CTA);
 // launched as a programmatic dependent of the residual slicing.
@@ -214,7 +242,14 @@ cudaError_t launch_tc_finalize(const TcSegDev* segs, int nseg, int64_t maxK, cud
 
 cudaError_t launch_bounded_wait_probe(DevStatus* status, int64_t limit_ns, cudaStream_t st);
 
-// tensor map encoding (driver API)
-td_status encode_maps(td_segment* s, const __nv_bfloat16* rs, int64_t K, int64_t capK, TcSegDev* host);
+// tensor maps of one segment: residual slices (A, boxes of a_rows columns)
+// and an operator's packed slices (B, tiles of bn rows, nsl slices); op =
+// nullptr takes the segment's whitening operator
+td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out, int a_rows = TC_COLS,
+                          const __nv_bfloat16* op = nullptr);
+// one refinement step (td_options.refine), launched on st
+td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl,
+                       int64_t wait_limit_ns, cudaStream_t st);
+void free_refine_state(td_segment* s);
 
 }  // namespace td

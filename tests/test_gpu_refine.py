@@ -1,0 +1,142 @@
+"""The refinement step (td_options.refine) against the CPU FP64 oracle.
+
+One step w = w~ + L^{-1}(r - L w~), with the residual formed from ten split
+products, brings every first-pass precision within the bar (chi2 1e-7
+relative, |delta logL| 1e-3), 3xBF16 included, whose single pass is ~3e-5
+relative.  What it cannot remove is the residual product's own error: its
+correction accumulator (about 2^-8 of L w~) is truncated to FP32 once per
+16-deep MMA step, so s = r - L w~, itself only ~1e-5 of r, carries a
+relative error of order 1e-3 and the refined chi2 about 1e-8 (2.2e-8
+measured at N' = 1100).  3xBF16 must improve at least a hundredfold.
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_06010_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REF_CHI2_REL = 1e-7
+REF_DLOGL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+def _mask(n, spans):
+    m = np.ones(n, np.uint8)
+    for a, b in spans:
+        m[a:b] = 0
+    return m
+
+
+def _run(torch, seg, R_kn, opt):
+    R = torch.from_numpy(np.ascontiguousarray(R_kn)).cuda()
+    logL, chi2 = seg.loglike(R, opt, with_chi2=True)
+    torch.cuda.synchronize()
+    seg.check()
+    return logL.cpu().numpy(), chi2.cpu().numpy()
+
+
+CASES = [   # (name, n, fs, gap spans, K): several 128-row tiles, ragged rows and columns
+    ("n1", 1, 1024.0, None, 3),
+    ("n257_gaps_k129", 257, 1024.0, [(10, 30), (100, 120)], 129),
+    ("one_kept_k5", 700, 2048.0, [(0, 350), (351, 700)], 5),
+    ("n2048_gaps_k300", 2048, 2048.0, [(500, 1012), (1500, 1600)], 300),
+    ("n1100_k257", 1100, 4096.0, None, 257),
+    ("n3000_gap_k64", 3000, 2048.0, [(1000, 1512)], 64),
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6", "bf16x10"])
+@pytest.mark.parametrize("case", CASES, ids=[c[0] for c in CASES])
+def test_refined_parity(torch_cuda, gpu_lib, case, prec):
+    from paper_2603_06010_b300 import td
+    name, n, fs, spans, K = case
+    p = {"bf16x3": td.TD_PREC_BF16X3, "bf16x6": td.TD_PREC_BF16X6, "bf16x10": td.TD_PREC_BF16X10}[prec]
+    mask = None if spans is None else _mask(n, spans)
+    acf = inputs.acf_from_psd(n, fs) if n > 1 else np.array([2.5])
+    o = oracle.OracleSegment(acf, mask)
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    R = inputs.noise_residuals(n, fs, K, 31, mask=mask) if n > 1 else \
+        rng.standard_normal((K, 1)).astype(np.float32)
+    exp_chi = o.chi2(R)
+    exp_ll = oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept)
+    seg = td.Segment(acf, mask)
+    ll1, chi1 = _run(torch_cuda, seg, R, td.options(precision=p))
+    llr, chir = _run(torch_cuda, seg, R, td.options(precision=p, refine=1))
+    rel1 = np.max(np.abs(chi1 - exp_chi) / exp_chi)
+    relr = np.max(np.abs(chir - exp_chi) / exp_chi)
+    assert np.all(np.isfinite(llr))
+    assert relr <= REF_CHI2_REL, f"{name} {prec}: refined chi2 rel {relr:.3e} (one pass {rel1:.3e})"
+    assert np.max(np.abs(llr - exp_ll)) <= REF_DLOGL
+    if prec == "bf16x3" and n > 1:
+        # the step is what brings the 3-product pass under the bar
+        assert rel1 > 1e-7 and relr < rel1 / 100, (rel1, relr)
+
+
+def test_refined_column_alone_equals_in_batch(torch_cuda, gpu_lib):
+    """The refined path's tiles and chunks depend on N' alone, so a column's
+    result is the same bits in any batch."""
+    from paper_2603_06010_b300 import td
+    n = 1500
+    mask = _mask(n, [(700, 800)])
+    seg = td.Segment(inputs.acf_from_psd(n, 2048.0), mask)
+    R = inputs.noise_residuals(n, 2048.0, 300, 41, mask=mask)
+    Rd = torch_cuda.from_numpy(R).cuda()
+    opt = td.options(precision=td.TD_PREC_BF16X3, refine=1)
+
+    def run(Rsub):
+        ll = seg.loglike(Rsub.contiguous(), opt)
+        torch_cuda.cuda.synchronize()
+        seg.check()
+        return ll.cpu().numpy()
+
+    full = run(Rd)
+    for k in (0, 1, 127, 128, 299):
+        assert run(Rd[k:k + 1])[0] == full[k], k
+    assert np.array_equal(run(Rd[100:229]), full[100:229])
+    assert np.array_equal(run(Rd), full)
+
+
+def test_refine_after_refactor_and_growth(torch_cuda, gpu_lib):
+    """The slices of L follow a re-factor; the buffers follow a wider batch."""
+    from paper_2603_06010_b300 import td
+    n = 900
+    acf = inputs.acf_from_psd(n, 2048.0)
+    o = oracle.OracleSegment(acf)
+    seg = td.Segment(acf)
+    opt = td.options(precision=td.TD_PREC_BF16X3, refine=1)
+    for K, seed in ((7, 1), (200, 2), (7, 3)):
+        R = inputs.noise_residuals(n, 2048.0, K, seed)
+        _, chi = _run(torch_cuda, seg, R, opt)
+        assert np.max(np.abs(chi - o.chi2(R)) / o.chi2(R)) <= REF_CHI2_REL
+        seg.factor()
+
+
+def test_refine_unsupported_and_invalid(torch_cuda, gpu_lib):
+    from paper_2603_06010_b300 import td
+    n = 512
+    acf = inputs.acf_from_psd(n, 2048.0)
+    R = torch_cuda.from_numpy(inputs.noise_residuals(n, 2048.0, 4, 5)).cuda()
+    lev = td.Segment(acf, factor=False)
+    td.factor_many([lev])            # operator from the Levinson-Durbin route: no L
+    with pytest.raises(td.TdError) as e:
+        lev.loglike(R, td.options(refine=1))
+    assert e.value.code == td.TD_ERR_UNSUPPORTED
+    seg = td.Segment(acf)
+    with pytest.raises(td.TdError) as e:
+        seg.loglike(R, td.options(precision=td.TD_PREC_FP64, refine=1))
+    assert e.value.code == td.TD_ERR_INVALID
+    seg.release_fp64()
+    with pytest.raises(td.TdError) as e:
+        seg.loglike(R, td.options(refine=1))
+    assert e.value.code == td.TD_ERR_UNSUPPORTED

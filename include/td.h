@@ -83,7 +83,15 @@ typedef enum {
                            columns; the packed operator streams once (default for K <= 32) */
   TD_PATH_TENSOR128 = 6, /* as TD_PATH_TENSOR with 128-row operator tiles (two accumulator
                             pairs in TMEM: a tile's epilogue overlaps the next tile's MMAs) */
-  TD_PATH_STREAM128 = 7  /* as TD_PATH_STREAM with 128-row operator tiles */
+  TD_PATH_STREAM128 = 7, /* as TD_PATH_STREAM with 128-row operator tiles */
+  TD_PATH_GSCE = 8      /* gap-free segments prepared by td_gs_prepare: chi2 by the
+                           Gohberg-Semencul formula with circulant-embedded FFTs
+                           (Sec. III.A), O(N log N) per column, FP32 FFTs with
+                           double-float sums, one 8-CTA thread-block cluster per
+                           column pair; `precision` is not used.  A column is
+                           transformed together with its neighbour (columns 2j, 2j+1
+                           share one complex FFT), so results agree across batches
+                           within rounding, not bitwise. */
 } td_path;
 
 typedef struct {
@@ -162,7 +170,24 @@ td_status td_segment_release_fp64(td_segment* s);
 #define TD_FACTOR_NO_FP64 1
 td_status td_factor_many(td_segment* const* segs, int nseg, int flags, void* stream);
 
-/* log det C_kept (host scalar).  Requires a successful td_factor. */
+/*
+ * td_gs_prepare -- Gohberg-Semencul form of a gap-free segment's inverse
+ * covariance (Sec. III.A, the GS formula and Eq. eq:toeplitz_fft), for
+ * td_loglike_batch with path TD_PATH_GSCE.  x = C^{-1} e_1 by the
+ * Levinson-Durbin recursion in FP64 (O(N^2) once; no N^2 storage), log det C
+ * = sum log v_t, then the spectra of the two circulant embeddings (length M
+ * = the power of two >= 2N) by an FP64 FFT, rounded to FP32.  Keeps
+ * 9 M / 4 x 8 bytes on the device (M = 16384 at N = 8192: 288 KB).  chi2
+ * from FP32 FFTs is ~1.5e-8 rms relative at N = 1024 (below: too few terms
+ * to average the rounding, so N >= 1024).
+ * Independent of td_factor: a segment may have both.  Synchronises `stream`.
+ * Errors: TD_ERR_UNSUPPORTED for a segment with gaps, N < 1024 or N > 32768;
+ * TD_ERR_NOT_PD (td_last_pivot gives the order); TD_ERR_OOM.
+ */
+td_status td_gs_prepare(td_segment* s, void* stream);
+
+/* log det C_kept (host scalar).  Requires a successful td_factor (or, for a
+   segment only prepared by td_gs_prepare, gives the recursion's value). */
 td_status td_logdet(const td_segment* s, double* out);
 
 /* N' (kept sample count); -1 for a NULL segment. */

@@ -377,6 +377,10 @@ int64_t td_last_pivot(const td_segment* s) { return s ? s->pivot : -1; }
 
 td_status td_logdet(const td_segment* s, double* out) {
   if (!s || !out) return fail(TD_ERR_INVALID, "NULL argument");
+  if (!s->factored && s->gs.ready) {
+    *out = s->gs.logdet;
+    return TD_OK;
+  }
   if (!s->factored) return fail(TD_ERR_NOT_FACTORED, "segment not factored");
   *out = s->logdet;
   return TD_OK;
@@ -469,12 +473,19 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   if (K == 0) return TD_OK;
   if (!R || !logL) return fail(TD_ERR_INVALID, "R or logL is NULL");
   if (ldr < s->nk) return fail(TD_ERR_INVALID, "ldr < N'");
-  if (!s->factored) return fail(TD_ERR_NOT_FACTORED, "segment not factored");
-  td_status r = check_device(s);
-  if (r != TD_OK) return r;
   td_options o;
   td_options_default(&o);
   if (opt) o = *opt;
+  if (o.path == TD_PATH_GSCE) {
+    td_status rg = check_device(s);
+    if (rg != TD_OK) return rg;
+    if (o.refine) return fail(TD_ERR_INVALID, "refinement applies to the split-product paths, not to GSCE");
+    if (!s->gs.ready) return fail(TD_ERR_NOT_FACTORED, "GSCE path: call td_gs_prepare first");
+    return gs_batch(s, R, ldr, K, logL, chi2, reinterpret_cast<cudaStream_t>(stream));
+  }
+  if (!s->factored) return fail(TD_ERR_NOT_FACTORED, "segment not factored");
+  td_status r = check_device(s);
+  if (r != TD_OK) return r;
   if (o.wait_limit_ns <= 0) o.wait_limit_ns = 1000000000LL;
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   const bool fp64 = (o.precision == TD_PREC_FP64) || (o.path == TD_PATH_FP64);
@@ -623,6 +634,7 @@ void td_segment_destroy(td_segment* s) {
   free_host_stage(s->hst);
   free_template_state(s->tpl);
   free_refine_state(s);
+  free_gs_state(s);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);
   if (prev >= 0 && prev != s->device) cudaSetDevice(prev);
   delete s;

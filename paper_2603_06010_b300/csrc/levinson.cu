@@ -34,16 +34,6 @@ namespace cg = cooperative_groups;
 
 namespace td {
 
-struct LevJob {
-  const double* acf;       // device, n lags
-  int64_t n;               // samples (gap-free: N' = n)
-  double* a0;              // device scratch, n doubles
-  double* a1;              // device scratch, n doubles
-  double* linv;            // device, row t at linv + t ld, columns 0..t written
-  int64_t ld;
-  double* logdet;          // device, one double
-  DevStatus* status;       // NOT_PD pivot
-};
 
 constexpr int LEV_THREADS = 1024;
 constexpr int64_t LEV_MAX_N = 1 << 20;
@@ -124,10 +114,21 @@ __global__ void __launch_bounds__(LEV_THREADS, 1) k_levinson_rows(const LevJob* 
     // row t-1 of L^{-1}: column c < t-1 holds -a_{t-1, t-1-c} / sqrt(v_{t-1}), column t-1 holds 1 / sqrt(v_{t-1})
     if (lead) logdet += log(v);
     const double inv = 1.0 / sqrt(v);
-    double* row = jb.linv + (t - 1) * jb.ld;
-    for (int64_t c = g; c < t - 1; c += STRIDE) row[c] = -a[t - 1 - c] * inv;
-    if (lead) row[t - 1] = inv;
-    if (t == n) break;
+    if (jb.linv) {
+      double* row = jb.linv + (t - 1) * jb.ld;
+      for (int64_t c = g; c < t - 1; c += STRIDE) row[c] = -a[t - 1 - c] * inv;
+      if (lead) row[t - 1] = inv;
+    }
+    if (t == n) {
+      // C^{-1} e_1 = (1, -a_{n-1,1}, ..., -a_{n-1,n-1}) / v_{n-1} (persymmetry of the
+      // Toeplitz inverse; its last column is the last row of L^{-1} over sqrt(v_{n-1}))
+      if (jb.x) {
+        const double iv = 1.0 / v;
+        for (int64_t j = 1 + g; j < n; j += STRIDE) jb.x[j] = -a[j] * iv;
+        if (lead) jb.x[0] = iv;
+      }
+      break;
+    }
     if (!(vn > 0.0) || !isfinite(vn)) {
       if (lead) {
         atomicMin((unsigned long long*)&jb.status->pivot, (unsigned long long)t);
@@ -241,7 +242,7 @@ td_status run_lev_batch(std::vector<LevSeg>& b, cudaStream_t st) {
     }
     DevStatus h{0, 0, LLONG_MAX};
     cudaMemcpyAsync(s->status, &h, sizeof h, cudaMemcpyHostToDevice, st);
-    jobs.push_back(LevJob{s->acf, s->n, x.a0, x.a1, x.linv, s->nkp, x.ld, s->status});
+    jobs.push_back(LevJob{s->acf, s->n, x.a0, x.a1, x.linv, s->nkp, x.ld, s->status, nullptr});
   }
   LevJob* dj = nullptr;
   if (r == TD_OK) {

@@ -90,6 +90,20 @@ struct Scratch {
   uint64_t use_clock = 0;
 };
 
+// one Levinson-Durbin chain (gap-free segment of n samples)
+struct LevJob {
+  const double* acf;       // device, n lags
+  int64_t n;               // samples (gap-free: N' = n)
+  double* a0;              // device scratch, n doubles
+  double* a1;              // device scratch, n doubles
+  double* linv;            // device, row t at linv + t ld, columns 0..t written; nullptr: rows not stored
+  int64_t ld;
+  double* logdet;          // device, one double
+  DevStatus* status;       // NOT_PD pivot
+  double* x;               // nullptr, or device n doubles: receives C^{-1} e_1
+};
+cudaError_t launch_levinson_rows(const LevJob* jobs, int njobs, cudaStream_t st);
+
 int split_chunk(int64_t nk, int64_t nkp, int bn);
 void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
                         std::vector<SplitUnit>& units, int& n_slots, bool all_slots = false);
@@ -137,6 +151,18 @@ struct RefineState {          // td_options.refine
   td::TcSegDev* seg_op = nullptr;   // [0]: L^{-1} slices (nsl), [1]: L slices (4)
 };
 
+struct GsState {              // td_gs_prepare / TD_PATH_GSCE (gap-free segments)
+  int logm = 0;                 // circulant length M = 2^logm >= 2N
+  float2* S1 = nullptr;         // spectra of the two circulant embeddings, bit-reversed order,
+  float2* S2 = nullptr;         //   scaled by 1 / (M x_0); [M]
+  double x0 = 0.0;              // (C^{-1})_00
+  float2* tw = nullptr;         // twiddle shears (-tan(theta/2), sin(theta)), theta = -2 pi j / M, j < M/4
+  float2* scr = nullptr;        // per-CTA product buffer of a batch
+  int64_t scr_elems = 0;
+  double logdet = 0.0;          // from the recursion's prediction-error variances
+  bool ready = false;
+};
+
 struct td_segment {
   int device = 0;
   int64_t n = 0;          // samples
@@ -158,6 +184,7 @@ struct td_segment {
   HostStage hst;
   TemplateState tpl;
   RefineState ref;
+  GsState gs;
   // instrumentation
   bool prof = false;
   std::vector<cudaEvent_t> ev;   // start/stop pairs
@@ -251,5 +278,9 @@ td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* o
 td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl,
                        int64_t wait_limit_ns, cudaStream_t st);
 void free_refine_state(td_segment* s);
+// Gohberg-Semencul path (TD_PATH_GSCE)
+td_status gs_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2,
+                   cudaStream_t st);
+void free_gs_state(td_segment* s);
 
 }  // namespace td

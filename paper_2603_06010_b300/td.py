@@ -20,7 +20,7 @@ TD_OK, TD_ERR_INVALID, TD_ERR_NOT_PD, TD_ERR_OOM, TD_ERR_CUDA, TD_ERR_TIMEOUT, T
     TD_ERR_UNSUPPORTED, TD_ERR_BUSY = range(9)
 TD_PREC_FP64, TD_PREC_BF16X6, TD_PREC_BF16X3, TD_PREC_AUTO, TD_PREC_BF16X10 = range(5)
 (TD_PATH_AUTO, TD_PATH_TENSOR, TD_PATH_STREAM, TD_PATH_FP64, TD_PATH_STREAM64, TD_PATH_SMALLK,
- TD_PATH_TENSOR128, TD_PATH_STREAM128) = range(8)
+ TD_PATH_TENSOR128, TD_PATH_STREAM128, TD_PATH_GSCE) = range(9)
 
 STATUS_NAMES = {0: "TD_OK", 1: "TD_ERR_INVALID", 2: "TD_ERR_NOT_PD", 3: "TD_ERR_OOM", 4: "TD_ERR_CUDA",
                 5: "TD_ERR_TIMEOUT", 6: "TD_ERR_NOT_FACTORED", 7: "TD_ERR_UNSUPPORTED", 8: "TD_ERR_BUSY"}
@@ -51,6 +51,7 @@ SIGNATURES = {
     "td_template_batch": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "td_group_create": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp, _c.POINTER(_vp)]),
     "td_group_set_joint": (_c.c_int, [_vp, _vp]),
+    "td_gs_prepare": (_c.c_int, [_vp, _vp]),
     "td_group_launch": (_c.c_int, [_vp, _vp]),
     "td_group_graph_launch": (_c.c_int, [_vp, _vp]),
     "td_group_tune": (_c.c_int, [_vp, _vp, _c.POINTER(_c.c_double)]),
@@ -183,6 +184,10 @@ class Segment:
 
     def release_fp64(self):
         _check(lib().td_segment_release_fp64(self.handle))
+
+    def gs_prepare(self, stream=None):
+        """td_gs_prepare: Gohberg-Semencul spectra for path TD_PATH_GSCE (gap-free, 1024 <= N <= 32768)."""
+        _check(lib().td_gs_prepare(self.handle, _stream_ptr(stream)))
 
     def reserve(self, K: int, opt: TdOptions | None = None):
         _check(lib().td_reserve(self.handle, int(K), None if opt is None else ctypes.byref(opt)))

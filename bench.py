@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=3.0)
-    p.add_argument("--only", default=None, choices=["grouped", "serving", "gapped3", "refine"],
+    p.add_argument("--only", default=None, choices=["grouped", "serving", "gapped3", "refine", "gsce"],
                    help="run one extra workload alone and print its JSON object (profiling; not the bench line)")
     return p.parse_args()
 
@@ -323,6 +323,65 @@ def refine_extra(td, torch, seg, R, K):
                     "inputs (134 MB) and the operator larger than L2", "runs": runs}
 
 
+def gsce_extra(td, torch, seg_in, R, K):
+    """Gohberg-Semencul path (gap-free segments): the benchmark batch and small batches at
+    N=8192, then a long segment (N=32768) beside the dense path on the same segment."""
+    from paper_2603_06010_b300 import inputs
+    stream = torch.cuda.current_stream()
+
+    def timed(seg, Rs, opt, reps):
+        out = torch.empty(Rs.shape[0], dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            seg.loglike_into(Rs, out, opt)
+        torch.cuda.synchronize()
+        seg.check()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(reps):
+            seg.loglike_into(Rs, out, opt)
+        eb.record(stream)
+        torch.cuda.synchronize()
+        return ea.elapsed_time(eb) / reps, out
+
+    gs = td.TD_PATH_GSCE
+    seg = td.Segment(seg_in.acf, factor=False)
+    t0 = time.perf_counter()
+    seg.gs_prepare()
+    prep = time.perf_counter() - t0
+    ms, out = timed(seg, R, td.options(path=gs), 5)
+    res = {"note": "chi2 = (|L_x^T r|^2 - |R_x r|^2)/x_0 with x = C^-1 e_1 (Levinson-Durbin, FP64), the two "
+                   "triangular Toeplitz products as FP32 circular convolutions of length M = 2^m >= 2N, one "
+                   "8-CTA cluster per column pair; call_ms of back-to-back calls",
+           "gapfree_n8192": {"prepare_s": prep, "K": K, "call_ms": ms, "evals_per_s": K / (ms / 1e3),
+                             "max_abs_dlogL_vs_oracle": golden_dlogl(out.cpu().numpy()),
+                             "small_batches": []}}
+    for k in (1, 8, 64):
+        mk, _ = timed(seg, R[:k].contiguous(), td.options(path=gs), 20)
+        res["gapfree_n8192"]["small_batches"].append({"K": k, "call_ms": mk, "evals_per_s": k / (mk / 1e3)})
+    seg.close()
+    n, fs = 32768, 4096.0
+    acf = inputs.acf_from_psd(n, fs)
+    Rl = torch.from_numpy(inputs.noise_residuals(n, fs, 512, 11)).cuda()
+    long_seg = td.Segment(acf, factor=False)
+    t0 = time.perf_counter()
+    long_seg.gs_prepare()
+    prep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    td.factor_many([long_seg])          # dense operator of the same segment, for comparison
+    fac = time.perf_counter() - t0
+    runs = []
+    for k in (1, 64, 512):
+        Rk = Rl[:k].contiguous()
+        mg, og = timed(long_seg, Rk, td.options(path=gs), 10)
+        md, od = timed(long_seg, Rk, td.options(), 10)
+        runs.append({"K": k, "gsce_call_ms": mg, "dense_call_ms": md,
+                     "max_abs_dlogL_gsce_vs_dense": float((og - od).abs().max().item())})
+    long_seg.close()
+    res["gapfree_n32768"] = {"prepare_s": prep, "dense_operator_build_s": fac, "runs": runs,
+                             "dense": "td_factor_many operator, default options (BF16X6, automatic path)"}
+    return res
+
+
 def serving_extra(td, torch, seconds):
     """Open-loop Poisson serving on a fleet of resident segments: the whole fleet,
     then the gapped N=8192 and gapped N=16384 segments alone (per-size latency)."""
@@ -471,8 +530,11 @@ def main():
             c, seg_in, R_host = make_workload(0)
             seg = td.Segment(seg_in.acf, seg_in.mask)
             return refine_extra(td, torch, seg, torch.from_numpy(R_host).cuda(), R_host.shape[0])
+        def only_gsce():
+            c, seg_in, R_host = make_workload(0)
+            return gsce_extra(td, torch, seg_in, torch.from_numpy(R_host).cuda(), R_host.shape[0])
         fn = {"grouped": lambda: grouped_extra(td, torch), "serving": lambda: serving_extra(td, torch, args.serve_seconds),
-              "gapped3": lambda: gapped_joint_extra(td, torch), "refine": only_refine}[args.only]
+              "gapped3": lambda: gapped_joint_extra(td, torch), "refine": only_refine, "gsce": only_gsce}[args.only]
         print(json.dumps({"only": args.only, "result": fn()}), flush=True)
         return
 
@@ -675,6 +737,7 @@ def main():
     if world == 1:
         line["template_form"] = template_extra(td, torch, seg, seg_in, K)
         line["refinement"] = refine_extra(td, torch, seg, R, K)
+        line["gsce"] = gsce_extra(td, torch, seg_in, R, K)
     if world == 1 and not args.no_grouped:
         line["gapped_n16384_3det"] = gapped_joint_extra(td, torch)
         line["grouped"] = grouped_extra(td, torch)

@@ -25,6 +25,12 @@
  *     on that stream has completed.
  *   - Errors are returned as td_status, never trapped; td_last_error()
  *     gives a thread-local message for the last failing call on the thread.
+ *   - A segment is used by one host thread at a time, and its evaluation
+ *     calls are ordered with each other on the device (one stream, or
+ *     streams ordered by events): they share the segment's scratch buffers
+ *     and cached work lists.  Different segments may run concurrently from
+ *     different threads and streams (the server keeps at most one batch per
+ *     segment in flight for this reason).
  *   - No device kernel spins without a bound: every wait inside a kernel
  *     gives up after a time limit (td_options.wait_limit_ns) and the call
  *     reports TD_ERR_TIMEOUT on the next synchronising call.

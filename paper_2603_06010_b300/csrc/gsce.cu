@@ -426,13 +426,13 @@ td_status gs_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double
   if (K > INT_MAX - 1) return fail(TD_ERR_INVALID, "K too large for the GSCE path");
   const int threads = gs_threads(g.logm);
   const size_t smem = gs_smem(g.logm);
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_done{0};
+  if (device_needs_setup(attr_done)) {
     TD_CUDA(cudaFuncSetAttribute(k_gs_chi2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)gs_smem(GS_MAX_LOGM)));
     // small CTAs (22 KB at N = 8192): let as many share an SM as the registers allow
     TD_CUDA(cudaFuncSetAttribute(k_gs_chi2, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
-    attr_set = true;
+    mark_device_done(attr_done);
   }
   const int64_t npairs = (K + 1) / 2;
   cudaLaunchConfig_t cfg = {};

@@ -385,12 +385,12 @@ template <int NSL, int BN, int MODE>
 static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int n_items, const TcSegDev* segs,
                                DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl) {
   using C = tc::Cfg<NSL, BN>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_done{0};
+  if (device_needs_setup(attr_done)) {
     cudaError_t e =
         cudaFuncSetAttribute(k_tc_cdo<NSL, BN, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    mark_device_done(attr_done);
   }
   const int n_total = MODE != 0 ? n_items : single.nm * single.nc;
   if (n_total <= 0) return cudaSuccess;

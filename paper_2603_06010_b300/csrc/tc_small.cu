@@ -446,11 +446,11 @@ template <int NSL, int NC>
 static cudaError_t launch_small_impl(const TcItem* items, int n_items, const TcSegDev* segs, DevStatus* status,
                                      int64_t lim, cudaStream_t st) {
   using C = tsm::Cfg<NSL, NC>;
-  static bool attr_set = false;
-  if (!attr_set) {
+  static std::atomic<unsigned long long> attr_done{0};
+  if (device_needs_setup(attr_done)) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_small<NSL, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    mark_device_done(attr_done);
   }
   if (n_items <= 0) return cudaSuccess;
   int grid = tc_num_sms();

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -103,6 +104,20 @@ struct LevJob {
   double* x;               // nullptr, or device n doubles: receives C^{-1} e_1
 };
 cudaError_t launch_levinson_rows(const LevJob* jobs, int njobs, cudaStream_t st);
+
+// Kernel attributes (dynamic shared memory above 48 KB) are per device: true
+// while the current device's bit in `done` is clear.  Set the attribute, then
+// mark_device_done; setting it twice (two threads at once) is harmless.
+inline bool device_needs_setup(const std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return !(done.load(std::memory_order_acquire) & (1ull << (dev & 63)));
+}
+inline void mark_device_done(std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  done.fetch_or(1ull << (dev & 63), std::memory_order_release);
+}
 
 int split_chunk(int64_t nk, int64_t nkp, int bn);
 void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,

@@ -63,6 +63,7 @@ namespace td {
 constexpr int GS_CL = 8;          // CTAs per column pair: one thread-block cluster
 constexpr int GS_MAX_LOGM = 16;   // M <= 65536 (N <= 32768): M/8 <= 8192 values per CTA
 constexpr int64_t GS_MIN_N = 1024;
+constexpr int GS_TWO_SIGNAL_LOGM = 16;
 
 // one spare slot per 16: every register pass of the 2^14 network then reads and
 // writes its groups at the two-wavefront minimum of 8-byte accesses
@@ -159,8 +160,11 @@ __device__ __forceinline__ void group_op(float2 (&v)[1 << R], int theta, int log
   }
 }
 
-// one register pass of a local length-2^logl network in this CTA's buffer
-template <int R, bool INV>
+// One register pass of the local length-2^logl networks of NSIG signals kept
+// one after another in this CTA's buffer (signal j's value l at index
+// j 2^logl + l); a thread takes the same group of every signal, so their
+// arithmetic interleaves.
+template <int R, bool INV, int NSIG>
 __device__ __forceinline__ void fft_pass(float2* buf, const float2* lift, int logl, int s0) {
   const int lq = logl - s0 - R;
   const int q = 1 << lq;
@@ -168,56 +172,68 @@ __device__ __forceinline__ void fft_pass(float2* buf, const float2* lift, int lo
   for (int g = threadIdx.x; g < groups; g += blockDim.x) {
     const int o = g & (q - 1);
     const int base = ((g >> lq) << (logl - s0)) + o;
-    float2 v[1 << R];
+    float2 v[NSIG][1 << R];
 #pragma unroll
-    for (int k = 0; k < (1 << R); ++k) v[k] = buf[gpad(base + k * q)];
-    group_op<R, INV>(v, o << s0, logl, lift);
+    for (int j = 0; j < NSIG; ++j)
 #pragma unroll
-    for (int k = 0; k < (1 << R); ++k) buf[gpad(base + k * q)] = v[k];
+      for (int k = 0; k < (1 << R); ++k) v[j][k] = buf[gpad((j << logl) + base + k * q)];
+#pragma unroll
+    for (int j = 0; j < NSIG; ++j) group_op<R, INV>(v[j], o << s0, logl, lift);
+#pragma unroll
+    for (int j = 0; j < NSIG; ++j)
+#pragma unroll
+      for (int k = 0; k < (1 << R); ++k) buf[gpad((j << logl) + base + k * q)] = v[j][k];
   }
 }
 
-template <bool INV>
+template <bool INV, int NSIG>
 __device__ __forceinline__ void fft_run_pass(float2* buf, const float2* lift, int logl, int s0) {
   const int R = min(3, logl - s0);
   if (R == 3)
-    fft_pass<3, INV>(buf, lift, logl, s0);
+    fft_pass<3, INV, NSIG>(buf, lift, logl, s0);
   else if (R == 2)
-    fft_pass<2, INV>(buf, lift, logl, s0);
+    fft_pass<2, INV, NSIG>(buf, lift, logl, s0);
   else
-    fft_pass<1, INV>(buf, lift, logl, s0);
+    fft_pass<1, INV, NSIG>(buf, lift, logl, s0);
   __syncthreads();
 }
 
+template <int NSIG>
 __device__ void fft_forward(float2* buf, const float2* lift, int logl) {
-  for (int s0 = 0; s0 < logl; s0 += 3) fft_run_pass<false>(buf, lift, logl, s0);
+  for (int s0 = 0; s0 < logl; s0 += 3) fft_run_pass<false, NSIG>(buf, lift, logl, s0);
 }
+template <int NSIG>
 __device__ void fft_inverse(float2* buf, const float2* lift, int logl) {
-  for (int s0 = ((logl - 1) / 3) * 3; s0 >= 0; s0 -= 3) fft_run_pass<true>(buf, lift, logl, s0);
+  for (int s0 = ((logl - 1) / 3) * 3; s0 >= 0; s0 -= 3) fft_run_pass<true, NSIG>(buf, lift, logl, s0);
 }
 
 // Stages 0..2 of the length-M network: elements M/2, M/4, M/8 apart, i.e. the
-// group (o + k M/8, k = 0..7) holds local element o of every CTA of the
-// cluster.  CTA r owns the groups o in [r ml/8, (r+1) ml/8): it reads the
-// eight elements from the eight CTAs' shared memory, runs the three stages and
-// writes them back; every element has one owner, so the pass needs no other
-// ordering than the cluster barriers around it.
-template <bool INV>
+// group (o + k M/8, k = 0..7) holds local value o of every CTA of the
+// cluster.  CTA r owns the groups o in [r ml/8, (r+1) ml/8) of every signal:
+// it reads the eight values from the eight CTAs' shared memory, runs the three
+// stages and writes them back; every value has one owner, so the pass needs
+// no other ordering than the cluster barriers around it.
+template <bool INV, int NSIG>
 __device__ __forceinline__ void cross_pass(float2* buf, int logm, const float2* __restrict__ lift_g) {
   cg::cluster_group cl = cg::this_cluster();
-  const int ml = 1 << (logm - 3), per = ml / GS_CL;
+  const int logml = logm - 3, per = (1 << logml) / GS_CL;
   const int o0 = (int)cl.block_rank() * per;
   float2* peer[GS_CL];
 #pragma unroll
   for (int k = 0; k < GS_CL; ++k) peer[k] = cl.map_shared_rank(buf, k);
   for (int t = threadIdx.x; t < per; t += blockDim.x) {
     const int o = o0 + t;
-    float2 v[GS_CL];
+    float2 v[NSIG][GS_CL];
 #pragma unroll
-    for (int k = 0; k < GS_CL; ++k) v[k] = peer[k][gpad(o)];
-    group_op<3, INV>(v, o, logm, lift_g);
+    for (int j = 0; j < NSIG; ++j)
 #pragma unroll
-    for (int k = 0; k < GS_CL; ++k) peer[k][gpad(o)] = v[k];
+      for (int k = 0; k < GS_CL; ++k) v[j][k] = peer[k][gpad((j << logml) + o)];
+#pragma unroll
+    for (int j = 0; j < NSIG; ++j) group_op<3, INV>(v[j], o, logm, lift_g);
+#pragma unroll
+    for (int j = 0; j < NSIG; ++j)
+#pragma unroll
+      for (int k = 0; k < GS_CL; ++k) peer[k][gpad((j << logml) + o)] = v[j][k];
   }
 }
 
@@ -262,83 +278,99 @@ __device__ __forceinline__ void sum_squares(const float2* buf, int base, int ml,
   }
 }
 
-// One cluster of GS_CL CTAs per column pair (persistent over pairs).  CTA r
-// holds elements [r ml, (r+1) ml) of the length-M signal, ml = M / GS_CL:
+// One cluster of GS_CL CTAs per NSIG column pairs (persistent over pairs).
+// CTA r holds values [r ml, (r+1) ml) of each length-M signal, ml = M / GS_CL:
 // cluster barrier, the cross pass (stages 0..2), cluster barrier, the local
 // stages 3..m-1 (a length-ml network), the spectral products, and for each
-// product the inverse in the opposite order.  Each CTA's four partial sums
-// are added by rank 0 in rank order.
-__global__ void __cluster_dims__(GS_CL, 1, 1) __launch_bounds__(1024)
+// product the inverse in the opposite order.  Each CTA's partial sums are
+// added by rank 0 in rank order.
+template <int NSIG>
+__global__ void __cluster_dims__(GS_CL, 1, 1) __launch_bounds__(NSIG == 1 ? 1024 : 512)
     k_gs_chi2(const float* __restrict__ R, int64_t ldr, int n, int K, int logm, const float2* __restrict__ S1,
               const float2* __restrict__ S2, const float2* __restrict__ lift_g, float2* __restrict__ scr, double x0,
               double logdet, double* __restrict__ logL, double* __restrict__ chi2) {
-  extern __shared__ float2 buf[];   // gpad(ml) signal slots, then the ml/4 local twiddle shears
-  __shared__ float red[32 * 4 * 2];
-  __shared__ double part[4];
+  extern __shared__ float2 buf[];   // NSIG signals (gpad(NSIG ml) slots), then the ml/4 local twiddle shears
+  __shared__ float red[32 * 4 * NSIG * 2];
+  __shared__ double part[4 * NSIG];
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int logml = logm - 3, ml = 1 << logml;
   const int npairs = (K + 1) / 2;
   const int cid = blockIdx.x / GS_CL, ncl = gridDim.x / GS_CL;
   const int base = rank * ml;
-  float2* my = scr + ((int64_t)cid * GS_CL + rank) * ml;
-  float2* tws = buf + gpad(ml);
+  float2* my = scr + ((int64_t)cid * GS_CL + rank) * ml * NSIG;
+  float2* tws = buf + gpad(NSIG * ml);
   for (int i = threadIdx.x; i < ml / 4; i += blockDim.x) tws[i] = lift_g[GS_CL * i];   // exp(-2 pi i j / ml)
-  for (int pair = cid; pair < npairs; pair += ncl) {
-    const int ca = 2 * pair, cb = ca + 1;
-    const bool has_b = cb < K;
-    const float* ra = R + (int64_t)ca * ldr;
-    const float* rb = R + (int64_t)(has_b ? cb : ca) * ldr;
-    for (int l = threadIdx.x; l < ml; l += blockDim.x) {
-      const int i = base + l;
-      buf[gpad(l)] = make_float2(i < n ? ra[i] : 0.f, (i < n && has_b) ? rb[i] : 0.f);
+  for (int p0 = cid * NSIG; p0 < npairs; p0 += ncl * NSIG) {
+#pragma unroll
+    for (int j = 0; j < NSIG; ++j) {
+      const int ca = 2 * (p0 + j), cb = ca + 1;
+      const bool has_a = ca < K, has_b = cb < K;
+      const float* ra = R + (int64_t)(has_a ? ca : 0) * ldr;
+      const float* rb = R + (int64_t)(has_b ? cb : 0) * ldr;
+      for (int l = threadIdx.x; l < ml; l += blockDim.x) {
+        const int i = base + l;
+        buf[gpad(j * ml + l)] = make_float2((i < n && has_a) ? ra[i] : 0.f, (i < n && has_b) ? rb[i] : 0.f);
+      }
     }
     cl.sync();
-    cross_pass<false>(buf, logm, lift_g);
+    cross_pass<false, NSIG>(buf, logm, lift_g);
     cl.sync();
-    fft_forward(buf, tws, logml);
-    for (int l = threadIdx.x; l < ml; l += blockDim.x) {
+    fft_forward<NSIG>(buf, tws, logml);
+    for (int l = threadIdx.x; l < NSIG * ml; l += blockDim.x) {
+      const int g = base + (l & (ml - 1));
       const float2 y = buf[gpad(l)];
-      buf[gpad(l)] = c_mul(y, __ldg(&S1[base + l]));
-      my[l] = c_mul(y, __ldg(&S2[base + l]));   // the same thread reads it back below
+      buf[gpad(l)] = c_mul(y, __ldg(&S1[g]));
+      my[l] = c_mul(y, __ldg(&S2[g]));   // the same thread reads it back below
     }
     __syncthreads();
-    float h[4] = {0.f, 0.f, 0.f, 0.f}, lo[4] = {0.f, 0.f, 0.f, 0.f};
-    fft_inverse(buf, tws, logml);
+    float h[4 * NSIG], lo[4 * NSIG];
+#pragma unroll
+    for (int j = 0; j < 4 * NSIG; ++j) h[j] = lo[j] = 0.f;
+    fft_inverse<NSIG>(buf, tws, logml);
     cl.sync();
-    cross_pass<true>(buf, logm, lift_g);
+    cross_pass<true, NSIG>(buf, logm, lift_g);
     cl.sync();
-    sum_squares(buf, base, ml, n, h[0], lo[0], h[1], lo[1]);
+#pragma unroll
+    for (int j = 0; j < NSIG; ++j)
+      sum_squares(buf + gpad(j * ml), base, ml, n, h[4 * j], lo[4 * j], h[4 * j + 1], lo[4 * j + 1]);
     __syncthreads();
-    for (int l = threadIdx.x; l < ml; l += blockDim.x) buf[gpad(l)] = my[l];
+    for (int l = threadIdx.x; l < NSIG * ml; l += blockDim.x) buf[gpad(l)] = my[l];
     __syncthreads();
-    fft_inverse(buf, tws, logml);
+    fft_inverse<NSIG>(buf, tws, logml);
     cl.sync();
-    cross_pass<true>(buf, logm, lift_g);
+    cross_pass<true, NSIG>(buf, logm, lift_g);
     cl.sync();
-    sum_squares(buf, base, ml, n, h[2], lo[2], h[3], lo[3]);
-    double s[4] = {0.0, 0.0, 0.0, 0.0};
-    block_sum_ff<4>(h, lo, red, s);
+#pragma unroll
+    for (int j = 0; j < NSIG; ++j)
+      sum_squares(buf + gpad(j * ml), base, ml, n, h[4 * j + 2], lo[4 * j + 2], h[4 * j + 3], lo[4 * j + 3]);
+    double s[4 * NSIG];
+#pragma unroll
+    for (int j = 0; j < 4 * NSIG; ++j) s[j] = 0.0;
+    block_sum_ff<4 * NSIG>(h, lo, red, s);
     if (threadIdx.x == 0)
-      for (int j = 0; j < 4; ++j) part[j] = s[j];
+      for (int j = 0; j < 4 * NSIG; ++j) part[j] = s[j];
     cl.sync();
     if (rank == 0 && threadIdx.x == 0) {
-      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      double t[4 * NSIG];
+      for (int j = 0; j < 4 * NSIG; ++j) t[j] = 0.0;
       for (int r = 0; r < GS_CL; ++r) {
         const double* pr = cl.map_shared_rank(part, r);
-        for (int j = 0; j < 4; ++j) t[j] += pr[j];
+        for (int j = 0; j < 4 * NSIG; ++j) t[j] += pr[j];
       }
-      const double c2a = x0 * (t[0] - t[2]);
-      logL[ca] = -0.5 * c2a - 0.5 * logdet - 0.5 * (double)n * LOG2PI;
-      if (chi2) chi2[ca] = c2a;
-      if (has_b) {
-        const double c2b = x0 * (t[1] - t[3]);
-        logL[cb] = -0.5 * c2b - 0.5 * logdet - 0.5 * (double)n * LOG2PI;
-        if (chi2) chi2[cb] = c2b;
+      for (int j = 0; j < NSIG; ++j) {
+        const int ca = 2 * (p0 + j), cb = ca + 1;
+        for (int c = 0; c < 2; ++c) {
+          const int col = c == 0 ? ca : cb;
+          if (col >= K) continue;
+          const double c2 = x0 * (t[4 * j + c] - t[4 * j + 2 + c]);
+          logL[col] = -0.5 * c2 - 0.5 * logdet - 0.5 * (double)n * LOG2PI;
+          if (chi2) chi2[col] = c2;
+        }
       }
     }
-    // the next pair's first cluster barrier orders rank 0's reads of part[]
-    // before any CTA writes it again
+    // the next iteration's first cluster barrier orders rank 0's reads of
+    // part[] before any CTA writes it again
   }
   cl.sync();   // no CTA leaves while rank 0 may still read its partial sums
 }
@@ -413,39 +445,41 @@ void free_gs_state(td_segment* s) {
   g.ready = false;
 }
 
-// per CTA: ml = M / GS_CL values; one thread per radix-8 group of the local passes
-static int gs_threads(int logm) { return std::max(32, std::min(1024, (1 << (logm - 3)) / 8)); }
-static size_t gs_smem(int logm) {
-  const int ml = 1 << (logm - 3);
-  return (size_t)(ml + (ml >> 4) + (ml >> 2)) * sizeof(float2);
+// per CTA: ml = M / GS_CL values per signal; one thread per radix-8 group of the local passes
+static int gs_threads(int logm, int nsig) {
+  return std::max(32, std::min(nsig == 1 ? 1024 : 512, (1 << (logm - 3)) / 8));
+}
+static size_t gs_smem(int logm, int nsig) {
+  const int ml = 1 << (logm - 3), tot = nsig * ml;
+  return (size_t)(tot + (tot >> 4) + (ml >> 2)) * sizeof(float2);
 }
 
-td_status gs_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2,
-                   cudaStream_t st) {
-  GsState& g = s->gs;
-  if (K > INT_MAX - 1) return fail(TD_ERR_INVALID, "K too large for the GSCE path");
-  const int threads = gs_threads(g.logm);
-  const size_t smem = gs_smem(g.logm);
+template <int NSIG>
+static td_status gs_launch(GsState& g, const float* R, int64_t ldr, int n, int64_t K, double* logL, double* chi2,
+                           cudaStream_t st, bool query_only, int* clusters_out) {
+  const int threads = gs_threads(g.logm, NSIG);
+  const size_t smem = gs_smem(g.logm, NSIG);
   static std::atomic<unsigned long long> attr_done{0};
   if (device_needs_setup(attr_done)) {
-    TD_CUDA(cudaFuncSetAttribute(k_gs_chi2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)gs_smem(GS_MAX_LOGM)));
+    TD_CUDA(cudaFuncSetAttribute(k_gs_chi2<NSIG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)gs_smem(GS_MAX_LOGM, NSIG)));
     // small CTAs (22 KB at N = 8192): let as many share an SM as the registers allow
-    TD_CUDA(cudaFuncSetAttribute(k_gs_chi2, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+    TD_CUDA(cudaFuncSetAttribute(k_gs_chi2<NSIG>, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
     mark_device_done(attr_done);
   }
-  const int64_t npairs = (K + 1) / 2;
+  const int64_t npairs = (K + 1) / 2, units = (npairs + NSIG - 1) / NSIG;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(GS_CL * std::min<int64_t>(npairs, 4096)));
+  cfg.gridDim = dim3((unsigned)(GS_CL * std::min<int64_t>(units, 4096)));
   cfg.blockDim = dim3((unsigned)threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   int max_clusters = 0;
-  TD_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, k_gs_chi2, &cfg));
+  TD_CUDA(cudaOccupancyMaxActiveClusters(&max_clusters, k_gs_chi2<NSIG>, &cfg));
   if (max_clusters < 1) return fail(TD_ERR_CUDA, "GSCE cluster does not fit the device");
-  const int clusters = (int)std::min<int64_t>(npairs, max_clusters);
-  const int grid = clusters * GS_CL;
-  const int64_t need = (int64_t)clusters << g.logm;   // one length-M product buffer per cluster
+  const int clusters = (int)std::min<int64_t>(units, max_clusters);
+  *clusters_out = clusters;
+  if (query_only) return TD_OK;
+  const int64_t need = ((int64_t)clusters * NSIG) << g.logm;   // NSIG length-M product buffers per cluster
   if (need > g.scr_elems) {
     cudaStreamSynchronize(st);
     gs_free(g.scr);
@@ -456,9 +490,32 @@ td_status gs_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double
     }
     g.scr_elems = need;
   }
-  k_gs_chi2<<<grid, threads, smem, st>>>(R, ldr, (int)s->n, (int)K, g.logm, g.S1, g.S2, g.tw, g.scr, g.x0,
-                                         g.logdet, logL, chi2);
+  k_gs_chi2<NSIG><<<clusters * GS_CL, threads, smem, st>>>(R, ldr, n, (int)K, g.logm, g.S1, g.S2, g.tw, g.scr,
+                                                           g.x0, g.logdet, logL, chi2);
   TD_CUDA(cudaGetLastError());
+  return TD_OK;
+}
+
+// Two signals per CTA halve the barriers per column pair and let each thread
+// interleave two groups, at 127 registers a thread.  Measured at K = 2048-4096:
+// N = 32768 (M = 65536) 4.8 ms against 5.9 ms with one signal; N = 16384 2.8 ms
+// against 2.1 ms and N = 8192 2.0 ms against 1.4 ms (the registers then halve
+// the resident CTAs).  So two
+// signals from M = 2^GS_TWO_SIGNAL_LOGM on, and only once the pairs outnumber
+// the clusters one signal keeps resident (small batches keep one pair per
+// cluster, for latency).
+td_status gs_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2,
+                   cudaStream_t st) {
+  GsState& g = s->gs;
+  if (K > INT_MAX - 1) return fail(TD_ERR_INVALID, "K too large for the GSCE path");
+  int resident1 = 0;
+  td_status r = gs_launch<1>(g, R, ldr, (int)s->n, K, logL, chi2, st, true, &resident1);
+  if (r != TD_OK) return r;
+  const int64_t npairs = (K + 1) / 2;
+  int used = 0;
+  r = (g.logm >= GS_TWO_SIGNAL_LOGM && npairs > (int64_t)resident1) ? gs_launch<2>(g, R, ldr, (int)s->n, K, logL, chi2, st, false, &used)
+                                  : gs_launch<1>(g, R, ldr, (int)s->n, K, logL, chi2, st, false, &used);
+  if (r != TD_OK) return r;
   s->prof_kernels += 1;
   return TD_OK;
 }

@@ -67,6 +67,20 @@ def test_gsce_parity(torch_cuda, gpu_lib, n, fs, K):
     assert np.max(np.abs(ll - exp_ll)) <= GS_DLOGL
 
 
+def test_gsce_many_pairs_ragged(torch_cuda, gpu_lib):
+    """Enough column pairs that each CTA carries two signals, with an odd K
+    (the last pair's second column missing) and an odd number of pairs."""
+    from paper_2603_06010_b300 import td
+    n, fs, K = 2048, 2048.0, 1001
+    acf = inputs.acf_from_psd(n, fs)
+    o = oracle.OracleSegment(acf)
+    R = inputs.noise_residuals(n, fs, K, 4242)
+    exp_chi = o.chi2(R)
+    ll, chi = _run(torch_cuda, td, _gs(td, acf), R)
+    assert np.max(np.abs(chi - exp_chi) / exp_chi) <= GS_CHI2_REL
+    assert np.max(np.abs(ll - oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept))) <= GS_DLOGL
+
+
 def test_gsce_white_noise_closed_form(torch_cuda, gpu_lib):
     """C = s2 I: x = e_1 / s2, R_x = 0, chi2 = |r|^2 / s2."""
     from paper_2603_06010_b300 import td

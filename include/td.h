@@ -106,11 +106,13 @@ typedef struct {
   int refine;           /* nonzero: one refinement step (Sec. III.C precision scheme).
                            w~ = L^{-1} r at `precision`; s = r - L w~ from bf16 slices of
                            L with ten products (exact hi*hi, ~1e-9 of |L||w~|); delta =
-                           L^{-1} s at `precision`; chi2 = |w~ + delta|^2.  The result
-                           reaches about the ten-product accuracy from any precision
-                           (BF16X3 included) at about three passes' cost; `path` is
-                           ignored (128-row tiles, every row tile through the chunk
-                           reduction).  Needs the FP64 factor L: TD_ERR_UNSUPPORTED on
+                           L^{-1} s at `precision`; chi2 = |w~ + delta|^2.  Brings
+                           any precision (BF16X3 included) to about 1e-8 in chi2 at
+                           about three passes' cost.  128-row tiles: whole rows with
+                           element-wise epilogues when they fill the GPU, else split-k
+                           through the chunk reduction; TD_PATH_TENSOR* / TD_PATH_STREAM*
+                           fix that choice (and so a column's bits across batches).
+                           Needs the FP64 factor L: TD_ERR_UNSUPPORTED on
                            segments built by td_factor_many(TD_FACTOR_NO_FP64) or after
                            td_segment_release_fp64; TD_ERR_INVALID with TD_PREC_FP64 or
                            TD_PATH_FP64; grouped launches: TD_ERR_UNSUPPORTED.  The

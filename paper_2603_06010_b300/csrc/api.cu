@@ -508,7 +508,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     return TD_OK;
   }
   const int nsl = nslices_for(o.precision, s->nk);
-  if (o.refine) return refine_batch(s, R, ldr, K, logL, chi2, nsl, o.wait_limit_ns, st);
+  if (o.refine) return refine_batch(s, R, ldr, K, logL, chi2, nsl, o.path, o.wait_limit_ns, st);
   const Shape shape = choose_shape(s, K, o.path);
   const int bn = shape.bn;
   const int ngroups = (int)(s->nkp / 64);

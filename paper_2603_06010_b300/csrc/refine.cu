@@ -12,11 +12,13 @@
 // |L| |w~|) is what the corrected w keeps: the result lands near the
 // ten-product accuracy whatever the first pass's precision was.
 //
-// All three products run in the split-k tensor-core kernel with every row
-// tile leaving its accumulator pairs to the chunk reduction (128-row operator
-// tiles, chunks of at least 64 k-blocks, a length fixed by N' alone, so a
-// column's result does not depend on its batch).  The reduction's modes do the
-// element-wise parts: write w~, form s from r, add w~ and square.
+// All three products run on 128-row operator tiles.  With enough tiles to
+// fill the GPU they cover whole rows and do the element-wise part in their
+// epilogue (write w~, form s from r, add w~ and square).  Otherwise they run
+// split-k with every row tile leaving its accumulator pairs (chunks of at
+// least 64 k-blocks, a length fixed by N' alone) and the chunk reduction's
+// modes do it.  A fixed path (TD_PATH_TENSOR*/STREAM*) fixes the shape, so a
+// column's result then does not depend on its batch.
 //
 // Needs the FP64 factor L to slice (once per factor); segments whose L was
 // released, or whose operator came from the Levinson-Durbin route, return
@@ -29,6 +31,9 @@
 #include "td_internal.h"
 
 namespace td {
+
+constexpr int REF_BN = 128;        // operator rows per tile
+constexpr int REF_MIN_CHUNK = 64;  // k-blocks
 
 template <class T>
 static td_status ref_alloc(T** p, size_t count, const char* what) {
@@ -48,6 +53,37 @@ static void ref_free(T*& p) {
   p = nullptr;
 }
 
+static bool refine_whole_rows(const td_segment* s, int64_t K, int path) {
+  if (path == TD_PATH_TENSOR || path == TD_PATH_TENSOR128) return true;
+  if (path != TD_PATH_AUTO) return false;
+  const int64_t items128 = (s->nkp / 128) * ceil_div(K, TC_COLS);
+  return 4 * items128 >= 3 * (int64_t)tc_num_sms();   // the one-pass rule for 128-row whole rows
+}
+
+static td_status refine_whole_maps(td_segment* s, int64_t K, int nsl) {
+  RefineState& f = s->ref;
+  const Scratch& sc = s->scr;
+  if (f.whole_K == K && f.whole_nsl == nsl && f.whole_rs == sc.rs && f.whole_op == s->op) return TD_OK;
+  f.whole_K = -1;
+  for (int w = 0; w < 2; ++w) {
+    TcSegDev& d = f.whole[w];
+    memset(&d, 0, sizeof d);
+    td_status r = encode_seg_maps(s, K, w == 0 ? nsl : OP_SLICES, REF_BN, &d, TC_COLS, w == 0 ? s->op : f.lop);
+    if (r != TD_OK) return r;
+    d.partials = sc.partials;
+    d.nk = (int)s->nk;
+    d.K = (int)K;
+    d.ldp = (int)sc.capK;
+    d.nm = (int)(s->nkp / 64);
+    d.logdet = s->logdet;
+  }
+  f.whole_K = K;
+  f.whole_nsl = nsl;
+  f.whole_rs = sc.rs;
+  f.whole_op = s->op;
+  return TD_OK;
+}
+
 static void drop_plan(RefineState& f) {
   ref_free(f.items);
   ref_free(f.units);
@@ -56,6 +92,7 @@ static void drop_plan(RefineState& f) {
   f.K = -1;
   f.nsl = 0;
   f.rs = f.op = nullptr;
+  f.whole_K = -1;
 }
 
 void free_refine_state(td_segment* s) {
@@ -93,9 +130,6 @@ static td_status build_lop(td_segment* s, cudaStream_t st) {
   }
   return TD_OK;
 }
-
-constexpr int REF_BN = 128;      // operator rows per tile
-constexpr int REF_MIN_CHUNK = 64;   // k-blocks
 
 static td_status refine_plan(td_segment* s, int64_t K, int nsl, cudaStream_t st) {
   RefineState& f = s->ref;
@@ -151,7 +185,7 @@ static td_status refine_plan(td_segment* s, int64_t K, int nsl, cudaStream_t st)
 }
 
 td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl,
-                       int64_t wait_limit_ns, cudaStream_t st) {
+                       int path, int64_t wait_limit_ns, cudaStream_t st) {
   RefineState& f = s->ref;
   Scratch& sc = s->scr;
   td_status r;
@@ -166,10 +200,34 @@ td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, do
       return r;
     f.cap = sc.capK;
   }
+  const int64_t ld = s->nkp;
+  if (refine_whole_rows(s, K, path)) {
+    if ((r = refine_whole_maps(s, K, nsl)) != TD_OK) return r;
+    const int nc = (int)ceil_div(K, TC_COLS), nkb_max = (int)ceil_div(s->nk, OP_KB);
+    RefineIO io;
+    io.out = f.w32;
+    io.ldo = ld;
+    TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
+    TD_CUDA(launch_tc_single_ew(f.whole[0], 3, nc, nkb_max, nsl, io, s->status, wait_limit_ns, st));
+    io = RefineIO();
+    io.in = R;
+    io.ldi = ldr;
+    io.out = f.s32;
+    io.ldo = ld;
+    TD_CUDA(launch_r_slices(f.w32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, OP_SLICES, st));
+    TD_CUDA(launch_tc_single_ew(f.whole[1], 4, nc, nkb_max, OP_SLICES, io, s->status, wait_limit_ns, st));
+    io = RefineIO();
+    io.in = f.w32;
+    io.ldi = ld;
+    TD_CUDA(launch_r_slices(f.s32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
+    TD_CUDA(launch_tc_single_ew(f.whole[0], 5, nc, nkb_max, nsl, io, s->status, wait_limit_ns, st));
+    TD_CUDA(launch_finalize(sc.partials, sc.capK, (int)(s->nkp / 64), K, s->logdet, s->nk, logL, chi2, st));
+    s->prof_kernels += 7;
+    return TD_OK;
+  }
   if ((r = refine_plan(s, K, nsl, st)) != TD_OK) return r;
   const TcSegDev* seg_linv = f.seg_op;
   const TcSegDev* seg_l = f.seg_op + 1;
-  const int64_t ld = s->nkp;
   // w~ = L^{-1} r, rounded to FP32
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_linv, nsl, REF_BN, true, s->status, wait_limit_ns, st));

@@ -87,6 +87,7 @@ struct TcSingle {           // single-segment launch: item list is implicit
   int nm;                   // row tiles of BN rows
   int nc;                   // column tiles
   int nkb_max;              // k-blocks available (ceil(N'/32))
+  RefineIO io;              // element-wise modes 3..5: element (i, k) of in / out at [i + k ld]
 };
 
 template <int BN>
@@ -107,6 +108,9 @@ __device__ __forceinline__ TcItem single_item(const TcSingle& p, int idx) {
 // MODE 2: explicit item list whose items may cover part of a row's k-range
 //         (slot >= 0): the epilogue stores the accumulator pair and
 //         k_split_reduce finishes; items with slot < 0 cover whole rows
+// MODE 3..5: one segment, whole rows, the refinement step's element-wise
+//         epilogues (w = hi + corrections of each element):
+//         3 out = fl32(w);  4 out = fl32(in - w);  5 chi2 partials of in + w
 template <int NSL, int BN, int MODE>
 __global__ void __launch_bounds__(tc::THREADS, 1)
     k_tc_cdo(const __grid_constant__ TcSingle single, const TcItem* __restrict__ items, int n_items,
@@ -150,7 +154,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   }
   // residual rows the TMA box does not cover must read as zero in every stage
   // (a narrow box is only used when every item of the launch has it)
-  if ((MODE != 0 ? segs[0].a_rows : single.seg.a_rows) < BM) {
+  constexpr bool GROUPED = MODE == 1 || MODE == 2;
+  if ((GROUPED ? segs[0].a_rows : single.seg.a_rows) < BM) {
     for (int s = 0; s < STAGES; ++s) {
       uint4* a = reinterpret_cast<uint4*>(smem + s * STAGE);
       for (int i = threadIdx.x; i < A_STAGE / 16; i += blockDim.x) a[i] = make_uint4(0, 0, 0, 0);
@@ -162,7 +167,6 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
   const int G = gridDim.x, b = blockIdx.x;
-  constexpr bool GROUPED = MODE != 0;
   const int n_total = GROUPED ? n_items : single.nm * single.nc;
 
   if (warp == 0) {
@@ -333,6 +337,36 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(&tempty[buf]);
+      } else if (MODE == 3 || MODE == 4) {
+        // 32 consecutive rows of this thread's column per TMEM load
+        const RefineIO& io = single.io;
+#pragma unroll 1
+        for (int ch = 0; ch < BN / 32; ++ch) {
+          float v0[32], v1[32];
+          tmem_ld32(ta + (uint32_t)(ch * 32), v0);
+          tmem_ld32(ta + (uint32_t)(BN + ch * 32), v1);
+          if (col < sd->K) {
+            const int64_t row0 = (int64_t)it.m * BN + ch * 32;
+            float4* d4 = reinterpret_cast<float4*>(io.out + (int64_t)col * io.ldo + row0);
+            float o[32];
+            if (MODE == 3) {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) o[i] = v0[i] + v1[i];
+            } else {
+              const float* r = io.in + (int64_t)col * io.ldi;
+#pragma unroll
+              for (int i = 0; i < 32; ++i) {
+                const float x = row0 + i < sd->nk ? r[row0 + i] : 0.f;
+                o[i] = (x - v0[i]) - v1[i];   // x - v0 is exact while they are within a factor 2
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) d4[i] = make_float4(o[4 * i], o[4 * i + 1], o[4 * i + 2], o[4 * i + 3]);
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tempty[buf]);
       } else {
         double part[C::GROUPS];
 #pragma unroll
@@ -343,8 +377,22 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             float v0[32], v1[32];
             tmem_ld32(ta + (uint32_t)(ch * 32), v0);
             tmem_ld32(ta + (uint32_t)(BN + ch * 32), v1);
+            if (MODE == 5) {
+              // w = w~ + delta: two-sum of w~ and the exact hi*hi part, the corrections
+              // joining the tail; rows past N' and columns past K read w~ = 0
+              const int64_t row0 = (int64_t)it.m * BN + ch * 32;
+              const float* wt = single.io.in + (int64_t)(col < sd->K ? col : 0) * single.io.ldi;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) ff_add_square2(v0[i], v1[i], hi, lo);
+              for (int i = 0; i < 32; ++i) {
+                const float x = (col < sd->K && row0 + i < sd->nk) ? wt[row0 + i] : 0.f;
+                const float t = x + v0[i], bp = t - x;
+                const float et = (x - (t - bp)) + (v0[i] - bp);
+                ff_add_square2(t, et + v1[i], hi, lo);
+              }
+            } else {
+#pragma unroll
+              for (int i = 0; i < 32; ++i) ff_add_square2(v0[i], v1[i], hi, lo);
+            }
           }
           part[g] = (double)hi + (double)lo;
         }
@@ -392,7 +440,7 @@ static cudaError_t launch_impl(const TcSingle& single, const TcItem* items, int 
     if (e != cudaSuccess) return e;
     mark_device_done(attr_done);
   }
-  const int n_total = MODE != 0 ? n_items : single.nm * single.nc;
+  const int n_total = (MODE == 1 || MODE == 2) ? n_items : single.nm * single.nc;
   if (n_total <= 0) return cudaSuccess;
   int grid = tc_num_sms();
   if (grid > n_total) grid = n_total;
@@ -441,6 +489,27 @@ cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, i
   p.nc = nc;
   p.nkb_max = nkb_max;
   return dispatch<0>(nslices, bn, p, nullptr, 0, nullptr, status, wait_limit_ns, st, true);
+}
+
+// the refinement step's whole-row element-wise products (128-row tiles)
+cudaError_t launch_tc_single_ew(const TcSegDev& seg, int mode, int nc, int nkb_max, int nslices,
+                                const RefineIO& io, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+  TcSingle p;
+  memset(&p, 0, sizeof(p));
+  p.seg = seg;
+  p.nm = (int)(ceil_div((int64_t)seg.nk, OP_ROWS) * OP_ROWS / 128);
+  p.nc = nc;
+  p.nkb_max = nkb_max;
+  p.io = io;
+#define TD_EW_CASE(MODE_)                                                                                         \
+  if (mode == MODE_) {                                                                                            \
+    if (nslices == 2) return launch_impl<2, 128, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
+    if (nslices == 3) return launch_impl<3, 128, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
+    if (nslices == 4) return launch_impl<4, 128, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
+  }
+  TD_EW_CASE(3) TD_EW_CASE(4) TD_EW_CASE(5)
+#undef TD_EW_CASE
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,

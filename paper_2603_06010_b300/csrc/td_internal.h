@@ -164,6 +164,12 @@ struct RefineState {          // td_options.refine
   td::SplitUnit* units = nullptr;
   int n_units = 0;
   td::TcSegDev* seg_op = nullptr;   // [0]: L^{-1} slices (nsl), [1]: L slices (4)
+  // whole-row descriptors (host copies, passed by value to the kernel)
+  td::TcSegDev whole[2];
+  int64_t whole_K = -1;
+  int whole_nsl = 0;
+  const void* whole_rs = nullptr;
+  const void* whole_op = nullptr;
 };
 
 struct GsState {              // td_gs_prepare / TD_PATH_GSCE (gap-free segments)
@@ -279,6 +285,10 @@ cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* se
 cudaError_t launch_small_reduce(const TcSegDev* segs, const SmallFinal& fin, cudaStream_t st);
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st);
+// refinement products over whole 128-row tiles with an element-wise epilogue:
+// mode 3 out = fl32(w), 4 out = fl32(in - w), 5 chi2 partials of in + w
+cudaError_t launch_tc_single_ew(const TcSegDev& seg, int mode, int nc, int nkb_max, int nslices,
+                                const RefineIO& io, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
 int tc_num_sms();
 cudaError_t launch_tc_finalize(const TcSegDev* segs, int nseg, int64_t maxK, cudaStream_t st);
 
@@ -291,7 +301,7 @@ td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* o
                           const __nv_bfloat16* op = nullptr);
 // one refinement step (td_options.refine), launched on st
 td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl,
-                       int64_t wait_limit_ns, cudaStream_t st);
+                       int path, int64_t wait_limit_ns, cudaStream_t st);
 void free_refine_state(td_segment* s);
 // Gohberg-Semencul path (TD_PATH_GSCE)
 td_status gs_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2,

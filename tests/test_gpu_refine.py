@@ -140,3 +140,29 @@ def test_refine_unsupported_and_invalid(torch_cuda, gpu_lib):
     with pytest.raises(td.TdError) as e:
         seg.loglike(R, td.options(refine=1))
     assert e.value.code == td.TD_ERR_UNSUPPORTED
+
+
+def test_refined_whole_rows(torch_cuda, gpu_lib):
+    """Enough 128-row tiles that the refined products cover whole rows and do the
+    element-wise steps in their epilogues; both fixed shapes meet the bar, and
+    with a fixed shape a column alone gives the bits it gives in the batch."""
+    from paper_2603_06010_b300 import td
+    n, K = 2100, 900
+    mask = _mask(n, [(1000, 1100)])
+    acf = inputs.acf_from_psd(n, 2048.0)
+    o = oracle.OracleSegment(acf, mask)
+    R = inputs.noise_residuals(n, 2048.0, K, 57, mask=mask)
+    exp_chi = o.chi2(R)
+    seg = td.Segment(acf, mask)
+    _, chi1 = _run(torch_cuda, seg, R, td.options(precision=td.TD_PREC_BF16X3))
+    rel1 = np.max(np.abs(chi1 - exp_chi) / exp_chi)
+    for path in (td.TD_PATH_AUTO, td.TD_PATH_TENSOR128, td.TD_PATH_STREAM128):
+        ll, chi = _run(torch_cuda, seg, R, td.options(precision=td.TD_PREC_BF16X3, refine=1, path=path))
+        rel = np.max(np.abs(chi - exp_chi) / exp_chi)
+        assert rel <= REF_CHI2_REL and rel < rel1 / 100, (path, rel, rel1)
+        assert np.max(np.abs(ll - oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept))) <= REF_DLOGL
+    opt = td.options(precision=td.TD_PREC_BF16X3, refine=1, path=td.TD_PATH_TENSOR128)
+    full, _ = _run(torch_cuda, seg, R, opt)
+    for k in (0, 517, 899):
+        one, _ = _run(torch_cuda, seg, R[k:k + 1], opt)
+        assert one[0] == full[k], k

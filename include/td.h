@@ -97,7 +97,11 @@ typedef enum {
                            column pair; `precision` is not used.  A column is
                            transformed together with its neighbour (columns 2j, 2j+1
                            share one complex FFT), so results agree across batches
-                           within rounding, not bitwise. */
+                           within rounding, not bitwise.  TD_PATH_AUTO takes this path
+                           too on a prepared segment where it measured faster than the
+                           dense product (K <= 256, or N >= 24576), or when the
+                           segment has no dense operator (prepared only), except with
+                           refinement or TD_PREC_FP64. */
 } td_path;
 
 typedef struct {

@@ -187,8 +187,37 @@ def test_gsce_same_as_dense_paths(torch_cuda, gpu_lib):
     R = inputs.noise_residuals(n, 2048.0, 70, 5)
     Rd = torch_cuda.from_numpy(R).cuda()
     a = seg.loglike(Rd, td.options(path=td.TD_PATH_GSCE)).cpu().numpy()
-    b = seg.loglike(Rd, td.options(precision=td.TD_PREC_BF16X10)).cpu().numpy()
+    b = seg.loglike(Rd, td.options(precision=td.TD_PREC_BF16X10, path=td.TD_PATH_TENSOR128)).cpu().numpy()
     assert np.max(np.abs(a - b)) <= 1e-3
+
+
+def test_gsce_auto_policy(torch_cuda, gpu_lib):
+    """TD_PATH_AUTO on a prepared gap-free segment: GSCE for small batches, the
+    dense product for large ones below N = 24576, GSCE when only prepared."""
+    from paper_2603_06010_b300 import td
+    n = 3000
+    acf = inputs.acf_from_psd(n, 2048.0)
+    both = td.Segment(acf)
+    both.gs_prepare()
+    dense = td.Segment(acf)
+    only = td.Segment(acf, factor=False)
+    only.gs_prepare()
+    R = torch_cuda.from_numpy(inputs.noise_residuals(n, 2048.0, 300, 6)).cuda()
+
+    def ll(seg, Rs, opt):
+        out = seg.loglike(Rs.contiguous(), opt).cpu().numpy()
+        seg.check()
+        return out
+
+    gs = td.options(path=td.TD_PATH_GSCE)
+    small = R[:8]
+    assert np.array_equal(ll(both, small, td.options()), ll(both, small, gs))
+    assert np.array_equal(ll(only, small, td.options()), ll(only, small, gs))
+    assert np.array_equal(ll(both, R, td.options()), ll(dense, R, td.options()))   # K = 300 > 256
+    assert np.array_equal(ll(only, R, td.options()), ll(only, R, gs))
+    # refinement is not a GSCE option: AUTO keeps the dense path for it
+    ref = td.options(precision=td.TD_PREC_BF16X3, refine=1)
+    assert np.array_equal(ll(both, small, ref), ll(dense, small, ref))
 
 
 def test_gsce_errors(torch_cuda, gpu_lib):

@@ -391,7 +391,9 @@ def serving_extra(td, torch, seconds):
     rng = np.random.default_rng(5050)
     # 8 segments each of N = 4096, 8192, 16384 with 0..3 gaps of 512; 4 gap-free N = 32768
     fleet = [(n, i % 4) for n in (4096, 8192, 16384) for i in range(8)] + [(32768, 0)] * 4
-    srv = td.Server(max_batch_cols=2048, n_streams=4, max_kept=32768, max_pending_cols=1 << 22)
+    # gap-free segments also get the Gohberg-Semencul form: batches of K <= 256 (any K at N = 32768)
+    # run on it without the dense operator
+    srv = td.Server(max_batch_cols=2048, n_streams=4, max_kept=32768, max_pending_cols=1 << 22, gs_gapfree=True)
     ids, pools, info, models = [], [], [], []
     t0 = time.perf_counter()
     for n, g in fleet:
@@ -475,7 +477,8 @@ def serving_extra(td, torch, seconds):
     out = {"note": f"{len(fleet)} resident segments: 8 each of N = 4096, 8192, 16384 with 0-3 gaps of 512, "
                    "4 gap-free N = 32768 (a gapped N = 32768 factor takes ~22 s of B300 FP64); Poisson 2000 req/s "
                    "open loop (native replay), K in {1, 8, 64, 512}; phases: whole fleet, gapped N=8192 only, "
-                   "gapped N=16384 only",
+                   "gapped N=16384 only; gap-free segments also hold the Gohberg-Semencul form (server gs_gapfree), "
+                   "so their batches of K <= 256 (any K at N = 32768) run through GSCE",
            "fleet": mix, "gapped_n8192": g8, "gapped_n16384": g16,
            "max_abs_dlogL_vs_oracle_sampled": dlogl,
            "dlogL_sample": "served requests on the gapped N=4096 segments (up to 12 per phase), CPU FP64 oracle",

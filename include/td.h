@@ -424,6 +424,12 @@ typedef struct {
   int n_streams;                 /* concurrent batches, 1..16 */
   int precision;                 /* td_precision of the tensor-core path */
   int64_t max_kept;              /* largest N' a segment may have (sizes batch buffers) */
+  int gs_gapfree;                /* nonzero: gap-free segments with 1024 <= N <= 32768 also get
+                                    the Gohberg-Semencul form (td_gs_prepare) on first use;
+                                    batches that TD_PATH_AUTO sends to GSCE (K <= 256, or
+                                    N >= 24576) then run without loading the dense operator
+                                    (O(N) device memory for such segments).  Default 0. */
+  int reserved0;
 } td_server_config;
 typedef struct {
   double p50_us, p99_us, max_us, evals_per_s;

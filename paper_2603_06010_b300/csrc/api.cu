@@ -185,10 +185,12 @@ static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaSt
 // 39 vs 68 us at K = 64, 175 vs ~155 us at K = 512; N = 32768: 0.09 vs 0.57 ms
 // at K = 1, 1.15 vs 1.64 ms at K = 512), and whenever the dense operator is
 // absent; not with refinement or FP64, which it does not provide.
+bool gs_preferred(const td_segment* s, int64_t K) { return K <= 256 || s->nk >= 24576; }
+
 static bool gs_auto(const td_segment* s, int64_t K, const td_options& o) {
   if (o.path != TD_PATH_AUTO || !s->gs.ready || o.refine || o.precision == TD_PREC_FP64) return false;
   if (!s->factored || !s->op) return true;
-  return K <= 256 || s->nk >= 24576;
+  return gs_preferred(s, K);
 }
 
 static int64_t plan_width(int64_t K) {

@@ -435,6 +435,10 @@ static void gs_free(T*& p) {
   p = nullptr;
 }
 
+bool gs_supported(const td_segment* s) {
+  return s->nk == s->n && s->n >= GS_MIN_N && s->n <= ((int64_t)1 << (GS_MAX_LOGM - 1));
+}
+
 void free_gs_state(td_segment* s) {
   GsState& g = s->gs;
   gs_free(g.S1);

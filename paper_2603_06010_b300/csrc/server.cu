@@ -127,9 +127,20 @@ static void seg_evict(td_server* srv, SegEntry& e) {
 
 // make the segment's operator resident (evicting least recently used idle
 // segments while over budget); called with the lock held
-static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st) {
+// cols > 0: the width of the batch about to run; a batch that TD_PATH_AUTO
+// sends to GSCE needs only the segment's Gohberg-Semencul data (made here on
+// first use when the server is configured for it), not the dense operator
+static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st, int64_t cols = 0) {
   SegEntry& e = srv->segs[(size_t)id];
   e.last_use = ++srv->clock;
+  if (srv->cfg.gs_gapfree && !e.s->gs.ready && gs_supported(e.s)) {
+    const td_status rg = td_gs_prepare(e.s, st);
+    if (rg != TD_OK) return rg;
+  }
+  if (cols > 0 && e.s->gs.ready && srv->cfg.precision != TD_PREC_FP64 && gs_preferred(e.s, cols)) {
+    srv->hits++;   // the batch runs on the (resident) GS data whether or not the operator is
+    return TD_OK;
+  }
   if (e.resident) {
     srv->hits++;
     return TD_OK;
@@ -225,7 +236,7 @@ static void scheduler_loop(td_server* srv) {
       cols += r.K;
     }
     if (sl.tickets.empty()) continue;
-    td_status st = seg_make_resident(srv, pick, sl.st);
+    td_status st = seg_make_resident(srv, pick, sl.st, cols);
     const int64_t nk = e.s->nk;
     if (st == TD_OK && sl.tickets.size() == 1) {
       // one request: evaluate it in place (its R and logL are device buffers)

@@ -307,5 +307,7 @@ void free_refine_state(td_segment* s);
 td_status gs_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2,
                    cudaStream_t st);
 void free_gs_state(td_segment* s);
+bool gs_supported(const td_segment* s);             // gap-free, 1024 <= N <= 32768
+bool gs_preferred(const td_segment* s, int64_t K);  // TD_PATH_AUTO's choice when both forms are there
 
 }  // namespace td

@@ -81,7 +81,7 @@ SIGNATURES = {
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_batch_cols", ctypes.c_int64), ("max_pending_cols", ctypes.c_int64),
                 ("resident_bytes_budget", ctypes.c_int64), ("n_streams", ctypes.c_int), ("precision", ctypes.c_int),
-                ("max_kept", ctypes.c_int64)]
+                ("max_kept", ctypes.c_int64), ("gs_gapfree", ctypes.c_int), ("reserved0", ctypes.c_int)]
 
 
 class ServerStats(ctypes.Structure):
@@ -356,12 +356,13 @@ class Server:
     PENDING, RUNNING, DONE, CANCELLED, FAILED = range(5)
 
     def __init__(self, max_batch_cols=4096, max_pending_cols=1 << 20, resident_bytes_budget=0, n_streams=4,
-                 precision=TD_PREC_BF16X6, max_kept=32768):
+                 precision=TD_PREC_BF16X6, max_kept=32768, gs_gapfree=False):
         c = ServerConfig()
         lib().td_server_config_default(ctypes.byref(c))
         c.max_batch_cols, c.max_pending_cols = max_batch_cols, max_pending_cols
         c.resident_bytes_budget, c.n_streams, c.precision, c.max_kept = (resident_bytes_budget, n_streams,
                                                                          precision, max_kept)
+        c.gs_gapfree = 1 if gs_gapfree else 0
         h = ctypes.c_void_p()
         _check(lib().td_server_create(ctypes.byref(c), ctypes.byref(h)))
         self.handle = h

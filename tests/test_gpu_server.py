@@ -192,3 +192,24 @@ def test_concurrent_submitters(torch_cuda, gpu_lib):
     for _, R, out, exp in work:
         assert np.max(np.abs(out.cpu().numpy() - exp)) <= DLOGL_ABS
     srv.close()
+
+
+def test_gapfree_segment_served_through_gsce(torch_cuda, gpu_lib):
+    """gs_gapfree: batches that TD_PATH_AUTO sends to GSCE run on the segment's
+    Gohberg-Semencul data without loading its dense operator; results match
+    the oracle."""
+    from paper_2603_06010_b300 import td
+    n = 3000
+    acf = inputs.acf_from_psd(n, 2048.0)
+    o = oracle.OracleSegment(acf)
+    srv = td.Server(max_batch_cols=256, n_streams=2, max_kept=4096, gs_gapfree=True)
+    sid = srv.add_segment(acf)
+    reqs = []
+    for q in range(12):
+        R, out, exp = _request(torch_cuda, o, [1, 8, 64][q % 3], 900 + q)
+        reqs.append((srv.submit(sid, R, out), out, exp))
+    srv.drain()
+    for t, out, exp in reqs:
+        assert srv.poll(t) == td.Server.DONE
+        assert np.max(np.abs(out.cpu().numpy() - exp)) <= DLOGL_ABS
+    assert srv.stats()["resident_bytes"] == 0

@@ -12,12 +12,12 @@
 // |L| |w~|) is what the corrected w keeps: the result lands near the
 // ten-product accuracy whatever the first pass's precision was.
 //
-// All three products run on 128-row operator tiles.  With enough tiles to
-// fill the GPU they cover whole rows and do the element-wise part in their
-// epilogue (write w~, form s from r, add w~ and square).  Otherwise they run
-// split-k with every row tile leaving its accumulator pairs (chunks of at
-// least 64 k-blocks, a length fixed by N' alone) and the chunk reduction's
-// modes do it.  A fixed path (TD_PATH_TENSOR*/STREAM*) fixes the shape, so a
+// With enough tiles to fill the GPU the three products cover whole rows
+// (256- or 128-row tiles, by the one-pass rules) and do the element-wise part
+// in their epilogue (write w~, form s from r, add w~ and square).  Otherwise
+// they run split-k on 128-row tiles with every row tile leaving its
+// accumulator pairs (chunks of at least 64 k-blocks, a length fixed by N'
+// alone) and the chunk reduction's modes do it.  A fixed path (TD_PATH_TENSOR*/STREAM*) fixes the shape, so a
 // column's result then does not depend on its batch.
 //
 // Needs the FP64 factor L to slice (once per factor); segments whose L was
@@ -53,22 +53,30 @@ static void ref_free(T*& p) {
   p = nullptr;
 }
 
-static bool refine_whole_rows(const td_segment* s, int64_t K, int path) {
-  if (path == TD_PATH_TENSOR || path == TD_PATH_TENSOR128) return true;
-  if (path != TD_PATH_AUTO) return false;
-  const int64_t items128 = (s->nkp / 128) * ceil_div(K, TC_COLS);
-  return 4 * items128 >= 3 * (int64_t)tc_num_sms();   // the one-pass rule for 128-row whole rows
+// Whole-row tile rows for the refined products, 0 for the split form: the
+// one-pass rules (256-row tiles from two waves of them, 128-row tiles from
+// three quarters of a wave with two TMEM accumulator pairs); a fixed path
+// fixes the shape.
+static int refine_whole_rows(const td_segment* s, int64_t K, int path) {
+  if (path == TD_PATH_TENSOR) return 256;
+  if (path == TD_PATH_TENSOR128) return 128;
+  if (path != TD_PATH_AUTO) return 0;
+  const int64_t nc = ceil_div(K, TC_COLS), sms = tc_num_sms();
+  if (2 * (s->nkp / 256) * nc >= 3 * sms) return 256;
+  if (4 * (s->nkp / 128) * nc >= 3 * sms) return 128;
+  return 0;
 }
 
-static td_status refine_whole_maps(td_segment* s, int64_t K, int nsl) {
+static td_status refine_whole_maps(td_segment* s, int64_t K, int nsl, int bn) {
   RefineState& f = s->ref;
   const Scratch& sc = s->scr;
-  if (f.whole_K == K && f.whole_nsl == nsl && f.whole_rs == sc.rs && f.whole_op == s->op) return TD_OK;
+  if (f.whole_K == K && f.whole_nsl == nsl && f.whole_bn == bn && f.whole_rs == sc.rs && f.whole_op == s->op)
+    return TD_OK;
   f.whole_K = -1;
   for (int w = 0; w < 2; ++w) {
     TcSegDev& d = f.whole[w];
     memset(&d, 0, sizeof d);
-    td_status r = encode_seg_maps(s, K, w == 0 ? nsl : OP_SLICES, REF_BN, &d, TC_COLS, w == 0 ? s->op : f.lop);
+    td_status r = encode_seg_maps(s, K, w == 0 ? nsl : OP_SLICES, bn, &d, TC_COLS, w == 0 ? s->op : f.lop);
     if (r != TD_OK) return r;
     d.partials = sc.partials;
     d.nk = (int)s->nk;
@@ -79,6 +87,7 @@ static td_status refine_whole_maps(td_segment* s, int64_t K, int nsl) {
   }
   f.whole_K = K;
   f.whole_nsl = nsl;
+  f.whole_bn = bn;
   f.whole_rs = sc.rs;
   f.whole_op = s->op;
   return TD_OK;
@@ -201,26 +210,26 @@ td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, do
     f.cap = sc.capK;
   }
   const int64_t ld = s->nkp;
-  if (refine_whole_rows(s, K, path)) {
-    if ((r = refine_whole_maps(s, K, nsl)) != TD_OK) return r;
+  if (const int bn = refine_whole_rows(s, K, path)) {
+    if ((r = refine_whole_maps(s, K, nsl, bn)) != TD_OK) return r;
     const int nc = (int)ceil_div(K, TC_COLS), nkb_max = (int)ceil_div(s->nk, OP_KB);
     RefineIO io;
     io.out = f.w32;
     io.ldo = ld;
     TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
-    TD_CUDA(launch_tc_single_ew(f.whole[0], 3, nc, nkb_max, nsl, io, s->status, wait_limit_ns, st));
+    TD_CUDA(launch_tc_single_ew(f.whole[0], bn, 3, nc, nkb_max, nsl, io, s->status, wait_limit_ns, st));
     io = RefineIO();
     io.in = R;
     io.ldi = ldr;
     io.out = f.s32;
     io.ldo = ld;
     TD_CUDA(launch_r_slices(f.w32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, OP_SLICES, st));
-    TD_CUDA(launch_tc_single_ew(f.whole[1], 4, nc, nkb_max, OP_SLICES, io, s->status, wait_limit_ns, st));
+    TD_CUDA(launch_tc_single_ew(f.whole[1], bn, 4, nc, nkb_max, OP_SLICES, io, s->status, wait_limit_ns, st));
     io = RefineIO();
     io.in = f.w32;
     io.ldi = ld;
     TD_CUDA(launch_r_slices(f.s32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
-    TD_CUDA(launch_tc_single_ew(f.whole[0], 5, nc, nkb_max, nsl, io, s->status, wait_limit_ns, st));
+    TD_CUDA(launch_tc_single_ew(f.whole[0], bn, 5, nc, nkb_max, nsl, io, s->status, wait_limit_ns, st));
     TD_CUDA(launch_finalize(sc.partials, sc.capK, (int)(s->nkp / 64), K, s->logdet, s->nk, logL, chi2, st));
     s->prof_kernels += 7;
     return TD_OK;

@@ -491,23 +491,24 @@ cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, i
   return dispatch<0>(nslices, bn, p, nullptr, 0, nullptr, status, wait_limit_ns, st, true);
 }
 
-// the refinement step's whole-row element-wise products (128-row tiles)
-cudaError_t launch_tc_single_ew(const TcSegDev& seg, int mode, int nc, int nkb_max, int nslices,
+// the refinement step's whole-row element-wise products (256- or 128-row tiles)
+cudaError_t launch_tc_single_ew(const TcSegDev& seg, int bn, int mode, int nc, int nkb_max, int nslices,
                                 const RefineIO& io, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
   TcSingle p;
   memset(&p, 0, sizeof(p));
   p.seg = seg;
-  p.nm = (int)(ceil_div((int64_t)seg.nk, OP_ROWS) * OP_ROWS / 128);
+  p.nm = (int)(ceil_div((int64_t)seg.nk, OP_ROWS) * OP_ROWS / bn);
   p.nc = nc;
   p.nkb_max = nkb_max;
   p.io = io;
-#define TD_EW_CASE(MODE_)                                                                                         \
-  if (mode == MODE_) {                                                                                            \
-    if (nslices == 2) return launch_impl<2, 128, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
-    if (nslices == 3) return launch_impl<3, 128, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
-    if (nslices == 4) return launch_impl<4, 128, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
+#define TD_EW_CASE(BN_, MODE_)                                                                                    \
+  if (bn == BN_ && mode == MODE_) {                                                                               \
+    if (nslices == 2) return launch_impl<2, BN_, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
+    if (nslices == 3) return launch_impl<3, BN_, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
+    if (nslices == 4) return launch_impl<4, BN_, MODE_>(p, nullptr, 0, nullptr, status, wait_limit_ns, st, true); \
   }
-  TD_EW_CASE(3) TD_EW_CASE(4) TD_EW_CASE(5)
+  TD_EW_CASE(128, 3) TD_EW_CASE(128, 4) TD_EW_CASE(128, 5)
+  TD_EW_CASE(256, 3) TD_EW_CASE(256, 4) TD_EW_CASE(256, 5)
 #undef TD_EW_CASE
   return cudaErrorInvalidValue;
 }

@@ -168,6 +168,7 @@ struct RefineState {          // td_options.refine
   td::TcSegDev whole[2];
   int64_t whole_K = -1;
   int whole_nsl = 0;
+  int whole_bn = 0;
   const void* whole_rs = nullptr;
   const void* whole_op = nullptr;
 };
@@ -285,9 +286,9 @@ cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* se
 cudaError_t launch_small_reduce(const TcSegDev* segs, const SmallFinal& fin, cudaStream_t st);
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st);
-// refinement products over whole 128-row tiles with an element-wise epilogue:
-// mode 3 out = fl32(w), 4 out = fl32(in - w), 5 chi2 partials of in + w
-cudaError_t launch_tc_single_ew(const TcSegDev& seg, int mode, int nc, int nkb_max, int nslices,
+// refinement products over whole bn-row tiles (256 or 128) with an element-wise
+// epilogue: mode 3 out = fl32(w), 4 out = fl32(in - w), 5 chi2 partials of in + w
+cudaError_t launch_tc_single_ew(const TcSegDev& seg, int bn, int mode, int nc, int nkb_max, int nslices,
                                 const RefineIO& io, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
 int tc_num_sms();
 cudaError_t launch_tc_finalize(const TcSegDev* segs, int nseg, int64_t maxK, cudaStream_t st);

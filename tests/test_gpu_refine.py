@@ -156,7 +156,7 @@ def test_refined_whole_rows(torch_cuda, gpu_lib):
     seg = td.Segment(acf, mask)
     _, chi1 = _run(torch_cuda, seg, R, td.options(precision=td.TD_PREC_BF16X3))
     rel1 = np.max(np.abs(chi1 - exp_chi) / exp_chi)
-    for path in (td.TD_PATH_AUTO, td.TD_PATH_TENSOR128, td.TD_PATH_STREAM128):
+    for path in (td.TD_PATH_AUTO, td.TD_PATH_TENSOR, td.TD_PATH_TENSOR128, td.TD_PATH_STREAM128):
         ll, chi = _run(torch_cuda, seg, R, td.options(precision=td.TD_PREC_BF16X3, refine=1, path=path))
         rel = np.max(np.abs(chi - exp_chi) / exp_chi)
         assert rel <= REF_CHI2_REL and rel < rel1 / 100, (path, rel, rel1)

@@ -147,6 +147,27 @@ def test_gsce_long_ar1(torch_cuda, gpu_lib, n):
     assert np.max(np.abs(chi - exp_chi) / exp_chi) <= GS_CHI2_REL
 
 
+def test_gsce_ill_conditioned_ar1(torch_cuda, gpu_lib):
+    """AR(1) with phi = 0.99 (condition number ~4e4), residuals drawn from the
+    process itself: still within the bar (CPU emulation of the FP32 network:
+    5.8e-8 at this phi, 8.6e-8 at phi = 0.999)."""
+    from scipy.signal import lfilter
+    from paper_2603_06010_b300 import td
+    n, phi, s2 = 8192, 0.99, 1.0
+    acf = s2 * phi ** np.arange(n) / (1 - phi * phi)
+    rng = np.random.default_rng(99)
+    z = rng.standard_normal((6, n))
+    z[:, 0] /= np.sqrt(1 - phi * phi)
+    R = lfilter([1.0], [1.0, -phi], z, axis=1).astype(np.float32)
+    R64 = R.astype(np.float64)
+    w = np.empty_like(R64)
+    w[:, 0] = R64[:, 0] * np.sqrt(1 - phi * phi)
+    w[:, 1:] = R64[:, 1:] - phi * R64[:, :-1]
+    exp_chi = np.sum(w * w, 1) / s2
+    _, chi = _run(torch_cuda, td, _gs(td, acf), R)
+    assert np.max(np.abs(chi - exp_chi) / exp_chi) <= GS_CHI2_REL
+
+
 def test_gsce_mix64_longest(torch_cuda, gpu_lib):
     """The longest gap-free segment of the 64-segment mix (N=32257) against
     stored oracle values."""

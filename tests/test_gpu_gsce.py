@@ -272,3 +272,32 @@ def test_gsce_errors(torch_cuda, gpu_lib):
         nd.gs_prepare()
     assert e.value.code == td.TD_ERR_NOT_PD
     assert nd.last_pivot == 1
+
+
+def test_gsce_and_refine_strided_and_host_buffers(torch_cuda, gpu_lib):
+    """ldr > N' (residuals inside a wider buffer) and the host-buffer entry point
+    (600 columns: two chunks) for GSCE and for the refinement step: the same
+    values as a packed device batch, within the bar of the oracle."""
+    from paper_2603_06010_b300 import td
+    n, K, pad = 2500, 600, 37
+    acf = inputs.acf_from_psd(n, 2048.0)
+    o = oracle.OracleSegment(acf)
+    R = inputs.noise_residuals(n, 2048.0, K, 31337)
+    exp = oracle.loglike_from_chi2(o.chi2(R), o.logdet, o.n_kept)
+    wide = np.zeros((K, n + pad), np.float32)
+    wide[:, :n] = R
+    seg = td.Segment(acf)
+    seg.gs_prepare()
+    for opt in (td.options(path=td.TD_PATH_GSCE), td.options(precision=td.TD_PREC_BF16X3, refine=1)):
+        packed = seg.loglike(torch_cuda.from_numpy(R).cuda(), opt).cpu().numpy()
+        Wd = torch_cuda.from_numpy(wide).cuda()
+        out = torch_cuda.empty(K, dtype=torch_cuda.float64, device="cuda")
+        seg.loglike_into(Wd, out, opt, ldr=n + pad)
+        torch_cuda.cuda.synchronize()
+        seg.check()
+        strided = out.cpu().numpy()
+        host = np.empty(K)
+        seg.loglike_host_into(torch_cuda.from_numpy(wide).pin_memory(), host, opt)
+        assert np.max(np.abs(packed - exp)) <= GS_DLOGL
+        assert np.max(np.abs(strided - packed)) <= 1e-6 * np.max(np.abs(packed))
+        assert np.max(np.abs(host - packed)) <= 1e-6 * np.max(np.abs(packed))

@@ -61,17 +61,22 @@ typedef enum {
 
 typedef enum {
   TD_PREC_FP64 = 0,    /* plain FP64 blocked forward substitution (CUDA cores) */
-  TD_PREC_BF16X6 = 1,  /* default: L^{-1} and R as 3 bf16 slices each -- a fixed-point hi
+  TD_PREC_BF16X6 = 1,  /* L^{-1} and R as 3 bf16 slices each -- a fixed-point hi
                           slice (|.| <= 255 times a per-row / per-column power-of-two
                           quantum) and 2 floating remainder slices; 6 tensor-core
                           products; the hi*hi sum accumulates exactly in one FP32
                           accumulator, the 5 others in a second; combined in
-                          double-float.  chi2 ~2e-8 relative to FP64. */
+                          double-float.  chi2 ~2e-8 relative to FP64 when many rows
+                          share the sum; up to ~1.2e-7 for a column of a few rows
+                          whose chi2 rests on one row (N' below a few hundred). */
   TD_PREC_BF16X3 = 2,  /* hi + 1 remainder slice, 3 products: ~1e-5 relative, below
                           the accuracy bar (kept to show why more products are needed) */
-  TD_PREC_AUTO = 3,    /* TD_PREC_BF16X6 up to N' = 32768, TD_PREC_BF16X10 beyond (the
-                          6-product |dlogL| grows as ~N' x 1e-8: 3.4e-4 measured at
-                          N' = 32257) */
+  TD_PREC_AUTO = 3,    /* default: TD_PREC_BF16X6 for 512 <= N' <= 32768, TD_PREC_BF16X10 beyond
+                          (the 6-product |dlogL| grows as ~N' x 1e-8: 3.4e-4 measured
+                          at N' = 32257) and below (with few rows one column's chi2 can
+                          rest on one row, good to ~6e-8 with six products: 1.15e-7
+                          measured at N' = 47).  Grouped launches take one count for
+                          all segments: ten once any exceeds 32768 or all are below 512. */
   TD_PREC_BF16X10 = 4  /* 4 slices each, the 10 products a+b <= 3: chi2 ~1e-9 relative */
 } td_precision;
 
@@ -105,7 +110,7 @@ typedef enum {
 } td_path;
 
 typedef struct {
-  int precision;        /* td_precision; default TD_PREC_BF16X6 */
+  int precision;        /* td_precision; default TD_PREC_AUTO */
   int path;             /* td_path; default TD_PATH_AUTO */
   int refine;           /* nonzero: one refinement step (Sec. III.C precision scheme).
                            w~ = L^{-1} r at `precision`; s = r - L w~ from bf16 slices of
@@ -126,7 +131,7 @@ typedef struct {
   int64_t wait_limit_ns;/* bound on any in-kernel wait; <= 0 -> 1 s */
 } td_options;
 
-/* Fill *opt with the defaults (BF16X6, auto path, no refinement, 1 s waits). */
+/* Fill *opt with the defaults (TD_PREC_AUTO, auto path, no refinement, 1 s waits). */
 void td_options_default(td_options* opt);
 
 /*
@@ -422,7 +427,7 @@ typedef struct {
   int64_t max_pending_cols;      /* admission capacity: queued + running columns */
   int64_t resident_bytes_budget; /* HBM budget for resident operators; 0 = unlimited */
   int n_streams;                 /* concurrent batches, 1..16 */
-  int precision;                 /* td_precision of the tensor-core path */
+  int precision;                 /* td_precision of the tensor-core path; default TD_PREC_AUTO */
   int64_t max_kept;              /* largest N' a segment may have (sizes batch buffers) */
   int gs_gapfree;                /* nonzero: gap-free segments with 1024 <= N <= 32768 also get
                                     the Gohberg-Semencul form (td_gs_prepare) on first use;

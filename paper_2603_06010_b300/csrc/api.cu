@@ -136,9 +136,12 @@ static td_status check_device(const td_segment* s) {
 
 // TD_PREC_AUTO: six products while the expected |dlogL| (about N' x 1e-8 from
 // chi2 ~ N' at ~2e-8 relative, measured) stays under a third of the 1e-3 bar,
-// ten products beyond N' = 32768
+// ten products beyond N' = 32768.  Ten products also below N' = 512: with few
+// rows one column's chi2 can rest on a single row, whose six-product value is
+// good to ~6e-8 relative, so chi2 can miss 1e-7 (1.15e-7 measured at N' = 47);
+// many rows average that away.  Small segments cost little either way.
 static int nslices_for(int precision, int64_t nk) {
-  if (precision == TD_PREC_AUTO) return nk > 32768 ? 4 : 3;
+  if (precision == TD_PREC_AUTO) return (nk > 32768 || nk < 512) ? 4 : 3;
   return precision == TD_PREC_BF16X3 ? 2 : (precision == TD_PREC_BF16X10 ? 4 : 3);
 }
 
@@ -332,7 +335,7 @@ extern "C" {
 void td_options_default(td_options* opt) {
   if (!opt) return;
   memset(opt, 0, sizeof *opt);
-  opt->precision = TD_PREC_BF16X6;
+  opt->precision = TD_PREC_AUTO;
   opt->path = TD_PATH_AUTO;
   opt->refine = 0;
   opt->wait_limit_ns = 1000000000LL;

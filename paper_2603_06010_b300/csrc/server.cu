@@ -360,7 +360,7 @@ void td_server_config_default(td_server_config* c) {
   c->max_pending_cols = 1 << 20;
   c->resident_bytes_budget = 0;
   c->n_streams = 4;
-  c->precision = TD_PREC_BF16X6;
+  c->precision = TD_PREC_AUTO;
   c->max_kept = 32768;
 }
 

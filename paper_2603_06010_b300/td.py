@@ -131,7 +131,7 @@ def _check(code: int):
         raise TdError(code, lib().td_last_error().decode())
 
 
-def options(precision: int = TD_PREC_BF16X6, path: int = TD_PATH_AUTO, refine: int = 0,
+def options(precision: int = TD_PREC_AUTO, path: int = TD_PATH_AUTO, refine: int = 0,
             wait_limit_ns: int = 1_000_000_000) -> TdOptions:
     o = TdOptions()
     lib().td_options_default(ctypes.byref(o))
@@ -356,7 +356,7 @@ class Server:
     PENDING, RUNNING, DONE, CANCELLED, FAILED = range(5)
 
     def __init__(self, max_batch_cols=4096, max_pending_cols=1 << 20, resident_bytes_budget=0, n_streams=4,
-                 precision=TD_PREC_BF16X6, max_kept=32768, gs_gapfree=False):
+                 precision=TD_PREC_AUTO, max_kept=32768, gs_gapfree=False):
         c = ServerConfig()
         lib().td_server_config_default(ctypes.byref(c))
         c.max_batch_cols, c.max_pending_cols = max_batch_cols, max_pending_cols

@@ -247,10 +247,11 @@ def test_grouped_launch_over_levinson_segments(torch_cuda, gpu_lib):
 
 
 def test_auto_precision_switches_above_32768(torch_cuda, gpu_lib):
-    """TD_PREC_AUTO: six products up to N' = 32768, ten beyond (same bits as the
-    explicit choice)."""
+    """TD_PREC_AUTO (the default): six products for 512 <= N' <= 32768, ten
+    beyond and below (same bits as the explicit choice)."""
     from paper_2603_06010_b300 import td
-    for n, expect in ((2000, td.TD_PREC_BF16X6), (33000, td.TD_PREC_BF16X10)):
+    assert td.options().precision == td.TD_PREC_AUTO
+    for n, expect in ((300, td.TD_PREC_BF16X10), (2000, td.TD_PREC_BF16X6), (33000, td.TD_PREC_BF16X10)):
         acf = inputs.acf_from_psd(n, 4096.0)
         seg = td.Segment(acf, factor=False)
         td.factor_many([seg])

@@ -47,7 +47,7 @@ static td_status get_encode(PFN_cuTensorMapEncodeTiled_v12000* out) {
 
 static td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2,
                            uint64_t s1_bytes, uint64_t s2_bytes, uint32_t b0, uint32_t b1, uint32_t b2) {
-  PFN_cuTensorMapEncodeTiled_v12000 enc;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   td_status st = get_encode(&enc);
   if (st != TD_OK) return st;
   cuuint64_t dims[3] = {d0, d1, d2};

@@ -266,10 +266,9 @@ static std::string group_signature(const td_group* g) {
     const double n = (double)g->segs[(size_t)i]->nk;
     work += n * n * (double)g->host_seg[(size_t)i].K;
   }
-  char buf[256];
-  snprintf(buf, sizeof buf, "%s|nsl%d|w%d|s%d", prop.name, g->nsl, (int)std::log2(std::max(1.0, work)),
-           (int)std::log2((double)std::max(1, g->nseg)));
-  return buf;
+  return std::string(prop.name) + "|nsl" + std::to_string(g->nsl) + "|w" +
+         std::to_string((int)std::log2(std::max(1.0, work))) + "|s" +
+         std::to_string((int)std::log2((double)std::max(1, g->nseg)));
 }
 
 }  // namespace td

@@ -482,8 +482,7 @@ static cudaError_t dispatch(int nslices, int bn, const TcSingle& p, const TcItem
 // 64-row group, seg.ldp apart
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st) {
-  TcSingle p;
-  memset(&p, 0, sizeof(p));
+  TcSingle p{};
   p.seg = seg;
   p.nm = (int)(ceil_div((int64_t)seg.nk, OP_ROWS) * OP_ROWS / bn);
   p.nc = nc;
@@ -494,8 +493,7 @@ cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, i
 // the refinement step's whole-row element-wise products (256- or 128-row tiles)
 cudaError_t launch_tc_single_ew(const TcSegDev& seg, int bn, int mode, int nc, int nkb_max, int nslices,
                                 const RefineIO& io, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
-  TcSingle p;
-  memset(&p, 0, sizeof(p));
+  TcSingle p{};
   p.seg = seg;
   p.nm = (int)(ceil_div((int64_t)seg.nk, OP_ROWS) * OP_ROWS / bn);
   p.nc = nc;
@@ -515,8 +513,7 @@ cudaError_t launch_tc_single_ew(const TcSegDev& seg, int bn, int mode, int nc, i
 
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
                           bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl) {
-  TcSingle p;
-  memset(&p, 0, sizeof(p));
+  TcSingle p{};
   if (split) return dispatch<2>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st, pdl);
   return dispatch<1>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st, pdl);
 }
@@ -589,38 +586,38 @@ __global__ void __launch_bounds__(256) k_split_reduce(const SplitUnit* __restric
         io.out[i + k * io.ldo] = (r - wh[c]) - wl[c];   // r - wh is exact while they are within a factor 2
       }
     }
-    return;
-  }
-  if constexpr (RM == RED_FINAL) {
+  } else {   // RED_CHI2, RED_FINAL
+    if constexpr (RM == RED_FINAL) {
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const int cl = min(c16 + grp + 4 * c, ncol - 1);
+        const float x = i < sd.nk ? io.in[i + ((int64_t)u.c * 128 + cl) * io.ldi] : 0.f;
+        ff_add(x, wh[c], wl[c]);
+      }
+    }
 #pragma unroll
     for (int c = 0; c < CB; ++c) {
-      const int cl = min(c16 + grp + 4 * c, ncol - 1);
-      const float x = i < sd.nk ? io.in[i + ((int64_t)u.c * 128 + cl) * io.ldi] : 0.f;
-      ff_add(x, wh[c], wl[c]);
-    }
-  }
+      const int cl = c16 + grp + 4 * c;
+      float hi = 0.f, lo = 0.f;
+      ff_add_square2(wh[c], wl[c], hi, lo);
 #pragma unroll
-  for (int c = 0; c < CB; ++c) {
-    const int cl = c16 + grp + 4 * c;
-    float hi = 0.f, lo = 0.f;
-    ff_add_square2(wh[c], wl[c], hi, lo);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float oh = __shfl_down_sync(0xffffffffu, hi, off);
-      const float ol = __shfl_down_sync(0xffffffffu, lo, off);
-      ff_add(oh, hi, lo);
-      lo += ol;
+      for (int off = 16; off > 0; off >>= 1) {
+        const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+        const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+        ff_add(oh, hi, lo);
+        lo += ol;
+      }
+      if (lane == 0 && cl < ncol) {
+        red_hi[cl - c16][wig] = hi;
+        red_lo[cl - c16][wig] = lo;
+      }
     }
-    if (lane == 0 && cl < ncol) {
-      red_hi[cl - c16][wig] = hi;
-      red_lo[cl - c16][wig] = lo;
+    __syncthreads();
+    if (threadIdx.x < 16 && c16 + (int)threadIdx.x < ncol) {
+      const int cl = threadIdx.x;
+      const double s = ((double)red_hi[cl][0] + (double)red_lo[cl][0]) + ((double)red_hi[cl][1] + (double)red_lo[cl][1]);
+      sd.partials[((int64_t)u.m * (bn / 64) + g64) * sd.ldp + u.c * 128 + c16 + cl] = s;
     }
-  }
-  __syncthreads();
-  if (threadIdx.x < 16 && c16 + (int)threadIdx.x < ncol) {
-    const int cl = threadIdx.x;
-    const double s = ((double)red_hi[cl][0] + (double)red_lo[cl][0]) + ((double)red_hi[cl][1] + (double)red_lo[cl][1]);
-    sd.partials[((int64_t)u.m * (bn / 64) + g64) * sd.ldp + u.c * 128 + c16 + cl] = s;
   }
 }
 

@@ -220,7 +220,7 @@ int64_t td_last_pivot(const td_segment* s);
  *   logL_k = -chi2_k/2 - logdet/2 - (N'/2) log 2 pi.
  *   R    : device, float32, column-major N' x K, leading dimension ldr >= N'.
  *          Read only; caller-owned.
- *   K    : number of residual columns; K = 0 is a no-op.
+ *   K    : number of residual columns, 0 <= K <= 2^30; K = 0 is a no-op.
  *   logL : device, float64[K], caller-owned, overwritten.
  *   opt  : NULL = defaults.
  *   chi2 : optional device float64[K] (NULL = not written).

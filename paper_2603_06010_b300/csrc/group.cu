@@ -309,7 +309,8 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
       delete g;
       return fail(!s ? TD_ERR_INVALID : TD_ERR_NOT_FACTORED, "segment missing or not factored");
     }
-    if (s->device != g->device || K[i] < 0 || (K[i] > 0 && (!R[i] || !logL[i])) || ldr[i] < s->nk) {
+    if (s->device != g->device || K[i] < 0 || K[i] > TD_MAX_K || (K[i] > 0 && (!R[i] || !logL[i])) ||
+        ldr[i] < s->nk) {
       delete g;
       return fail(TD_ERR_INVALID, "bad segment arguments");
     }

@@ -83,6 +83,7 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
                                               double* logL, double* chi2, void* stream) {
   if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
   if (K < 0) return fail(TD_ERR_INVALID, "K < 0");
+  if (K > TD_MAX_K) return fail(TD_ERR_INVALID, "K above 2^30 columns");
   if (K == 0) return TD_OK;
   if (!R || !logL) return fail(TD_ERR_INVALID, "R or logL is NULL");
   if (ldr < s->nk) return fail(TD_ERR_INVALID, "ldr < N'");

@@ -20,6 +20,7 @@ constexpr int OP_KB = 32;       // operator k-block (64 B of bf16)
 constexpr int TC_COLS = 128;    // residual columns per tensor-core tile (MMA M)
 constexpr int OP_SLICES = 4;    // bf16 slices per operand element (fixed-point hi + 3 floating)
 constexpr double LOG2PI = 1.8378770664093454836;   // log(2 pi), the constant of logL
+constexpr int64_t TD_MAX_K = (int64_t)1 << 30;     // columns per batch (tile and column indices stay in int)
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 inline int64_t ceil_div(int64_t x, int64_t m) { return (x + m - 1) / m; }

@@ -185,6 +185,10 @@ def test_not_factored_and_bad_args(torch_cuda, gpu_lib):
     with pytest.raises(td.TdError) as e:
         seg.loglike_into(R, torch_cuda.empty(2, dtype=torch_cuda.float64, device="cuda"), ldr=100)
     assert e.value.code == td.TD_ERR_INVALID
+    # more columns than the entry point takes: refused on the host, nothing launched
+    out = torch_cuda.empty(2, dtype=torch_cuda.float64, device="cuda")
+    assert td.lib().td_loglike_batch(seg.handle, R.data_ptr(), 128, (1 << 30) + 1, out.data_ptr(), None, None,
+                                     None) == td.TD_ERR_INVALID
 
 
 def test_bounded_wait_times_out_and_context_survives(torch_cuda, gpu_lib):

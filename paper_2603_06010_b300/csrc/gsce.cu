@@ -542,18 +542,19 @@ extern "C" td_status td_gs_prepare(td_segment* s, void* stream) {
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   free_gs_state(s);
   const int M = 1 << logm;
-  double *a0 = nullptr, *a1 = nullptr, *x = nullptr, *ld = nullptr;
+  double *a0 = nullptr, *a1 = nullptr, *x = nullptr, *ld = nullptr, *vh = nullptr;
   double2* c = nullptr;
   LevJob* dj = nullptr;
   GsState& g = s->gs;
   td_status r = TD_OK;
   auto cleanup = [&]() {
-    for (double** p : {&a0, &a1, &x, &ld}) gs_free(*p);
+    for (double** p : {&a0, &a1, &x, &ld, &vh}) gs_free(*p);
     gs_free(c);
     gs_free(dj);
   };
   if (cudaMalloc((void**)&a0, (size_t)s->n * 8) != cudaSuccess || cudaMalloc((void**)&a1, (size_t)s->n * 8) != cudaSuccess ||
       cudaMalloc((void**)&x, (size_t)s->n * 8) != cudaSuccess || cudaMalloc((void**)&ld, 8) != cudaSuccess ||
+      cudaMalloc((void**)&vh, (size_t)s->n * 8) != cudaSuccess ||
       cudaMalloc((void**)&c, (size_t)2 * M * sizeof(double2)) != cudaSuccess ||
       cudaMalloc((void**)&dj, sizeof(LevJob)) != cudaSuccess ||
       cudaMalloc((void**)&g.S1, (size_t)M * sizeof(float2)) != cudaSuccess ||
@@ -564,7 +565,7 @@ extern "C" td_status td_gs_prepare(td_segment* s, void* stream) {
     free_gs_state(s);
     return fail(TD_ERR_OOM, "GSCE setup buffers");
   }
-  const LevJob job{s->acf, s->n, a0, a1, nullptr, 0, ld, s->status, x};
+  const LevJob job{s->acf, s->n, a0, a1, nullptr, 0, ld, s->status, x, vh};
   DevStatus h0{0, 0, LLONG_MAX};
   cudaError_t e = cudaMemcpyAsync(s->status, &h0, sizeof h0, cudaMemcpyHostToDevice, st);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dj, &job, sizeof job, cudaMemcpyHostToDevice, st);

@@ -16,7 +16,7 @@
 // orders form a chain; the O(t) work of an order (one dot product, one
 // predictor update, one row of L^{-1}) is spread over the cluster, the
 // predictor lives in global memory (L2-resident), and each row is stored in
-// FP64, row-major.
+// FP64, row-major.  The order's scalars are formed by one thread per CTA.
 // FP64 is a slow pipe on this part, so the chain does only these three
 // multiply-adds per element; the per-row quantum and the bf16 slicing then
 // run over all SMs in the same kernels the Cholesky route uses.  Segments
@@ -38,38 +38,43 @@ namespace td {
 constexpr int LEV_THREADS = 1024;
 constexpr int64_t LEV_MAX_N = 1 << 20;
 
-__device__ __forceinline__ double block_sum(double v, double* red) {
+// Sum of the block's values in a fixed order, into lane 0 of warp 0: the
+// values go through shared memory to one warp (each lane adds 32 of them in
+// order, then a fixed shuffle tree).  FP64 is a slow pipe on this part, so the
+// reduction keeps FP64 adds to one warp rather than a shuffle tree in every warp.
+__device__ __forceinline__ double block_sum_to_lead(double v, double* red) {
+  red[threadIdx.x] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < LEV_THREADS; i += 32) s += red[i];
 #pragma unroll
-  for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  __syncthreads();
-  if (l == 0) red[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double s = 0.0;
-    for (int i = 0; i < LEV_THREADS / 32; ++i) s += red[i];   // fixed order
-    red[32] = s;
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
   }
-  __syncthreads();
-  return red[32];
+  return s;   // valid in thread 0
 }
 
 // One thread-block cluster of CL CTAs per segment (CL = 1: one CTA): the
 // O(t) work of an order is spread over CL x 1024 threads (element j to
 // cluster thread (j - 1) mod CL*1024, so warps stay coalesced, the mirrored
-// index too).  One barrier per order: order t's dot product reads only the
-// predictor elements this thread itself wrote at order t-1 (the newest one,
-// k_{t-1}, from a register), so it needs no barrier; after the barrier every
-// thread adds the CL partials in rank order (all CTAs get the same bits, so
-// the same k_t, v_t and decisions), writes its share of row t-1 of L^{-1}
-// (a_{t-1} is complete everywhere now) and updates its share of the
-// predictor.  The cluster size is a launch attribute, chosen per batch.
+// index too).  Per order: each CTA's dot-product partial; one cluster barrier
+// (order t's dot product reads only the predictor elements this thread itself
+// wrote at order t-1, the newest one, k_{t-1}, from a register, so it needs
+// no barrier before it); thread 0 of every CTA then adds the CL partials in
+// rank order and forms k_t, v_t and 1/sqrt(v_{t-1}) (the same bits in every
+// CTA), which one CTA barrier hands to its threads; every thread writes its
+// share of row t-1 of L^{-1} (a_{t-1} is complete everywhere now) and updates
+// its share of the predictor.  The FP64 division, square root and log stay
+// off the other 1023 threads of a CTA (they would saturate the FP64 pipe);
+// the log det is summed once at the end from the v_t history.  The cluster
+// size is a launch attribute, chosen per batch.
 template <int CL>
 __global__ void __launch_bounds__(LEV_THREADS, 1) k_levinson_rows(const LevJob* __restrict__ jobs) {
-  __shared__ double red[40];
-  // partials double-buffered by order parity: with one barrier per order a
-  // CTA may publish order t+1's partial while a peer still reads order t's
+  __shared__ double red[LEV_THREADS];
+  // partials double-buffered by order parity: with one cluster barrier per
+  // order a CTA may publish order t+1's partial while a peer still reads order t's
   __shared__ double sh_part[2];
+  __shared__ double sh_bc[3];   // k_t, v_t, 1/sqrt(v_{t-1}) of the current order
   const int rank = CL > 1 ? (int)cg::this_cluster().block_rank() : 0;
   const LevJob jb = jobs[blockIdx.x / CL];
   const int64_t n = jb.n;
@@ -79,7 +84,6 @@ __global__ void __launch_bounds__(LEV_THREADS, 1) k_levinson_rows(const LevJob* 
   const bool lead = (g == 0);
   double* a = jb.a0;      // a_{t-1}[1..t-1]
   double* an = jb.a1;     // a_t
-  double logdet = 0.0;
   double v = jb.acf[0];   // v_{t-1}, the same in every thread
   double kp = 0.0;        // k_{t-1} = a_{t-1}[t-1]
   bool bad = !(v > 0.0) || !isfinite(v);
@@ -88,32 +92,38 @@ __global__ void __launch_bounds__(LEV_THREADS, 1) k_levinson_rows(const LevJob* 
     atomicCAS(&jb.status->code, 0, ST_NOT_PD);
   }
   for (int64_t t = 1; t <= n && !bad; ++t) {
-    double k = 0.0, vn = v;
     if (t < n) {
       // k_t = (acf[t] - sum_{j=1}^{t-1} a_{t-1,j} acf[t-j]) / v_{t-1}
       double part = 0.0;
       for (int64_t j = 1 + g; j < t; j += STRIDE) part = fma(j == t - 1 ? kp : a[j], jb.acf[t - j], part);
-      part = block_sum(part, red);
+      part = block_sum_to_lead(part, red);
       if (tid == 0) sh_part[t & 1] = part;
     }
     if constexpr (CL > 1)
       cg::this_cluster().sync();   // partials published; a_{t-1} complete in every share
     else
       __syncthreads();
-    if (t < n) {
-      double dot = 0.0;
-      if constexpr (CL > 1) {
+    if (tid == 0) {
+      double k = 0.0, vn = v;
+      if (t < n) {
+        double dot = 0.0;
+        if constexpr (CL > 1) {
 #pragma unroll
-        for (int r = 0; r < CL; ++r) dot += *cg::this_cluster().map_shared_rank(&sh_part[t & 1], r);
-      } else {
-        dot = sh_part[t & 1];
+          for (int r = 0; r < CL; ++r) dot += *cg::this_cluster().map_shared_rank(&sh_part[t & 1], r);
+        } else {
+          dot = sh_part[t & 1];
+        }
+        k = (jb.acf[t] - dot) / v;
+        vn = v * (1.0 - k * k);
       }
-      k = (jb.acf[t] - dot) / v;
-      vn = v * (1.0 - k * k);
+      sh_bc[0] = k;
+      sh_bc[1] = vn;
+      sh_bc[2] = 1.0 / sqrt(v);
     }
+    __syncthreads();
+    const double k = sh_bc[0], vn = sh_bc[1], inv = sh_bc[2];
+    if (lead) jb.vhist[t - 1] = v;   // log det = sum_t log v_t, added at the end
     // row t-1 of L^{-1}: column c < t-1 holds -a_{t-1, t-1-c} / sqrt(v_{t-1}), column t-1 holds 1 / sqrt(v_{t-1})
-    if (lead) logdet += log(v);
-    const double inv = 1.0 / sqrt(v);
     if (jb.linv) {
       double* row = jb.linv + (t - 1) * jb.ld;
       for (int64_t c = g; c < t - 1; c += STRIDE) row[c] = -a[t - 1 - c] * inv;
@@ -134,7 +144,7 @@ __global__ void __launch_bounds__(LEV_THREADS, 1) k_levinson_rows(const LevJob* 
         atomicMin((unsigned long long*)&jb.status->pivot, (unsigned long long)t);
         atomicCAS(&jb.status->code, 0, ST_NOT_PD);
       }
-      bad = true;   // every thread of the cluster computed the same vn
+      bad = true;   // every thread of the cluster holds the same vn
       break;
     }
     for (int64_t j = 1 + g; j < t; j += STRIDE) an[j] = fma(-k, a[t - j], a[j]);
@@ -145,7 +155,14 @@ __global__ void __launch_bounds__(LEV_THREADS, 1) k_levinson_rows(const LevJob* 
     a = an;
     an = tmp;
   }
-  if (lead) *jb.logdet = logdet;
+  if (rank == 0 && !bad) {
+    // log det C = sum_{t=0}^{n-1} log v_t: the logs spread over the CTA, added in a fixed order
+    __syncthreads();   // the lead's v_t stores are visible to the CTA
+    double sl = 0.0;
+    for (int64_t i = tid; i < n; i += LEV_THREADS) sl += log(jb.vhist[i]);
+    sl = block_sum_to_lead(sl, red);
+    if (tid == 0) *jb.logdet = sl;
+  }
   if constexpr (CL > 1) cg::this_cluster().sync();   // no CTA leaves while a peer may still read its partial
 }
 
@@ -209,11 +226,12 @@ struct LevSeg {
   double* qrow = nullptr;
   double* a0 = nullptr;
   double* a1 = nullptr;
+  double* vh = nullptr;
   double* ld = nullptr;
 };
 
 void free_lev(LevSeg& x) {
-  for (double** p : {&x.linv, &x.qrow, &x.a0, &x.a1, &x.ld}) {
+  for (double** p : {&x.linv, &x.qrow, &x.a0, &x.a1, &x.vh, &x.ld}) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
@@ -235,14 +253,15 @@ td_status run_lev_batch(std::vector<LevSeg>& b, cudaStream_t st) {
     if (cudaMalloc((void**)&x.linv, (size_t)s->nkp * s->nkp * 8) != cudaSuccess ||
         cudaMalloc((void**)&x.qrow, (size_t)s->nkp * 8) != cudaSuccess ||
         cudaMalloc((void**)&x.a0, (size_t)s->n * 8) != cudaSuccess ||
-        cudaMalloc((void**)&x.a1, (size_t)s->n * 8) != cudaSuccess || cudaMalloc((void**)&x.ld, 8) != cudaSuccess) {
+        cudaMalloc((void**)&x.a1, (size_t)s->n * 8) != cudaSuccess ||
+        cudaMalloc((void**)&x.vh, (size_t)s->n * 8) != cudaSuccess || cudaMalloc((void**)&x.ld, 8) != cudaSuccess) {
       cudaGetLastError();
       r = fail(TD_ERR_OOM, "Levinson scratch");
       break;
     }
     DevStatus h{0, 0, LLONG_MAX};
     cudaMemcpyAsync(s->status, &h, sizeof h, cudaMemcpyHostToDevice, st);
-    jobs.push_back(LevJob{s->acf, s->n, x.a0, x.a1, x.linv, s->nkp, x.ld, s->status, nullptr});
+    jobs.push_back(LevJob{s->acf, s->n, x.a0, x.a1, x.linv, s->nkp, x.ld, s->status, nullptr, x.vh});
   }
   LevJob* dj = nullptr;
   if (r == TD_OK) {

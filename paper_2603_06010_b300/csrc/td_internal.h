@@ -103,6 +103,7 @@ struct LevJob {
   double* logdet;          // device, one double
   DevStatus* status;       // NOT_PD pivot
   double* x;               // nullptr, or device n doubles: receives C^{-1} e_1
+  double* vhist;           // device scratch, n doubles: the prediction-error variances v_0 .. v_{n-1}
 };
 cudaError_t launch_levinson_rows(const LevJob* jobs, int njobs, cudaStream_t st);
 

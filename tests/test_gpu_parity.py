@@ -6,6 +6,7 @@ plain FP64 path is held to 1e-11 relative.  The 3xBF16 (two-slice) option
 is checked against the error band its arithmetic gives (~1e-5 relative),
 which is above the bar by design.
 """
+import ctypes
 import json
 import os
 import zlib
@@ -330,3 +331,37 @@ def test_extreme_and_transition_shapes(torch_cuda, gpu_lib, n, K):
     _compare("bf16x6", ll[cols], chi[cols], oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept), exp_chi,
              f"n={n} K={K}")
     seg.close()
+
+
+def test_empty_batch_every_form(torch_cuda, gpu_lib):
+    """K = 0 is a no-op on every form of the call: status OK, outputs untouched."""
+    from paper_2603_06010_b300 import td
+    n = 1500
+    acf = inputs.acf_from_psd(n, 2048.0)
+    seg = td.Segment(acf)
+    seg.gs_prepare()
+    R = torch_cuda.zeros((0, n), dtype=torch_cuda.float32, device="cuda")
+    out = torch_cuda.full((4,), 7.0, dtype=torch_cuda.float64, device="cuda")
+    for opt in (td.options(), td.options(precision=td.TD_PREC_FP64), td.options(path=td.TD_PATH_GSCE),
+                td.options(precision=td.TD_PREC_BF16X3, refine=1), td.options(path=td.TD_PATH_SMALLK)):
+        assert td.lib().td_loglike_batch(seg.handle, R.data_ptr(), n, 0, out.data_ptr(), ctypes.byref(opt),
+                                         None, None) == td.TD_OK
+    host = np.full(4, 7.0)
+    seg.loglike_host_into(np.zeros((0, n), np.float32), host)
+    torch_cuda.cuda.synchronize()
+    seg.check()
+    assert np.all(out.cpu().numpy() == 7.0) and np.all(host == 7.0)
+
+
+def test_many_column_tiles(torch_cuda, gpu_lib):
+    """K = 20000 on a small gapped segment: 157 column tiles, a ragged last one."""
+    from paper_2603_06010_b300 import td
+    n = 300
+    mask = _mask(n, [(40, 70)])
+    acf = inputs.acf_from_psd(n, 1024.0)
+    o = oracle.OracleSegment(acf, mask)
+    R = inputs.noise_residuals(n, 1024.0, 20000, 99, mask=mask)
+    seg = td.Segment(acf, mask)
+    ll, chi = _run(torch_cuda, td, seg, R, "bf16x10")
+    exp_chi = o.chi2(R)
+    _compare("bf16x10", ll, chi, oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept), exp_chi, "K=20000")

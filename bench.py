@@ -36,7 +36,7 @@ UNIT = "logL evals/s"
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--steps", type=int, default=50)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="bf16x6", choices=["bf16x6", "bf16x10", "bf16x3", "fp64"])
@@ -61,54 +61,66 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (every 20 ms, timestamped); mark() brackets the timed
+    region and stop() keeps the samples taken inside it (all samples if none)."""
 
     def __init__(self):
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
             fd, self.path = tempfile.mkstemp(suffix=".csv")
             os.close(fd)
-            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+            q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
             dev = os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0] or "0"
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
             time.sleep(0.3)
         except Exception:
             self.proc = None
 
+    def mark(self, begin):
+        import datetime
+        if begin:
+            self.t0 = datetime.datetime.now()
+        else:
+            self.t1 = datetime.datetime.now()
+
     def stop(self):
+        import datetime
         if self.proc is None:
             return None
+        time.sleep(0.05)   # the sample after the region
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f")
+                rows.append((ts, float(f[2]), float(f[3]), [nm for nm, v in zip(names, f[6:10])
+                                                             if v.lower() == "active"]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
         os.unlink(self.path)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        inside = [r for r in rows if self.t0 and self.t1 and self.t0 <= r[0] <= self.t1]
+        use = inside or rows
+        return {"sm_mhz": float(np.median([r[1] for r in use])), "sm_max_mhz": float(max(r[2] for r in use)),
+                "reasons": sorted({nm for r in use for nm in r[3]}), "samples": len(use),
+                "samples_in_timed_region": len(inside)}
 
 
 def make_workload(rank: int):
@@ -585,12 +597,14 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     seg.profile(True)
+    clocks.mark(True)
     for i in range(args.steps):
         flush.zero_()                      # L2 flush between timed steps (not timed)
         ev[i][0].record(stream)
         seg.loglike_into(R, logL, opt)
         ev[i][1].record(stream)
     torch.cuda.synchronize()
+    clocks.mark(False)
     if world > 1:
         dist.barrier()
     clk = clocks.stop()

@@ -13,7 +13,9 @@ by mathematics rather than by the oracle itself:
 * Gohberg-Semencul with FFT circulant-embedded Toeplitz products
   (Sec. III.A, GS formula and Eq. eq:toeplitz_fft), with C^{-1} e1 found by
   conjugate gradients on FFT matvecs;
-* invariants -- PSD scale, time reversal, mirrored gaps, spectral bounds.
+* invariants -- PSD scale, time reversal, mirrored gaps, spectral bounds;
+* a library density -- scipy's multivariate-normal log-density of the
+  block-diagonal covariance of two gapped detectors (Sec. II.B item 3).
 
 None of these call the oracle's own routines to produce an expected value.
 """
@@ -355,6 +357,30 @@ def check_noise_chi2_distribution(orc, n=512, fs=2048.0, K=800, seed=19):
     assert abs(W.mean()) < 0.01 and abs(W.std() - 1) < 0.01
 
 
+# ---------------------------------------------------------------------------
+# library density: the full logL (whitening, log det and the constant) of two
+# gapped detectors against scipy's multivariate-normal log-density of the
+# block-diagonal covariance (an eigendecomposition, no Cholesky)
+# ---------------------------------------------------------------------------
+def check_mvn_joint(orc, seed=20):
+    from scipy import linalg, stats
+    rng = np.random.default_rng(seed)
+    segs, blocks, Rs = [], [], []
+    for n, fs, gap in ((180, 1024.0, (20, 55)), (137, 2048.0, (100, 104))):
+        acf = inputs.acf_from_psd(n, fs)
+        mask = np.ones(n, np.uint8)
+        mask[gap[0]:gap[1]] = 0
+        keep = np.flatnonzero(mask)
+        blocks.append(linalg.toeplitz(acf)[np.ix_(keep, keep)])
+        segs.append(orc.OracleSegment(acf, mask))
+        Rs.append((rng.standard_normal((4, keep.size)) * 3).astype(np.float32))
+    C = linalg.block_diag(*blocks)
+    X = np.concatenate([R.astype(np.float64) for R in Rs], axis=1)
+    expect = stats.multivariate_normal(mean=np.zeros(C.shape[0]), cov=C).logpdf(X)
+    got = orc.joint_loglike(segs, Rs)
+    assert np.allclose(got, expect, rtol=1e-10, atol=1e-8), (got, expect)
+
+
 ALL_CHECKS = [
     ("white", lambda o: (check_white(o, gaps=False), check_white(o, gaps=True))),
     ("ar1", lambda o: check_ar1(o, gaps=False)),
@@ -365,4 +391,5 @@ ALL_CHECKS = [
     ("gs", check_gs),
     ("scaling", check_scaling),
     ("reversal", check_reversal),
+    ("mvn_joint", check_mvn_joint),
 ]

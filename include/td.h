@@ -89,9 +89,10 @@ typedef enum {
                            chunk results added in double-float by a reduce kernel */
   TD_PATH_FP64 = 3,     /* plain FP64 forward substitution */
   TD_PATH_STREAM64 = 4, /* as TD_PATH_STREAM with 64-row operator tiles */
-  TD_PATH_SMALLK = 5,   /* K <= 64: operator rows as the MMA M dimension and the residual
-                           columns as N (16, 32 or 64), so the MMA is not padded to 128
-                           columns; the packed operator streams once (default for K <= 32) */
+  TD_PATH_SMALLK = 5,   /* K <= 256: operator rows as the MMA M dimension and the residual
+                           columns as N (16, 32, 64, 128 or 256), so the MMA is not padded
+                           to 128 columns and every operator tile is read once; default
+                           for K <= 32, and for 64 < K <= 256 while N' < 24576 */
   TD_PATH_TENSOR128 = 6, /* as TD_PATH_TENSOR with 128-row operator tiles (two accumulator
                             pairs in TMEM: a tile's epilogue overlaps the next tile's MMAs) */
   TD_PATH_STREAM128 = 7, /* as TD_PATH_STREAM with 128-row operator tiles */

@@ -79,9 +79,10 @@ td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* o
                    (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, (uint32_t)bn, (uint32_t)nsl);
 }
 
-// Tile shape and split for a batch: 256-row tiles over whole rows while they
-// give at least two waves of work items; otherwise rows are split into
-// balanced chunks (256-row tiles), and td_options.path can force any shape.
+// Tile shape and split for a batch: the small-batch kernel (bn = 0) for few
+// and mid-size batches, 128-row chunks between them; for wide batches 256- or
+// 128-row tiles over whole rows, chosen by how many work items they give, else
+// 128-row chunks.  td_options.path can force any shape.
 struct Shape {
   int bn;
   bool split;
@@ -92,9 +93,15 @@ static Shape choose_shape(const td_segment* s, int64_t K, int path) {
   if (path == TD_PATH_STREAM64) return {64, true};
   if (path == TD_PATH_TENSOR128) return {128, false};
   if (path == TD_PATH_STREAM128) return {128, true};
-  // small-batch kernel: K <= 32 automatically (measured at N' = 8192: K = 64 takes
-  // 97 us there against 91 us as 128-row chunks); up to 64 when asked for
-  if (path == TD_PATH_SMALLK || (path == TD_PATH_AUTO && K <= 32)) return {0, true};
+  // measured on B300 (one call after an L2 flush, N' = 2048 ... 32768):
+  // K <= 32 and 64 < K <= 256 take the small-batch kernel (N' = 8192, K = 256:
+  // 108 us against 135 us as 128-row chunks and 152 us as 128-row whole rows;
+  // N' = 16384, K = 256: 284 / 329 / 291 us) up to N' = 16384; at N' = 32768
+  // 256-row whole rows win (923 against 992 us).  32 < K <= 64 takes 128-row
+  // chunks (N' = 16384: 178 us; whole rows 286 us, held back by the longest row)
+  if (path == TD_PATH_SMALLK) return {0, true};
+  if (path == TD_PATH_AUTO && (K <= 32 || (K > 64 && K <= 256 && s->nk < 24576))) return {0, true};
+  if (path == TD_PATH_AUTO && K <= 64) return {128, true};
   // measured on B300 (N' = 8192, one call after an L2 flush): 256-row whole
   // rows win from K = 1024 (250 us vs 275 us for 128-row); 128-row whole rows
   // (two TMEM accumulator pairs, so epilogues overlap MMAs) at K = 384..512
@@ -229,8 +236,11 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   std::vector<TcItem> items;
   std::vector<SplitUnit> units;
   int n_slots = 0;
-  plan_split_segment(0, s->nk, s->nkp, K, bn, S, items, units, n_slots);
-  const int64_t slot_elems = (int64_t)TC_COLS * bn;   // float2 per slot
+  // from 128 columns on every row tile of the small-batch kernel goes through
+  // the chunk reduction: its in-kernel chi2 epilogue (a shuffle tree per
+  // column) would hold back the CTAs that take whole rows
+  plan_split_segment(0, s->nk, s->nkp, K, bn, S, items, units, n_slots, nc >= 128, nc > 0 ? nc : TC_COLS);
+  const int64_t slot_elems = (int64_t)std::max(TC_COLS, nc) * bn;   // float2 per slot
   sort_items(items);
   td_status r;
   if (n_slots * slot_elems > sc.wpart_slots) {   // wpart_slots counts float2 elements
@@ -270,20 +280,20 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   seg.wpart = sc.wpart;
   seg.nk = (int)s->nk;
   seg.K = (int)K;
-  seg.ldp = nc > 0 ? (int)(sc.capK / 2) : (int)sc.capK;     // small: the buffer as [N'p/128][capK/2]
+  seg.ldp = (int)sc.capK;                                   // small: the buffer as [N'p/128][capK]
   seg.nm = nc > 0 ? (int)(s->nkp / 128) : (int)(s->nkp / 64);   // partials: per 128-row tile (small) or 64 rows
   seg.logdet = s->logdet;
   if ((r = dev_alloc(&p.items, items.size(), "work items")) != TD_OK ||
       (r = dev_alloc(&p.units, std::max<size_t>(1, units.size()), "split units")) != TD_OK ||
       (r = dev_alloc(&p.segdev, 1, "segment descriptor")) != TD_OK ||
-      (nc > 0 && (r = dev_alloc(&p.counters, units.size() + 1, "completion counters")) != TD_OK)) {
+      (nc > 0 && (r = dev_alloc(&p.counters, SMALL_GROUPS, "completion counters")) != TD_OK)) {
     dev_free(p.items);
     dev_free(p.units);
     dev_free(p.segdev);
     dev_free(p.counters);
     return r;
   }
-  if (p.counters) TD_CUDA(cudaMemset(p.counters, 0, (units.size() + 1) * sizeof(int)));
+  if (p.counters) TD_CUDA(cudaMemset(p.counters, 0, SMALL_GROUPS * sizeof(int)));
   TD_CUDA(cudaMemcpy(p.items, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice));
   if (!units.empty())
     TD_CUDA(cudaMemcpy(p.units, units.data(), units.size() * sizeof(SplitUnit), cudaMemcpyHostToDevice));
@@ -533,18 +543,18 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   const int nkb_max = (int)ceil_div(s->nk, OP_KB);
   const bool pm = s->prof && s->ev_used + 2 <= 8192;
   if (bn == 0) {   // small batch: operator rows as the MMA M dimension
-    if (K > 64) return fail(TD_ERR_UNSUPPORTED, "the small-batch path takes K <= 64");
-    const int ncs = K <= 16 ? 16 : (K <= 32 ? 32 : 64);
+    if (K > 256) return fail(TD_ERR_UNSUPPORTED, "the small-batch path takes K <= 256");
+    const int ncs = K <= 16 ? 16 : (K <= 32 ? 32 : (K <= 64 ? 64 : (K <= 128 ? 128 : 256)));
     SplitPlan* plan = nullptr;
     if ((r = get_split_plan(s, ncs, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
     // three launches chained as programmatic dependents: the slicing (which also
     // clears the plan's completion counter), the product, the chunk reduction
     // with chi2 and logL
-    TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st, plan->counters, plan->n_units + 1));
+    TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st, plan->counters, SMALL_GROUPS));
     if (pm) prof_mark(s, st, true);   // the events bracket the product kernel alone
     TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, st));
     if (pm) prof_mark(s, st, false);
-    const SmallFinal fin{plan->units, plan->counters, plan->n_units, (int)K, logL, chi2};
+    const SmallFinal fin{plan->units, plan->counters, plan->n_units, (int)K, logL, chi2, std::max(TC_COLS, ncs)};
     TD_CUDA(launch_small_reduce(plan->segdev, fin, st));
     s->prof_kernels += 3;
     return TD_OK;

@@ -26,30 +26,37 @@ int split_chunk(int64_t nk, int64_t nkp, int bn) {
   return (int)S;
 }
 
-// append the items of one segment (bn-row tiles, chunk S) to the lists
+// append the items of one segment (bn-row tiles, column tiles of `cols`,
+// chunk S) to the lists.  The column tiles of one (row tile, chunk) are
+// emitted next to each other: the kernel hands out neighbouring items in the
+// same round, so those CTAs stream the same operator chunk together and all
+// but the first read it from L2 (an operator larger than L2 would otherwise
+// come from HBM once per column tile).  A unit's chunks still take
+// consecutive slots.
 void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
-                        std::vector<SplitUnit>& units, int& n_slots, bool all_slots) {
+                        std::vector<SplitUnit>& units, int& n_slots, bool all_slots, int cols) {
   const int nm = (int)(nkp / bn);
   const int per = bn / OP_KB;
-  const int nc = (int)ceil_div(K, TC_COLS);
+  const int nc = (int)ceil_div(K, cols);
   const int nkb_max = (int)ceil_div(nk, OP_KB);
-  for (int c = 0; c < nc; ++c) {
-    for (int m = 0; m < nm; ++m) {
-      const int nkb = std::min(per * (m + 1), nkb_max);
-      const int nch = (nkb + S - 1) / S;
-      if (nch <= 1 && !all_slots) {
-        items.push_back(TcItem{seg, m, c, nkb, 0, -1, -1});
-        continue;
-      }
-      // chunks of exactly S k-blocks and one shorter remainder: the remainders
-      // fill the gaps of the longest-first schedule
-      const int unit = (int)units.size();
-      units.push_back(SplitUnit{seg, m, c, n_slots, nch, 0});
-      for (int ch = 0; ch < nch; ++ch) {
-        const int kb0 = ch * S;
-        items.push_back(TcItem{seg, m, c, std::min(S, nkb - kb0), kb0, n_slots++, unit});
-      }
+  for (int m = 0; m < nm; ++m) {
+    const int nkb = std::min(per * (m + 1), nkb_max);
+    const int nch = (nkb + S - 1) / S;
+    if (nch <= 1 && !all_slots) {
+      for (int c = 0; c < nc; ++c) items.push_back(TcItem{seg, m, c, nkb, 0, -1, -1});
+      continue;
     }
+    // chunks of exactly S k-blocks and one shorter remainder: the remainders
+    // fill the gaps of the longest-first schedule
+    const int unit0 = (int)units.size();
+    const int slot_base = n_slots;
+    for (int c = 0; c < nc; ++c) units.push_back(SplitUnit{seg, m, c, slot_base + c * nch, nch, 0});
+    for (int ch = 0; ch < nch; ++ch) {
+      const int kb0 = ch * S;
+      for (int c = 0; c < nc; ++c)
+        items.push_back(TcItem{seg, m, c, std::min(S, nkb - kb0), kb0, slot_base + c * nch + ch, unit0 + c});
+    }
+    n_slots += nc * nch;
   }
 }
 

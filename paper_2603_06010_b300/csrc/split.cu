@@ -214,9 +214,12 @@ __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, i
 template <int THREADS, int V>
 __global__ void __launch_bounds__(THREADS) k_r_slices_reg(const float* __restrict__ R, int64_t ldr, int64_t nk,
                                                           int64_t K, int64_t nkp8, int64_t capK,
-                                                          __nv_bfloat16* __restrict__ rs, int nslices) {
+                                                          __nv_bfloat16* __restrict__ rs, int nslices,
+                                                          int* __restrict__ zero, int nzero) {
   __shared__ float red[THREADS / 32];
   pdl_launch_dependents();
+  if (zero && blockIdx.x == 0)
+    for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0;
   const int64_t k = blockIdx.x;
   const float4* col = reinterpret_cast<const float4*>(R + k * ldr);
   const int64_t nv = nk / 4;
@@ -289,18 +292,21 @@ __global__ void __cluster_dims__(RS_CL, 1, 1) __launch_bounds__(256)
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8, int64_t capK,
                             __nv_bfloat16* rs, int nslices, cudaStream_t st, int* zero, int nzero) {
   if (K <= 0) return cudaSuccess;
-  if (K <= 256) {
+  const bool reg_ok = K <= 2147483647LL && ldr % 4 == 0 && nk % 4 == 0 &&
+                      (reinterpret_cast<uintptr_t>(R) & 15) == 0 && nk <= 4 * 8 * 1024;
+  if (K <= 64 || (K <= 256 && !reg_ok)) {
+    // few columns: a cluster per column puts more SMs on them
     k_r_slices_cl<<<(unsigned)(K * RS_CL), 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
-  } else if (!zero && K <= 2147483647LL && ldr % 4 == 0 && nk % 4 == 0 && (reinterpret_cast<uintptr_t>(R) & 15) == 0 &&
-             nk <= 4 * 8 * 1024) {
-    // column in registers: 8 float4 per thread
+  } else if (reg_ok) {
+    // column in registers: 8 float4 per thread (at K = 256, N' = 8192: one
+    // read of R instead of the cluster form's two, and no cluster barriers)
     const unsigned grid = (unsigned)K;
     if (nk <= 4 * 8 * 256)
-      k_r_slices_reg<256, 8><<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
+      k_r_slices_reg<256, 8><<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
     else if (nk <= 4 * 8 * 512)
-      k_r_slices_reg<512, 8><<<grid, 512, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
+      k_r_slices_reg<512, 8><<<grid, 512, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
     else
-      k_r_slices_reg<1024, 8><<<grid, 1024, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices);
+      k_r_slices_reg<1024, 8><<<grid, 1024, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
   } else {
     const int grid = (int)(K < 4096 ? K : 4096);
     k_r_slices<<<grid, 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);

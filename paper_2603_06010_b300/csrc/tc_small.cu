@@ -1,13 +1,18 @@
-// Tensor-core whitening for small batches (K <= 64 residual columns).
+// Tensor-core whitening for small and mid-size batches (K <= 256 residual
+// columns).
 //
 // Same method and slices as the main kernel (Sec. II.A, W = L^{-1}; Sec.
 // III.A, the cached-operator evaluation), with the operand roles swapped so
 // the MMA is not padded to 128 residual columns:
 //   MMA M = 128 rows of W           (A = L^{-1} slices, K-major),
-//   MMA N = NC residual columns, 16, 32 or 64 (B = R^T slices, K-major),
-// so D[lane i][col n] = W[i][n].  Per 32-column k-block the operator tile is
-// 24 KB (three slices) and the MMA work is tiny, so the kernel streams the
-// packed operator from HBM once.  Long rows are cut into balanced k-chunks;
+//   MMA N = NC residual columns, 16 ... 256 (B = R^T slices, K-major),
+// so D[lane i][col n] = W[i][n].  Every operator tile is read once, whatever
+// the batch width: at NC <= 64 the MMA work per 24 KB tile (three slices) is
+// tiny and the kernel streams the packed operator from HBM; at NC = 256 a
+// k-block moves 72 KB of operands for 12.6 MFLOP of products, the ratio of
+// the 256-row main kernel, so mid-size batches stay on the tensor pipe
+// (128-column residual tiles against 128-row operator tiles move a third
+// more bytes per product).  Long rows are cut into balanced k-chunks;
 // a chunk stores its accumulator pair (exact hi*hi sum, corrections) for
 // k_small_reduce; a whole row reduces chi2 directly: w = hi + corrections in
 // double-float, exact squares, a fixed shuffle tree over the 32 rows of a
@@ -38,8 +43,11 @@ template <int NSL, int NC> struct Cfg {
   // four stages: measured at N' = 8192 (one call, K = 1): 44.0 us against 47.0 us
   // with eight and 55.5 us with two; deeper queues did not raise the rate
   static constexpr int STAGES = (216 * 1024) / STAGE > 4 ? 4 : (216 * 1024) / STAGE;
-  static constexpr int NBUF = 4;                         // accumulator pairs in TMEM
+  // accumulator pairs in TMEM: four up to NC = 64, two at 128, one at 256
+  static constexpr int NBUF = (512 / (2 * NC)) < 4 ? (512 / (2 * NC)) : 4;
   static constexpr uint32_t TMEM_COLS = (NBUF * 2 * NC <= 128) ? 128 : ((NBUF * 2 * NC <= 256) ? 256 : 512);
+  // split slots hold 128 columns (NC <= 128) or NC
+  static constexpr int SLOT_COLS = NC > 128 ? NC : 128;
   static constexpr int SMEM = STAGES * STAGE + 256 + 1024;   // stages + barriers + alignment
 };
 }  // namespace tsm
@@ -274,43 +282,41 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
       }
       tc_fence_after();
       const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(buf * 2 * NC);
-      float a0[NC], a1[NC];
-#pragma unroll
+      const int ncol = min(NC, sd->K - it.c * NC);
+      // 16 columns at a time: both accumulators of a column group, then its
+      // stores or its chi2 terms (NC = 256 would not fit in registers at once)
+      float2* dst = it.slot >= 0 ? sd->wpart + (int64_t)it.slot * C::SLOT_COLS * BM + q * 32 + lane : nullptr;
+#pragma unroll 1
       for (int h = 0; h < NC / 16; ++h) {
         float t0[16], t1[16];
         tmem_ld16(ta + (uint32_t)(h * 16), t0);
         tmem_ld16(ta + (uint32_t)(NC + h * 16), t1);
+        if (it.slot >= 0) {
+          // accumulator pair of this chunk: [slot][SLOT_COLS columns][128 rows]
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          a0[h * 16 + i] = t0[i];
-          a1[h * 16 + i] = t1[i];
+          for (int i = 0; i < 16; ++i)
+            if (h * 16 + i < ncol) dst[(int64_t)(h * 16 + i) * BM] = make_float2(t0[i], t1[i]);
+        } else {
+          // chi2 of this warp's 32 rows per column: exact squares, fixed shuffle tree
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            float hi = 0.f, lo = 0.f;
+            ff_add_square2(t0[i], t1[i], hi, lo);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+              const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+              const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+              ff_add(oh, hi, lo);
+              lo += ol;
+            }
+            if (lane == 0) sh_part[q][h * 16 + i] = (double)hi + (double)lo;
+          }
         }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(&tempty[buf]);
-      const int ncol = min(NC, sd->K - it.c * NC);
-      if (it.slot >= 0) {
-        // accumulator pair of this chunk: [slot][128 columns][128 rows]
-        float2* dst = sd->wpart + (int64_t)it.slot * 128 * BM + q * 32 + lane;
-#pragma unroll
-        for (int n = 0; n < NC; ++n)
-          if (n < ncol) dst[(int64_t)n * BM] = make_float2(a0[n], a1[n]);
-      } else {
-        // chi2 of this warp's 32 rows per column: exact squares, fixed shuffle tree
-#pragma unroll
-        for (int n = 0; n < NC; ++n) {
-          float hi = 0.f, lo = 0.f;
-          ff_add_square2(a0[n], a1[n], hi, lo);
-#pragma unroll
-          for (int off = 16; off > 0; off >>= 1) {
-            const float oh = __shfl_down_sync(0xffffffffu, hi, off);
-            const float ol = __shfl_down_sync(0xffffffffu, lo, off);
-            ff_add(oh, hi, lo);
-            lo += ol;
-          }
-          if (lane == 0) sh_part[q][n] = (double)hi + (double)lo;
-        }
+      if (it.slot < 0) {
         // the tile's four 32-row groups in a fixed order
         epi_bar();
         if (q == 0)
@@ -334,81 +340,21 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
 // Chunk reduction + chi2 / logL for the small-batch kernel.  Grid: (split
 // units, column groups of 4); 128 threads, one per row of the 128-row tile.
 // A thread adds its row's chunk pairs in chunk order (double-float, loads
-// issued 16 chunks x 4 columns ahead), squares exactly; a fixed shuffle tree
+// issued 4 chunks x 4 columns ahead), squares exactly; a fixed shuffle tree
 // per 32 rows and the four groups in order give the tile's partial.  The
-// last CTA to finish sums each column's tile partials in a fixed order (one
-// lane per column, tiles in order within each quarter, quarters in order)
-// into chi2 and logL.
-__global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict__ segs, const SmallFinal fin) {
-  __shared__ int sh_last;
-  __shared__ double sh[4][32];
-  pdl_wait();   // the product kernel's pairs and partials are complete and visible
-  const TcSegDev* sd = &segs[0];
+// last CTA of each column group (one arrival counter per group) sums its four
+// columns' tile partials in a fixed order into chi2 and logL: thread (q, c)
+// adds the tiles of quarter q in order, then the four quarters in order.
+// Without split units (short segments) one CTA does the same for all columns.
+__device__ __forceinline__ void small_final_cols(const TcSegDev* sd, const SmallFinal& fin, int c0, int ncols,
+                                                 double (*sh)[32]) {
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-  if (fin.n_units > 0) {
-    const SplitUnit u = fin.units[blockIdx.x];
-    const int n0 = blockIdx.y * 4;
-    const float2* base = sd->wpart + (int64_t)u.slot0 * 128 * 128 + threadIdx.x;
-    constexpr int CB = 4, CH = 16;
-    float wh[CB], wl[CB];
-#pragma unroll
-    for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
-    for (int ch0 = 0; ch0 < u.nchunk; ch0 += CH) {
-      float2 v[CH][CB];
-      // unconditional loads from clamped (in-range) addresses, selected after:
-      // all of them are in flight at once
-#pragma unroll
-      for (int i = 0; i < CH; ++i)
-#pragma unroll
-        for (int c = 0; c < CB; ++c) {
-          const int ch = min(ch0 + i, u.nchunk - 1), n = min(n0 + c, fin.K - 1);
-          v[i][c] = __ldcg(base + ((int64_t)ch * 128 + n) * 128);
-        }
-#pragma unroll
-      for (int i = 0; i < CH; ++i)
-        if (ch0 + i < u.nchunk) {
-#pragma unroll
-          for (int c = 0; c < CB; ++c) {
-            ff_add(v[i][c].x, wh[c], wl[c]);
-            ff_add(v[i][c].y, wh[c], wl[c]);
-          }
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < CB; ++c) {
-      float hi = 0.f, lo = 0.f;
-      ff_add_square2(wh[c], wl[c], hi, lo);
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) {
-        const float oh = __shfl_down_sync(0xffffffffu, hi, off);
-        const float ol = __shfl_down_sync(0xffffffffu, lo, off);
-        ff_add(oh, hi, lo);
-        lo += ol;
-      }
-      if (lane == 0) sh[q][c] = (double)hi + (double)lo;
-    }
-    __syncthreads();
-    // the tile's four 32-row groups in a fixed order
-    if (threadIdx.x < CB && n0 + threadIdx.x < fin.K) {
-      const int c = threadIdx.x;
-      sd->partials[(int64_t)u.m * sd->ldp + u.c * 128 + n0 + c] = ((sh[0][c] + sh[1][c]) + sh[2][c]) + sh[3][c];
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) sh_last = (atomicAdd(&fin.counters[fin.n_units], 1) == (int)(gridDim.x * gridDim.y) - 1);
-    __syncthreads();
-    if (!sh_last) return;
-    __threadfence();
-  }
-  // chi2 and logL: lane = column (32 columns per pass, coalesced rows of
-  // partials); warp q adds the tiles of its quarter in order, then the four
-  // quarters in order
   const int nparts = sd->nm;
   const int per = (nparts + 3) / 4;
   const int p0 = q * per, p1 = min(nparts, p0 + per);
-  for (int c0 = 0; c0 < fin.K; c0 += 32) {
-    const int col = min(c0 + lane, fin.K - 1);
-    double s = 0.0;
+  const int col = min(c0 + lane, fin.K - 1);
+  double s = 0.0;
+  if (lane < ncols)
     for (int pb = p0; pb < p1; pb += 8) {
       double v[8];   // eight loads in flight (clamped addresses), then the additions in order
 #pragma unroll
@@ -417,15 +363,81 @@ __global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict
       for (int i = 0; i < 8; ++i)
         if (pb + i < p1) s += v[i];
     }
-    __syncthreads();   // sh is free (previous pass read it)
-    sh[q][lane] = s;
-    __syncthreads();
-    if (q == 0 && c0 + lane < fin.K) {
-      const double t = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
-      if (fin.chi2) fin.chi2[c0 + lane] = t;
-      fin.logL[c0 + lane] = -0.5 * t - 0.5 * sd->logdet - 0.5 * (double)sd->nk * LOG2PI;
-    }
+  __syncthreads();   // sh is free
+  sh[q][lane] = s;
+  __syncthreads();
+  if (q == 0 && lane < ncols && c0 + lane < fin.K) {
+    const double t = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
+    if (fin.chi2) fin.chi2[c0 + lane] = t;
+    fin.logL[c0 + lane] = -0.5 * t - 0.5 * sd->logdet - 0.5 * (double)sd->nk * LOG2PI;
   }
+}
+
+__global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict__ segs, const SmallFinal fin) {
+  __shared__ int sh_last;
+  __shared__ double sh[4][32];
+  pdl_wait();   // the product kernel's pairs and partials are complete and visible
+  const TcSegDev* sd = &segs[0];
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  if (fin.n_units == 0) {
+    for (int c0 = 0; c0 < fin.K; c0 += 32) small_final_cols(sd, fin, c0, 32, sh);
+    return;
+  }
+  const SplitUnit u = fin.units[blockIdx.x];
+  const int n0 = blockIdx.y * 4;
+  const float2* base = sd->wpart + (int64_t)u.slot0 * fin.slot_cols * 128 + threadIdx.x;
+  constexpr int CB = 4, CH = 4;
+  float wh[CB], wl[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
+  for (int ch0 = 0; ch0 < u.nchunk; ch0 += CH) {
+    float2 v[CH][CB];
+    // CH x CB predicated loads in flight at once (few registers, so many CTAs
+    // per SM), then the additions in chunk order
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const int n = min(n0 + c, fin.K - 1);
+        v[i][c] = ch0 + i < u.nchunk ? __ldcg(base + ((int64_t)(ch0 + i) * fin.slot_cols + n) * 128)
+                                     : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (ch0 + i < u.nchunk) {
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          ff_add(v[i][c].x, wh[c], wl[c]);
+          ff_add(v[i][c].y, wh[c], wl[c]);
+        }
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < CB; ++c) {
+    float hi = 0.f, lo = 0.f;
+    ff_add_square2(wh[c], wl[c], hi, lo);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+      const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+      ff_add(oh, hi, lo);
+      lo += ol;
+    }
+    if (lane == 0) sh[q][c] = (double)hi + (double)lo;
+  }
+  __syncthreads();
+  // the tile's four 32-row groups in a fixed order
+  if (threadIdx.x < CB && n0 + threadIdx.x < fin.K) {
+    const int c = threadIdx.x;
+    sd->partials[(int64_t)u.m * sd->ldp + u.c * 128 + n0 + c] = ((sh[0][c] + sh[1][c]) + sh[2][c]) + sh[3][c];
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) sh_last = (atomicAdd(&fin.counters[blockIdx.y], 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (!sh_last) return;
+  __threadfence();
+  small_final_cols(sd, fin, n0, CB, sh);
 }
 
 static cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void** args) {
@@ -467,6 +479,8 @@ cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* se
   TD_SMALL_CASE(3, 16) TD_SMALL_CASE(4, 16) TD_SMALL_CASE(2, 16)
   TD_SMALL_CASE(3, 32) TD_SMALL_CASE(4, 32) TD_SMALL_CASE(2, 32)
   TD_SMALL_CASE(3, 64) TD_SMALL_CASE(4, 64) TD_SMALL_CASE(2, 64)
+  TD_SMALL_CASE(3, 128) TD_SMALL_CASE(4, 128) TD_SMALL_CASE(2, 128)
+  TD_SMALL_CASE(3, 256) TD_SMALL_CASE(4, 256) TD_SMALL_CASE(2, 256)
 #undef TD_SMALL_CASE
   return cudaErrorInvalidValue;
 }

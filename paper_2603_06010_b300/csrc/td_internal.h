@@ -75,7 +75,7 @@ struct SplitPlan {           // device work lists for one batch width (split mod
   int n_units = 0;
   int n_slots = 0;
   TcSegDev* segdev = nullptr;
-  int* counters = nullptr;    // small-batch plans: [n_units] chunk arrivals + 1 finished-CTA count
+  int* counters = nullptr;    // small-batch plans: one arrival count per 4-column group (SMALL_GROUPS)
   const void* op = nullptr;   // operator the tensor maps in segdev were encoded for
   double logdet = 0.0;        // and the log det copied into it
   uint64_t last_use = 0;
@@ -123,7 +123,7 @@ inline void mark_device_done(std::atomic<unsigned long long>& done) {
 
 int split_chunk(int64_t nk, int64_t nkp, int bn);
 void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
-                        std::vector<SplitUnit>& units, int& n_slots, bool all_slots = false);
+                        std::vector<SplitUnit>& units, int& n_slots, bool all_slots = false, int cols = TC_COLS);
 void sort_items(std::vector<TcItem>& items);
 
 }  // namespace td
@@ -275,13 +275,15 @@ cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSeg
 // Small batches, one segment: the chunk reduction and the final chi2 / logL
 // run inside the kernel (the last chunk of a row tile, then the last CTA);
 // launched as a programmatic dependent of the residual slicing.
+constexpr int SMALL_GROUPS = 64;   // 4-column groups of the widest small batch (256 columns)
 struct SmallFinal {
   const SplitUnit* units;
-  int* counters;     // [n_units] chunk arrivals, [n_units] finished CTAs; zero at launch
+  int* counters;     // [SMALL_GROUPS] arrivals per 4-column group; zero at launch
   int n_units;
   int K;             // columns of this call (the plan may be wider)
   double* logL;
   double* chi2;      // optional
+  int slot_cols;     // columns per split slot: max(128, the kernel's column tile)
 };
 cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
                             DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);

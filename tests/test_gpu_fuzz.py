@@ -38,7 +38,7 @@ def _case(i, td):
     K = int(rng.choice([1, 2, 7, 16, 31, 33, 64, 100, 129, 255, 300, 513, 700]))
     paths = [td.TD_PATH_AUTO, td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64, td.TD_PATH_TENSOR128,
              td.TD_PATH_STREAM128, td.TD_PATH_FP64]
-    if K <= 64:
+    if K <= 256:
         paths.append(td.TD_PATH_SMALLK)
     path = int(rng.choice(paths))
     prec = int(rng.choice([td.TD_PREC_BF16X6, td.TD_PREC_BF16X10, td.TD_PREC_AUTO, td.TD_PREC_BF16X3]))

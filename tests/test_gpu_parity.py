@@ -137,12 +137,19 @@ def test_column_alone_equals_in_batch(torch_cuda, gpu_lib):
 
     for prec in (td.TD_PREC_FP64, td.TD_PREC_BF16X6, td.TD_PREC_BF16X10):
         for path in ((td.TD_PATH_FP64,) if prec == td.TD_PREC_FP64 else
-                     (td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64)):
+                     (td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64, td.TD_PATH_TENSOR128,
+                      td.TD_PATH_STREAM128, td.TD_PATH_SMALLK)):
             opt = td.options(precision=prec, path=path)
-            full = run(Rd, opt)
-            for k in (0, 1, 127, 128, 299):
+            # the small-batch kernel takes up to 256 columns: its widths 16 ... 256
+            # (whole rows reduced in the kernel below 128 columns, all rows by
+            # the chunk reduction from 128) give the same bits
+            last = 255 if path == td.TD_PATH_SMALLK else 299
+            full = run(Rd[:last + 1], opt)
+            for k in (0, 1, 127, 128, last):
                 assert run(Rd[k:k + 1], opt)[0] == full[k], (prec, path, k)
             assert np.array_equal(run(Rd[100:229], opt), full[100:229]), (prec, path)
+            assert np.array_equal(run(Rd[60:100], opt), full[60:100]), (prec, path)
+            assert np.array_equal(run(Rd[20:120], opt), full[20:120]), (prec, path)
     auto_full = run(Rd, td.options())
     for k in (0, 5, 299):
         assert abs(run(Rd[k:k + 1], td.options())[0] - auto_full[k]) <= 1e-3
@@ -252,7 +259,51 @@ def test_full_gapped_n16384_three_detectors(torch_cuda, gpu_lib, prec):
     assert np.max(np.abs(joint - np.array(gg["joint_logL"]))) <= 1e-3
 
 
-@pytest.mark.parametrize("K", [1, 5, 17, 32, 48, 64, 130, 300])
+@pytest.mark.parametrize("K", [100, 256])
+def test_full_gapfree_n8192_mid_batches(torch_cuda, gpu_lib, K):
+    """Mid-size batches of the N = 8192 workload on the small-batch kernel with
+    128- and 256-column tiles (and on the automatic choice): the stored oracle
+    columns, placed at the start, the middle and the end of the batch."""
+    from paper_2603_06010_b300 import td
+    g = _golden()["gapfree_n8192_k4096"]
+    seg_in = inputs.make_segment(g["n"], g["fs"], g["seed"], n_gaps=g["n_gaps"], gap_len=g["gap_len"],
+                                 scale=g["scale"])
+    R = inputs.residual_batch(seg_in, g["K"], g["rseed"])
+    cols = list(g["columns"])
+    fill = [c for c in range(g["K"]) if c not in cols][:K - len(cols)]
+    order = fill[:K // 2 - 5] + cols[:6] + fill[K // 2 - 5:] + cols[6:]
+    assert len(order) == K
+    pos = [order.index(c) for c in cols]
+    seg = td.Segment(seg_in.acf, seg_in.mask, factor=False)
+    td.factor_many([seg])
+    Rd = torch_cuda.from_numpy(np.ascontiguousarray(R[order])).cuda()
+    for path in (td.TD_PATH_SMALLK, td.TD_PATH_AUTO):
+        ll, chi = seg.loglike(Rd, td.options(path=path), with_chi2=True)
+        torch_cuda.cuda.synchronize()
+        seg.check()
+        _compare("bf16x6", ll.cpu().numpy()[pos], chi.cpu().numpy()[pos], np.array(g["logL"]),
+                 np.array(g["chi2"]), f"N=8192 K={K} path {path}")
+    seg.close()
+
+
+def test_small_batch_path_width_limit(torch_cuda, gpu_lib):
+    """The small-batch kernel takes up to 256 columns; wider batches are refused."""
+    from paper_2603_06010_b300 import td
+    n = 600
+    seg = td.Segment(inputs.acf_from_psd(n, 2048.0))
+    R = torch_cuda.zeros((257, n), dtype=torch_cuda.float32, device="cuda")
+    out = torch_cuda.empty(257, dtype=torch_cuda.float64, device="cuda")
+    opt = td.options(path=td.TD_PATH_SMALLK)
+    assert td.lib().td_loglike_batch(seg.handle, R.data_ptr(), n, 257, out.data_ptr(), ctypes.byref(opt),
+                                     None, None) == td.TD_ERR_UNSUPPORTED
+    assert td.lib().td_loglike_batch(seg.handle, R.data_ptr(), n, 256, out.data_ptr(), ctypes.byref(opt),
+                                     None, None) == td.TD_OK
+    torch_cuda.cuda.synchronize()
+    seg.check()
+    seg.close()
+
+
+@pytest.mark.parametrize("K", [1, 5, 17, 32, 48, 64, 100, 130, 256, 300])
 def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     """256- and 128-row whole-row tiles, 256/128/64-row split tiles and the
     small-batch kernel agree within the bar (their correction sums round
@@ -264,7 +315,7 @@ def test_tile_shapes_agree(torch_cuda, gpu_lib, K):
     R = torch_cuda.from_numpy(inputs.noise_residuals(n, 2048.0, K, 31, mask=mask)).cuda()
     out = {}
     paths = [td.TD_PATH_TENSOR, td.TD_PATH_STREAM, td.TD_PATH_STREAM64, td.TD_PATH_TENSOR128,
-             td.TD_PATH_STREAM128] + ([td.TD_PATH_SMALLK] if K <= 64 else [])
+             td.TD_PATH_STREAM128] + ([td.TD_PATH_SMALLK] if K <= 256 else [])
     for path in paths:
         ll, chi = seg.loglike(R, td.options(path=path), with_chi2=True)
         torch_cuda.cuda.synchronize()

@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=3.0)
-    p.add_argument("--only", default=None, choices=["grouped", "serving", "gapped3", "refine", "gsce"],
+    p.add_argument("--only", default=None, choices=["grouped", "serving", "gapped3", "refine", "gsce", "small"],
                    help="run one extra workload alone and print its JSON object (profiling; not the bench line)")
     return p.parse_args()
 
@@ -534,6 +534,59 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def small_batches(td, torch, seg, R, N, prec, prec_name):
+    """Batches of K = 1 ... 256 columns of the N' = 8192 workload on each tile
+    shape, back to back: the product kernel alone (CUDA events around it, as
+    operator GB/s and as TFLOP/s against bf16 peak / products) and the whole
+    call."""
+    small = []
+    if prec_name not in ("bf16x6", "bf16x10"):
+        return small
+    stream = torch.cuda.current_stream()
+    nsl = 3 if prec_name == "bf16x6" else 4
+    products = 6 if prec_name == "bf16x6" else 10
+    op_bytes = (N // 256) * ((N // 256) + 1) // 2 * 8 * nsl * 256 * 32 * 2   # operator slices read once
+    for Ks in (1, 8, 64, 128, 256):
+        Rs = R[:Ks].contiguous()
+        ls = torch.empty(Ks, dtype=torch.float64, device="cuda")
+        cand = [("auto", td.TD_PATH_AUTO), ("stream128", td.TD_PATH_STREAM128)]
+        if Ks <= 8:
+            cand.append(("stream256", td.TD_PATH_STREAM))
+        if Ks >= 64:
+            cand += [("smallk", td.TD_PATH_SMALLK), ("tensor128", td.TD_PATH_TENSOR128)]
+        for pname, path in cand:
+            o2 = td.options(precision=prec, path=path)
+            for _ in range(3):
+                seg.loglike_into(Rs, ls, o2)
+            torch.cuda.synchronize()
+            # no L2 flush: the operator streamed by every call (201 MB at N'=8192) is larger
+            # than L2 (126 MB); calls are back to back, as a sampler issues them
+            ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ea.record(stream)
+            for _ in range(20):
+                seg.loglike_into(Rs, ls, o2)
+            eb.record(stream)
+            torch.cuda.synchronize()
+            tot = ea.elapsed_time(eb)
+            seg.profile(True)
+            for _ in range(20):
+                seg.loglike_into(Rs, ls, o2)
+            torch.cuda.synchronize()
+            kms, kn, _ = seg.profile_read()
+            seg.profile(False)
+            kavg = kms / max(kn, 1)
+            gbs = op_bytes / (kavg / 1e3) / 1e9
+            tfl = float(N) * float(N) * Ks / (kavg / 1e3) / 1e12
+            tpeak = peaks()[0]["bf16_tflops"] / products
+            small.append({"K": Ks, "path": pname, "kernel_ms": kavg, "call_ms": tot / 20,
+                          "evals_per_s": Ks / (tot / 20 / 1e3),
+                          "operator_GBps": gbs, "hbm_frac": gbs / peaks()[0]["hbm_gbs"],
+                          "call_hbm_frac": op_bytes / (tot / 20 / 1e3) / 1e9 / peaks()[0]["hbm_gbs"],
+                          "kernel_tflops": tfl, "tensor_frac": tfl / tpeak,
+                          "call_tensor_frac": float(N) * float(N) * Ks / (tot / 20 / 1e3) / 1e12 / tpeak})
+    return small
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -553,8 +606,14 @@ def main():
         def only_gsce():
             c, seg_in, R_host = make_workload(0)
             return gsce_extra(td, torch, seg_in, torch.from_numpy(R_host).cuda(), R_host.shape[0])
+        def only_small():
+            c, seg_in, R_host = make_workload(0)
+            seg = td.Segment(seg_in.acf, seg_in.mask)
+            return small_batches(td, torch, seg, torch.from_numpy(R_host).cuda(), R_host.shape[1],
+                                 td.TD_PREC_BF16X6, "bf16x6")
         fn = {"grouped": lambda: grouped_extra(td, torch), "serving": lambda: serving_extra(td, torch, args.serve_seconds),
-              "gapped3": lambda: gapped_joint_extra(td, torch), "refine": only_refine, "gsce": only_gsce}[args.only]
+              "gapped3": lambda: gapped_joint_extra(td, torch), "refine": only_refine, "gsce": only_gsce,
+              "small": only_small}[args.only]
         print(json.dumps({"only": args.only, "result": fn()}), flush=True)
         return
 
@@ -663,44 +722,8 @@ def main():
         fp64 = {"value": K / (ms64 / 1e3), "unit": UNIT, "ms_per_step": ms64,
                 "max_abs_dlogL_vs_oracle": golden_dlogl(logL.cpu().numpy()) if rank == 0 else None}
 
-    # small batches: rows split into chunks so the operator streams from HBM
-    small = []
-    if args.precision in ("bf16x6", "bf16x10"):
-        nsl = 3 if args.precision == "bf16x6" else 4
-        op_bytes = (N // 256) * ((N // 256) + 1) // 2 * 8 * nsl * 256 * 32 * 2   # operator slices read once
-        for Ks in (1, 8, 64, 256):
-            Rs = R[:Ks].contiguous()
-            ls = torch.empty(Ks, dtype=torch.float64, device="cuda")
-            cand = [("auto", td.TD_PATH_AUTO), ("stream256", td.TD_PATH_STREAM),
-                    ("stream128", td.TD_PATH_STREAM128)]
-            if Ks >= 64:
-                cand.append(("tensor128", td.TD_PATH_TENSOR128))
-            for pname, path in cand:
-                o2 = td.options(precision=prec, path=path)
-                for _ in range(3):
-                    seg.loglike_into(Rs, ls, o2)
-                torch.cuda.synchronize()
-                # no L2 flush: the operator streamed by every call (201 MB at N'=8192) is larger
-                # than L2 (126 MB); calls are back to back, as a sampler issues them
-                ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                ea.record(stream)
-                for _ in range(20):
-                    seg.loglike_into(Rs, ls, o2)
-                eb.record(stream)
-                torch.cuda.synchronize()
-                tot = ea.elapsed_time(eb)
-                seg.profile(True)
-                for _ in range(20):
-                    seg.loglike_into(Rs, ls, o2)
-                torch.cuda.synchronize()
-                kms, kn, _ = seg.profile_read()
-                seg.profile(False)
-                kavg = kms / max(kn, 1)
-                gbs = op_bytes / (kavg / 1e3) / 1e9
-                small.append({"K": Ks, "path": pname, "kernel_ms": kavg, "call_ms": tot / 20,
-                              "evals_per_s": Ks / (tot / 20 / 1e3),
-                              "operator_GBps": gbs, "hbm_frac": gbs / peaks()[0]["hbm_gbs"],
-                              "call_hbm_frac": op_bytes / (tot / 20 / 1e3) / 1e9 / peaks()[0]["hbm_gbs"]})
+    # small and mid-size batches on the same segment
+    small = small_batches(td, torch, seg, R, N, prec, args.precision)
 
     if rank != 0:
         if world > 1:
@@ -752,7 +775,8 @@ def main():
                                   "20 calls back to back; no L2 flush (the operator read by each call is larger "
                                   "than L2); algorithmic bytes = operator slices read once (3 x 2 B per packed "
                                   "lower-triangle element); hbm_frac = of the kernel, call_hbm_frac = of the "
-                                  "whole call, both of measured HBM bandwidth",
+                                  "whole call, both of measured HBM bandwidth; kernel_tflops = N'^2 K / kernel "
+                                  "time, tensor_frac / call_tensor_frac = of measured bf16 burst / products",
                           "runs": small},
         "clocks": clk,
     }

@@ -27,7 +27,9 @@ Residuals arrive as float32 and are promoted exactly to float64 (the FP32
 rounding of d - h is part of the input, not an error of the method).
 
 Also here (the NEXT rows of the hot path, Sec. II.B item 7 and Sec. III.A):
-matched-filter and effective SNR definitions.
+matched-filter and effective SNR definitions, and the detector projection and
+placement of a template (Sec. II.B waveform conditioning, Sec. III.A data
+projection and conditioning).
 """
 from __future__ import annotations
 
@@ -159,6 +161,37 @@ def eff_snr2(seg: OracleSegment, d, h) -> float:
     """rho_eff^2 = <d, d> - <r, r>, r = d - h."""
     r = np.asarray(d) - np.asarray(h)
     return inner(seg, d, d) - inner(seg, r, r)
+
+
+# ---------------------------------------------------------------------------
+# Detector projection and placement of a template (Sec. II.B, waveform
+# conditioning; Sec. III.A, data projection and conditioning)
+# ---------------------------------------------------------------------------
+def project_template(n: int, hp, hc, fp: float, fc: float, offset: int) -> np.ndarray:
+    """Detector-frame template on the segment's n sample times, FP64.
+
+    The polarizations are combined with the detector's antenna factors,
+    h = fp h_plus + fc h_cross, and the result is placed so that waveform
+    sample u lands on segment sample t = u + offset; segment samples that no
+    waveform sample reaches are zero (the zero padding that positions the
+    peak).  Waveform samples that fall outside the segment are dropped.
+    hc = None means no cross polarization."""
+    hp = np.asarray(hp, dtype=np.float64)
+    lw = hp.shape[0]
+    h = np.zeros(n)
+    t = np.arange(n)
+    u = t - int(offset)
+    on = (u >= 0) & (u < lw)
+    h[on] = fp * hp[u[on]]
+    if hc is not None:
+        h[on] = h[on] + fc * np.asarray(hc, dtype=np.float64)[u[on]]
+    return h
+
+
+def projected_residual(seg: OracleSegment, d_kept, hp, hc, fp: float, fc: float, offset: int) -> np.ndarray:
+    """r = d - h over the kept samples, FP64 (d given on the kept samples)."""
+    h = project_template(seg.n, hp, hc, fp, fc, offset)
+    return np.asarray(d_kept, dtype=np.float64) - h[seg.kept]
 
 
 # ---------------------------------------------------------------------------

@@ -233,6 +233,34 @@ def template_batch(seg: Segment, K: int, seed: int) -> np.ndarray:
     return H
 
 
+def polarization_batch(seg: Segment, K: int, lw: int, seed: int):
+    """Polarizations of K chirps on a waveform grid of lw samples at the
+    segment's rate, with the coalescence on the last sample (h_plus with the
+    cos phase, h_cross with the sin phase, the segment's injection amplitude),
+    and per-template detector inputs: antenna factors F_plus, F_cross uniform
+    in [-1, 1] and integer offsets (segment sample of waveform sample 0) that
+    put the coalescence anywhere from before the segment's start to after its
+    end.  Returns hp, hc float32 (K, lw); fp, fc float64 (K,); off int64 (K,)."""
+    rng = np.random.default_rng(seed)
+    th = draw_theta(rng, seg.n / seg.fs, K)
+    t = np.arange(lw, dtype=np.float64) / seg.fs
+    tc = lw / seg.fs
+    hp = np.zeros((K, lw), dtype=np.float32)
+    hc = np.zeros((K, lw), dtype=np.float32)
+    for k in range(K):
+        tau = tc - t
+        on = tau > 1.0 / seg.fs
+        ta = tau[on]
+        phase = th[k, 2] - 2.0 * (ta / (5.0 * TSUN * th[k, 0])) ** 0.625
+        amp = seg.amp * ta ** (-0.25)
+        hp[k, on] = (amp * np.cos(phase)).astype(np.float32)
+        hc[k, on] = (amp * np.sin(phase)).astype(np.float32)
+    fp = rng.uniform(-1.0, 1.0, K)
+    fc = rng.uniform(-1.0, 1.0, K)
+    off = rng.integers(-lw // 4, seg.n - lw + lw // 4, K).astype(np.int64)
+    return hp, hc, fp, fc, off
+
+
 def noise_residuals(n: int, fs: float, K: int, seed: int, mask: np.ndarray | None = None,
                     a: float = -4.0, floor: float = 2.0, scale: float = 1.0) -> np.ndarray:
     """K pure-noise residuals on the kept samples, float32 (K, n')."""

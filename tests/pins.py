@@ -15,7 +15,10 @@ by mathematics rather than by the oracle itself:
   conjugate gradients on FFT matvecs;
 * invariants -- PSD scale, time reversal, mirrored gaps, spectral bounds;
 * a library density -- scipy's multivariate-normal log-density of the
-  block-diagonal covariance of two gapped detectors (Sec. II.B item 3).
+  block-diagonal covariance of two gapped detectors (Sec. II.B item 3);
+* detector projection and placement -- energy of a placed waveform, nothing
+  subtracted outside the segment or inside a gap, the plain template form as
+  a special case, linearity in the antenna factors.
 
 None of these call the oracle's own routines to produce an expected value.
 """
@@ -381,6 +384,55 @@ def check_mvn_joint(orc, seed=20):
     assert np.allclose(got, expect, rtol=1e-10, atol=1e-8), (got, expect)
 
 
+# ---------------------------------------------------------------------------
+# detector projection and placement of a template (Sec. II.B waveform
+# conditioning, Sec. III.A data projection and conditioning)
+# ---------------------------------------------------------------------------
+def check_projection(orc, seed=21):
+    rng = np.random.default_rng(seed)
+    n, lw, s2 = 160, 48, 1.9
+    hp = rng.standard_normal(lw)
+    hc = rng.standard_normal(lw)
+    fp, fc = 0.62, -0.47
+    white = orc.OracleSegment(inputs.white_acf(n, s2))
+    zero = np.zeros(n)
+    # placed fully inside the segment, anywhere: the energy of the detector
+    # signal is fp^2|hp|^2 + 2 fp fc <hp, hc> + fc^2 |hc|^2, so with d = 0 and
+    # white noise chi2 = that / s2 whatever the offset
+    energy = fp * fp * (hp @ hp) + 2 * fp * fc * (hp @ hc) + fc * fc * (hc @ hc)
+    for off in (0, 1, 37, n - lw):
+        r = orc.projected_residual(white, zero, hp, hc, fp, fc, off)
+        assert abs(float(white.chi2(r[None, :])[0]) - energy / s2) < 1e-10 * energy / s2, off
+    # outside the segment entirely (before or after): nothing is subtracted
+    d = rng.standard_normal(n)
+    for off in (n, n + 5, -lw, -lw - 9):
+        assert np.array_equal(orc.projected_residual(white, d, hp, hc, fp, fc, off), d), off
+    # fp = 1, fc = 0, offset 0 and a waveform as long as the segment: the plain
+    # template form d - h, sample for sample
+    hfull = rng.standard_normal(n)
+    r = orc.projected_residual(white, d, hfull, None, 1.0, 0.0, 0)
+    assert np.array_equal(r, d - hfull)
+    # partly outside: only the overlap is subtracted (first and last samples)
+    r = orc.projected_residual(white, zero, hp, None, 1.0, 0.0, -10)
+    assert np.array_equal(-r[:lw - 10], hp[10:]) and np.all(r[lw - 10:] == 0)
+    r = orc.projected_residual(white, zero, hp, None, 1.0, 0.0, n - 10)
+    assert np.array_equal(-r[n - 10:], hp[:10]) and np.all(r[:n - 10] == 0)
+    # linear in the antenna factors
+    a = orc.projected_residual(white, zero, hp, hc, 1.0, 0.0, 20)
+    b = orc.projected_residual(white, zero, hp, hc, 0.0, 1.0, 20)
+    c = orc.projected_residual(white, zero, hp, hc, fp, fc, 20)
+    assert np.allclose(c, fp * a + fc * b, rtol=0, atol=1e-14)
+    # gaps: a waveform that lies inside a gap subtracts nothing; one that
+    # straddles the gap's edge keeps exactly its samples on kept times
+    mask = np.ones(n, np.uint8)
+    mask[60:120] = 0
+    g = orc.OracleSegment(inputs.white_acf(n, s2), mask)
+    dk = rng.standard_normal(int(mask.sum()))
+    assert np.array_equal(orc.projected_residual(g, dk, hp, hc, fp, fc, 65), dk)
+    r = orc.projected_residual(g, np.zeros(int(mask.sum())), hp, None, 1.0, 0.0, 40)
+    assert np.array_equal(-r[40:60], hp[:20]) and np.all(r[60:] == 0) and np.all(r[:40] == 0)
+
+
 ALL_CHECKS = [
     ("white", lambda o: (check_white(o, gaps=False), check_white(o, gaps=True))),
     ("ar1", lambda o: check_ar1(o, gaps=False)),
@@ -392,4 +444,5 @@ ALL_CHECKS = [
     ("scaling", check_scaling),
     ("reversal", check_reversal),
     ("mvn_joint", check_mvn_joint),
+    ("projection", check_projection),
 ]

@@ -113,3 +113,39 @@ def test_pins_catch_planted_mistake(kind):
         except AssertionError:
             failed.append(name)
     assert failed, f"no pin caught the planted mistake {kind}"
+
+
+def _projection_mutant(kind):
+    def project(n, hp, hc, fp, fc, offset):
+        hp = np.asarray(hp, dtype=np.float64)
+        hc = None if hc is None else np.asarray(hc, dtype=np.float64)
+        lw = hp.shape[0]
+        h = np.zeros(n)
+        for t in range(n):
+            u = {"off_by_one": t - offset + 1, "offset_sign": t + offset}.get(kind, t - offset)
+            if kind == "wrap":
+                u %= lw
+            elif not 0 <= u < lw:
+                continue
+            v = fp * hp[u]
+            if hc is not None and kind != "drop_cross":
+                v += fc * (hp[u] if kind == "cross_on_plus" else hc[u])
+            h[t] = v
+        return h
+
+    def projected_residual(seg, d_kept, hp, hc, fp, fc, offset):
+        return np.asarray(d_kept, dtype=np.float64) - project(seg.n, hp, hc, fp, fc, offset)[seg.kept]
+
+    ns = types.SimpleNamespace(**{k: getattr(td_oracle, k) for k in dir(td_oracle) if not k.startswith("__")})
+    ns.project_template = project
+    ns.projected_residual = projected_residual
+    return ns
+
+
+@pytest.mark.parametrize("kind", ["off_by_one", "offset_sign", "wrap", "drop_cross", "cross_on_plus"])
+def test_projection_pin_catches_planted_mistake(kind):
+    """Each plausible slip in the projection and placement fails the pin
+    (the unmutated loop form of the same definition passes it)."""
+    pins.check_projection(_projection_mutant("none"))
+    with pytest.raises(AssertionError):
+        pins.check_projection(_projection_mutant(kind))

@@ -294,6 +294,33 @@ td_status td_template_batch(td_segment* s, const float* H, int64_t ldh, int64_t 
                             const td_template_out* out, const td_options* opt, void* stream);
 
 /*
+ * td_project_batch -- the template form with the detector projection and the
+ * placement of each template done on the device, ahead of the same path
+ * (Sec. II.B, waveform conditioning: zeros around the waveform place its
+ * peak at the requested time; Sec. III.A, data projection and conditioning:
+ * h = F_plus h_plus + F_cross h_cross).  For template k and segment sample t
+ * (0 <= t < n; only kept samples are used):
+ *   u = t - offset[k];
+ *   h_k(t) = fp[k] hp[k ldw + u] + fc[k] hc[k ldw + u]   if 0 <= u < lw, else 0,
+ * in float64 rounded one operation at a time; the residual is fl32(d - h_k)
+ * at the kept samples (d from td_set_data) and, when <h, h> is asked for, the
+ * template fl32(h_k) is whitened in the same batch.  Outputs as for
+ * td_template_batch.  The polarizations of a network's detectors are the same
+ * arrays: one upload of hp, hc serves every detector's segment.
+ *   hp, hc : device float32, template k's waveform at hp + k ldw (lw samples at
+ *            the segment's rate); hc = NULL: no cross polarization (fc unused).
+ *   ldw    : >= max(lw, 1).   lw >= 0 (lw = 0: h = 0).
+ *   fp, fc : device float64[K] antenna factors.
+ *   offset : device int64[K], the segment sample of waveform sample 0 (any
+ *            value; waveform samples outside the segment or in a gap drop out).
+ * Asynchronous on `stream`; buffers as td_template_batch (K <= 65535).
+ * TD_ERR_INVALID for NULL or inconsistent arguments or without td_set_data.
+ */
+td_status td_project_batch(td_segment* s, const float* hp, const float* hc, int64_t ldw, int64_t lw,
+                           int64_t K, const double* fp, const double* fc, const int64_t* offset,
+                           const td_template_out* out, const td_options* opt, void* stream);
+
+/*
  * td_loglike_batch_noalloc -- the same evaluation as td_loglike_batch with the
  * default options, for callers that cannot allocate device memory while they
  * run: an application whose device memory is all reserved by its own caching

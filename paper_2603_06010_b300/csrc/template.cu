@@ -7,7 +7,9 @@
 // <d, d> is computed once by td_set_data.  A batch forms r_k = d - h_k (the
 // FP64 difference rounded once to FP32) and, when <h, h> is asked for,
 // appends the templates themselves; both go through td_loglike_batch, and
-// <d, h> = (<d, d> + <h, h> - chi2) / 2.
+// <d, h> = (<d, d> + <h, h> - chi2) / 2.  td_project_batch forms the templates
+// on the device from polarizations, antenna factors and sample offsets
+// (detector projection and placement, fused ahead of the same path).
 #include <algorithm>
 #include <string>
 
@@ -28,6 +30,34 @@ __global__ void k_form_residuals(const double* __restrict__ d, const float* __re
     const float hv = H[k * ldh + i];
     R[k * nk + i] = (float)(d[i] - (double)hv);
     if (with_h) R[(K + k) * nk + i] = hv;
+  }
+}
+
+// Detector projection and placement (Sec. II.B waveform conditioning; Sec.
+// III.A data projection and conditioning), gathered to the kept samples:
+//   h_k(t) = fp[k] hp[k][t - off[k]] + fc[k] hc[k][t - off[k]]  for 0 <= t - off[k] < lw, else 0
+//   R[:, k] = fl32(d - h_k(t_j)),  R[:, K + k] = fl32(h_k(t_j)) when with_h.
+// FP64 products and sum rounded one operation at a time (no contraction), so
+// a host computing fp*hp + fc*hc - then d - h in float64 gets the same R.
+__global__ void k_project_residuals(const double* __restrict__ d, const int32_t* __restrict__ t,
+                                    const float* __restrict__ hp, const float* __restrict__ hc, int64_t ldw,
+                                    int64_t lw, const double* __restrict__ fp, const double* __restrict__ fc,
+                                    const int64_t* __restrict__ off, int64_t nk, int64_t K, int with_h,
+                                    float* __restrict__ R) {
+  const int64_t k = blockIdx.y;
+  const double a = fp[k], b = hc ? fc[k] : 0.0;
+  const int64_t o = off[k];
+  const float* wp = hp + k * ldw;
+  const float* wc = hc ? hc + k * ldw : nullptr;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t u = (int64_t)t[i] - o;
+    double h = 0.0;
+    if (u >= 0 && u < lw) {
+      h = __dmul_rn(a, (double)wp[u]);
+      if (wc) h = __dadd_rn(h, __dmul_rn(b, (double)wc[u]));
+    }
+    R[k * nk + i] = (float)__dsub_rn(d[i], h);
+    if (with_h) R[(K + k) * nk + i] = (float)h;
   }
 }
 
@@ -104,26 +134,63 @@ extern "C" td_status td_data_inner(const td_segment* s, double* dd) {
   return TD_OK;
 }
 
+// the batch of residuals (and templates) already in T.R through the dense path
+static td_status template_tail(td_segment* s, int64_t K, int with_h, const td_template_out* out,
+                               const td_options* opt, void* stream) {
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  TemplateState& T = s->tpl;
+  const int64_t Kt = with_h ? 2 * K : K;
+  double* ll = T.res;
+  double* c2 = T.res + Kt;
+  td_status r;
+  if ((r = td_loglike_batch(s, T.R, s->nk, Kt, ll, opt, c2, stream)) != TD_OK) return r;
+  k_template_finalize<<<(unsigned)ceil_div(K, 256), 256, 0, st>>>(ll, c2, K, with_h, T.dd, *out);
+  TD_CUDA(cudaGetLastError());
+  return TD_OK;
+}
+
+static td_status template_buffers(td_segment* s, int64_t K, int with_h) {
+  TemplateState& T = s->tpl;
+  const int64_t Kt = with_h ? 2 * K : K;
+  td_status r;
+  if ((r = grow((void**)&T.R, T.R_cap, (size_t)Kt * s->nk * 4, "template residuals")) != TD_OK) return r;
+  return grow((void**)&T.res, T.res_cap, (size_t)2 * Kt * 8, "template results");
+}
+
 extern "C" td_status td_template_batch(td_segment* s, const float* H, int64_t ldh, int64_t K,
                                        const td_template_out* out, const td_options* opt, void* stream) {
   if (!s || !out || K < 0 || (K > 0 && (!H || !out->logL))) return fail(TD_ERR_INVALID, "bad arguments");
   if (!s->tpl.has_data) return fail(TD_ERR_INVALID, "no data vector set (td_set_data)");
   if (K == 0) return TD_OK;
   if (ldh < s->nk) return fail(TD_ERR_INVALID, "ldh < N'");
+  if (K > 65535) return fail(TD_ERR_INVALID, "at most 65535 templates per call");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   TemplateState& T = s->tpl;
   const int with_h = (out->hh || out->dh || out->rho_mf) ? 1 : 0;
-  const int64_t Kt = with_h ? 2 * K : K;
   td_status r;
-  if ((r = grow((void**)&T.R, T.R_cap, (size_t)Kt * s->nk * 4, "template residuals")) != TD_OK) return r;
-  if ((r = grow((void**)&T.res, T.res_cap, (size_t)2 * Kt * 8, "template results")) != TD_OK) return r;
-  if (K > 65535) return fail(TD_ERR_INVALID, "at most 65535 templates per call");
+  if ((r = template_buffers(s, K, with_h)) != TD_OK) return r;
   k_form_residuals<<<dim3(row_blocks(s->nk), (unsigned)K), 256, 0, st>>>(T.d, H, ldh, s->nk, K, with_h, T.R);
   TD_CUDA(cudaGetLastError());
-  double* ll = T.res;
-  double* c2 = T.res + Kt;
-  if ((r = td_loglike_batch(s, T.R, s->nk, Kt, ll, opt, c2, stream)) != TD_OK) return r;
-  k_template_finalize<<<(unsigned)ceil_div(K, 256), 256, 0, st>>>(ll, c2, K, with_h, T.dd, *out);
+  return template_tail(s, K, with_h, out, opt, stream);
+}
+
+extern "C" td_status td_project_batch(td_segment* s, const float* hp, const float* hc, int64_t ldw, int64_t lw,
+                                      int64_t K, const double* fp, const double* fc, const int64_t* offset,
+                                      const td_template_out* out, const td_options* opt, void* stream) {
+  if (!s || !out || K < 0 || lw < 0) return fail(TD_ERR_INVALID, "bad arguments");
+  if (K > 0 && (!out->logL || !hp || !fp || !offset || (hc && !fc)))
+    return fail(TD_ERR_INVALID, "NULL argument (hp, fp, offset, logL; fc with hc)");
+  if (!s->tpl.has_data) return fail(TD_ERR_INVALID, "no data vector set (td_set_data)");
+  if (K == 0) return TD_OK;
+  if (ldw < lw || ldw < 1) return fail(TD_ERR_INVALID, "ldw < lw");
+  if (K > 65535) return fail(TD_ERR_INVALID, "at most 65535 templates per call");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  TemplateState& T = s->tpl;
+  const int with_h = (out->hh || out->dh || out->rho_mf) ? 1 : 0;
+  td_status r;
+  if ((r = template_buffers(s, K, with_h)) != TD_OK) return r;
+  k_project_residuals<<<dim3(row_blocks(s->nk), (unsigned)K), 256, 0, st>>>(T.d, s->t, hp, hc, ldw, lw, fp, fc,
+                                                                           offset, s->nk, K, with_h, T.R);
   TD_CUDA(cudaGetLastError());
-  return TD_OK;
+  return template_tail(s, K, with_h, out, opt, stream);
 }

@@ -49,6 +49,7 @@ SIGNATURES = {
     "td_set_data": (_c.c_int, [_vp, _vp, _vp, _vp]),
     "td_data_inner": (_c.c_int, [_vp, _c.POINTER(_c.c_double)]),
     "td_template_batch": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
+    "td_project_batch": (_c.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "td_group_create": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp, _c.POINTER(_vp)]),
     "td_group_set_joint": (_c.c_int, [_vp, _vp]),
     "td_gs_prepare": (_c.c_int, [_vp, _vp]),
@@ -250,6 +251,20 @@ class Segment:
         _check(lib().td_template_batch(self.handle, H.data_ptr(), int(H.stride(0)), int(H.shape[0]),
                                        ctypes.byref(out), None if opt is None else ctypes.byref(opt),
                                        _stream_ptr(stream)))
+
+    def project_into(self, hp, hc, fp, fc, offset, logL, chi2=None, hh=None, dh=None, rho_mf=None,
+                     rho_eff2=None, lw=None, opt: TdOptions | None = None, stream=None):
+        """td_project_batch: hp, hc CUDA float32 (K, ldw) (hc may be None);
+        fp, fc CUDA float64 (K,); offset CUDA int64 (K,); outputs CUDA float64
+        (K,) or None.  lw defaults to hp's row length."""
+        p = (lambda x: None if x is None else x.data_ptr())
+        out = TemplateOut(p(logL), p(chi2), p(hh), p(dh), p(rho_mf), p(rho_eff2))
+        if hc is not None and hc.stride(0) != hp.stride(0):
+            raise ValueError("hp and hc need the same leading dimension")
+        lw = int(hp.shape[1]) if lw is None else int(lw)
+        _check(lib().td_project_batch(self.handle, hp.data_ptr(), p(hc), int(hp.stride(0)), lw, int(hp.shape[0]),
+                                      fp.data_ptr(), p(fc), offset.data_ptr(), ctypes.byref(out),
+                                      None if opt is None else ctypes.byref(opt), _stream_ptr(stream)))
 
     def profile(self, enable: bool = True):
         _check(lib().td_profile_enable(self.handle, 1 if enable else 0))

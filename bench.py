@@ -196,6 +196,30 @@ def template_extra(td, torch, seg, seg_in, K):
     res.update({"note": f"K={K} chirp templates per call on the gap-free N=8192 segment; <d,d> once "
                         "(td_set_data); SNR outputs whiten the templates in the same batch (2K columns)",
                 "set_data_ms": set_ms, "rho_mf_max": float(np.max(rho))})
+    # the same call with the detector projection and placement on the device
+    # (td_project_batch): polarizations of lw = N/2 samples, antenna factors and
+    # sample offsets per template
+    lw = seg_in.n // 2
+    hp, hc, fp, fc, off = inputs.polarization_batch(seg_in, K, lw, 7071)
+    hpd, hcd = torch.from_numpy(hp).cuda(), torch.from_numpy(hc).cuda()
+    fpd, fcd, offd = torch.from_numpy(fp).cuda(), torch.from_numpy(fc).cuda(), torch.from_numpy(off).cuda()
+    for _ in range(3):
+        seg.project_into(hpd, hcd, fpd, fcd, offd, outs["logL"])
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(10):
+        seg.project_into(hpd, hcd, fpd, fcd, offd, outs["logL"])
+    b.record()
+    torch.cuda.synchronize()
+    seg.check()
+    ms = a.elapsed_time(b) / 10
+    res["projected"] = {"ms_per_call": ms, "templates_per_s": K / (ms / 1e3), "waveform_samples": lw,
+                        "h2d_bytes_per_template_3det": 2 * lw * 4,
+                        "h2d_bytes_per_template_3det_detector_frame": 3 * seg_in.n_kept * 4,
+                        "note": "td_project_batch: F+ h+ + Fx hx placed at an integer sample offset and "
+                                "gathered on the device; a network's detectors share one upload of the "
+                                "two polarizations instead of one detector-frame template each"}
     return res
 
 

@@ -164,12 +164,37 @@ td_status td_segment_create(const double* acf, int64_t n, const uint8_t* mask,
 td_status td_factor(td_segment* s, void* stream);
 
 /*
- * Free the segment's FP64 factor (L and its diagonal-tile inverses), keeping
- * the whitening operator slices and log det: the tensor-core paths keep
- * working, the FP64 path then returns TD_ERR_UNSUPPORTED.  Saves 8 N'^2
- * bytes of device memory.  Synchronises the device.
+ * Free the segment's FP64 factor (L and its diagonal-tile inverses), and the
+ * refinement's slices of L if a refined call made them, keeping the whitening
+ * operator slices and log det: the tensor-core paths keep working, the FP64
+ * path and refinement then return TD_ERR_UNSUPPORTED.  Saves 8 N'^2 bytes of
+ * device memory (more with the refinement state).  Synchronises the device.
  */
 td_status td_segment_release_fp64(td_segment* s);
+
+/*
+ * Factor checkpoint and resume.  The factor is the O(N'^3) step of the
+ * method (Sec. II.A; Sec. III.A: computed once and cached); these calls keep
+ * it across device evictions and process restarts.
+ * td_segment_save -- write the segment's evaluation state to the file `path`:
+ *   the ACF and kept indices, and whichever of these are resident: the
+ *   whitening operator slices and log det (after td_factor or
+ *   td_factor_many), the FP64 factor L with its diagonal-tile inverses
+ *   (unless released), the Gohberg-Semencul spectra (after td_gs_prepare).
+ *   The file is written as "<path>.tmp" and renamed onto `path`, so a failed
+ *   save leaves no partial file.  Device reads are ordered on `stream` and the
+ *   call synchronises it.  TD_ERR_NOT_FACTORED when there is nothing to save;
+ *   TD_ERR_INVALID when the file cannot be written.
+ * td_segment_load -- create a new segment on the current device from such a
+ *   file, with the same resident state; its results are bit-identical to the
+ *   saved segment's.  The header (magic, version, sizes) is checked against
+ *   the file size before any device work, and a 64-bit FNV-1a checksum of
+ *   the payload after it has been read: a wrong, truncated or corrupted file
+ *   returns TD_ERR_INVALID and *out = NULL.  The caller owns *out
+ *   (td_segment_destroy).  Synchronises `stream`.
+ */
+td_status td_segment_save(const td_segment* s, const char* path, void* stream);
+td_status td_segment_load(const char* path, void* stream, td_segment** out);
 
 /*
  * td_factor_many -- factor several segments.  flags = 0: td_factor on each.

@@ -594,6 +594,7 @@ td_status td_segment_release_fp64(td_segment* s) {
   dev_free(s->L);
   dev_free(s->dinv);
   dev_free(s->scr.w64);
+  free_refine_state(s);   // the slices of L go with L: refinement then returns TD_ERR_UNSUPPORTED
   return TD_OK;
 }
 

@@ -50,6 +50,8 @@ SIGNATURES = {
     "td_data_inner": (_c.c_int, [_vp, _c.POINTER(_c.c_double)]),
     "td_template_batch": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "td_project_batch": (_c.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "td_segment_save": (_c.c_int, [_vp, _c.c_char_p, _vp]),
+    "td_segment_load": (_c.c_int, [_c.c_char_p, _vp, _vp]),
     "td_group_create": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp, _c.POINTER(_vp)]),
     "td_group_set_joint": (_c.c_int, [_vp, _vp]),
     "td_gs_prepare": (_c.c_int, [_vp, _vp]),
@@ -164,6 +166,20 @@ class Segment:
 
     def factor(self, stream=None):
         _check(lib().td_factor(self.handle, _stream_ptr(stream)))
+
+    def save(self, path, stream=None):
+        """td_segment_save: the resident evaluation state to a file."""
+        _check(lib().td_segment_save(self.handle, os.fsencode(path), _stream_ptr(stream)))
+
+    @classmethod
+    def load(cls, path, stream=None) -> "Segment":
+        """td_segment_load: a new segment from a file written by save()."""
+        h = ctypes.c_void_p()
+        _check(lib().td_segment_load(os.fsencode(path), _stream_ptr(stream), ctypes.byref(h)))
+        seg = cls.__new__(cls)
+        seg.handle = h
+        seg.n = None
+        return seg
 
     @property
     def n_kept(self) -> int:

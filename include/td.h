@@ -326,11 +326,11 @@ td_status td_template_batch(td_segment* s, const float* H, int64_t ldh, int64_t 
  * h = F_plus h_plus + F_cross h_cross).  For template k and segment sample t
  * (0 <= t < n; only kept samples are used):
  *   u = t - offset[k];
- *   h_k(t) = fp[k] hp[k ldw + u] + fc[k] hc[k ldw + u]   if 0 <= u < lw, else 0,
- * in float64 rounded one operation at a time; the residual is fl32(d - h_k)
- * at the kept samples (d from td_set_data) and, when <h, h> is asked for, the
- * template fl32(h_k) is whitened in the same batch.  Outputs as for
- * td_template_batch.  The polarizations of a network's detectors are the same
+ *   h_k(t) = fl32(fl32(fp[k] hp[k ldw + u]) + fl32(fc[k] hc[k ldw + u]))   if 0 <= u < lw, else 0,
+ * with fp[k], fc[k] rounded to float32 first (float32 products and sum, no
+ * fused multiply-add); the residual is fl32(d - h_k) at the kept samples (d
+ * from td_set_data), so the results equal td_template_batch on those
+ * templates bit for bit.  Outputs as for td_template_batch.  The polarizations of a network's detectors are the same
  * arrays: one upload of hp, hc serves every detector's segment.
  *   hp, hc : device float32, template k's waveform at hp + k ldw (lw samples at
  *            the segment's rate); hc = NULL: no cross polarization (fc unused).

@@ -36,28 +36,33 @@ __global__ void k_form_residuals(const double* __restrict__ d, const float* __re
 // Detector projection and placement (Sec. II.B waveform conditioning; Sec.
 // III.A data projection and conditioning), gathered to the kept samples:
 //   h_k(t) = fp[k] hp[k][t - off[k]] + fc[k] hc[k][t - off[k]]  for 0 <= t - off[k] < lw, else 0
-//   R[:, k] = fl32(d - h_k(t_j)),  R[:, K + k] = fl32(h_k(t_j)) when with_h.
-// FP64 products and sum rounded one operation at a time (no contraction), so
-// a host computing fp*hp + fc*hc - then d - h in float64 gets the same R.
+//   R[:, k] = fl32(d - h_k(t_j)),  R[:, K + k] = h_k(t_j) when with_h.
+// h is formed in FP32 (antenna factors rounded to FP32, products and sum
+// rounded one operation at a time, no contraction) and subtracted from d in
+// FP64 as in td_template_batch: the batch equals td_template_batch on the
+// templates fl32(fl32(fp hp) + fl32(fc hc)) built anywhere, bit for bit.  The
+// FP32 sum adds one rounding of h, the size of the FP32 rounding of r itself;
+// FP64 products here would cost more than the whole residual pass (FP64 runs
+// at about 1.2 TFLOP/s on this GPU).
 __global__ void k_project_residuals(const double* __restrict__ d, const int32_t* __restrict__ t,
                                     const float* __restrict__ hp, const float* __restrict__ hc, int64_t ldw,
                                     int64_t lw, const double* __restrict__ fp, const double* __restrict__ fc,
                                     const int64_t* __restrict__ off, int64_t nk, int64_t K, int with_h,
                                     float* __restrict__ R) {
   const int64_t k = blockIdx.y;
-  const double a = fp[k], b = hc ? fc[k] : 0.0;
+  const float a = (float)fp[k], b = hc ? (float)fc[k] : 0.f;
   const int64_t o = off[k];
   const float* wp = hp + k * ldw;
   const float* wc = hc ? hc + k * ldw : nullptr;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk; i += (int64_t)gridDim.x * blockDim.x) {
     const int64_t u = (int64_t)t[i] - o;
-    double h = 0.0;
+    float h = 0.f;
     if (u >= 0 && u < lw) {
-      h = __dmul_rn(a, (double)wp[u]);
-      if (wc) h = __dadd_rn(h, __dmul_rn(b, (double)wc[u]));
+      h = __fmul_rn(a, wp[u]);
+      if (wc) h = __fadd_rn(h, __fmul_rn(b, wc[u]));
     }
-    R[k * nk + i] = (float)__dsub_rn(d[i], h);
-    if (with_h) R[(K + k) * nk + i] = (float)h;
+    R[k * nk + i] = (float)(d[i] - (double)h);
+    if (with_h) R[(K + k) * nk + i] = h;
   }
 }
 

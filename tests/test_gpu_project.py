@@ -69,10 +69,10 @@ def test_project_matches_oracle(torch_cuda, gpu_lib, gaps, lw):
     seg.close()
 
 
-def test_project_equals_residual_path_bitwise(torch_cuda, gpu_lib):
-    """The fused residuals are fl32(d - (fp hp + fc hc)) with one rounding per
-    float64 operation: the batch path on that R, built here in float64 numpy,
-    gives the same bits."""
+def test_project_equals_template_path_bitwise(torch_cuda, gpu_lib):
+    """The fused templates are fl32(fl32(fp hp) + fl32(fc hc)) placed and
+    gathered: td_template_batch on those templates, built here with float32
+    numpy, gives the same bits for every output."""
     from paper_2603_06010_b300 import td
     n, K, lw = 1500, 50, 900
     seg_in = inputs.make_segment(n, 2048.0, 7300, n_gaps=1, gap_len=150)
@@ -80,21 +80,22 @@ def test_project_equals_residual_path_bitwise(torch_cuda, gpu_lib):
     d = seg_in.d[seg_in.kept]
     seg = td.Segment(seg_in.acf, seg_in.mask)
     seg.set_data(d)
-    R = np.empty((K, seg_in.n_kept), np.float32)
+    H = np.zeros((K, seg_in.n_kept), np.float32)
     t = seg_in.kept
     for k in range(K):
         u = t - off[k]
         on = (u >= 0) & (u < lw)
-        h = np.zeros(t.size)
-        h[on] = fp[k] * hp[k, u[on]].astype(np.float64) + fc[k] * hc[k, u[on]].astype(np.float64)
-        R[k] = (d - h).astype(np.float32)
+        H[k, on] = np.float32(fp[k]) * hp[k, u[on]] + np.float32(fc[k]) * hc[k, u[on]]
     hpd, hcd, fpd, fcd, offd = _dev(torch_cuda, hp, hc, fp, fc, off)
-    ll_p = torch_cuda.empty(K, dtype=torch_cuda.float64, device="cuda")
-    seg.project_into(hpd, hcd, fpd, fcd, offd, ll_p)
-    ll_r = seg.loglike(torch_cuda.from_numpy(R).cuda(), td.options())
+    a, b = _outs(torch_cuda, K), _outs(torch_cuda, K)
+    seg.project_into(hpd, hcd, fpd, fcd, offd, a["logL"], chi2=a["chi2"], hh=a["hh"], dh=a["dh"],
+                     rho_mf=a["rho_mf"], rho_eff2=a["rho_eff2"])
+    seg.template_into(torch_cuda.from_numpy(H).cuda(), b["logL"], chi2=b["chi2"], hh=b["hh"], dh=b["dh"],
+                      rho_mf=b["rho_mf"], rho_eff2=b["rho_eff2"])
     torch_cuda.cuda.synchronize()
     seg.check()
-    assert np.array_equal(ll_p.cpu().numpy(), ll_r.cpu().numpy())
+    for key in a:
+        assert torch_cuda.equal(a[key], b[key]), key
     seg.close()
 
 

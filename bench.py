@@ -266,6 +266,29 @@ def gapped_joint_extra(td, torch):
         pass
     nk = segs[0].n_kept
     g.close()
+    # factor checkpoint and resume: detector 0 (its operator) to a file and back,
+    # against the factor it replaces; the loaded segment must give the same bits
+    import tempfile
+    ck = {}
+    with tempfile.TemporaryDirectory() as tmpd:
+        path = os.path.join(tmpd, "det0.ckpt")
+        t1 = time.perf_counter()
+        segs[0].save(path)
+        ck["save_s"] = time.perf_counter() - t1
+        ck["file_bytes"] = os.path.getsize(path)
+        t1 = time.perf_counter()
+        loaded = td.Segment.load(path)
+        ck["load_s"] = time.perf_counter() - t1
+        a_ll = torch.empty(c["K"], dtype=torch.float64, device="cuda")
+        b_ll = torch.empty(c["K"], dtype=torch.float64, device="cuda")
+        segs[0].loglike_into(Rs[0], a_ll)
+        loaded.loglike_into(Rs[0], b_ll)
+        torch.cuda.synchronize()
+        ck["same_bits"] = bool(torch.equal(a_ll, b_ll))
+        loaded.close()
+    ck["factor_s_per_detector"] = factor_s / len(segs)
+    ck["note"] = ("td_segment_save / td_segment_load of one N'=14848 detector (operator slices; FP64 factor "
+                  "released), file in a temporary directory, against the FP64 factor it replaces")
     for sg in segs:
         sg.close()
     return {"note": "3 detectors, N=16384 with 3 gaps of 512 (N'=14848), K=1024 each; one captured grouped "
@@ -273,7 +296,7 @@ def gapped_joint_extra(td, torch):
             "ms_per_launch": ms, "joint_evals_per_s": c["K"] / (ms / 1e3),
             "detector_evals_per_s": 3 * c["K"] / (ms / 1e3),
             "algorithmic_tflops": 3 * float(nk) ** 2 * c["K"] / (ms / 1e3) / 1e12,
-            "max_abs_dlogL_joint_vs_oracle": dlogl, "factor_s": factor_s}
+            "max_abs_dlogL_joint_vs_oracle": dlogl, "factor_s": factor_s, "checkpoint": ck}
 
 
 def grouped_extra(td, torch):

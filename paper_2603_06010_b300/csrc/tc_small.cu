@@ -112,7 +112,13 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
   __shared__ double sh_part[4][NC];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  pdl_trigger();   // the reduction kernel may be scheduled now; it waits for this grid
+  // The reduction kernel may be scheduled once every CTA has triggered (it
+  // waits for this grid's completion in any case).  Small batches trigger at
+  // once, so its few CTAs are resident before the product ends.  From 128
+  // columns its grid is units x K/4 CTAs; resident early they would hold SM
+  // slots that kernels of other streams (a server's other requests) need for
+  // the whole product, so those CTAs trigger when their last item is done.
+  if constexpr (NC < 128) pdl_trigger();
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -328,6 +334,7 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
       ++tl;
     }
   }
+  if constexpr (NC >= 128) pdl_trigger();
   tc_fence_before();
   __syncthreads();
   if (warp == 1) {

@@ -4,12 +4,15 @@
  *
  * Input file:  int64 n, int64 K, int64 has_mask, double acf[n],
  *              uint8 mask[n] (if has_mask), float R[K][N'] (column k = residual k)
- * Output file: double logL[K], double chi2[K], double logdet
+ * Output file: double logL[K], double chi2[K], double logdet, double same
+ *   (same = 1 when a segment saved to "<output>.ckpt" with td_segment_save and
+ *   read back with td_segment_load gives the same log L bits, else 0)
  * Exit status 0 on success; a td_status or CUDA failure prints td_last_error(). */
 #include <cuda_runtime_api.h>
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <string.h>
 
 #include "td.h"
 
@@ -71,13 +74,30 @@ int main(int argc, char** argv) {
   CHECK_TD(td_loglike_batch(s, dR, nk, K, dL, &opt, dC, NULL));
   CHECK_TD(td_check(s, NULL));
 
-  double* out = (double*)malloc((size_t)(2 * K + 1) * sizeof(double));
+  double* out = (double*)malloc((size_t)(2 * K + 2) * sizeof(double));
   CHECK_CUDA(cudaMemcpy(out, dL, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost));
   CHECK_CUDA(cudaMemcpy(out + K, dC, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost));
   out[2 * K] = logdet;
+
+  /* factor checkpoint and resume through the same ABI */
+  char* ckpt = (char*)malloc(strlen(argv[2]) + 6);
+  sprintf(ckpt, "%s.ckpt", argv[2]);
+  CHECK_TD(td_segment_save(s, ckpt, NULL));
+  td_segment* s2 = NULL;
+  CHECK_TD(td_segment_load(ckpt, NULL, &s2));
+  CHECK_TD(td_loglike_batch(s2, dR, nk, K, dL, &opt, NULL, NULL));
+  CHECK_TD(td_check(s2, NULL));
+  double* again = (double*)malloc((size_t)K * sizeof(double));
+  CHECK_CUDA(cudaMemcpy(again, dL, (size_t)K * sizeof(double), cudaMemcpyDeviceToHost));
+  out[2 * K + 1] = memcmp(again, out, (size_t)K * sizeof(double)) == 0 ? 1.0 : 0.0;
+  td_segment_destroy(s2);
+  remove(ckpt);
+  free(ckpt);
+  free(again);
+
   f = fopen(argv[2], "wb");
   if (!f) return 1;
-  fwrite(out, sizeof(double), (size_t)(2 * K + 1), f);
+  fwrite(out, sizeof(double), (size_t)(2 * K + 2), f);
   fclose(f);
 
   cudaFree(dR);

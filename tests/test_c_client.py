@@ -50,7 +50,8 @@ def test_c_client_matches_oracle(tmp_path):
     r = subprocess.run([exe, str(inp), str(outp)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stderr
     out = np.fromfile(outp, np.float64)
-    logL, chi2, logdet = out[:K], out[K:2 * K], out[2 * K]
+    logL, chi2, logdet, same = out[:K], out[K:2 * K], out[2 * K], out[2 * K + 1]
+    assert same == 1.0, "segment saved and loaded through the C ABI gave different bits"
     o = oracle.OracleSegment(acf, mask)
     exp_chi = o.chi2(R)
     assert abs(logdet - o.logdet) <= 1e-9 * abs(o.logdet)

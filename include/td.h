@@ -264,6 +264,19 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
                            void* stream);
 
 /*
+ * td_loglike_batch_gather -- td_loglike_batch for residuals given at every
+ * sample of the segment (gaps included): R is device float32, column-major
+ * n x K, leading dimension ldr >= n; the kept rows (Sec. II.B items 1-2: gap
+ * samples are deleted) are gathered on the device into a buffer the segment
+ * owns (it grows on first use for a given K and is freed with the segment),
+ * then evaluated exactly as td_loglike_batch on them (same results, bit for
+ * bit).  K <= 65535 per call.  Asynchronous on `stream`.
+ */
+td_status td_loglike_batch_gather(td_segment* s, const float* R, int64_t ldr, int64_t K,
+                                  double* logL, const td_options* opt, double* chi2,
+                                  void* stream);
+
+/*
  * td_loglike_batch_host -- the same evaluation with HOST buffers (the
  * batched evaluation of Sec. III.A fed from CPU memory).
  *   R    : host, float32, column-major N' x K, leading dimension ldr >= N'.

@@ -661,6 +661,7 @@ void td_segment_destroy(td_segment* s) {
   free_plans(s->scr);
   free_host_stage(s->hst);
   free_template_state(s->tpl);
+  if (s->gat) cudaFree(s->gat);
   free_refine_state(s);
   free_gs_state(s);
   for (cudaEvent_t e : s->ev) cudaEventDestroy(e);

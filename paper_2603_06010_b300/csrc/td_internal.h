@@ -207,6 +207,8 @@ struct td_segment {
   td::Scratch scr;
   HostStage hst;
   TemplateState tpl;
+  float* gat = nullptr;    // td_loglike_batch_gather: kept rows of a full-length batch [cap][N']
+  int64_t gat_cap = 0;     // columns
   RefineState ref;
   GsState gs;
   // instrumentation

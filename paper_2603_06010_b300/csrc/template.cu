@@ -66,6 +66,14 @@ __global__ void k_project_residuals(const double* __restrict__ d, const int32_t*
   }
 }
 
+// G[:, k] = R[t_j, k]: the kept rows of a full-length column-major batch
+__global__ void k_gather_kept(const float* __restrict__ R, int64_t ldr, const int32_t* __restrict__ t, int64_t nk,
+                              float* __restrict__ G) {
+  const int64_t k = blockIdx.y;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nk; i += (int64_t)gridDim.x * blockDim.x)
+    G[k * nk + i] = R[k * ldr + t[i]];
+}
+
 __global__ void k_template_finalize(const double* __restrict__ ll, const double* __restrict__ c2, int64_t K,
                                     int with_h, double dd, td_template_out out) {
   const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -198,4 +206,28 @@ extern "C" td_status td_project_batch(td_segment* s, const float* hp, const floa
                                                                            offset, s->nk, K, with_h, T.R);
   TD_CUDA(cudaGetLastError());
   return template_tail(s, K, with_h, out, opt, stream);
+}
+
+extern "C" td_status td_loglike_batch_gather(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL,
+                                             const td_options* opt, double* chi2, void* stream) {
+  if (!s || K < 0 || (K > 0 && (!R || !logL))) return fail(TD_ERR_INVALID, "bad arguments");
+  if (K == 0) return TD_OK;
+  if (ldr < s->n) return fail(TD_ERR_INVALID, "ldr < n (full-length columns)");
+  if (K > 65535) return fail(TD_ERR_INVALID, "at most 65535 columns per call");
+  if (!s->factored && !s->gs.ready) return fail(TD_ERR_NOT_FACTORED, "segment not factored");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  if (K > s->gat_cap) {
+    cudaStreamSynchronize(st);   // the old buffer may still be read on this stream
+    if (s->gat) cudaFree(s->gat);
+    s->gat = nullptr;
+    s->gat_cap = 0;
+    if (cudaMalloc((void**)&s->gat, (size_t)K * s->nk * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      return fail(TD_ERR_OOM, "gather buffer");
+    }
+    s->gat_cap = K;
+  }
+  k_gather_kept<<<dim3(row_blocks(s->nk), (unsigned)K), 256, 0, st>>>(R, ldr, s->t, s->nk, s->gat);
+  TD_CUDA(cudaGetLastError());
+  return td_loglike_batch(s, s->gat, s->nk, K, logL, opt, chi2, stream);
 }

@@ -51,6 +51,7 @@ SIGNATURES = {
     "td_template_batch": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "td_project_batch": (_c.c_int, [_vp, _vp, _vp, _i64, _i64, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
     "td_segment_save": (_c.c_int, [_vp, _c.c_char_p, _vp]),
+    "td_loglike_batch_gather": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
     "td_segment_load": (_c.c_int, [_c.c_char_p, _vp, _vp]),
     "td_group_create": (_c.c_int, [_vp, _vp, _vp, _vp, _vp, _vp, _c.c_int, _vp, _vp, _c.POINTER(_vp)]),
     "td_group_set_joint": (_c.c_int, [_vp, _vp]),
@@ -166,6 +167,13 @@ class Segment:
 
     def factor(self, stream=None):
         _check(lib().td_factor(self.handle, _stream_ptr(stream)))
+
+    def loglike_gather_into(self, R, logL, opt: TdOptions | None = None, chi2=None, stream=None):
+        """td_loglike_batch_gather: R CUDA float32 (K, ldr >= n), every sample of the
+        segment; the kept rows are gathered on the device."""
+        _check(lib().td_loglike_batch_gather(self.handle, R.data_ptr(), int(R.stride(0)), int(R.shape[0]),
+                                             logL.data_ptr(), None if opt is None else ctypes.byref(opt),
+                                             None if chi2 is None else chi2.data_ptr(), _stream_ptr(stream)))
 
     def save(self, path, stream=None):
         """td_segment_save: the resident evaluation state to a file."""

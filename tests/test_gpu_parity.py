@@ -416,3 +416,37 @@ def test_many_column_tiles(torch_cuda, gpu_lib):
     ll, chi = _run(torch_cuda, td, seg, R, "bf16x10")
     exp_chi = o.chi2(R)
     _compare("bf16x10", ll, chi, oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept), exp_chi, "K=20000")
+
+
+@pytest.mark.parametrize("gaps", [0, 3])
+def test_gather_entry_point_equals_kept_rows(torch_cuda, gpu_lib, gaps):
+    """td_loglike_batch_gather on full-length residuals (gap samples included)
+    gives the bits of td_loglike_batch on their kept rows, and the oracle's
+    values within the bar; bad leading dimensions are refused."""
+    from paper_2603_06010_b300 import td
+    n, K = 1800, 45
+    seg_in = inputs.make_segment(n, 2048.0, 9100 + gaps, n_gaps=gaps, gap_len=150)
+    rng = np.random.default_rng(9101)
+    Rfull = (rng.standard_normal((K, n + 7)) * np.sqrt(seg_in.acf[0])).astype(np.float32)   # ldr = n + 7
+    Rkept = np.ascontiguousarray(Rfull[:, seg_in.kept])
+    seg = td.Segment(seg_in.acf, seg_in.mask)
+    a = torch_cuda.empty(K, dtype=torch_cuda.float64, device="cuda")
+    c = torch_cuda.empty(K, dtype=torch_cuda.float64, device="cuda")
+    seg.loglike_gather_into(torch_cuda.from_numpy(Rfull).cuda(), a, chi2=c)
+    b = seg.loglike(torch_cuda.from_numpy(Rkept).cuda(), td.options())
+    torch_cuda.cuda.synchronize()
+    seg.check()
+    assert torch_cuda.equal(a, b)
+    o = oracle.OracleSegment(seg_in.acf, seg_in.mask)
+    exp = o.chi2(Rkept)
+    _compare("bf16x6", a.cpu().numpy(), c.cpu().numpy(), oracle.loglike_from_chi2(exp, o.logdet, o.n_kept), exp,
+             f"gather gaps={gaps}")
+    out = torch_cuda.full((K,), 7.0, dtype=torch_cuda.float64, device="cuda")
+    Rd = torch_cuda.from_numpy(Rfull).cuda()
+    L = td.lib()
+    assert L.td_loglike_batch_gather(seg.handle, Rd.data_ptr(), n - 1, K, out.data_ptr(), None, None,
+                                     None) == td.TD_ERR_INVALID
+    assert L.td_loglike_batch_gather(seg.handle, Rd.data_ptr(), n, 0, out.data_ptr(), None, None, None) == td.TD_OK
+    torch_cuda.cuda.synchronize()
+    assert np.all(out.cpu().numpy() == 7.0)
+    seg.close()

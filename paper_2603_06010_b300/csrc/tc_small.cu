@@ -334,9 +334,9 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
       ++tl;
     }
   }
-  if constexpr (NC >= 128) pdl_trigger();
   tc_fence_before();
   __syncthreads();
+  if constexpr (NC >= 128) pdl_trigger();   // after every role of this CTA is done
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();

@@ -16,6 +16,8 @@ by mathematics rather than by the oracle itself:
 * invariants -- PSD scale, time reversal, mirrored gaps, spectral bounds;
 * a library density -- scipy's multivariate-normal log-density of the
   block-diagonal covariance of two gapped detectors (Sec. II.B item 3);
+* LU on a gapped coloured segment (N' = 1299) -- chi2 and log det by numpy
+  solve / slogdet;
 * detector projection and placement -- energy of a placed waveform, nothing
   subtracted outside the segment or inside a gap, the plain template form as
   a special case, linearity in the antenna factors.
@@ -433,6 +435,29 @@ def check_projection(orc, seed=21):
     assert np.array_equal(-r[40:60], hp[:20]) and np.all(r[60:] == 0) and np.all(r[:40] == 0)
 
 
+# ---------------------------------------------------------------------------
+# gapped coloured segment at moderate N': chi2 = r^T C^{-1} r and log det C by
+# LU (numpy solve / slogdet), a factorisation the oracle does not use
+# ---------------------------------------------------------------------------
+def check_lu_gapped(orc, n=1500, fs=2048.0, seed=22):
+    from scipy import linalg
+    rng = np.random.default_rng(seed)
+    mask = np.ones(n, np.uint8)
+    mask[200:330] = 0
+    mask[900:971] = 0
+    keep = np.flatnonzero(mask)
+    acf = inputs.acf_from_psd(n, fs)
+    C = linalg.toeplitz(acf)[np.ix_(keep, keep)]
+    R = (rng.standard_normal((3, keep.size)) * 5).astype(np.float32)
+    seg = orc.OracleSegment(acf, mask)
+    X = np.linalg.solve(C, R.astype(np.float64).T)
+    chi2 = np.einsum("ij,ij->j", R.astype(np.float64).T, X)
+    sign, ld = np.linalg.slogdet(C)
+    assert sign > 0
+    assert abs(seg.logdet - ld) < 1e-9 * abs(ld), (seg.logdet, ld)
+    assert np.allclose(seg.chi2(R), chi2, rtol=1e-10), (seg.chi2(R), chi2)
+
+
 ALL_CHECKS = [
     ("white", lambda o: (check_white(o, gaps=False), check_white(o, gaps=True))),
     ("ar1", lambda o: check_ar1(o, gaps=False)),
@@ -445,4 +470,5 @@ ALL_CHECKS = [
     ("reversal", check_reversal),
     ("mvn_joint", check_mvn_joint),
     ("projection", check_projection),
+    ("lu_gapped", check_lu_gapped),
 ]

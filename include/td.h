@@ -154,12 +154,18 @@ td_status td_segment_create(const double* acf, int64_t n, const uint8_t* mask,
 /*
  * td_factor -- C_kept = L L^T (Sec. II.A; Sec. III.A "Factorization of the
  * covariance matrix": once per segment, cached).  Blocked right-looking
- * Cholesky in FP64 on the device, then log det C = 2 sum log L_ii (FP64),
- * then the whitening operator L^{-1} (FP64) and its bf16 slices for the
- * tensor-core path.  All results stay resident on the device and are owned
- * by the segment.  Synchronises `stream`.
+ * Cholesky in blocks of 128 that carries the identity along, so the same
+ * eliminations give the whitening operator L^{-1}; each block's factor and
+ * inverse are FP64 on the CUDA cores, and the O(N'^3) panel and trailing
+ * updates are FP64-accurate split products on the bf16 tensor cores (six
+ * exact bf16 slices per FP64 operand row, about 2^-46 of sum |a||b| per
+ * product; TD_FACTOR_FP64_CORES in td_factor_many selects the all-FP64
+ * CUDA-core route instead).  Then log det C = 2 sum log L_ii (FP64) and the
+ * operator's bf16 slices for the per-evaluation paths.  All results stay
+ * resident on the device and are owned by the segment.  Synchronises `stream`.
  * Returns TD_ERR_NOT_PD if a pivot is <= 0 or not finite; td_last_pivot
  * then gives the 0-based kept-sample index of the first failing pivot.
+ * TD_ERR_TIMEOUT if a bounded in-kernel wait ran out (2 s).
  */
 td_status td_factor(td_segment* s, void* stream);
 
@@ -211,6 +217,9 @@ td_status td_segment_load(const char* path, void* stream, td_segment** out);
  * `stream`; TD_ERR_NOT_PD as td_factor (td_last_pivot gives the order).
  */
 #define TD_FACTOR_NO_FP64 1
+#define TD_FACTOR_FP64_CORES 2   /* factor segments that take the Cholesky on the FP64 CUDA cores
+                                    (64-wide blocks, L^{-1} by forward substitution; several times
+                                    slower than the default tensor-core route; FP64 arithmetic throughout) */
 td_status td_factor_many(td_segment* const* segs, int nseg, int flags, void* stream);
 
 /*
@@ -359,8 +368,11 @@ td_status td_project_batch(td_segment* s, const float* hp, const float* hc, int6
                            const td_template_out* out, const td_options* opt, void* stream);
 
 /*
- * td_loglike_batch_noalloc -- the same evaluation as td_loglike_batch with the
- * default options, for callers that cannot allocate device memory while they
+ * td_loglike_batch_noalloc -- the evaluation td_loglike_batch makes with the
+ * default precision (TD_PREC_AUTO: six split products, ten below 512 and above
+ * 32768 kept samples) on one fixed tile shape (64 operator rows per tile), so
+ * results agree with td_loglike_batch within rounding, not bit for bit; for
+ * callers that cannot allocate device memory while they
  * run: an application whose device memory is all reserved by its own caching
  * pool, a process under a hard device-memory cap, or a latency-critical loop
  * that must not enter cudaMalloc (which can synchronise the device).  This call
@@ -369,7 +381,8 @@ td_status td_project_batch(td_segment* s, const float* hp, const float* hc, int6
  * every GPU that loads the library holds until the process exits.  The paper
  * has no counterpart; it is a property of this library's interface.
  *   Arguments as for td_loglike_batch (R, ldr, K, logL, chi2 caller-owned,
- *   device memory).  The segment must be factored (td_factor allocates).
+ *   device memory).  The segment must be factored (td_factor allocates) with
+ *   its operator resident (else TD_ERR_NOT_FACTORED).
  *   Size limit: 8 K N8 + 8 K ceil(N'/256) * 4 bytes must fit (N8 = N' rounded
  *   up to 8, the slices' row rounded to 256 bytes), e.g. N' = 8192 with K up
  *   to 504;
@@ -466,13 +479,18 @@ void td_segment_destroy(td_segment* s);
  * the next batch of their segment); batches of different segments run
  * concurrently.  Whitening operators stay resident in HBM under
  * resident_bytes_budget with LRU eviction; an evicted operator is kept in
- * pinned host memory and copied back on its next use.  All calls are
- * thread-safe.  Results of a request are within the library's accuracy bar of
- * the same request evaluated alone (the batch's tile shape depends on its
- * width).
+ * pinned host memory and copied back on its next use.  Operators live in the
+ * server's stream-ordered device pool and their spill copies in a pinned
+ * host pool reserved at creation (host_spill_bytes), so eviction (an
+ * asynchronous copy out, the first time, and a release to the pool) and
+ * reload (an asynchronous copy in) synchronise neither the host nor the
+ * device while serving.  All calls are thread-safe.  Results of a request are within the
+ * library's accuracy bar of the same request evaluated alone; bit-identical
+ * with `deterministic` set.
  *   add_segment: host acf/mask as td_segment_create; the factor is computed on
  *     first use or by td_server_prefetch (synchronous; also reserves scratch
- *     for max_batch_cols).  The FP64 factor is released after factoring.
+ *     and builds the work lists for batches up to max_batch_cols, so serving
+ *     allocates nothing).  The FP64 factor is released after factoring.
  *   submit: R (device, float32, N' x K column-major, leading dimension ldr) and
  *     logL (device, float64[K]) are caller-owned and must stay valid until the
  *     request completes; 1 <= K <= max_batch_cols.  Returns TD_ERR_BUSY when
@@ -500,20 +518,37 @@ typedef struct {
                                     batches that TD_PATH_AUTO sends to GSCE (K <= 256, or
                                     N >= 24576) then run without loading the dense operator
                                     (O(N) device memory for such segments).  Default 0. */
-  int reserved0;
+  int deterministic;             /* nonzero: every batch takes one fixed path per segment (the
+                                    small-batch kernel in chunks of at most 256 columns; no GSCE),
+                                    so a request's logL is bit-identical alone and in any mix of
+                                    other requests (a column's arithmetic then depends on its own
+                                    values and its segment only).  Default 0: the automatic path,
+                                    whose tile shape follows the batch width (results agree within
+                                    the accuracy bar, not bit for bit). */
+  int64_t host_spill_bytes;      /* pinned host memory reserved at creation for the spill copies of
+                                    evicted operators (carved per segment at its first eviction);
+                                    beyond it each copy is pinned on its own (cudaMallocHost, which
+                                    blocks the scheduler).  Default 0. */
 } td_server_config;
 typedef struct {
   double p50_us, p99_us, max_us, evals_per_s;
   int64_t requests_done, evals, batches, hits, misses, evictions, refused, failed, resident_bytes;
+  int64_t reloads;               /* misses served by copying a spilled operator back from pinned host memory */
 } td_server_stats;
 void td_server_config_default(td_server_config* c);
 td_status td_server_create(const td_server_config* cfg, td_server** out);
 td_status td_server_add_segment(td_server* srv, const double* acf, int64_t n, const uint8_t* mask,
                                 int64_t* seg_id);
 td_status td_server_prefetch(td_server* srv, int64_t seg_id);
+/* Change the HBM budget for resident operators (0 = unlimited); segments are
+ * evicted, least recently used first, as later batches need room. */
+td_status td_server_set_budget(td_server* srv, int64_t resident_bytes_budget);
 td_status td_server_submit(td_server* srv, int64_t seg_id, const float* R, int64_t ldr, int64_t K,
                            double* logL, int64_t* ticket);
 td_status td_server_poll(td_server* srv, int64_t ticket, int* state);
+/* Latency of a finished request (submission to completion, microseconds);
+ * TD_ERR_BUSY while it is not done. */
+td_status td_server_latency(td_server* srv, int64_t ticket, double* us);
 td_status td_server_wait(td_server* srv, int64_t ticket, int64_t timeout_us);
 td_status td_server_cancel(td_server* srv, int64_t ticket);
 td_status td_server_pause(td_server* srv, int paused);

@@ -202,13 +202,15 @@ def time_per_eval_path(seg: OracleSegment, R_kn, threads: int | None = None,
     """Time whiten + chi2 + logL for the columns of R_kn on `threads` BLAS
     threads (default: all host cores).  Returns (seconds, threads_used)."""
     import contextlib
-    threads = threads or (os.cpu_count() or 1)
+    ncpu = os.cpu_count() or 1
+    threads = threads or ncpu
     try:
         from threadpoolctl import threadpool_limits
         ctx = threadpool_limits(limits=threads)
-    except ImportError:          # BLAS then uses its default: all host cores
+    except ImportError:
+        if threads < ncpu:       # a thread count below the BLAS default cannot be honoured
+            raise RuntimeError("threadpoolctl is needed to time the oracle on fewer than all host cores")
         ctx = contextlib.nullcontext()
-        threads = os.cpu_count() or 1
     with ctx:
         reps = 0
         t0 = time.perf_counter()

@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import glob
+import hashlib
 import os
 import subprocess
 import sys
@@ -24,16 +25,32 @@ def deps() -> list[str]:
                               + glob.glob(os.path.join(HERE, "..", "include", "*.h")))
 
 
+STAMP = os.path.join(HERE, "_build", "libtd.sha256")
+
+
+def source_hash() -> str:
+    """SHA-256 over the compiler command and every source and header, by content."""
+    h = hashlib.sha256()
+    h.update(" ".join([NVCC, *ARCH, *FLAGS]).encode())
+    for d in deps():
+        h.update(os.path.relpath(d, HERE).encode())
+        with open(d, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    """True when libtd.so was built from exactly the current sources (content hash, not mtime)."""
+    if not (os.path.exists(LIB) and os.path.exists(STAMP)):
         return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in deps())
+    with open(STAMP) as f:
+        return f.read().strip() == source_hash()
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
     if not force and up_to_date():
         return LIB
+    digest = source_hash()   # of the sources this build compiles
     objdir = os.path.join(HERE, "_build")
     os.makedirs(objdir, exist_ok=True)
     objs = []
@@ -59,6 +76,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-Xcompiler", "-fPIC"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(digest + "\n")
     return LIB
 
 

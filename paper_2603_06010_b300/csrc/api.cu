@@ -45,7 +45,7 @@ static td_status get_encode(PFN_cuTensorMapEncodeTiled_v12000* out) {
   return TD_OK;
 }
 
-static td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2,
+td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2,
                            uint64_t s1_bytes, uint64_t s2_bytes, uint32_t b0, uint32_t b1, uint32_t b2) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   td_status st = get_encode(&enc);
@@ -69,10 +69,11 @@ static td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint6
 // residual-slice map (A operand: a box of a_rows residual columns) and operator
 // map (B operand, tiles of bn rows) of one segment
 td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out, int a_rows,
-                          const __nv_bfloat16* op) {
+                          const __nv_bfloat16* op, const Scratch* sc) {
+  if (!sc) sc = &s->scr;
   out->a_rows = a_rows;
-  td_status st = encode_3d(&out->mapA, s->scr.rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES,
-                           (uint64_t)s->nkp8 * 2, (uint64_t)s->scr.capK * s->nkp8 * 2, OP_KB, (uint32_t)a_rows,
+  td_status st = encode_3d(&out->mapA, sc->rs, (uint64_t)s->nk, (uint64_t)K, OP_SLICES,
+                           (uint64_t)s->nkp8 * 2, (uint64_t)sc->capK * s->nkp8 * 2, OP_KB, (uint32_t)a_rows,
                            1);
   if (st != TD_OK) return st;
   return encode_3d(&out->mapB, op ? op : s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
@@ -147,24 +148,58 @@ static td_status check_device(const td_segment* s) {
 // rows one column's chi2 can rest on a single row, whose six-product value is
 // good to ~6e-8 relative, so chi2 can miss 1e-7 (1.15e-7 measured at N' = 47);
 // many rows average that away.  Small segments cost little either way.
-static int nslices_for(int precision, int64_t nk) {
+int nslices_for(int precision, int64_t nk) {
   if (precision == TD_PREC_AUTO) return (nk > 32768 || nk < 512) ? 4 : 3;
   return precision == TD_PREC_BF16X3 ? 2 : (precision == TD_PREC_BF16X10 ? 4 : 3);
 }
 
+static void free_plan(SplitPlan& p) {
+  dev_free(p.items);
+  dev_free(p.units);
+  dev_free(p.segdev);
+  dev_free(p.counters);
+}
+
 static void free_plans(Scratch& sc) {
-  for (SplitPlan& p : sc.plans) {
-    dev_free(p.items);
-    dev_free(p.units);
-    dev_free(p.segdev);
-    dev_free(p.counters);
-  }
+  for (SplitPlan& p : sc.plans) free_plan(p);
   sc.plans.clear();
 }
 
-// Grow the per-segment scratch so batches of K columns fit.
-static td_status ensure_scratch(td_segment* s, int64_t K, bool fp64_path, cudaStream_t st) {
-  Scratch& sc = s->scr;
+void scratch_free(Scratch& sc) {
+  free_plans(sc);
+  dev_free(sc.rs);
+  dev_free(sc.partials);
+  dev_free(sc.w64);
+  dev_free(sc.wpart);
+  for (float2*& w : sc.wpart_old) dev_free(w);
+  sc.wpart_old.clear();
+  sc.capK = sc.wpart_slots = sc.rs_elems = sc.part_elems = 0;
+}
+
+// A scratch for any segment of up to max_kept samples and batches of up to
+// maxK columns, allocated once (a server stream's).
+td_status scratch_init_shared(Scratch& sc, int64_t max_kept, int64_t maxK) {
+  const int64_t cap = round_up(std::max<int64_t>(maxK, 1), TC_COLS);
+  const int64_t nkp = round_up(max_kept, OP_ROWS), nkp8 = round_up(max_kept, 8);
+  sc.shared = true;
+  sc.max_plans = 1u << 14;
+  sc.capK = cap;
+  sc.rs_elems = OP_SLICES * cap * nkp8;
+  sc.part_elems = (nkp / FT) * cap;
+  td_status r = dev_alloc(&sc.rs, (size_t)sc.rs_elems, "residual slices");
+  if (r == TD_OK) r = dev_alloc(&sc.partials, (size_t)sc.part_elems, "chi2 partials");
+  return r;
+}
+
+// Grow the scratch so batches of K columns of segment s fit (a shared scratch
+// only checks: it was sized for every segment it may serve).
+static td_status ensure_scratch(td_segment* s, Scratch& sc, int64_t K, bool fp64_path, cudaStream_t st) {
+  if (sc.shared) {
+    if (fp64_path) return fail(TD_ERR_UNSUPPORTED, "the FP64 path runs on the segment's own scratch");
+    if (K > sc.capK || OP_SLICES * sc.capK * s->nkp8 > sc.rs_elems || (s->nkp / FT) * sc.capK > sc.part_elems)
+      return fail(TD_ERR_INVALID, "batch wider or segment longer than the shared scratch was sized for");
+    return TD_OK;
+  }
   if (K > sc.capK) {
     cudaStreamSynchronize(st);   // old buffers may still be in use on this stream
     free_plans(sc);              // their tensor maps point at the old residual slices
@@ -213,21 +248,36 @@ static int64_t plan_width(int64_t K) {
 // device work lists for a 64-row-tile batch of K columns (cached per width)
 // nc > 0: plan for the small-batch kernel (128-row operator tiles as the MMA
 // M dimension, nc residual columns per tile, chi2 partials per 32 rows).
-static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaStream_t st, SplitPlan** out,
-                                int nc = 0) {
-  Scratch& sc = s->scr;
+static td_status get_split_plan(td_segment* s, Scratch& sc, int64_t K, int nsl, int bn, cudaStream_t st,
+                                SplitPlan** out, int nc = 0) {
   ++sc.use_clock;
   const int key_bn = nc > 0 ? -nc : bn;
-  // an operator that was freed and rebuilt or reloaded (re-factor, eviction)
-  // sits at a new address: plans encoded for the old one are dropped
-  for (const SplitPlan& p : sc.plans)
-    if (p.op != (const void*)s->op || p.logdet != s->logdet) {
+  // a re-factored segment (new log det) drops its plans; an operator that only
+  // moved (evicted and reloaded by a server) keeps them: their operator maps
+  // are re-encoded and the descriptors re-uploaded on `st`, with no device
+  // synchronisation (no kernel of this segment runs while its operator moves)
+  for (size_t i = 0; i < sc.plans.size();)
+    if (sc.plans[i].seg == (const void*)s && sc.plans[i].logdet != s->logdet) {
       cudaStreamSynchronize(st);
-      free_plans(sc);
-      break;
+      free_plan(sc.plans[i]);
+      sc.plans.erase(sc.plans.begin() + (long)i);
+    } else {
+      ++i;
     }
   for (SplitPlan& p : sc.plans)
-    if (p.K == K && p.nsl == nsl && p.bn == key_bn) {
+    if (p.seg == (const void*)s && p.op != (const void*)s->op) {
+      td_status rr = encode_3d(&p.host_seg.mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES,
+                               OP_KB * 2, (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, (uint32_t)p.map_bn,
+                               (uint32_t)p.nsl);
+      if (rr != TD_OK) return rr;
+      if (st)
+        TD_CUDA(cudaMemcpyAsync(p.segdev, &p.host_seg, sizeof(TcSegDev), cudaMemcpyHostToDevice, st));
+      else   // the legacy stream: copy synchronously, so streams created non-blocking see it too
+        TD_CUDA(cudaMemcpy(p.segdev, &p.host_seg, sizeof(TcSegDev), cudaMemcpyHostToDevice));
+      p.op = s->op;
+    }
+  for (SplitPlan& p : sc.plans)
+    if (p.seg == (const void*)s && p.K == K && p.nsl == nsl && p.bn == key_bn) {
       p.last_use = sc.use_clock;
       *out = &p;
       return TD_OK;
@@ -244,14 +294,16 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   sort_items(items);
   td_status r;
   if (n_slots * slot_elems > sc.wpart_slots) {   // wpart_slots counts float2 elements
-    cudaStreamSynchronize(st);
-    free_plans(sc);
-    dev_free(sc.wpart);
-    sc.wpart_slots = 0;
-    if ((r = dev_alloc(&sc.wpart, (size_t)(n_slots * slot_elems), "split accumulators")) != TD_OK) return r;
+    // a larger buffer for this and later plans; the older plans keep naming
+    // the old one, which stays allocated with the scratch (their batches run
+    // in stream order on the scratch's stream, so the two are never in use at once)
+    float2* w = nullptr;
+    if ((r = dev_alloc(&w, (size_t)(n_slots * slot_elems), "split accumulators")) != TD_OK) return r;
+    if (sc.wpart) sc.wpart_old.push_back(sc.wpart);
+    sc.wpart = w;
     sc.wpart_slots = n_slots * slot_elems;
   }
-  if (sc.plans.size() >= 24) {   // evict the least recently used plan
+  if (sc.plans.size() >= sc.max_plans) {   // evict the least recently used plan
     size_t lru = 0;
     for (size_t i = 1; i < sc.plans.size(); ++i)
       if (sc.plans[i].last_use < sc.plans[lru].last_use) lru = i;
@@ -263,6 +315,7 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
     sc.plans.erase(sc.plans.begin() + (long)lru);
   }
   SplitPlan p;
+  p.seg = s;
   p.K = K;
   p.nsl = nsl;
   p.bn = key_bn;
@@ -275,7 +328,7 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
   const int a_rows = nc > 0 ? nc : (int)std::min<int64_t>(TC_COLS, round_up(K, 8));
-  if ((r = encode_seg_maps(s, K, nsl, bn, &seg, a_rows)) != TD_OK) return r;
+  if ((r = encode_seg_maps(s, K, nsl, bn, &seg, a_rows, nullptr, &sc)) != TD_OK) return r;
   seg.partials = sc.partials;
   seg.wpart = sc.wpart;
   seg.nk = (int)s->nk;
@@ -298,19 +351,21 @@ static td_status get_split_plan(td_segment* s, int64_t K, int nsl, int bn, cudaS
   if (!units.empty())
     TD_CUDA(cudaMemcpy(p.units, units.data(), units.size() * sizeof(SplitUnit), cudaMemcpyHostToDevice));
   TD_CUDA(cudaMemcpy(p.segdev, &seg, sizeof seg, cudaMemcpyHostToDevice));
+  p.host_seg = seg;
+  p.map_bn = bn;
   p.last_use = sc.use_clock;
   sc.plans.push_back(p);
   *out = &sc.plans.back();
   return TD_OK;
 }
 
-static td_status read_status(td_segment* s, cudaStream_t st, DevStatus* out) {
+td_status read_status(td_segment* s, cudaStream_t st, DevStatus* out) {
   TD_CUDA(cudaMemcpyAsync(out, s->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, st));
   TD_CUDA(cudaStreamSynchronize(st));
   return TD_OK;
 }
 
-static td_status reset_status(td_segment* s, cudaStream_t st) {
+td_status reset_status(td_segment* s, cudaStream_t st) {
   DevStatus h{0, 0, LLONG_MAX};
   TD_CUDA(cudaMemcpyAsync(s->status, &h, sizeof h, cudaMemcpyHostToDevice, st));
   TD_CUDA(cudaStreamSynchronize(st));
@@ -425,75 +480,58 @@ td_status td_factor(td_segment* s, void* stream) {
   if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
   td_status r = check_device(s);
   if (r != TD_OK) return r;
-  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  s->factored = false;
-  s->pivot = -1;
-  free_refine_state(s);   // slices of the old L
-  const int64_t nkp = s->nkp;
-  const int nt = (int)(nkp / FT);
-  if (!s->L && (r = dev_alloc(&s->L, (size_t)(nkp * nkp), "factor L")) != TD_OK) return r;
-  if (!s->dinv && (r = dev_alloc(&s->dinv, (size_t)nt * FT * FT, "diagonal inverses")) != TD_OK) return r;
-  if (!s->ldpart && (r = dev_alloc(&s->ldpart, (size_t)nt, "logdet partials")) != TD_OK) return r;
-  if ((r = reset_status(s, st)) != TD_OK) return r;
-  TD_CUDA(launch_gather(s->acf, s->t, s->nk, nkp, s->L, st));
-  for (int j = 0; j < nt; ++j) {
-    TD_CUDA(launch_potrf_diag(s->L, nkp, s->nk, j, s->dinv, s->ldpart, s->status, st));
-    TD_CUDA(launch_panel(s->L, nkp, j, nt, s->dinv, st));
-    TD_CUDA(launch_syrk(s->L, nkp, j, nt, st));
-  }
-  DevStatus hs;
-  if ((r = read_status(s, st, &hs)) != TD_OK) return r;
-  if (hs.code == ST_NOT_PD) {
-    s->pivot = hs.pivot;
-    char buf[128];
-    snprintf(buf, sizeof buf, "covariance not positive definite at kept sample %lld", (long long)hs.pivot);
-    return fail(TD_ERR_NOT_PD, buf);
-  }
-  std::vector<double> ld((size_t)nt);
-  TD_CUDA(cudaMemcpy(ld.data(), s->ldpart, (size_t)nt * sizeof(double), cudaMemcpyDeviceToHost));
-  double logdet = 0.0;
-  for (int j = 0; j < nt; ++j) logdet += ld[(size_t)j];
-  // whitening operator L^{-1} (FP64), then its bf16 slices
-  double* linv = nullptr;
-  if ((r = dev_alloc(&linv, (size_t)(nkp * nkp), "L^{-1} (temporary)")) != TD_OK) return r;
-  cudaError_t e = cudaMemsetAsync(linv, 0, (size_t)(nkp * nkp) * sizeof(double), st);
-  for (int I = 0; I < nt && e == cudaSuccess; ++I)
-    e = launch_trsm_f64_row(s->L, nkp, s->dinv, I, nullptr, 0, s->nk, nkp, linv, nkp, nullptr, 0, st);
-  const int64_t nm = nkp / OP_ROWS;
-  s->op_blocks = op_row_offset(nm);
-  if (e == cudaSuccess && !s->op) {
-    r = dev_alloc(&s->op, (size_t)(s->op_blocks * OP_SLICES * OP_ROWS * OP_KB), "operator slices");
-    if (r != TD_OK) {
-      cudaFree(linv);
-      return r;
-    }
-  }
-  double* qrow = nullptr;
-  if (e == cudaSuccess && (r = dev_alloc(&qrow, (size_t)nkp, "row quanta")) != TD_OK) {
-    cudaFree(linv);
-    return r;
-  }
-  if (e == cudaSuccess) e = launch_row_quantum(linv, nkp, s->nk, nkp, qrow, st);
-  if (e == cudaSuccess) e = launch_op_slices(linv, nkp, s->nk, nkp, qrow, s->op, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  cudaFree(linv);
-  if (qrow) cudaFree(qrow);
-  if (e != cudaSuccess) return cuda_fail(e, "td_factor operator build");
-  s->logdet = logdet;
-  s->factored = true;
-  return TD_OK;
+  return factor_tensor(s, reinterpret_cast<cudaStream_t>(stream), EMU_SLICES);
 }
 
-td_status td_reserve(td_segment* s, int64_t K, const td_options* opt) {
+}  // extern "C"
+
+namespace td {
+
+td_status reserve_with(td_segment* s, Scratch& sc, int64_t K, const td_options* opt) {
   if (!s || K < 0) return fail(TD_ERR_INVALID, "bad argument");
   td_options o;
   td_options_default(&o);
   if (opt) o = *opt;
-  return ensure_scratch(s, K, o.path == TD_PATH_FP64 || o.precision == TD_PREC_FP64, 0);
+  const bool fp64 = o.path == TD_PATH_FP64 || o.precision == TD_PREC_FP64;
+  td_status r = ensure_scratch(s, sc, K, fp64, 0);
+  if (r != TD_OK || fp64 || !s->factored || !s->op) return r;
+  // the work lists the batch path will use for widths up to K, built now so
+  // that later calls allocate nothing
+  const int nsl = nslices_for(o.precision, s->nk);
+  SplitPlan* plan = nullptr;
+  for (int ncs = 16; ncs <= 256; ncs *= 2)
+    if ((o.path == TD_PATH_AUTO || o.path == TD_PATH_SMALLK) &&
+        (r = get_split_plan(s, sc, ncs, nsl, 128, 0, &plan, ncs)) != TD_OK)
+      return r;
+  for (int64_t k = 8; k <= K; k = (k < TC_COLS) ? 2 * k : k + TC_COLS) {
+    const Shape sh = choose_shape(s, k, o.path);
+    if (sh.bn != 0 && sh.split && (r = get_split_plan(s, sc, plan_width(k), nsl, sh.bn, 0, &plan)) != TD_OK)
+      return r;
+  }
+  return TD_OK;
+}
+
+}  // namespace td
+
+extern "C" {
+
+td_status td_reserve(td_segment* s, int64_t K, const td_options* opt) {
+  if (!s) return fail(TD_ERR_INVALID, "bad argument");
+  return reserve_with(s, s->scr, K, opt);
 }
 
 td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL,
                            const td_options* opt, double* chi2, void* stream) {
+  if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
+  return loglike_batch_with(s, s->scr, R, ldr, K, logL, opt, chi2, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"
+
+namespace td {
+
+td_status loglike_batch_with(td_segment* s, Scratch& sc, const float* R, int64_t ldr, int64_t K, double* logL,
+                             const td_options* opt, double* chi2, cudaStream_t stream) {
   if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
   if (K < 0) return fail(TD_ERR_INVALID, "K < 0");
   if (K > TD_MAX_K) return fail(TD_ERR_INVALID, "K above 2^30 columns");
@@ -519,8 +557,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   if (fp64 && o.refine) return fail(TD_ERR_INVALID, "refinement applies to the split-product paths, not to FP64");
   if (fp64 && !s->L) return fail(TD_ERR_UNSUPPORTED, "the FP64 factor of this segment was released");
   if (!fp64 && !s->op) return fail(TD_ERR_NOT_FACTORED, "the operator of this segment is not resident");
-  if ((r = ensure_scratch(s, K, fp64, st)) != TD_OK) return r;
-  Scratch& sc = s->scr;
+  if ((r = ensure_scratch(s, sc, K, fp64, st)) != TD_OK) return r;
   const int64_t ldp = sc.capK;
   if (fp64) {
     const int nt = (int)(s->nkp / FT);
@@ -535,7 +572,10 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     return TD_OK;
   }
   const int nsl = nslices_for(o.precision, s->nk);
-  if (o.refine) return refine_batch(s, R, ldr, K, logL, chi2, nsl, o.path, o.wait_limit_ns, st);
+  if (o.refine) {
+    if (&sc != &s->scr) return fail(TD_ERR_UNSUPPORTED, "refinement runs on the segment's own scratch");
+    return refine_batch(s, R, ldr, K, logL, chi2, nsl, o.path, o.wait_limit_ns, st);
+  }
   const Shape shape = choose_shape(s, K, o.path);
   const int bn = shape.bn;
   const int ngroups = (int)(s->nkp / 64);
@@ -546,7 +586,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
     if (K > 256) return fail(TD_ERR_UNSUPPORTED, "the small-batch path takes K <= 256");
     const int ncs = K <= 16 ? 16 : (K <= 32 ? 32 : (K <= 64 ? 64 : (K <= 128 ? 128 : 256)));
     SplitPlan* plan = nullptr;
-    if ((r = get_split_plan(s, ncs, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
+    if ((r = get_split_plan(s, sc, ncs, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
     // three launches chained as programmatic dependents: the slicing (which also
     // clears the plan's completion counter), the product, the chunk reduction
     // with chi2 and logL
@@ -562,7 +602,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   if (shape.split) {
     SplitPlan* plan = nullptr;
-    if ((r = get_split_plan(s, plan_width(K), nsl, bn, st, &plan)) != TD_OK) return r;
+    if ((r = get_split_plan(s, sc, plan_width(K), nsl, bn, st, &plan)) != TD_OK) return r;
     if (pm) prof_mark(s, st, true);   // the events bracket the product kernel alone
     TD_CUDA(launch_tc_cdo(plan->items, plan->n_items, plan->segdev, nsl, bn, true, s->status, o.wait_limit_ns,
                           st));
@@ -574,7 +614,7 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   }
   TcSegDev seg;   // whole rows: one segment, implicit item list
   memset(&seg, 0, sizeof seg);
-  if ((r = encode_seg_maps(s, K, nsl, bn, &seg)) != TD_OK) return r;
+  if ((r = encode_seg_maps(s, K, nsl, bn, &seg, TC_COLS, nullptr, &sc)) != TD_OK) return r;
   seg.partials = sc.partials;
   seg.nk = (int)s->nk;
   seg.K = (int)K;
@@ -587,6 +627,10 @@ td_status td_loglike_batch(td_segment* s, const float* R, int64_t ldr, int64_t K
   s->prof_kernels += 3;
   return TD_OK;
 }
+
+}  // namespace td
+
+extern "C" {
 
 td_status td_segment_release_fp64(td_segment* s) {
   if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
@@ -654,11 +698,7 @@ void td_segment_destroy(td_segment* s) {
   dev_free(s->ldpart);
   dev_free(s->op);
   dev_free(s->status);
-  dev_free(s->scr.rs);
-  dev_free(s->scr.partials);
-  dev_free(s->scr.w64);
-  dev_free(s->scr.wpart);
-  free_plans(s->scr);
+  scratch_free(s->scr);
   free_host_stage(s->hst);
   free_template_state(s->tpl);
   if (s->gat) cudaFree(s->gat);

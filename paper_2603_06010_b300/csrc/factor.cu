@@ -5,6 +5,10 @@
 // Storage: A is nkp x nkp column-major FP64 (nkp = N' rounded up to 256).
 // The padding is the identity, so the factor of the padded matrix is
 // blockdiag(L, I) and every 64 x 64 tile is full.
+#include <cstdio>
+#include <string>
+#include <vector>
+
 #include "td_internal.h"
 
 namespace td {
@@ -198,6 +202,107 @@ cudaError_t launch_syrk(double* A, int64_t ld, int j, int nt, cudaStream_t st) {
   const int64_t blocks = m * (m + 1) / 2;
   k_syrk<<<(unsigned)blocks, 256, 0, st>>>(A, ld, j, nt);
   return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- host drivers
+template <class T>
+static td_status falloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return TD_OK;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(TD_ERR_OOM, std::string("device allocation failed: ") + what);
+  }
+  return TD_OK;
+}
+
+td_status factor_begin(td_segment* s, cudaStream_t st) {
+  s->factored = false;
+  s->pivot = -1;
+  free_refine_state(s);   // slices of the old L
+  const int64_t nkp = s->nkp;
+  const int nt = (int)(nkp / FT);
+  td_status r;
+  if (!s->L && (r = falloc(&s->L, (size_t)(nkp * nkp), "factor L")) != TD_OK) return r;
+  if (!s->dinv && (r = falloc(&s->dinv, (size_t)nt * FT * FT, "diagonal inverses")) != TD_OK) return r;
+  if (!s->ldpart && (r = falloc(&s->ldpart, (size_t)nt, "logdet partials")) != TD_OK) return r;
+  if ((r = reset_status(s, st)) != TD_OK) return r;
+  TD_CUDA(launch_gather(s->acf, s->t, s->nk, nkp, s->L, st));
+  return TD_OK;
+}
+
+td_status factor_end(td_segment* s, double* linv, cudaStream_t st) {
+  const int64_t nkp = s->nkp;
+  const int nt = (int)(nkp / FT);
+  DevStatus hs;
+  td_status r = read_status(s, st, &hs);
+  if (r != TD_OK || hs.code == ST_NOT_PD) {
+    cudaFree(linv);
+    if (r != TD_OK) return r;
+    s->pivot = hs.pivot;
+    char buf[128];
+    snprintf(buf, sizeof buf, "covariance not positive definite at kept sample %lld", (long long)hs.pivot);
+    return fail(TD_ERR_NOT_PD, buf);
+  }
+  if (hs.code == ST_TIMEOUT) {
+    cudaFree(linv);
+    reset_status(s, st);
+    return fail(TD_ERR_TIMEOUT, "a bounded in-kernel wait of the factor ran out");
+  }
+  std::vector<double> ld((size_t)nt);
+  cudaError_t e = cudaMemcpy(ld.data(), s->ldpart, (size_t)nt * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    cudaFree(linv);
+    return cuda_fail(e, "log det shares");
+  }
+  double logdet = 0.0;
+  for (int j = 0; j < nt; ++j) logdet += ld[(size_t)j];
+  // bf16 slices of the whitening operator
+  const int64_t nm = nkp / OP_ROWS;
+  s->op_blocks = op_row_offset(nm);
+  if (!s->op && (r = falloc(&s->op, (size_t)(s->op_blocks * OP_SLICES * OP_ROWS * OP_KB), "operator slices")) != TD_OK) {
+    cudaFree(linv);
+    return r;
+  }
+  double* qrow = nullptr;
+  if ((r = falloc(&qrow, (size_t)nkp, "row quanta")) != TD_OK) {
+    cudaFree(linv);
+    return r;
+  }
+  e = launch_row_quantum(linv, nkp, s->nk, nkp, qrow, st);
+  if (e == cudaSuccess) e = launch_op_slices(linv, nkp, s->nk, nkp, qrow, s->op, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(linv);
+  cudaFree(qrow);
+  if (e != cudaSuccess) return cuda_fail(e, "td_factor operator build");
+  s->logdet = logdet;
+  s->factored = true;
+  return TD_OK;
+}
+
+// The FP64 CUDA-core route: 64-wide blocked right-looking Cholesky, then L^{-1}
+// by forward substitution of the identity (both O(N'^3) on DFMA).
+td_status factor_fp64_cores(td_segment* s, cudaStream_t st) {
+  td_status r = factor_begin(s, st);
+  if (r != TD_OK) return r;
+  const int64_t nkp = s->nkp;
+  const int nt = (int)(nkp / FT);
+  for (int j = 0; j < nt; ++j) {
+    TD_CUDA(launch_potrf_diag(s->L, nkp, s->nk, j, s->dinv, s->ldpart, s->status, st));
+    TD_CUDA(launch_panel(s->L, nkp, j, nt, s->dinv, st));
+    TD_CUDA(launch_syrk(s->L, nkp, j, nt, st));
+  }
+  double* linv = nullptr;
+  if ((r = falloc(&linv, (size_t)(nkp * nkp), "L^{-1} (temporary)")) != TD_OK) return r;
+  cudaError_t e = cudaMemsetAsync(linv, 0, (size_t)(nkp * nkp) * sizeof(double), st);
+  for (int I = 0; I < nt && e == cudaSuccess; ++I)
+    e = launch_trsm_f64_row(s->L, nkp, s->dinv, I, nullptr, 0, s->nk, nkp, linv, nkp, nullptr, 0, st);
+  if (e != cudaSuccess) {
+    cudaFree(linv);
+    return cuda_fail(e, "FP64 inverse");
+  }
+  return factor_end(s, linv, st);
 }
 
 }  // namespace td

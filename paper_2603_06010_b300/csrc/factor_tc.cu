@@ -1,0 +1,307 @@
+// The covariance factor C = L L^T and the whitening operator L^{-1} with the
+// O(N'^3) work on the tensor cores (Sec. II.A, C = L L^T and W = L^{-1};
+// Sec. III.A, "Factorization of the covariance matrix": once per segment).
+//
+// Blocked right-looking Cholesky in blocks of b = 128, carrying the identity
+// along so that the same eliminations turn it into L^{-1} (forward
+// substitution of the identity, block row by block row).  Step p:
+//   1. L_pp = chol(A_pp) and X_pp = L_pp^{-1}: one CTA, FP64 (k_potrf_blk)
+//   2. panel   L_{>p,p} = A_{>p,p} X_pp^T                   (split product)
+//      block row of the inverse  X_{p,<p} = X_pp B_{p,<p}   (split product)
+//   3. trailing A_{>p,>p} -= L_{>p,p} L_{>p,p}^T (lower tiles) and
+//      B_{>p,<=p} -= L_{>p,p} X_{p,<=p}                      (split products)
+// where B starts as the identity and block row p of B, once updated by the
+// steps before it, is X_pp^{-1} times block row p of L^{-1}.  The split
+// products are the FP64-accurate emulation on bf16 tensor cores of
+// emu_gemm.cu (contraction 128 = b, so every product is one exact pass);
+// the block factor and its inverse stay in FP64 on the CUDA cores.
+//
+// Storage: L (in place of C) and X = L^{-1} are nkp x nkp column-major FP64
+// (nkp = N' rounded up to 256; identity padding, so both factor as blockdiag
+// with an identity).  Operand slices [ns][rows][128] bf16 per product.
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "emu_gemm.h"
+
+namespace td {
+
+namespace {
+constexpr int PB = EK;                      // block size of the factor (128)
+constexpr int PK_ELEMS = PB * (PB + 1) / 2; // packed lower triangle
+__device__ __forceinline__ int pk(int r, int c) { return c * (2 * PB - 1 - c) / 2 + r; }   // r >= c
+constexpr size_t POTRF_SMEM = (size_t)(2 * PK_ELEMS + 64 * 64) * sizeof(double);
+}  // namespace
+
+// One CTA of 512 threads on the diagonal block p of A (column-major, ld):
+// unblocked right-looking Cholesky in shared memory (packed lower triangle),
+// its inverse by 64-row halves (X11 = L11^{-1}, X22 = L22^{-1} one column per
+// thread, X21 = -X22 L21 X11), then:
+//   A_pp <- L_pp (upper part zero),  X_pp <- L_pp^{-1},  linv <- L_pp^{-1}
+//   (128 x 128 column-major), dinv tiles 2p, 2p+1 <- the two 64 x 64 diagonal
+//   inverses (the FP64 path's tiles), ldpart[2p + h] <- 2 sum log L_ii over the
+//   kept rows of half h.
+// A pivot that is not positive and finite records TD_ERR_NOT_PD with its
+// kept-sample index (the smallest over the factor) and continues with NaN.
+__global__ void __launch_bounds__(512) k_potrf_blk(double* __restrict__ A, double* __restrict__ X, int64_t ld,
+                                                    int64_t nk, int p, double* __restrict__ linv,
+                                                    double* __restrict__ dinv, double* __restrict__ ldpart,
+                                                    DevStatus* status) {
+  extern __shared__ double sm[];
+  double* a = sm;                  // L, packed
+  double* x = sm + PK_ELEMS;       // L^{-1}, packed
+  double* t = x + PK_ELEMS;        // 64 x 64 scratch, t[r + 64 c]
+  __shared__ double logd[PB];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t o = (int64_t)p * PB;
+  for (int e = tid; e < PB * PB; e += 512) {
+    const int r = e % PB, c = e / PB;
+    if (r >= c) a[pk(r, c)] = A[(o + r) + (o + c) * ld];
+  }
+  __syncthreads();
+  // Right-looking elimination on the unscaled columns, one barrier per
+  // column: column k stays as A's values (l_rk d_k) until the end, and the
+  // trailing update uses a_rk a_ck / p_k.  The pivot p_{k+1} is final as soon
+  // as element (k+1, k+1) has had its update in step k; the thread that makes
+  // that update (warp 0, lane 0) prepares 1/p_{k+1} and 1/sqrt(p_{k+1}) for
+  // step k+1 (FP64 square roots and divisions are slow here: one thread).
+  __shared__ double ipv[PB], idg[PB];
+  auto pivot = [&](int k) {
+    double pv = a[pk(k, k)];
+    if (!(pv > 0.0) || !isfinite(pv)) {
+      const long long g = o + k;
+      if (g < nk) {
+        atomicMin((unsigned long long*)&status->pivot, (unsigned long long)g);
+        atomicCAS(&status->code, 0, ST_NOT_PD);
+      }
+      pv = nan("");
+    }
+    const double d = sqrt(pv);
+    a[pk(k, k)] = d;
+    ipv[k] = 1.0 / pv;
+    idg[k] = 1.0 / d;
+  };
+  if (tid == 0) pivot(0);
+  __syncthreads();
+  for (int k = 0; k < PB - 1; ++k) {
+    const double ip = ipv[k];
+    for (int c = k + 1 + warp; c < PB; c += 16) {
+      const double lck = a[pk(c, k)] * ip;
+      for (int r = c + lane; r < PB; r += 32) a[pk(r, c)] -= a[pk(r, k)] * lck;
+      if (c == k + 1 && lane == 0) pivot(k + 1);   // (k+1, k+1) was this thread's first element
+    }
+    __syncthreads();
+  }
+  // scale the columns: l_rk = a_rk / d_k, and log d_k
+  for (int c = warp; c < PB; c += 16) {
+    const double s = idg[c];
+    for (int r = c + 1 + lane; r < PB; r += 32) a[pk(r, c)] *= s;
+    if (lane == 0) logd[c] = log(a[pk(c, c)]);
+  }
+  __syncthreads();
+  // inverses of the two 64 x 64 diagonal halves, one column per thread
+  if (tid < PB) {
+    const int h = tid >> 6, c = tid;   // column c of half h
+    const int end = 64 * h + 64;
+    x[pk(c, c)] = 1.0 / a[pk(c, c)];
+    for (int r = c + 1; r < end; ++r) {
+      double sacc = 0.0;
+      for (int k = c; k < r; ++k) sacc += a[pk(r, k)] * x[pk(k, c)];
+      x[pk(r, c)] = -sacc / a[pk(r, r)];
+    }
+  }
+  __syncthreads();
+  // t = L21 X11   (t[r][c] = sum_{k >= c} L[64 + r][k] X[k][c])
+  for (int e = tid; e < 64 * 64; e += 512) {
+    const int r = e & 63, c = e >> 6;
+    double sacc = 0.0;
+    for (int k = c; k < 64; ++k) sacc += a[pk(64 + r, k)] * x[pk(k, c)];
+    t[r + 64 * c] = sacc;
+  }
+  __syncthreads();
+  // X21 = -X22 t   (X21[r][c] = -sum_{k <= r} X[64 + r][64 + k] t[k][c])
+  for (int e = tid; e < 64 * 64; e += 512) {
+    const int r = e & 63, c = e >> 6;
+    double sacc = 0.0;
+    for (int k = 0; k <= r; ++k) sacc += x[pk(64 + r, 64 + k)] * t[k + 64 * c];
+    x[pk(64 + r, c)] = -sacc;
+  }
+  __syncthreads();
+  for (int e = tid; e < PB * PB; e += 512) {
+    const int r = e % PB, c = e / PB;
+    const bool lo = r >= c;
+    const double lv = lo ? a[pk(r, c)] : 0.0, xv = lo ? x[pk(r, c)] : 0.0;
+    A[(o + r) + (o + c) * ld] = lv;
+    X[(o + r) + (o + c) * ld] = xv;
+    linv[e] = xv;
+    if ((r < 64) == (c < 64)) {   // the two 64 x 64 diagonal tiles, column-major
+      const int h = r >> 6;
+      dinv[(int64_t)(2 * p + h) * 64 * 64 + (r & 63) + 64 * (c & 63)] = xv;
+    }
+  }
+  if (tid < 2) {
+    double sacc = 0.0;
+    for (int k = 64 * tid; k < 64 * tid + 64; ++k)
+      if (o + k < nk) sacc += logd[k];
+    ldpart[2 * p + tid] = 2.0 * sacc;
+  }
+}
+
+// X = identity (nkp x nkp column-major)
+__global__ void k_eye(double* __restrict__ X, int64_t nkp) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nkp; i += (int64_t)gridDim.x * blockDim.x)
+    X[i + i * nkp] = 1.0;
+}
+
+namespace {
+template <class T>
+td_status talloc(T** p, size_t count, const char* what) {
+  *p = nullptr;
+  if (count == 0) return TD_OK;
+  if (cudaMalloc((void**)p, count * sizeof(T)) != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(TD_ERR_OOM, std::string("device allocation failed: ") + what);
+  }
+  return TD_OK;
+}
+
+struct SliceBuf {        // slices [ns][rows][EK] and exponents [rows]
+  __nv_bfloat16* v = nullptr;
+  int* e = nullptr;
+  int rows = 0;
+  CUtensorMap boxA, boxB;  // 128-row (A operand) and 64-row (B operand) boxes
+};
+
+td_status slice_buf(SliceBuf& b, int rows, int ns) {
+  b.rows = rows;
+  td_status r = talloc(&b.v, (size_t)ns * rows * EK, "operand slices");
+  if (r == TD_OK) r = talloc(&b.e, (size_t)rows, "operand exponents");
+  if (r == TD_OK)
+    r = encode_3d(&b.boxA, b.v, EK, (uint64_t)rows, (uint64_t)ns, EK * 2, (uint64_t)rows * EK * 2, 32, 128,
+                  (uint32_t)ns);
+  if (r == TD_OK)
+    r = encode_3d(&b.boxB, b.v, EK, (uint64_t)rows, (uint64_t)ns, EK * 2, (uint64_t)rows * EK * 2, 32, 64,
+                  (uint32_t)ns);
+  return r;
+}
+
+void free_slice_buf(SliceBuf& b) {
+  if (b.v) cudaFree(b.v);
+  if (b.e) cudaFree(b.e);
+  b.v = nullptr;
+  b.e = nullptr;
+}
+
+void add_job(EmuSplitParams& P, const double* src, int64_t rs, int64_t ks, int rows, SliceBuf& dst, int ns) {
+  if (rows <= 0) return;
+  EmuSplitJob& j = P.job[P.njobs++];
+  j.src = src;
+  j.rs = rs;
+  j.ks = ks;
+  j.rows = rows;
+  j.rows_alloc = dst.rows;
+  j.dst = dst.v;
+  j.e = dst.e;
+  j.ns = ns;
+  j.block0 = P.total_blocks;
+  P.total_blocks += (rows + 31) / 32;
+}
+
+void add_prob(EmuParams& P, const SliceBuf& A, const SliceBuf& B, double* C, int64_t ldc, double alpha, double beta,
+              int m_tiles, int n_tiles, bool lower) {
+  if (m_tiles <= 0 || n_tiles <= 0) return;
+  EmuProb& q = P.p[P.nprob++];
+  q.mapA = A.boxA;
+  q.mapB = B.boxB;
+  q.ea = A.e;
+  q.eb = B.e;
+  q.C = C;
+  q.ldc = ldc;
+  q.alpha = alpha;
+  q.beta = beta;
+  q.a_row0 = 0;
+  q.b_row0 = 0;
+  q.m_tiles = m_tiles;
+  q.n_tiles = n_tiles;
+  q.lower = lower ? 1 : 0;
+  q.tile_begin = P.total_tiles;
+  P.total_tiles += emu_tiles(q);
+}
+}  // namespace
+
+td_status factor_tensor(td_segment* s, cudaStream_t st, int ns) {
+  td_status r = factor_begin(s, st);
+  if (r != TD_OK) return r;
+  static std::atomic<unsigned long long> attr_done{0};
+  if (device_needs_setup(attr_done)) {
+    TD_CUDA(cudaFuncSetAttribute(k_potrf_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)POTRF_SMEM));
+    mark_device_done(attr_done);
+  }
+  const int64_t nkp = s->nkp, ld = nkp;
+  const int nb = (int)(nkp / PB);
+  double* X = nullptr;
+  double* lblk = nullptr;
+  SliceBuf sAP, sLI, sBP, sP, sX;
+  auto cleanup = [&]() {
+    free_slice_buf(sAP);
+    free_slice_buf(sLI);
+    free_slice_buf(sBP);
+    free_slice_buf(sP);
+    free_slice_buf(sX);
+    if (lblk) cudaFree(lblk);
+  };
+  if ((r = talloc(&X, (size_t)(nkp * nkp), "L^{-1} (temporary)")) != TD_OK ||
+      (r = talloc(&lblk, (size_t)PB * PB, "block inverse")) != TD_OK ||
+      (r = slice_buf(sAP, (int)nkp, ns)) != TD_OK || (r = slice_buf(sLI, PB, ns)) != TD_OK ||
+      (r = slice_buf(sBP, (int)nkp, ns)) != TD_OK || (r = slice_buf(sP, (int)nkp, ns)) != TD_OK ||
+      (r = slice_buf(sX, (int)nkp, ns)) != TD_OK) {
+    cleanup();
+    if (X) cudaFree(X);
+    return r;
+  }
+  const int64_t lim = 2000000000LL;   // bound on each in-kernel wait
+  cudaError_t e = cudaMemsetAsync(X, 0, (size_t)(nkp * nkp) * sizeof(double), st);
+  if (e == cudaSuccess) {
+    k_eye<<<(unsigned)std::min<int64_t>(1024, ceil_div(nkp, 256)), 256, 0, st>>>(X, nkp);
+    e = cudaGetLastError();
+  }
+  for (int p = 0; p < nb && e == cudaSuccess; ++p) {
+    const int64_t o = (int64_t)p * PB;
+    const int64_t T = nkp - o - PB;   // rows below the block
+    double* Lp = s->L + (o + PB) + o * ld;   // panel A_{>p,p}, then L_{>p,p}
+    k_potrf_blk<<<1, 512, POTRF_SMEM, st>>>(s->L, X, ld, s->nk, p, lblk, s->dinv, s->ldpart, s->status);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    // slices of X_pp (rows), of the panel (rows) and of block row p of B (columns)
+    EmuSplitParams S1{};
+    add_job(S1, lblk, 1, PB, PB, sLI, ns);
+    add_job(S1, Lp, 1, ld, (int)T, sAP, ns);
+    add_job(S1, X + o, ld, 1, (int)o, sBP, ns);
+    if ((e = launch_emu_split(S1, st)) != cudaSuccess) break;
+    EmuParams G1{};
+    add_prob(G1, sAP, sLI, Lp, ld, 1.0, 0.0, (int)(T / PB), PB / 64, false);
+    add_prob(G1, sLI, sBP, X + o, ld, 1.0, 0.0, 1, (int)(o / 64), false);
+    if ((e = launch_emu_gemm(G1, ns, s->status, lim, st)) != cudaSuccess) break;
+    if (T == 0) break;
+    // slices of L_{>p,p} (rows) and of block row p of L^{-1} up to the diagonal (columns)
+    EmuSplitParams S2{};
+    add_job(S2, Lp, 1, ld, (int)T, sP, ns);
+    add_job(S2, X + o, ld, 1, (int)(o + PB), sX, ns);
+    if ((e = launch_emu_split(S2, st)) != cudaSuccess) break;
+    EmuParams G2{};
+    add_prob(G2, sP, sP, s->L + (o + PB) * (1 + ld), ld, -1.0, 1.0, (int)(T / PB), (int)(T / 64), true);
+    add_prob(G2, sP, sX, X + (o + PB), ld, -1.0, 1.0, (int)(T / PB), (int)((o + PB) / 64), false);
+    if ((e = launch_emu_gemm(G2, ns, s->status, lim, st)) != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cleanup();
+  if (e != cudaSuccess) {
+    cudaFree(X);
+    return cuda_fail(e, "tensor-core factor");
+  }
+  return factor_end(s, X, st);
+}
+
+}  // namespace td

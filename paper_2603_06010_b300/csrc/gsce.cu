@@ -288,7 +288,7 @@ template <int NSIG>
 __global__ void __cluster_dims__(GS_CL, 1, 1) __launch_bounds__(NSIG == 1 ? 1024 : 512)
     k_gs_chi2(const float* __restrict__ R, int64_t ldr, int n, int K, int logm, const float2* __restrict__ S1,
               const float2* __restrict__ S2, const float2* __restrict__ lift_g, float2* __restrict__ scr, double x0,
-              double logdet, double* __restrict__ logL, double* __restrict__ chi2) {
+              double logdet, double* __restrict__ logL, double* __restrict__ chi2, float rscale) {
   extern __shared__ float2 buf[];   // NSIG signals (gpad(NSIG ml) slots), then the ml/4 local twiddle shears
   __shared__ float red[32 * 4 * NSIG * 2];
   __shared__ double part[4 * NSIG];
@@ -310,7 +310,8 @@ __global__ void __cluster_dims__(GS_CL, 1, 1) __launch_bounds__(NSIG == 1 ? 1024
       const float* rb = R + (int64_t)(has_b ? cb : 0) * ldr;
       for (int l = threadIdx.x; l < ml; l += blockDim.x) {
         const int i = base + l;
-        buf[gpad(j * ml + l)] = make_float2((i < n && has_a) ? ra[i] : 0.f, (i < n && has_b) ? rb[i] : 0.f);
+        buf[gpad(j * ml + l)] =
+            make_float2((i < n && has_a) ? ra[i] * rscale : 0.f, (i < n && has_b) ? rb[i] * rscale : 0.f);
       }
     }
     cl.sync();
@@ -494,8 +495,16 @@ static td_status gs_launch(GsState& g, const float* R, int64_t ldr, int n, int64
     }
     g.scr_elems = need;
   }
+  // Residuals enter the FP32 transforms multiplied by 2^k with 2^{2k} ~ x_0
+  // (so the whitened values are of order one whatever the units of the
+  // data: strain-scale residuals of ~1e-21 would otherwise square into FP32
+  // subnormals); chi2 takes x_0 / 2^{2k}.  A power of two scales every FP32
+  // step exactly, so the result's bits do not depend on k.
+  const int k = (int)std::max(-120L, std::min(120L, std::lround(0.5 * std::log2(g.x0))));
+  const float rscale = std::ldexp(1.0f, k);
   k_gs_chi2<NSIG><<<clusters * GS_CL, threads, smem, st>>>(R, ldr, n, (int)K, g.logm, g.S1, g.S2, g.tw, g.scr,
-                                                           g.x0, g.logdet, logL, chi2);
+                                                           std::ldexp(g.x0, -2 * k), g.logdet, logL, chi2,
+                                                           rscale);
   TD_CUDA(cudaGetLastError());
   return TD_OK;
 }

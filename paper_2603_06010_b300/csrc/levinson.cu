@@ -310,6 +310,12 @@ td_status run_lev_batch(std::vector<LevSeg>& b, cudaStream_t st) {
 // segments with gaps are factored by the blocked Cholesky.  The FP64 factor L
 // is not formed on the recursion route, so those segments' FP64 path is
 // unavailable (TD_ERR_UNSUPPORTED); the tensor-core paths are.
+static td_status check_device_of(const td_segment* s) {
+  int dev = -1;
+  cudaGetDevice(&dev);
+  return dev == s->device ? TD_OK : fail(TD_ERR_INVALID, "segment belongs to another device; set it current first");
+}
+
 extern "C" td_status td_factor_many(td_segment* const* segs, int nseg, int flags, void* stream) {
   if (nseg < 0 || (nseg > 0 && !segs)) return fail(TD_ERR_INVALID, "bad arguments");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -325,7 +331,13 @@ extern "C" td_status td_factor_many(td_segment* const* segs, int nseg, int flags
     td_segment* s = segs[i];
     const bool gapfree = (s->nk == s->n);
     if (!(flags & TD_FACTOR_NO_FP64) || !gapfree || s->nk > LEV_MAX_N) {
-      const td_status r = td_factor(s, stream);
+      td_status r = TD_OK;
+      if (flags & TD_FACTOR_FP64_CORES) {
+        r = check_device_of(s);
+        if (r == TD_OK) r = factor_fp64_cores(s, st);
+      } else {
+        r = td_factor(s, stream);
+      }
       if (r == TD_OK && (flags & TD_FACTOR_NO_FP64)) td_segment_release_fp64(s);
       if (r == TD_OK) continue;
       if (r != TD_ERR_NOT_PD) return r;

@@ -88,6 +88,7 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
   if (!R || !logL) return fail(TD_ERR_INVALID, "R or logL is NULL");
   if (ldr < s->nk) return fail(TD_ERR_INVALID, "ldr < N'");
   if (!s->factored) return fail(TD_ERR_NOT_FACTORED, "segment not factored");
+  if (!s->op) return fail(TD_ERR_NOT_FACTORED, "the operator of this segment is not resident");
   int dev = -1;
   cudaGetDevice(&dev);
   if (dev != s->device) return fail(TD_ERR_INVALID, "segment belongs to another device; set it current first");
@@ -110,6 +111,9 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
   __nv_bfloat16* rs = reinterpret_cast<__nv_bfloat16*>(base);
   double* partials = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(base) + part_off);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  // the slice count td_loglike_batch takes with its default options (ten
+  // products below 512 and above 32768 kept samples, six between)
+  const int nsl = nslices_for(TD_PREC_AUTO, s->nk);
 
   TcSegDev seg;
   memset(&seg, 0, sizeof seg);
@@ -117,7 +121,7 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
                      (uint64_t)K * s->nkp8 * 2, OP_KB, TC_COLS, 1)) != TD_OK)
     return r;
   if ((r = na_encode(&seg.mapB, s->op, OP_KB, OP_ROWS, (uint64_t)s->op_blocks * OP_SLICES, OP_KB * 2,
-                     (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, 64, 3)) != TD_OK)
+                     (uint64_t)OP_ROWS * OP_KB * 2, OP_KB, 64, (uint32_t)nsl)) != TD_OK)
     return r;
   seg.partials = partials;
   seg.a_rows = TC_COLS;
@@ -125,8 +129,8 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
   seg.K = (int)K;
   seg.ldp = (int)K;
   seg.nm = (int)nm;
-  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, K, rs, 3, st));
-  TD_CUDA(launch_tc_single(seg, 64, (int)ceil_div(K, TC_COLS), (int)ceil_div(s->nk, OP_KB), 3,
+  TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, K, rs, nsl, st));
+  TD_CUDA(launch_tc_single(seg, 64, (int)ceil_div(K, TC_COLS), (int)ceil_div(s->nk, OP_KB), nsl,
                            s->status, 1000000000LL, st));
   TD_CUDA(launch_finalize(partials, K, (int)nm, K, s->logdet, s->nk, logL, chi2, st));
   return TD_OK;

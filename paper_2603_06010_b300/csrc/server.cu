@@ -40,12 +40,16 @@ struct Request {
   double* logL;
   Clock::time_point t_submit;
   int state;   // 0 pending, 1 in flight, 2 done, 3 cancelled, 4 failed
+  double lat_us = -1.0;   // submission to completion, once done
 };
 
 struct SegEntry {
   td_segment* s = nullptr;
   bool resident = false;      // operator slices on the device
+  bool pooled = false;        // the device copy came from the server's memory pool
   void* host_op = nullptr;    // pinned host copy of the operator slices
+  bool host_op_pooled = false;  // carved from the server's spill pool (not freed on its own)
+  cudaEvent_t spilled = nullptr;  // recorded after the spill copy: a reload on any stream waits for it
   size_t op_bytes = 0;
   int inflight = 0;           // batches of this segment on the GPU
   uint64_t last_use = 0;
@@ -58,6 +62,7 @@ struct ColRef {               // one column of a batch: where it comes from, whe
 };
 
 struct Slot {                 // one stream and its batch buffers
+  td::Scratch scr;            // residual slices, partials and work lists of this stream's batches
   cudaStream_t st = nullptr;
   cudaEvent_t done = nullptr;
   float* Rb = nullptr;        // N'max x max_cols batch residuals
@@ -89,8 +94,11 @@ struct td_server {
   uint64_t clock = 0;
   size_t resident_bytes = 0;
   // statistics
+  cudaMemPool_t pool = nullptr;     // stream-ordered pool for reloaded operators
+  void* spill = nullptr;            // pinned host spill pool
+  size_t spill_cap = 0, spill_used = 0;
   std::vector<double> lat_us;
-  int64_t evals = 0, batches = 0, hits = 0, misses = 0, evictions = 0, refused = 0, failed = 0;
+  int64_t evals = 0, batches = 0, hits = 0, misses = 0, evictions = 0, refused = 0, failed = 0, reloads = 0;
   Clock::time_point t_first, t_last;
   bool any_done = false;
   td_status last_err = TD_OK;
@@ -112,17 +120,59 @@ __global__ void k_scatter_logl(const ColRef* __restrict__ refs, int64_t cols, co
   if (k < cols) *refs[k].dst = Lb[k];
 }
 
-static void seg_evict(td_server* srv, SegEntry& e) {
-  if (!e.resident) return;
-  if (!e.host_op) {
-    cudaMallocHost(&e.host_op, e.op_bytes);
-    cudaMemcpy(e.host_op, e.s->op, e.op_bytes, cudaMemcpyDeviceToHost);
+// The pinned host copy of a segment's operator, made once, at its first
+// eviction, by an asynchronous copy on `st` (the operator does not change
+// afterwards).  It is carved from the server's pinned spill pool
+// (host_spill_bytes, pinned once at creation) while that has room, else
+// allocated on its own (cudaMallocHost, which blocks).
+static td_status seg_spill_copy(td_server* srv, SegEntry& e, cudaStream_t st) {
+  if (e.host_op) return TD_OK;
+  const size_t need = (e.op_bytes + 255) & ~(size_t)255;
+  if (srv->spill && srv->spill_used + need <= srv->spill_cap) {
+    e.host_op = static_cast<unsigned char*>(srv->spill) + srv->spill_used;
+    e.host_op_pooled = true;
+    srv->spill_used += need;
+  } else if (cudaMallocHost(&e.host_op, e.op_bytes) != cudaSuccess) {
+    cudaGetLastError();
+    e.host_op = nullptr;
+    return fail(TD_ERR_OOM, "pinned host copy of an operator");
   }
-  cudaFree(e.s->op);
+  TD_CUDA(cudaMemcpyAsync(e.host_op, e.s->op, e.op_bytes, cudaMemcpyDeviceToHost, st));
+  if (!e.spilled) TD_CUDA(cudaEventCreateWithFlags(&e.spilled, cudaEventDisableTiming));
+  TD_CUDA(cudaEventRecord(e.spilled, st));
+  return TD_OK;
+}
+
+// Evict on `st` (the segment has no batch in flight): the spill copy (first
+// time only) and the release of the device copy to the pool are both queued
+// in stream order, with no host or device synchronisation.
+static td_status seg_evict(td_server* srv, SegEntry& e, cudaStream_t st) {
+  if (!e.resident) return TD_OK;
+  td_status r = seg_spill_copy(srv, e, st);
+  if (r != TD_OK) return r;
+  if (e.pooled)
+    TD_CUDA(cudaFreeAsync(e.s->op, st));
+  else
+    TD_CUDA(cudaFree(e.s->op));
   e.s->op = nullptr;
+  e.pooled = false;
   e.resident = false;
   srv->resident_bytes -= e.op_bytes;
   srv->evictions++;
+  return TD_OK;
+}
+
+// Move a freshly built operator into the server's device pool (set-up time):
+// later evictions and reloads of the segment then stay stream-ordered.
+static td_status seg_rehome(td_server* srv, SegEntry& e, cudaStream_t st) {
+  void* p = nullptr;
+  TD_CUDA(cudaMallocFromPoolAsync(&p, e.op_bytes, srv->pool, st));
+  TD_CUDA(cudaMemcpyAsync(p, e.s->op, e.op_bytes, cudaMemcpyDeviceToDevice, st));
+  TD_CUDA(cudaStreamSynchronize(st));
+  TD_CUDA(cudaFree(e.s->op));
+  e.s->op = reinterpret_cast<__nv_bfloat16*>(p);
+  e.pooled = true;
+  return TD_OK;
 }
 
 // make the segment's operator resident (evicting least recently used idle
@@ -133,11 +183,12 @@ static void seg_evict(td_server* srv, SegEntry& e) {
 static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st, int64_t cols = 0) {
   SegEntry& e = srv->segs[(size_t)id];
   e.last_use = ++srv->clock;
-  if (srv->cfg.gs_gapfree && !e.s->gs.ready && gs_supported(e.s)) {
+  const bool use_gs = srv->cfg.gs_gapfree && !srv->cfg.deterministic;
+  if (use_gs && !e.s->gs.ready && gs_supported(e.s)) {
     const td_status rg = td_gs_prepare(e.s, st);
     if (rg != TD_OK) return rg;
   }
-  if (cols > 0 && e.s->gs.ready && srv->cfg.precision != TD_PREC_FP64 && gs_preferred(e.s, cols)) {
+  if (cols > 0 && use_gs && e.s->gs.ready && srv->cfg.precision != TD_PREC_FP64 && gs_preferred(e.s, cols)) {
     srv->hits++;   // the batch runs on the (resident) GS data whether or not the operator is
     return TD_OK;
   }
@@ -156,25 +207,32 @@ static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st, 
       if (victim < 0 || c.last_use < srv->segs[(size_t)victim].last_use) victim = (int64_t)i;
     }
     if (victim < 0) break;   // everything else is busy: exceed the budget for now
-    seg_evict(srv, srv->segs[(size_t)victim]);
+    const td_status re = seg_evict(srv, srv->segs[(size_t)victim], st);
+    if (re != TD_OK) return re;
   }
   if (!e.s->factored) {
     // gap-free: O(N^2) Levinson-Durbin operator; gapped: Cholesky, FP64 factor then released
     td_segment* one = e.s;
     td_status r = td_factor_many(&one, 1, TD_FACTOR_NO_FP64, st);
     if (r != TD_OK) return r;
+    if ((r = seg_rehome(srv, e, st)) != TD_OK) return r;   // pooled, so eviction never synchronises
+    // work lists for every batch width on every stream's scratch up front: no
+    // allocation while serving
+    td_options o;
+    td_options_default(&o);
+    o.precision = srv->cfg.precision;
+    if (srv->cfg.deterministic) o.path = TD_PATH_SMALLK;
+    for (Slot& sl : srv->slots)
+      if ((r = reserve_with(e.s, sl.scr, srv->cfg.max_batch_cols, &o)) != TD_OK) return r;
   } else {
     void* p = nullptr;
-    if (cudaMalloc(&p, e.op_bytes) != cudaSuccess) {
-      cudaGetLastError();
-      return fail(TD_ERR_OOM, "operator reload");
-    }
+    TD_CUDA(cudaMallocFromPoolAsync(&p, e.op_bytes, srv->pool, st));
     e.s->op = reinterpret_cast<__nv_bfloat16*>(p);
+    e.pooled = true;
+    if (e.spilled) TD_CUDA(cudaStreamWaitEvent(st, e.spilled, 0));   // the spill copy may be on another stream
     TD_CUDA(cudaMemcpyAsync(e.s->op, e.host_op, e.op_bytes, cudaMemcpyHostToDevice, st));
+    srv->reloads++;
   }
-  // scratch for the widest batch up front: no regrowth (and plan rebuild) while serving
-  td_status rr = td_reserve(e.s, srv->cfg.max_batch_cols, nullptr);
-  if (rr != TD_OK) return rr;
   e.resident = true;
   srv->resident_bytes += e.op_bytes;
   return TD_OK;
@@ -185,6 +243,7 @@ static void scheduler_loop(td_server* srv) {
   td_options opt;
   td_options_default(&opt);
   opt.precision = srv->cfg.precision;
+  if (srv->cfg.deterministic) opt.path = TD_PATH_SMALLK;
   std::unique_lock<std::mutex> lk(srv->mu);
   Clock::time_point last_batch = Clock::now();
   while (!srv->stop) {
@@ -200,7 +259,10 @@ static void scheduler_loop(td_server* srv) {
     if (slot >= 0 && !srv->paused) {
       for (size_t i = 0; i < srv->segs.size(); ++i) {
         SegEntry& e = srv->segs[i];
-        if (e.queue.empty() || e.inflight > 0) continue;
+        // batches of one segment may run on several streams at once (each
+        // stream has its own scratch); the Gohberg-Semencul form keeps one
+        // product buffer per segment, so such segments take one at a time
+        if (e.queue.empty() || (e.inflight > 0 && (e.s->gs.ready || !e.resident))) continue;
         const Request& r = srv->reqs[e.queue.front()];
         if (r.t_submit < oldest) {
           oldest = r.t_submit;
@@ -238,10 +300,21 @@ static void scheduler_loop(td_server* srv) {
     if (sl.tickets.empty()) continue;
     td_status st = seg_make_resident(srv, pick, sl.st, cols);
     const int64_t nk = e.s->nk;
+    // deterministic: the small-batch path in chunks of at most 256 columns, whose
+    // per-column arithmetic does not depend on the other columns of the call
+    auto run = [&](const float* R, int64_t ldr, int64_t K, double* L) -> td_status {
+      if (!srv->cfg.deterministic) return loglike_batch_with(e.s, sl.scr, R, ldr, K, L, &opt, nullptr, sl.st);
+      for (int64_t c0 = 0; c0 < K; c0 += 256) {
+        const td_status rc = loglike_batch_with(e.s, sl.scr, R + c0 * ldr, ldr, std::min<int64_t>(256, K - c0),
+                                                L + c0, &opt, nullptr, sl.st);
+        if (rc != TD_OK) return rc;
+      }
+      return TD_OK;
+    };
     if (st == TD_OK && sl.tickets.size() == 1) {
       // one request: evaluate it in place (its R and logL are device buffers)
       const Request& r = srv->reqs[sl.tickets[0]];
-      st = td_loglike_batch(e.s, r.R, r.ldr, r.K, r.logL, &opt, nullptr, sl.st);
+      st = run(r.R, r.ldr, r.K, r.logL);
     } else if (st == TD_OK) {
       // the batch's column map (the slot's previous batch has completed, so the
       // pinned map is free), gather, evaluate, scatter logL
@@ -257,8 +330,7 @@ static void scheduler_loop(td_server* srv) {
         k_gather_cols<<<(unsigned)cols, 256, 0, sl.st>>>(sl.refs_d, nk, sl.Rb);
         ce = cudaGetLastError();
       }
-      st = ce == cudaSuccess ? td_loglike_batch(e.s, sl.Rb, nk, cols, sl.Lb, &opt, nullptr, sl.st)
-                             : cuda_fail(ce, "server batch gather");
+      st = ce == cudaSuccess ? run(sl.Rb, nk, cols, sl.Lb) : cuda_fail(ce, "server batch gather");
       if (st == TD_OK) {
         k_scatter_logl<<<(unsigned)ceil_div(cols, 256), 256, 0, sl.st>>>(sl.refs_d, cols, sl.Lb);
         if ((ce = cudaGetLastError()) != cudaSuccess) st = cuda_fail(ce, "server batch scatter");
@@ -317,7 +389,8 @@ static void completion_loop(td_server* srv) {
         }
         r.state = 2;
         cols += r.K;
-        srv->lat_us.push_back(std::chrono::duration<double, std::micro>(now - r.t_submit).count());
+        r.lat_us = std::chrono::duration<double, std::micro>(now - r.t_submit).count();
+        srv->lat_us.push_back(r.lat_us);
         if (!srv->any_done) {
           srv->t_first = r.t_submit;
           srv->any_done = true;
@@ -375,9 +448,35 @@ td_status td_server_create(const td_server_config* cfg, td_server** out) {
     return fail(TD_ERR_INVALID, "bad server configuration");
   }
   cudaGetDevice(&srv->device);
+  {
+    cudaMemPoolProps pp;
+    memset(&pp, 0, sizeof pp);
+    pp.allocType = cudaMemAllocationTypePinned;
+    pp.location.type = cudaMemLocationTypeDevice;
+    pp.location.id = srv->device;
+    uint64_t keep = UINT64_MAX;   // freed operator memory stays in the pool for the next reload
+    if (cudaMemPoolCreate(&srv->pool, &pp) != cudaSuccess ||
+        cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+      cudaGetLastError();
+      if (srv->pool) cudaMemPoolDestroy(srv->pool);
+      delete srv;
+      return fail(TD_ERR_CUDA, "server memory pool");
+    }
+  }
+  if (srv->cfg.host_spill_bytes > 0) {
+    if (cudaMallocHost(&srv->spill, (size_t)srv->cfg.host_spill_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      srv->spill = nullptr;
+      cudaMemPoolDestroy(srv->pool);
+      delete srv;
+      return fail(TD_ERR_OOM, "pinned host spill pool");
+    }
+    srv->spill_cap = (size_t)srv->cfg.host_spill_bytes;
+  }
   srv->slots.resize((size_t)srv->cfg.n_streams);
   for (Slot& sl : srv->slots) {
-    if (cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
+    if (scratch_init_shared(sl.scr, srv->cfg.max_kept, srv->cfg.max_batch_cols) != TD_OK ||
+        cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(&sl.Rb, (size_t)srv->cfg.max_kept * srv->cfg.max_batch_cols * 4) != cudaSuccess ||
         cudaMalloc(&sl.Lb, (size_t)srv->cfg.max_batch_cols * 8) != cudaSuccess ||
@@ -412,16 +511,23 @@ td_status td_server_add_segment(td_server* srv, const double* acf, int64_t n, co
   return TD_OK;
 }
 
+td_status td_server_set_budget(td_server* srv, int64_t resident_bytes_budget) {
+  if (!srv || resident_bytes_budget < 0) return fail(TD_ERR_INVALID, "bad argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  srv->cfg.resident_bytes_budget = resident_bytes_budget;
+  return TD_OK;
+}
+
 td_status td_server_prefetch(td_server* srv, int64_t seg_id) {
   if (!srv) return fail(TD_ERR_INVALID, "NULL server");
   std::lock_guard<std::mutex> lk(srv->mu);
   if (seg_id < 0 || seg_id >= (int64_t)srv->segs.size()) return fail(TD_ERR_INVALID, "bad segment id");
   cudaStream_t st = srv->slots[0].st;
-  const int64_t hits = srv->hits, misses = srv->misses;
+  const int64_t hits = srv->hits, misses = srv->misses, reloads = srv->reloads;
   td_status r = seg_make_resident(srv, seg_id, st);
   srv->hits = hits;       // set-up is not a request: do not count it
   srv->misses = misses;
-  if (r == TD_OK) r = td_reserve(srv->segs[(size_t)seg_id].s, srv->cfg.max_batch_cols, nullptr);
+  srv->reloads = reloads;
   cudaStreamSynchronize(st);
   return r;
 }
@@ -438,7 +544,7 @@ td_status td_server_submit(td_server* srv, int64_t seg_id, const float* R, int64
     srv->refused++;
     return fail(TD_ERR_BUSY, "admission refused: pending-column capacity reached");
   }
-  Request r{srv->next_ticket++, seg_id, R, ldr, K, logL, Clock::now(), 0};
+  Request r{srv->next_ticket++, seg_id, R, ldr, K, logL, Clock::now(), 0, -1.0};
   srv->reqs[r.ticket] = r;
   e.queue.push_back(r.ticket);
   srv->pending_cols += K;
@@ -453,6 +559,16 @@ td_status td_server_poll(td_server* srv, int64_t ticket, int* state) {
   auto it = srv->reqs.find(ticket);
   if (it == srv->reqs.end()) return fail(TD_ERR_INVALID, "unknown ticket");
   *state = it->second.state;
+  return TD_OK;
+}
+
+td_status td_server_latency(td_server* srv, int64_t ticket, double* us) {
+  if (!srv || !us) return fail(TD_ERR_INVALID, "NULL argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->reqs.find(ticket);
+  if (it == srv->reqs.end()) return fail(TD_ERR_INVALID, "unknown ticket");
+  if (it->second.state != 2) return fail(TD_ERR_BUSY, "request not done");
+  *us = it->second.lat_us;
   return TD_OK;
 }
 
@@ -524,6 +640,7 @@ td_status td_server_get_stats(td_server* srv, td_server_stats* out, int reset) {
   out->refused = srv->refused;
   out->failed = srv->failed;
   out->resident_bytes = (int64_t)srv->resident_bytes;
+  out->reloads = srv->reloads;
   if (srv->any_done) {
     const double secs = std::chrono::duration<double>(srv->t_last - srv->t_first).count();
     out->evals_per_s = secs > 0 ? (double)srv->evals / secs : 0.0;
@@ -531,6 +648,7 @@ td_status td_server_get_stats(td_server* srv, td_server_stats* out, int reset) {
   if (reset) {
     srv->lat_us.clear();
     srv->evals = srv->batches = srv->hits = srv->misses = srv->evictions = srv->refused = srv->failed = 0;
+    srv->reloads = 0;
     srv->any_done = false;
   }
   return TD_OK;
@@ -565,6 +683,7 @@ void td_server_destroy(td_server* srv) {
   if (srv->compl_thr.joinable()) srv->compl_thr.join();
   cudaDeviceSynchronize();
   for (Slot& sl : srv->slots) {
+    scratch_free(sl.scr);
     if (sl.Rb) cudaFree(sl.Rb);
     if (sl.Lb) cudaFree(sl.Lb);
     if (sl.refs_h) cudaFreeHost(sl.refs_h);
@@ -573,9 +692,17 @@ void td_server_destroy(td_server* srv) {
     if (sl.st) cudaStreamDestroy(sl.st);
   }
   for (SegEntry& e : srv->segs) {
-    if (e.host_op) cudaFreeHost(e.host_op);
-    td_segment_destroy(e.s);
+    if (e.host_op && !e.host_op_pooled) cudaFreeHost(e.host_op);
+    if (e.spilled) cudaEventDestroy(e.spilled);
+    if (e.pooled && e.s->op) {   // pool memory goes back to the pool, not through cudaFree
+      cudaFreeAsync(e.s->op, 0);
+      e.s->op = nullptr;
+    }
   }
+  cudaDeviceSynchronize();
+  for (SegEntry& e : srv->segs) td_segment_destroy(e.s);
+  if (srv->pool) cudaMemPoolDestroy(srv->pool);
+  if (srv->spill) cudaFreeHost(srv->spill);
   delete srv;
 }
 

@@ -65,6 +65,7 @@ struct TcSegDev {    // per-segment launch data (device-resident)
 static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
 
 struct SplitPlan {           // device work lists for one batch width (split mode)
+  const void* seg = nullptr;  // the segment it was built for (a scratch may serve several)
   int64_t K = -1;
   int nsl = 0;
   int bn = 0;
@@ -79,6 +80,8 @@ struct SplitPlan {           // device work lists for one batch width (split mod
   const void* op = nullptr;   // operator the tensor maps in segdev were encoded for
   double logdet = 0.0;        // and the log det copied into it
   uint64_t last_use = 0;
+  TcSegDev host_seg;          // host copy of *segdev
+  int map_bn = 0;             // operator tile rows its operator map was encoded with
 };
 
 struct Scratch {
@@ -88,8 +91,14 @@ struct Scratch {
   double* w64 = nullptr;        // FP64 W for the plain path [nkp][capK]
   float2* wpart = nullptr;      // split-mode accumulator pairs
   int64_t wpart_slots = 0;
+  std::vector<float2*> wpart_old;   // outgrown accumulator buffers, still named by older plans
   std::vector<SplitPlan> plans;
   uint64_t use_clock = 0;
+  // a scratch shared by several segments (a server stream's): buffers sized
+  // once for max_kept samples and capK columns, never regrown
+  bool shared = false;
+  int64_t rs_elems = 0, part_elems = 0;
+  size_t max_plans = 24;
 };
 
 // one Levinson-Durbin chain (gap-free segment of n samples)
@@ -122,6 +131,9 @@ inline void mark_device_done(std::atomic<unsigned long long>& done) {
 }
 
 int split_chunk(int64_t nk, int64_t nkp, int bn);
+// bf16 slices per operand element for a td_options precision on a segment of
+// nk kept samples (TD_PREC_AUTO: 3, or 4 below 512 and above 32768 kept samples)
+int nslices_for(int precision, int64_t nk);
 void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
                         std::vector<SplitUnit>& units, int& n_slots, bool all_slots = false, int cols = TC_COLS);
 void sort_items(std::vector<TcItem>& items);
@@ -301,11 +313,37 @@ cudaError_t launch_tc_finalize(const TcSegDev* segs, int nseg, int64_t maxK, cud
 
 cudaError_t launch_bounded_wait_probe(DevStatus* status, int64_t limit_ns, cudaStream_t st);
 
+// 3-D bf16 tensor map with 64-byte swizzle: dims d0 (innermost) .. d2, byte
+// strides of dims 1 and 2, box b0 x b1 x b2
+td_status encode_3d(CUtensorMap* map, const void* ptr, uint64_t d0, uint64_t d1, uint64_t d2, uint64_t s1_bytes,
+                    uint64_t s2_bytes, uint32_t b0, uint32_t b1, uint32_t b2);
+// the factor C = L L^T with L^{-1} and the operator slices: blocks of 128 on
+// the tensor cores (split products of ns bf16 slices), or the FP64 CUDA-core
+// route (64-wide tiles)
+td_status factor_tensor(td_segment* s, cudaStream_t st, int ns);
+td_status factor_fp64_cores(td_segment* s, cudaStream_t st);
+constexpr int EMU_SLICES = 6;   // bf16 slices per FP64 operand value in the tensor-core factor
+// shared steps of both routes: allocate L (and the diagonal-tile inverses and
+// log det shares), clear the status and gather C_kept into L; afterwards
+// check the pivots, sum log det and build the operator slices from the
+// column-major L^{-1} (freed by the call)
+td_status factor_begin(td_segment* s, cudaStream_t st);
+td_status factor_end(td_segment* s, double* linv, cudaStream_t st);
+td_status read_status(td_segment* s, cudaStream_t st, DevStatus* out);
+td_status reset_status(td_segment* s, cudaStream_t st);
+
 // tensor maps of one segment: residual slices (A, boxes of a_rows columns)
 // and an operator's packed slices (B, tiles of bn rows, nsl slices); op =
 // nullptr takes the segment's whitening operator
 td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* out, int a_rows = TC_COLS,
-                          const __nv_bfloat16* op = nullptr);
+                          const __nv_bfloat16* op = nullptr, const Scratch* sc = nullptr);
+// td_loglike_batch / td_reserve with an explicit scratch (a server stream's
+// shared one); the segment's own scratch otherwise
+td_status loglike_batch_with(td_segment* s, Scratch& sc, const float* R, int64_t ldr, int64_t K, double* logL,
+                             const td_options* opt, double* chi2, cudaStream_t st);
+td_status reserve_with(td_segment* s, Scratch& sc, int64_t K, const td_options* opt);
+td_status scratch_init_shared(Scratch& sc, int64_t max_kept, int64_t maxK);
+void scratch_free(Scratch& sc);
 // one refinement step (td_options.refine), launched on st
 td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl,
                        int path, int64_t wait_limit_ns, cudaStream_t st);

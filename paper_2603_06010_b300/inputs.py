@@ -270,6 +270,20 @@ def noise_residuals(n: int, fs: float, K: int, seed: int, mask: np.ndarray | Non
     return np.ascontiguousarray(x[:, kept], dtype=np.float32)
 
 
+def ar1_noise(n: int, phi: float, sigma2: float, K: int, seed: int,
+              mask: np.ndarray | None = None) -> np.ndarray:
+    """K draws of the stationary AR(1) process x_t = phi x_{t-1} + e_t,
+    Var(e) = sigma2 (x_0 from the stationary law), on the kept samples,
+    float32 (K, n')."""
+    rng = np.random.default_rng(seed)
+    e = rng.standard_normal((K, n)) * math.sqrt(sigma2)
+    x = np.empty((K, n))
+    x[:, 0] = e[:, 0] / math.sqrt(1.0 - phi * phi)
+    for t in range(1, n):
+        x[:, t] = phi * x[:, t - 1] + e[:, t]
+    return np.ascontiguousarray(x[:, kept_index(mask, n)], dtype=np.float32)
+
+
 # ----------------------------------------------------------------------------
 # the configurations of the benchmark suite (shapes of the paper's segments)
 # ----------------------------------------------------------------------------
@@ -277,6 +291,27 @@ SINGLE_N1024 = dict(name="single_n1024", n=1024, fs=1024.0, K=1, n_gaps=0, seed=
 GAPFREE_N8192_K4096 = dict(name="gapfree_n8192_k4096", n=8192, fs=2048.0, K=4096, n_gaps=0, seed=2002)
 GAPPED_N16384_3DET = dict(name="gapped_n16384_3det_k1024", n=16384, fs=2048.0, K=1024, n_gaps=3,
             gap_len=512, scales=(1.0, 1.3, 2.1), seed=3003)
+
+
+def serving_fleet(seed: int = 5005, count: int = 200) -> list[dict]:
+    """The serving workload's resident segments: N uniform over {4096, 8192,
+    16384, 32768} at 2048 Hz, 0-3 gaps of 512 samples each (seeded offsets),
+    the reference PSD."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        n = int(rng.choice([4096, 8192, 16384, 32768]))
+        g = int(rng.integers(0, 4))
+        mask = gap_mask(n, g, 512, rng) if g else None
+        out.append(dict(n=n, fs=2048.0, gaps=g, mask=mask, index=i))
+    return out
+
+
+def serving_pool(n: int, fs: float = 2048.0, count: int = 512, seed: int = 5151) -> np.ndarray:
+    """Full-length residual pool shared by the serving workload's segments of
+    length n: count coloured-noise draws, float32 (count, n); a segment's
+    requests take the first K columns of pool[:, kept samples]."""
+    return noise_residuals(n, fs, count, seed + n)
 
 
 def mix64_segments(seed: int = 4004, count: int = 64) -> list[dict]:

@@ -70,6 +70,8 @@ SIGNATURES = {
     "td_server_prefetch": (_c.c_int, [_vp, _i64]),
     "td_server_submit": (_c.c_int, [_vp, _i64, _vp, _i64, _i64, _vp, _c.POINTER(_i64)]),
     "td_server_poll": (_c.c_int, [_vp, _i64, _c.POINTER(_c.c_int)]),
+    "td_server_latency": (_c.c_int, [_vp, _i64, _c.POINTER(_c.c_double)]),
+    "td_server_set_budget": (_c.c_int, [_vp, _i64]),
     "td_server_wait": (_c.c_int, [_vp, _i64, _i64]),
     "td_server_cancel": (_c.c_int, [_vp, _i64]),
     "td_server_pause": (_c.c_int, [_vp, _c.c_int]),
@@ -85,7 +87,8 @@ SIGNATURES = {
 class ServerConfig(ctypes.Structure):
     _fields_ = [("max_batch_cols", ctypes.c_int64), ("max_pending_cols", ctypes.c_int64),
                 ("resident_bytes_budget", ctypes.c_int64), ("n_streams", ctypes.c_int), ("precision", ctypes.c_int),
-                ("max_kept", ctypes.c_int64), ("gs_gapfree", ctypes.c_int), ("reserved0", ctypes.c_int)]
+                ("max_kept", ctypes.c_int64), ("gs_gapfree", ctypes.c_int), ("deterministic", ctypes.c_int),
+                ("host_spill_bytes", ctypes.c_int64)]
 
 
 class ServerStats(ctypes.Structure):
@@ -93,7 +96,7 @@ class ServerStats(ctypes.Structure):
                 ("evals_per_s", ctypes.c_double), ("requests_done", ctypes.c_int64), ("evals", ctypes.c_int64),
                 ("batches", ctypes.c_int64), ("hits", ctypes.c_int64), ("misses", ctypes.c_int64),
                 ("evictions", ctypes.c_int64), ("refused", ctypes.c_int64), ("failed", ctypes.c_int64),
-                ("resident_bytes", ctypes.c_int64)]
+                ("resident_bytes", ctypes.c_int64), ("reloads", ctypes.c_int64)]
 
 
 class TemplateOut(ctypes.Structure):
@@ -315,6 +318,7 @@ class Segment:
 
 
 TD_FACTOR_NO_FP64 = 1
+TD_FACTOR_FP64_CORES = 2
 
 
 def factor_many(segments, flags: int = TD_FACTOR_NO_FP64, stream=None):
@@ -395,13 +399,16 @@ class Server:
     PENDING, RUNNING, DONE, CANCELLED, FAILED = range(5)
 
     def __init__(self, max_batch_cols=4096, max_pending_cols=1 << 20, resident_bytes_budget=0, n_streams=4,
-                 precision=TD_PREC_AUTO, max_kept=32768, gs_gapfree=False):
+                 precision=TD_PREC_AUTO, max_kept=32768, gs_gapfree=False, deterministic=False,
+                 host_spill_bytes=0):
         c = ServerConfig()
         lib().td_server_config_default(ctypes.byref(c))
         c.max_batch_cols, c.max_pending_cols = max_batch_cols, max_pending_cols
         c.resident_bytes_budget, c.n_streams, c.precision, c.max_kept = (resident_bytes_budget, n_streams,
                                                                          precision, max_kept)
         c.gs_gapfree = 1 if gs_gapfree else 0
+        c.deterministic = 1 if deterministic else 0
+        c.host_spill_bytes = int(host_spill_bytes)
         h = ctypes.c_void_p()
         _check(lib().td_server_create(ctypes.byref(c), ctypes.byref(h)))
         self.handle = h
@@ -413,6 +420,9 @@ class Server:
         _check(lib().td_server_add_segment(self.handle, acf.ctypes.data, int(acf.shape[0]),
                                            None if m is None else m.ctypes.data, ctypes.byref(sid)))
         return sid.value
+
+    def set_budget(self, resident_bytes_budget: int):
+        _check(lib().td_server_set_budget(self.handle, int(resident_bytes_budget)))
 
     def prefetch(self, seg_id: int):
         _check(lib().td_server_prefetch(self.handle, int(seg_id)))
@@ -428,6 +438,12 @@ class Server:
         st = ctypes.c_int()
         _check(lib().td_server_poll(self.handle, int(ticket), ctypes.byref(st)))
         return st.value
+
+    def latency_us(self, ticket: int) -> float:
+        """td_server_latency: submission-to-completion time of a finished request."""
+        v = ctypes.c_double()
+        _check(lib().td_server_latency(self.handle, int(ticket), ctypes.byref(v)))
+        return v.value
 
     def wait(self, ticket: int, timeout_us: int = 60_000_000):
         _check(lib().td_server_wait(self.handle, int(ticket), int(timeout_us)))

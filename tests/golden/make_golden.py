@@ -1,7 +1,8 @@
 """Write tests/golden/full_size.json: oracle logdet / chi2 / logL for sampled
 columns of the full-size workloads (one N=1024 segment; the gap-free N=8192
 batch of K=4096; the gapped three-detector N=16384 batch of K=1024; the
-longest segment, N=32257, of the 64-segment mix).
+longest segment, N=32257, of the 64-segment mix; every pool column of the
+serving workload's first gapped N=8192 and N=16384 segments).
 
 Calls only the CPU oracle and the seeded input generators.  Run from the
 repository root:  python tests/golden/make_golden.py [key ...]
@@ -60,6 +61,25 @@ def mix64_longest():
                 r_checksum=[float(np.sum(sub[j].astype(np.float64))) for j in range(len(cols))])
 
 
+def serving_checked():
+    """The serving workload's first gapped N=8192 and first gapped N=16384
+    segments: oracle logL of every column of their request pools (a request of
+    K columns on a segment takes the pool's first K columns)."""
+    fleet = inputs.serving_fleet()
+    out = []
+    for n in (8192, 16384):
+        sp = next(x for x in fleet if x["n"] == n and x["gaps"] > 0)
+        pool = inputs.serving_pool(n)
+        kept = inputs.kept_index(sp["mask"], n)
+        R = np.ascontiguousarray(pool[:, kept])
+        osg = oracle.OracleSegment(inputs.acf_from_psd(n, sp["fs"]), sp["mask"])
+        chi = osg.chi2(R)
+        ll = oracle.loglike_from_chi2(chi, osg.logdet, osg.n_kept)
+        out.append(dict(index=sp["index"], n=n, gaps=sp["gaps"], n_kept=osg.n_kept, logdet=osg.logdet,
+                        logL=ll.tolist(), r_checksum=float(np.sum(R[:8].astype(np.float64)))))
+    return out
+
+
 def main():
     t0 = time.time()
     keys = sys.argv[1:]
@@ -86,6 +106,8 @@ def main():
                            joint_logL=np.sum([d_["logL"] for d_ in dets], axis=0).tolist())
     if want("mix64_longest"):
         out["mix64_longest"] = mix64_longest()
+    if want("serving_checked"):
+        out["serving_checked"] = serving_checked()
     with open(OUT, "w") as f:
         json.dump(out, f, indent=1)
     print(f"wrote {OUT} in {time.time() - t0:.1f} s")

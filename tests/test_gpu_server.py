@@ -64,12 +64,13 @@ def test_server_results_match_oracle(torch_cuda, gpu_lib):
 
 
 def test_same_alone_and_in_the_mix(torch_cuda, gpu_lib):
-    """A request gives the same logL (within the bar) when it runs alone and
-    when it is batched with other requests arriving at the same time."""
+    """A request gives the same logL, bit for bit, when it runs alone and when
+    it is batched with other requests arriving at the same time (deterministic
+    server: one fixed path per segment, whatever the batch width)."""
     from paper_2603_06010_b300 import td
     segs = _segments()
     acf, mask, o = segs[1]
-    srv = td.Server(max_batch_cols=2048, n_streams=2, max_kept=4096)
+    srv = td.Server(max_batch_cols=2048, n_streams=2, max_kept=4096, deterministic=True)
     sid = srv.add_segment(acf, mask)
     srv.prefetch(sid)
     R, alone, exp = _request(torch_cuda, o, 8, 77)
@@ -84,7 +85,7 @@ def test_same_alone_and_in_the_mix(torch_cuda, gpu_lib):
     srv.drain()
     a, b = alone.cpu().numpy(), mixed.cpu().numpy()
     assert srv.poll(t_mix) == td.Server.DONE
-    assert np.max(np.abs(a - b)) <= DLOGL_ABS
+    assert np.array_equal(a, b)
     assert np.max(np.abs(a - exp)) <= DLOGL_ABS
     for (r, out, e), t in zip(others, ts):
         assert np.max(np.abs(out.cpu().numpy() - e)) <= DLOGL_ABS
@@ -135,7 +136,36 @@ def test_lru_eviction_and_reload(torch_cuda, gpu_lib):
     for out, exp in results:
         assert np.max(np.abs(out.cpu().numpy() - exp)) <= DLOGL_ABS
     st = srv.stats()
-    assert st["evictions"] > 0 and st["misses"] > 0
+    assert st["evictions"] > 0 and st["misses"] > 0 and st["reloads"] > 0
+    srv.close()
+
+
+def test_deterministic_mix_over_batch_widths(torch_cuda, gpu_lib):
+    """Deterministic server: requests of 1 .. 300 columns on one segment, each
+    submitted alone and then all together (one batch of more than 256 columns,
+    run in chunks), give identical bits; and the automatic server agrees with
+    them within the bar."""
+    torch = torch_cuda
+    from paper_2603_06010_b300 import td
+    acf, mask, o = _segments()[2]
+    reqs = [_request(torch, o, k, 1300 + k) for k in (1, 5, 40, 130, 300)]
+    srv = td.Server(max_batch_cols=1024, n_streams=3, max_kept=4096, deterministic=True)
+    sid = srv.add_segment(acf, mask)
+    srv.prefetch(sid)
+    alone = []
+    for R, _, _ in reqs:
+        out = torch.full((R.shape[0],), np.nan, dtype=torch.float64, device="cuda")
+        srv.wait(srv.submit(sid, R, out))
+        alone.append(out.cpu().numpy())
+    srv.pause(True)
+    mixed = [torch.full((R.shape[0],), np.nan, dtype=torch.float64, device="cuda") for R, _, _ in reqs]
+    ts = [srv.submit(sid, R, out) for (R, _, _), out in zip(reqs, mixed)]
+    srv.pause(False)
+    srv.drain()
+    assert all(srv.poll(t) == td.Server.DONE for t in ts)
+    for a, m, (_, _, exp) in zip(alone, mixed, reqs):
+        assert np.array_equal(a, m.cpu().numpy())
+        assert np.max(np.abs(a - exp)) <= DLOGL_ABS
     srv.close()
 
 
@@ -213,3 +243,33 @@ def test_gapfree_segment_served_through_gsce(torch_cuda, gpu_lib):
         assert srv.poll(t) == td.Server.DONE
         assert np.max(np.abs(out.cpu().numpy() - exp)) <= DLOGL_ABS
     assert srv.stats()["resident_bytes"] == 0
+
+
+def test_spill_pool_and_runtime_budget(torch_cuda, gpu_lib):
+    """Operators spilled to the pinned pool reserved at creation, after the budget
+    is lowered at run time; reloaded operators give the same bits as before."""
+    torch = torch_cuda
+    from paper_2603_06010_b300 import td
+    segs = _segments()
+    srv = td.Server(n_streams=2, max_kept=4096, host_spill_bytes=64 << 20)
+    ids = [srv.add_segment(a, m) for a, m, _ in segs]
+    for i in ids:
+        srv.prefetch(i)
+    reqs = [_request(torch, segs[i][2], 24, 1700 + i) for i in range(3)]
+    first = []
+    for i, (R, out, exp) in enumerate(reqs):
+        srv.wait(srv.submit(ids[i], R, out))
+        first.append(out.cpu().numpy().copy())
+        assert np.max(np.abs(first[-1] - exp)) <= DLOGL_ABS
+    srv.stats(reset=True)
+    srv.set_budget(1)            # nothing fits: every new segment evicts the others
+    for q in range(6):
+        i = q % 3
+        R, out, _ = reqs[i]
+        out.fill_(np.nan)
+        srv.wait(srv.submit(ids[i], R, out))
+        assert np.array_equal(out.cpu().numpy(), first[i])
+    st = srv.stats()
+    assert st["evictions"] >= 4 and st["reloads"] >= 4 and st["failed"] == 0
+    srv.close()
+

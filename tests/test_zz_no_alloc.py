@@ -53,6 +53,38 @@ def test_noalloc_matches_batch_entry_point_twice(torch_cuda, gpu_lib):
         assert np.max(np.abs(na_ll - ref_ll)) <= DLOGL_ABS
 
 
+def test_noalloc_small_segment_against_oracle(torch_cuda, gpu_lib):
+    """Below 512 kept samples the default precision takes ten products; so must this call."""
+    import oracle
+    from paper_2603_06010_b300 import td
+    n, fs = 300, 2048.0
+    mask = np.ones(n, np.uint8)
+    mask[100:160] = 0                        # N' = 240
+    acf = inputs.acf_from_psd(n, fs)
+    seg = td.Segment(acf, mask)
+    o = oracle.OracleSegment(acf, mask)
+    for seed, K in ((51, 40), (53, 7)):
+        R = inputs.noise_residuals(n, fs, K, seed, mask=mask)
+        ref_ll, ref_chi, na_ll, na_chi = _both(torch_cuda, seg, R)
+        exp_chi = o.chi2(R)
+        exp_ll = oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept)
+        assert np.max(np.abs(na_chi - exp_chi) / exp_chi) <= CHI2_REL
+        assert np.max(np.abs(na_ll - exp_ll)) <= DLOGL_ABS
+        assert np.max(np.abs(na_chi - ref_chi) / ref_chi) <= CHI2_REL
+
+
+def test_noalloc_largest_batch_that_fits(torch_cuda, gpu_lib):
+    """N' = 8192 with K = 504 is the widest batch the fixed scratch holds."""
+    from paper_2603_06010_b300 import td
+    n, fs = 8192, 2048.0
+    seg = td.Segment(inputs.acf_from_psd(n, fs))
+    R = inputs.noise_residuals(n, fs, 504, 55)
+    ref_ll, ref_chi, na_ll, na_chi = _both(torch_cuda, seg, R)
+    assert np.all(np.isfinite(na_ll))
+    assert np.max(np.abs(na_chi - ref_chi) / ref_chi) <= CHI2_REL
+    assert np.max(np.abs(na_ll - ref_ll)) <= DLOGL_ABS
+
+
 def test_noalloc_rejects_batches_beyond_its_scratch(torch_cuda, gpu_lib):
     from paper_2603_06010_b300 import td
     n = 8192

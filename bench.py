@@ -46,7 +46,8 @@ def parse():
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=5.0)
-    p.add_argument("--only", default=None, choices=["grouped", "serving", "gapped3", "refine", "gsce", "small"],
+    p.add_argument("--only", default=None,
+                   choices=["grouped", "serving", "gapped3", "refine", "gsce", "small", "factor"],
                    help="run one extra workload alone and print its JSON object (profiling; not the bench line)")
     return p.parse_args()
 
@@ -408,6 +409,43 @@ def grouped_extra(td, torch):
             "max_abs_dlogL_vs_oracle_4_shortest": dlogl}
 
 
+def factor_extra(td, torch, with_fp64_cores=True):
+    """The factor C = L L^T with L^{-1} and the operator slices (once per segment):
+    gapped N=16384 (3 gaps of 512, N'=14848) and gapped N=32768 (N'=31232) on the
+    tensor-core route, and the N=16384 segment on the FP64 CUDA-core route beside it."""
+    from paper_2603_06010_b300 import inputs
+    out = {"note": "td_factor: blocks of 128, the block factor and its inverse in FP64, panel and trailing "
+                   "updates as FP64-accurate split bf16 products on the tensor cores (six slices); wall time "
+                   "of the synchronous call (covariance gather, factor, L^-1, log det, operator slices)",
+           "runs": []}
+    for n, seed in ((16384, 3003), (32768, 3004)):
+        si = inputs.make_segment(n, 2048.0, seed, n_gaps=3, gap_len=512)
+        runs = {}
+        for route in (("tensor", 0), ("fp64_cores", td.TD_FACTOR_FP64_CORES)):
+            if route[0] == "fp64_cores" and (not with_fp64_cores or n > 16384):
+                continue
+            seg = td.Segment(si.acf, si.mask, factor=False)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            if route[1]:
+                td.factor_many([seg], flags=route[1])
+            else:
+                seg.factor()
+            torch.cuda.synchronize()
+            runs[route[0]] = {"s": time.perf_counter() - t0, "logdet": seg.logdet, "n_kept": seg.n_kept}
+            seg.close()
+        nk = runs["tensor"]["n_kept"]
+        r = {"N": n, "gaps": 3, "n_kept": nk, "tensor_s": runs["tensor"]["s"],
+             "fp64_equiv_tflops": (2.0 / 3.0) * float(nk) ** 3 / runs["tensor"]["s"] / 1e12}
+        if "fp64_cores" in runs:
+            r["fp64_cores_s"] = runs["fp64_cores"]["s"]
+            r["speedup"] = runs["fp64_cores"]["s"] / runs["tensor"]["s"]
+            r["logdet_rel_diff"] = abs(runs["tensor"]["logdet"] - runs["fp64_cores"]["logdet"]) / abs(
+                runs["fp64_cores"]["logdet"])
+        out["runs"].append(r)
+    return out
+
+
 def refine_extra(td, torch, seg, R, K):
     """The refinement step on the benchmark batch: per first-pass precision, one pass
     against one pass + refinement (time per call, max |dlogL| on the stored oracle columns)."""
@@ -514,12 +552,14 @@ def serving_extra(td, torch, seconds, evict_seconds=4.0):
     16384, 32768 at 2048 Hz, 0-3 gaps of 512 each), open-loop Poisson arrivals
     at 2000 req/s, K uniform over {1, 8, 64, 512}, the segment uniform over the
     200.  Phase 1: the whole fleet resident (no budget).  Phase 2: the budget
-    lowered to 60% of the fleet's operator bytes at 50 req/s, so that requests
-    evict operators to pinned host memory and reload them."""
+    lowered by 16 GB below the fleet's operator bytes, at 50 req/s, so that
+    requests evict operators to pinned host memory and reload them (pinning
+    host memory runs at a few GB/s, so the spill pool is sized for what the
+    phase evicts, not for the fleet)."""
     from paper_2603_06010_b300 import inputs
     fleet = inputs.serving_fleet()
     host = host_mem_bytes() or 0
-    spill = int(min(110e9, 0.45 * host)) if host else 0
+    spill = int(min(24e9, 0.25 * host)) if host else 0
     srv = td.Server(max_batch_cols=2048, n_streams=4, max_kept=32768, gs_gapfree=True, host_spill_bytes=spill)
     ids, pools = [None] * len(fleet), [None] * len(fleet)
     full = {n: torch.from_numpy(inputs.serving_pool(n)).cuda() for n in (4096, 8192, 16384, 32768)}
@@ -593,7 +633,8 @@ def serving_extra(td, torch, seconds, evict_seconds=4.0):
                                 for i in sorted(gold)]}
     except (OSError, KeyError) as ex:
         checked = {"error": repr(ex)}
-    srv.set_budget(int(0.6 * fleet_bytes))
+    budget = int(fleet_bytes - 16e9)
+    srv.set_budget(budget)
     p2, _ = phase(50.0, evict_seconds)
     srv.close()
     by_n = {k: {"segments": len(v), "mean_s": float(np.mean(v)), "max_s": float(np.max(v))}
@@ -606,9 +647,10 @@ def serving_extra(td, torch, seconds, evict_seconds=4.0):
            "segments": len(fleet), "operator_GB": fleet_bytes / 1e9,
            "setup_s": setup_s, "factor_s_by_kind": by_n,
            "fleet": p1, "served_accuracy": checked,
-           "eviction": dict(p2, budget_GB=0.6 * fleet_bytes / 1e9, host_spill_pool_GB=spill / 1e9,
-                            note="budget lowered to 60% of the fleet's operator bytes at run time; evicted "
-                                 "operators go to pinned host memory and come back on their next request")}
+           "eviction": dict(p2, budget_GB=budget / 1e9, host_spill_pool_GB=spill / 1e9,
+                            note="budget lowered at run time to 16 GB below the fleet's operator bytes; "
+                                 "evicted operators go to pinned host memory (a pool pinned at server creation) "
+                                 "and come back on their next request")}
     out.update({k: p1[k] for k in ("p50_ms", "p99_ms", "evals_per_s", "requests", "refused")})
     return out
 
@@ -723,7 +765,7 @@ def main():
                                  td.TD_PREC_BF16X6, "bf16x6")
         fn = {"grouped": lambda: grouped_extra(td, torch), "serving": lambda: serving_extra(td, torch, args.serve_seconds),
               "gapped3": lambda: gapped_joint_extra(td, torch), "refine": only_refine, "gsce": only_gsce,
-              "small": only_small}[args.only]
+              "small": only_small, "factor": lambda: factor_extra(td, torch)}[args.only]
         print(json.dumps({"only": args.only, "result": fn()}), flush=True)
         return
 
@@ -901,6 +943,7 @@ def main():
         "clocks": clk,
     }
     if world == 1:
+        line["factor"] = factor_extra(td, torch)
         line["template_form"] = template_extra(td, torch, seg, seg_in, K)
         line["refinement"] = refine_extra(td, torch, seg, R, K)
         line["gsce"] = gsce_extra(td, torch, seg_in, R, K)

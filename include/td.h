@@ -540,8 +540,9 @@ td_status td_server_create(const td_server_config* cfg, td_server** out);
 td_status td_server_add_segment(td_server* srv, const double* acf, int64_t n, const uint8_t* mask,
                                 int64_t* seg_id);
 td_status td_server_prefetch(td_server* srv, int64_t seg_id);
-/* Change the HBM budget for resident operators (0 = unlimited); segments are
- * evicted, least recently used first, as later batches need room. */
+/* Change the HBM budget for resident operators (0 = unlimited): idle
+ * segments are evicted at once, least recently used first, until it holds
+ * (synchronises); later misses evict as they need room. */
 td_status td_server_set_budget(td_server* srv, int64_t resident_bytes_budget);
 td_status td_server_submit(td_server* srv, int64_t seg_id, const float* R, int64_t ldr, int64_t K,
                            double* logL, int64_t* ticket);

@@ -290,18 +290,33 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
       const int ea = q.ea[q.a_row0 + row];
       const int col0 = ni * BN + half * 32;
       double* crow = q.C + row;
-      const bool sub = (q.beta == 1.0 && q.alpha == -1.0), put = (q.beta == 0.0 && q.alpha == 1.0);
+      // per half of the columns, every load first (the exponents, then the
+      // old values: 16 loads in flight, one memory latency), then the
+      // arithmetic, then the stores -- loads interleaved with stores to
+      // possibly aliasing addresses would wait out one latency per column
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int sc = ea + q.eb[q.b_row0 + col0 + j];
-        const double h = f32_to_f64_scaled(hi[j], sc), l = f32_to_f64_scaled(lo[j], sc);
-        double* dst = crow + (int64_t)(col0 + j) * q.ldc;
-        if (sub)
-          *dst = (*dst - h) - l;
-        else if (put)
-          *dst = h + l;
-        else
-          *dst = (q.beta == 0.0) ? q.alpha * (h + l) : fma(q.alpha, h + l, q.beta * *dst);
+      for (int hh = 0; hh < 2; ++hh) {
+        int sc[16];
+        double v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) sc[j] = ea + __ldg(q.eb + q.b_row0 + col0 + 16 * hh + j);
+        if (q.beta != 0.0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) v[j] = crow[(int64_t)(col0 + 16 * hh + j) * q.ldc];
+        }
+        if (q.beta == 1.0 && q.alpha == -1.0) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j)
+            v[j] = (v[j] - f32_to_f64_scaled(hi[16 * hh + j], sc[j])) - f32_to_f64_scaled(lo[16 * hh + j], sc[j]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const double w = f32_to_f64_scaled(hi[16 * hh + j], sc[j]) + f32_to_f64_scaled(lo[16 * hh + j], sc[j]);
+            v[j] = q.beta == 0.0 ? (q.alpha == 1.0 ? w : q.alpha * w) : fma(q.alpha, w, q.beta * v[j]);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) crow[(int64_t)(col0 + 16 * hh + j) * q.ldc] = v[j];
       }
     }
   }
@@ -418,7 +433,8 @@ cudaError_t launch_emu_split(const EmuSplitParams& P, cudaStream_t st) {
 }
 
 template <int NS>
-static cudaError_t emu_launch(const EmuParams& P, DevStatus* status, int64_t limit_ns, cudaStream_t st) {
+static cudaError_t emu_launch(const EmuParams& P, DevStatus* status, int64_t limit_ns, cudaStream_t st,
+                              int max_ctas) {
   static std::atomic<unsigned long long> done{0};
   if (device_needs_setup(done)) {
     cudaError_t e = cudaFuncSetAttribute(k_emu_gemm<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -426,15 +442,17 @@ static cudaError_t emu_launch(const EmuParams& P, DevStatus* status, int64_t lim
     if (e != cudaSuccess) return e;
     mark_device_done(done);
   }
-  const int grid = (int)std::min<int64_t>(P.total_tiles, tc_num_sms());
+  int grid = (int)std::min<int64_t>(P.total_tiles, tc_num_sms());
+  if (max_ctas > 0 && grid > max_ctas) grid = max_ctas;
   k_emu_gemm<NS><<<grid, emu::THREADS, emu::Cfg<NS>::SMEM, st>>>(P, status, (uint64_t)limit_ns);
   return cudaGetLastError();
 }
 
-cudaError_t launch_emu_gemm(const EmuParams& P, int ns, DevStatus* status, int64_t limit_ns, cudaStream_t st) {
+cudaError_t launch_emu_gemm(const EmuParams& P, int ns, DevStatus* status, int64_t limit_ns, cudaStream_t st,
+                            int max_ctas) {
   if (P.total_tiles <= 0) return cudaSuccess;
-  if (ns == 5) return emu_launch<5>(P, status, limit_ns, st);
-  if (ns == 6) return emu_launch<6>(P, status, limit_ns, st);
+  if (ns == 5) return emu_launch<5>(P, status, limit_ns, st, max_ctas);
+  if (ns == 6) return emu_launch<6>(P, status, limit_ns, st, max_ctas);
   return cudaErrorInvalidValue;
 }
 

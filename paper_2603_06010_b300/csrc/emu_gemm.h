@@ -47,6 +47,8 @@ struct EmuSplitParams {
 inline int emu_tiles(const EmuProb& q) { return q.lower ? q.m_tiles * (q.m_tiles + 1) : q.m_tiles * q.n_tiles; }
 
 cudaError_t launch_emu_split(const EmuSplitParams& P, cudaStream_t st);
-cudaError_t launch_emu_gemm(const EmuParams& P, int ns, DevStatus* status, int64_t limit_ns, cudaStream_t st);
+// max_ctas > 0 caps the persistent grid (to leave SMs to a kernel on another stream)
+cudaError_t launch_emu_gemm(const EmuParams& P, int ns, DevStatus* status, int64_t limit_ns, cudaStream_t st,
+                            int max_ctas = 0);
 
 }  // namespace td

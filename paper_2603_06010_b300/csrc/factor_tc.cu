@@ -211,7 +211,7 @@ void add_job(EmuSplitParams& P, const double* src, int64_t rs, int64_t ks, int r
 }
 
 void add_prob(EmuParams& P, const SliceBuf& A, const SliceBuf& B, double* C, int64_t ldc, double alpha, double beta,
-              int m_tiles, int n_tiles, bool lower) {
+              int m_tiles, int n_tiles, bool lower, int a_row0 = 0, int b_row0 = 0) {
   if (m_tiles <= 0 || n_tiles <= 0) return;
   EmuProb& q = P.p[P.nprob++];
   q.mapA = A.boxA;
@@ -222,8 +222,8 @@ void add_prob(EmuParams& P, const SliceBuf& A, const SliceBuf& B, double* C, int
   q.ldc = ldc;
   q.alpha = alpha;
   q.beta = beta;
-  q.a_row0 = 0;
-  q.b_row0 = 0;
+  q.a_row0 = a_row0;
+  q.b_row0 = b_row0;
   q.m_tiles = m_tiles;
   q.n_tiles = n_tiles;
   q.lower = lower ? 1 : 0;
@@ -268,12 +268,27 @@ td_status factor_tensor(td_segment* s, cudaStream_t st, int ns) {
     k_eye<<<(unsigned)std::min<int64_t>(1024, ceil_div(nkp, 256)), 256, 0, st>>>(X, nkp);
     e = cudaGetLastError();
   }
+  // Lookahead: step p's trailing update is issued in two parts.  The first
+  // (G2a) covers what step p+1 reads -- block column p+1 of the Schur
+  // complement and block row p+1 of the inverse --; the block factor of step
+  // p+1 (one CTA, FP64) then runs on a second stream while the rest (G2b,
+  // one SM short of the full grid) runs on the first.  G2b touches neither
+  // the diagonal block p+1 nor anything the block factor writes.
+  cudaStream_t la = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_p = nullptr;
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&la, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_a, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_p, cudaEventDisableTiming);
+  if (e == cudaSuccess) {
+    k_potrf_blk<<<1, 512, POTRF_SMEM, st>>>(s->L, X, ld, s->nk, 0, lblk, s->dinv, s->ldpart, s->status);
+    e = cudaGetLastError();
+  }
+  const int nsm = tc_num_sms();
   for (int p = 0; p < nb && e == cudaSuccess; ++p) {
     const int64_t o = (int64_t)p * PB;
     const int64_t T = nkp - o - PB;   // rows below the block
     double* Lp = s->L + (o + PB) + o * ld;   // panel A_{>p,p}, then L_{>p,p}
-    k_potrf_blk<<<1, 512, POTRF_SMEM, st>>>(s->L, X, ld, s->nk, p, lblk, s->dinv, s->ldpart, s->status);
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if (p > 0 && (e = cudaStreamWaitEvent(st, ev_p, 0)) != cudaSuccess) break;   // block factor p done
     // slices of X_pp (rows), of the panel (rows) and of block row p of B (columns)
     EmuSplitParams S1{};
     add_job(S1, lblk, 1, PB, PB, sLI, ns);
@@ -290,11 +305,30 @@ td_status factor_tensor(td_segment* s, cudaStream_t st, int ns) {
     add_job(S2, Lp, 1, ld, (int)T, sP, ns);
     add_job(S2, X + o, ld, 1, (int)(o + PB), sX, ns);
     if ((e = launch_emu_split(S2, st)) != cudaSuccess) break;
-    EmuParams G2{};
-    add_prob(G2, sP, sP, s->L + (o + PB) * (1 + ld), ld, -1.0, 1.0, (int)(T / PB), (int)(T / 64), true);
-    add_prob(G2, sP, sX, X + (o + PB), ld, -1.0, 1.0, (int)(T / PB), (int)((o + PB) / 64), false);
-    if ((e = launch_emu_gemm(G2, ns, s->status, lim, st)) != cudaSuccess) break;
+    // G2a: the first 128 columns of the Schur complement (all its rows) and
+    // block row p+1 of the inverse
+    EmuParams G2a{};
+    add_prob(G2a, sP, sP, s->L + (o + PB) * (1 + ld), ld, -1.0, 1.0, (int)(T / PB), PB / 64, false);
+    add_prob(G2a, sP, sX, X + (o + PB), ld, -1.0, 1.0, 1, (int)((o + PB) / 64), false);
+    if ((e = launch_emu_gemm(G2a, ns, s->status, lim, st)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(ev_a, st)) != cudaSuccess) break;
+    // block factor of step p+1 beside G2b
+    if ((e = cudaStreamWaitEvent(la, ev_a, 0)) != cudaSuccess) break;
+    k_potrf_blk<<<1, 512, POTRF_SMEM, la>>>(s->L, X, ld, s->nk, p + 1, lblk, s->dinv, s->ldpart, s->status);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cudaEventRecord(ev_p, la)) != cudaSuccess) break;
+    // G2b: the rest of the Schur complement (lower tiles) and of the inverse
+    const int64_t T2 = T - PB;
+    EmuParams G2b{};
+    add_prob(G2b, sP, sP, s->L + (o + 2 * PB) * (1 + ld), ld, -1.0, 1.0, (int)(T2 / PB), (int)(T2 / 64), true,
+             PB, PB);
+    add_prob(G2b, sP, sX, X + (o + 2 * PB), ld, -1.0, 1.0, (int)(T2 / PB), (int)((o + PB) / 64), false, PB, 0);
+    if ((e = launch_emu_gemm(G2b, ns, s->status, lim, st, nsm - 1)) != cudaSuccess) break;
   }
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_p, 0);
+  if (la) cudaStreamDestroy(la);
+  if (ev_a) cudaEventDestroy(ev_a);
+  if (ev_p) cudaEventDestroy(ev_p);
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   cleanup();
   if (e != cudaSuccess) {

@@ -204,9 +204,14 @@ static td_status seg_make_resident(td_server* srv, int64_t id, cudaStream_t st, 
     for (size_t i = 0; i < srv->segs.size(); ++i) {
       SegEntry& c = srv->segs[i];
       if ((int64_t)i == id || !c.resident || c.inflight > 0) continue;
+      // while serving, a victim needs a spill copy already or room for one in
+      // the pinned pool: pinning new host memory (cudaMallocHost) would block
+      // the scheduler for about a second per GB-scale operator
+      if (srv->spill && !c.host_op && srv->spill_used + ((c.op_bytes + 255) & ~(size_t)255) > srv->spill_cap)
+        continue;
       if (victim < 0 || c.last_use < srv->segs[(size_t)victim].last_use) victim = (int64_t)i;
     }
-    if (victim < 0) break;   // everything else is busy: exceed the budget for now
+    if (victim < 0) break;   // everything else is busy or cannot spill: exceed the budget for now
     const td_status re = seg_evict(srv, srv->segs[(size_t)victim], st);
     if (re != TD_OK) return re;
   }
@@ -515,6 +520,20 @@ td_status td_server_set_budget(td_server* srv, int64_t resident_bytes_budget) {
   if (!srv || resident_bytes_budget < 0) return fail(TD_ERR_INVALID, "bad argument");
   std::lock_guard<std::mutex> lk(srv->mu);
   srv->cfg.resident_bytes_budget = resident_bytes_budget;
+  // evict least recently used idle segments now until the new budget holds
+  cudaStream_t st = srv->slots[0].st;
+  while (resident_bytes_budget > 0 && (int64_t)srv->resident_bytes > resident_bytes_budget) {
+    int64_t victim = -1;
+    for (size_t i = 0; i < srv->segs.size(); ++i) {
+      const SegEntry& c = srv->segs[i];
+      if (!c.resident || c.inflight > 0) continue;
+      if (victim < 0 || c.last_use < srv->segs[(size_t)victim].last_use) victim = (int64_t)i;
+    }
+    if (victim < 0) break;   // the rest is busy: later misses evict it
+    const td_status r = seg_evict(srv, srv->segs[(size_t)victim], st);
+    if (r != TD_OK) return r;
+  }
+  TD_CUDA(cudaStreamSynchronize(st));
   return TD_OK;
 }
 

@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--no-serving", action="store_true")
     p.add_argument("--serve-seconds", type=float, default=5.0)
+    p.add_argument("--core", action="store_true",
+                   help="the headline workload, its end-to-end figure and the CPU baseline only (profiling)")
     p.add_argument("--only", default=None,
                    choices=["grouped", "serving", "gapped3", "refine", "gsce", "small", "factor"],
                    help="run one extra workload alone and print its JSON object (profiling; not the bench line)")
@@ -171,6 +173,17 @@ def profile_traffic(name):
             m = re.search(r"DRAM traffic per launch: ([0-9.]+) MB", f.read())
         return float(m.group(1)) * 1e6 if m else None
     except OSError:
+        return None
+
+
+def golden_chi2_rel(chi2_host):
+    """max relative chi2 error on the stored oracle columns."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "full_size.json")) as f:
+            g = json.load(f)["gapfree_n8192_k4096"]
+        exp = np.array(g["chi2"])
+        return float(np.max(np.abs(chi2_host[g["columns"]] - exp) / exp))
+    except Exception:
         return None
 
 
@@ -464,16 +477,19 @@ def refine_extra(td, torch, seg, R, K):
     against one pass + refinement (time per call, max |dlogL| on the stored oracle columns)."""
     stream = torch.cuda.current_stream()
     logL = torch.empty(K, dtype=torch.float64, device="cuda")
+    chi2 = torch.empty(K, dtype=torch.float64, device="cuda")
     runs = []
     for pname, prec, refine in (("bf16x3", td.TD_PREC_BF16X3, 0), ("bf16x3", td.TD_PREC_BF16X3, 1),
-                                ("bf16x6", td.TD_PREC_BF16X6, 0), ("bf16x6", td.TD_PREC_BF16X6, 1),
+                                ("bf16x3", td.TD_PREC_BF16X3, 2), ("bf16x6", td.TD_PREC_BF16X6, 0),
+                                ("bf16x6", td.TD_PREC_BF16X6, 1), ("bf16x6", td.TD_PREC_BF16X6, 2),
                                 ("bf16x10", td.TD_PREC_BF16X10, 0)):
         o = td.options(precision=prec, refine=refine)
         for _ in range(3):
-            seg.loglike_into(R, logL, o)
+            seg.loglike_into(R, logL, o, chi2=chi2)
         torch.cuda.synchronize()
         seg.check()
         dll = golden_dlogl(logL.cpu().numpy())
+        crel = golden_chi2_rel(chi2.cpu().numpy())
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ea.record(stream)
         for _ in range(5):
@@ -482,10 +498,12 @@ def refine_extra(td, torch, seg, R, K):
         torch.cuda.synchronize()
         ms = ea.elapsed_time(eb) / 5
         runs.append({"precision": pname, "refine": refine, "call_ms": ms, "evals_per_s": K / (ms / 1e3),
-                     "max_abs_dlogL_vs_oracle": dll})
-    return {"note": "one pass vs one pass + refinement (w~ at the precision, s = r - L w~ by ten split "
-                    "products of L's own slices, delta = L^{-1} s at the precision); calls back to back, "
-                    "inputs (134 MB) and the operator larger than L2", "runs": runs}
+                     "max_abs_dlogL_vs_oracle": dll, "max_chi2_rel_vs_oracle": crel})
+    return {"note": "one pass vs one pass + refinement: refine 1 = w~ at the precision, s = r - L w~ by ten "
+                    "split products of L's own slices, delta = L^{-1} s at the precision; refine 2 = s formed "
+                    "to FP64 accuracy (six-slice split products of L and w~ per 128-column chunk, FP64 "
+                    "accumulation), delta with at least six products; calls back to back, inputs (134 MB) and "
+                    "the operator larger than L2", "runs": runs}
 
 
 def gsce_extra(td, torch, seg_in, R, K):
@@ -888,7 +906,7 @@ def main():
                 "max_abs_dlogL_vs_oracle": golden_dlogl(logL.cpu().numpy()) if rank == 0 else None}
 
     # small and mid-size batches on the same segment
-    small = small_batches(td, torch, seg, R, N, prec, args.precision)
+    small = [] if args.core else small_batches(td, torch, seg, R, N, prec, args.precision)
 
     if rank != 0:
         if world > 1:
@@ -955,12 +973,12 @@ def main():
                           "runs": small},
         "clocks": clk,
     }
-    if world == 1:
+    if world == 1 and not args.core:
         line["factor"] = factor_extra(td, torch)
         line["template_form"] = template_extra(td, torch, seg, seg_in, K)
         line["refinement"] = refine_extra(td, torch, seg, R, K)
         line["gsce"] = gsce_extra(td, torch, seg_in, R, K)
-    if world == 1 and not args.no_grouped:
+    if world == 1 and not args.no_grouped and not args.core:
         gj = gapped_joint_extra(td, torch)
         line["metric_configs"] = {
             "note": "the two configurations the metric names, each as evals/s, p50/p99 latency of one call "
@@ -973,13 +991,13 @@ def main():
                                          "max_abs_dlogL_vs_oracle": gj["max_abs_dlogL_joint_vs_oracle"]}}
         line["gapped_n16384_3det"] = gj
         line["grouped"] = grouped_extra(td, torch)
-    if world == 1:
+    if world == 1 and not args.core:
         try:
             line["peaks_extra"] = {"tf32_tflops_burst": tf32_tflops(),
                                    "note": "cuBLAS fp32 GEMM with TF32 enabled, 8192^3, best of 5 (measured here)"}
         except Exception as ex:
             line["peaks_extra"] = {"error": repr(ex)}
-    if world == 1 and not args.no_serving:
+    if world == 1 and not args.no_serving and not args.core:
         line["serving"] = serving_extra(td, torch, args.serve_seconds)
     if not args.no_cpu_baseline:
         try:

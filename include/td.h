@@ -113,7 +113,7 @@ typedef enum {
 typedef struct {
   int precision;        /* td_precision; default TD_PREC_AUTO */
   int path;             /* td_path; default TD_PATH_AUTO */
-  int refine;           /* nonzero: one refinement step (Sec. III.C precision scheme).
+  int refine;           /* 1 (or any nonzero value but 2): one refinement step (Sec. III.C precision scheme).
                            w~ = L^{-1} r at `precision`; s = r - L w~ from bf16 slices of
                            L with ten products (exact hi*hi, ~1e-9 of |L||w~|); delta =
                            L^{-1} s at `precision`; chi2 = |w~ + delta|^2.  Brings
@@ -127,7 +127,14 @@ typedef struct {
                            td_segment_release_fp64; TD_ERR_INVALID with TD_PREC_FP64 or
                            TD_PATH_FP64; grouped launches: TD_ERR_UNSUPPORTED.  The
                            slices of L (as large as the operator's) are made on the
-                           first refined call, with two FP32 N'p x K buffers. */
+                           first refined call, with two FP32 N'p x K buffers.
+                           2: the same step with s = r - L w~ formed to FP64
+                           accuracy: split products of six exact bf16 slices of L
+                           and of w~ on the tensor cores, one 128-column chunk of L
+                           at a time, accumulated in FP64 (one more N'p x K FP64
+                           buffer), and delta computed with at least six products;
+                           chi2 then agrees with the FP64 oracle to ~1e-12 from any
+                           first-pass precision, at about three to six passes' cost. */
   int reserved0;
   int64_t wait_limit_ns;/* bound on any in-kernel wait; <= 0 -> 1 s */
 } td_options;

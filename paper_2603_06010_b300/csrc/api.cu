@@ -574,7 +574,7 @@ td_status loglike_batch_with(td_segment* s, Scratch& sc, const float* R, int64_t
   const int nsl = nslices_for(o.precision, s->nk);
   if (o.refine) {
     if (&sc != &s->scr) return fail(TD_ERR_UNSUPPORTED, "refinement runs on the segment's own scratch");
-    return refine_batch(s, R, ldr, K, logL, chi2, nsl, o.path, o.wait_limit_ns, st);
+    return refine_batch(s, R, ldr, K, logL, chi2, nsl, o.refine == 2 ? 2 : 1, o.path, o.wait_limit_ns, st);
   }
   const Shape shape = choose_shape(s, K, o.path);
   const int bn = shape.bn;

@@ -14,26 +14,29 @@
 // a_s 2^{-8s} is exact in bf16 (8 significant bits).
 //
 // Products: D = alpha A B^T + beta D over K = EK, A and B given as slices.
-// The product of slices s and t has weight 2^{-8(s+t)}; pairs of the same
-// level l = s + t share an FP32 accumulator in tensor memory.  With K = 128,
-// in units of the level's weight:
-//   level 0: |sum| <= 128 * 256^2                          = 2^23
-//   level 1: |sum| <= 128 * 2 * 256 * 128                  = 2^23
-//   level 2: |sum| <= 128 * (2 * 256 * 128 + 128^2)        < 2^24
-//   level 3: |sum| <= 128 * (2 * 256 * 128 + 2 * 128^2)    < 2^24
-// so each is an integer sum below 2^24 and its tensor-core accumulation is
-// exact.  Levels 4 .. NS-1 share a fifth accumulator (issued smallest first)
-// whose magnitude is about 2^-32 of the level-0 scale, so the tensor core's
-// FP32 truncation there is below 2^-46 of sum |a||b| per product; levels
-// >= NS are not formed (about 2^-47 for NS = 6), and the operand remainders
-// after NS slices are of the same order.  The epilogue adds the five
-// accumulators in FP64 (exact conversions, smallest first) and scales by
-// 2^{ea+eb}.  (With four accumulators, level 3 would join the merged one and
-// its truncation would cost up to about 2^-40 of sum |a||b| per product.)
+// The product of slices s and t has weight 2^{-8(s+t)}; products of the same
+// level l = s + t (l < NS) share an FP32 accumulator in tensor memory, one per
+// level.  With K = 128, in units of the level's weight, the level sums are
+// below 2^24 for every l <= 5 (level 0: 128 * 256^2 = 2^23; level l >= 1:
+// 128 * (2 * 256 * 128 + (l - 1) * 128^2) <= 2^24), so each is an integer sum
+// that FP32 holds exactly and its tensor-core accumulation is exact.  Levels
+// >= NS are not formed (about 2^-47 of sum |a||b| for NS = 6, 2^-39 for
+// NS = 5), and the operand remainders after NS slices are of the same order.
+// The epilogue adds the accumulators smallest first as an FP32 pair with
+// error-free additions and scales by 2^{ea+eb}.
+//
+// One MMA covers one A slice s against the B slices 0 .. NS-1-s, which sit
+// next to each other in shared memory, so that N runs over the levels s ..
+// NS-1 and the D columns of level l start at 64 l: B's stage is read as one
+// operand of up to 256 rows (four levels) instead of once per pair: NS = 6
+// takes 8 MMAs of N = 64 .. 256 per 16-deep step instead of 21 of N = 64, and
+// reads 74 KB of shared memory instead of 126 KB for the same 672 cycles of
+// tensor work (at 128 B per clock the pairwise form was bound by shared
+// memory, this one by the tensor pipe).
 //
 // Tiles: 128 rows (TMEM lanes) x 64 columns, K = 128 in four k-blocks of 32
 // (64-byte swizzle); a 3-stage TMA ring of (A, B) slice stages.  TMEM holds
-// one set of five accumulators (320 columns); the epilogue copies them to
+// one set of NS accumulators (64 columns each); the epilogue copies them to
 // registers and frees them before its global read-modify-write, so the MMAs
 // of the next tile overlap that traffic.  One launch serves up to two
 // problems (a tile list over both); a problem is rectangular or the lower
@@ -58,33 +61,30 @@ constexpr int THREADS = 320;
 constexpr int EPI_WARPS = 8;
 constexpr int A_SLICE = BM * BK * 2;   // 8 KB
 constexpr int B_SLICE = BN * BK * 2;   // 4 KB
-constexpr int NACC = 5;
+constexpr int NACC_MAX = 6;
 template <int NS> struct Cfg {
   static constexpr int STAGE = NS * (A_SLICE + B_SLICE);
   static constexpr int STAGES = 3;
   static constexpr int SMEM = STAGES * STAGE + 256 + 1024;
-  static constexpr int NPAIR = NS * (NS + 1) / 2;
 };
 static_assert(Cfg<6>::SMEM <= 227 * 1024, "shared memory");
-static_assert(NACC * BN <= 512, "tensor memory");
+static_assert(NACC_MAX * BN <= 512, "tensor memory");
 }  // namespace emu
 
-// pair p -> (s, t) slices in issue order: the merged accumulator's levels
-// (NS-1 down to 4) first, smallest first, then levels 3, 2, 1, 0
+// The MMAs of one 16-deep step: A slice s against B slices t0 .. t0+n-1
+// (levels s+t0 .. s+t0+n-1, N = 64 n <= 256).  The s = 0 MMAs come first and
+// cover every level, so they alone start the accumulators of a tile.
 template <int NS>
-struct Pairs {
-  int s[NS * (NS + 1) / 2], t[NS * (NS + 1) / 2], acc[NS * (NS + 1) / 2], first[NS * (NS + 1) / 2];
-  __host__ __device__ constexpr Pairs() : s(), t(), acc(), first() {
-    int p = 0;
-    int seen = 0;
-    for (int l = NS - 1; l >= 0; --l)
-      for (int a = 0; a <= l; ++a) {
-        s[p] = a;
-        t[p] = l - a;
-        acc[p] = l < 4 ? l : 4;
-        first[p] = (seen >> acc[p]) & 1 ? 0 : 1;   // the first product into its accumulator
-        seen |= 1 << acc[p];
-        ++p;
+struct Mmas {
+  int s[2 * NS], t0[2 * NS], n[2 * NS];
+  int count;
+  __host__ __device__ constexpr Mmas() : s(), t0(), n(), count(0) {
+    for (int a = 0; a < NS; ++a)
+      for (int t = 0; t < NS - a; t += 4) {
+        s[count] = a;
+        t0[count] = t;
+        n[count] = (NS - a - t) < 4 ? (NS - a - t) : 4;
+        ++count;
       }
   }
 };
@@ -125,9 +125,9 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
     k_emu_gemm(const __grid_constant__ EmuParams P, DevStatus* status, uint64_t limit_ns) {
   using namespace emu;
   using C = Cfg<NS>;
-  constexpr int STAGE = C::STAGE, STAGES = C::STAGES, NPAIR = C::NPAIR;
+  constexpr int STAGE = C::STAGE, STAGES = C::STAGES;
   constexpr int A_STAGE = NS * A_SLICE;
-  constexpr Pairs<NS> PR{};
+
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE);
@@ -202,7 +202,7 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ------------------------------------------------ MMA issuer
-      constexpr uint32_t idesc = idesc_bf16_f32(BM, BN);
+      constexpr Mmas<NS> MM{};
       int stage = 0;
       uint32_t phase = 0;
       int tl = 0;
@@ -213,7 +213,6 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
           break;
         }
         tc_fence_after();
-        const uint32_t d0 = tmem_base;
         bool ok = true;
         for (int kb = 0; kb < EK / BK; ++kb) {
           if (!mbar_wait(&full[stage], phase, limit_ns)) {
@@ -225,16 +224,18 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + stage * STAGE);
           // descriptors of every slice are the stage's plus the slice offset
-          // (in 16-byte units, the start-address field): no rebuild per MMA
+          // (in 16-byte units, the start-address field)
           const uint64_t ad0 = smem_desc_sw64(sa), bd0 = smem_desc_sw64(sa + A_STAGE);
           const uint32_t fresh = kb == 0 ? 0u : 1u;   // 0: this tile's first k-block
 #pragma unroll
           for (int kk = 0; kk < 2; ++kk) {
 #pragma unroll
-            for (int p = 0; p < NPAIR; ++p) {
-              const uint32_t accumulate = (kk > 0 || !PR.first[p]) ? 1u : fresh;
-              tc_mma_f16(d0 + (uint32_t)(PR.acc[p] * BN), ad0 + (uint64_t)((PR.s[p] * A_SLICE + kk * 32) >> 4),
-                         bd0 + (uint64_t)((PR.t[p] * B_SLICE + kk * 32) >> 4), idesc, accumulate);
+            for (int i = 0; i < MM.count; ++i) {
+              const uint32_t accumulate = (kk > 0 || MM.s[i] > 0) ? 1u : fresh;
+              tc_mma_f16(tmem_base + (uint32_t)((MM.s[i] + MM.t0[i]) * BN),
+                         ad0 + (uint64_t)((MM.s[i] * A_SLICE + kk * 32) >> 4),
+                         bd0 + (uint64_t)((MM.t0[i] * B_SLICE + kk * 32) >> 4), idesc_bf16_f32(BM, BN * MM.n[i]),
+                         accumulate);
             }
           }
           tc_commit(&empty[stage]);
@@ -268,11 +269,11 @@ __global__ void __launch_bounds__(emu::THREADS, 1)
       // with error-free additions: B300's FP64 rate is a few operations per
       // clock per SM, so FP64 is kept to the final one or two additions
       float hi[32], lo[32];
-      tmem_ld32(ta + (uint32_t)((NACC - 1) * BN), hi);
+      tmem_ld32(ta + (uint32_t)((NS - 1) * BN), hi);
 #pragma unroll
       for (int j = 0; j < 32; ++j) lo[j] = 0.f;
 #pragma unroll
-      for (int ac = NACC - 2; ac >= 0; --ac) {
+      for (int ac = NS - 2; ac >= 0; --ac) {
         float v[32];
         tmem_ld32(ta + (uint32_t)(ac * BN), v);
 #pragma unroll
@@ -373,16 +374,28 @@ __global__ void __launch_bounds__(256) k_emu_split(const EmuSplitParams P) {
   const EmuSplitJob& J = P.job[j];
   const int r0 = ((int)blockIdx.x - J.block0) * 32;
   const int tid = threadIdx.x;
-  const uint64_t* src = reinterpret_cast<const uint64_t*>(J.src);
+  const int nvalid = J.rows_valid < J.rows ? J.rows_valid : J.rows;
+  // the value's double bits (an FP32 value converts exactly), zero outside
+  auto value = [&](int r, int k) -> uint64_t {
+    if (r >= nvalid || k >= J.k_valid || (J.lower && k > r)) return 0ull;
+    const int64_t off = (int64_t)r * J.rs + (int64_t)k * J.ks;
+    if (J.src_f32) {   // FP32 bits -> FP64 bits with integer operations (subnormal FP32 as zero)
+      const uint32_t u = __float_as_uint(reinterpret_cast<const float*>(J.src)[off]);
+      const uint32_t ex = (u >> 23) & 0xFFu;
+      if (ex == 0) return 0ull;
+      return ((uint64_t)(u >> 31) << 63) | ((uint64_t)(ex + 896u) << 52) | ((uint64_t)(u & 0x7FFFFFu) << 29);
+    }
+    return reinterpret_cast<const uint64_t*>(J.src)[off];
+  };
   if (J.rs == 1) {            // rows contiguous: 32 rows per k
     for (int idx = tid; idx < 32 * EK; idx += 256) {
       const int r = idx & 31, k = idx >> 5;
-      tile[r][k] = (r0 + r < J.rows) ? src[(int64_t)(r0 + r) + (int64_t)k * J.ks] : 0ull;
+      tile[r][k] = value(r0 + r, k);
     }
   } else {                    // values of a row contiguous
     for (int idx = tid; idx < 32 * EK; idx += 256) {
       const int k = idx % EK, r = idx / EK;
-      tile[r][k] = (r0 + r < J.rows) ? src[(int64_t)(r0 + r) * J.rs + (int64_t)k * J.ks] : 0ull;
+      tile[r][k] = value(r0 + r, k);
     }
   }
   __syncthreads();
@@ -454,6 +467,73 @@ cudaError_t launch_emu_gemm(const EmuParams& P, int ns, DevStatus* status, int64
   if (ns == 5) return emu_launch<5>(P, status, limit_ns, st, max_ctas);
   if (ns == 6) return emu_launch<6>(P, status, limit_ns, st, max_ctas);
   return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------- host helpers
+td_status slice_buf(SliceBuf& b, int rows, int ns) {
+  b.rows = rows;
+  b.v = nullptr;
+  b.e = nullptr;
+  if (cudaMalloc((void**)&b.v, (size_t)ns * rows * EK * sizeof(__nv_bfloat16)) != cudaSuccess ||
+      cudaMalloc((void**)&b.e, (size_t)rows * sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    free_slice_buf(b);
+    return fail(TD_ERR_OOM, "device allocation failed: operand slices");
+  }
+  td_status r = encode_3d(&b.boxA, b.v, EK, (uint64_t)rows, (uint64_t)ns, EK * 2, (uint64_t)rows * EK * 2, 32,
+                          128, (uint32_t)ns);
+  if (r == TD_OK)
+    r = encode_3d(&b.boxB, b.v, EK, (uint64_t)rows, (uint64_t)ns, EK * 2, (uint64_t)rows * EK * 2, 32, 64,
+                  (uint32_t)ns);
+  return r;
+}
+
+void free_slice_buf(SliceBuf& b) {
+  if (b.v) cudaFree(b.v);
+  if (b.e) cudaFree(b.e);
+  b.v = nullptr;
+  b.e = nullptr;
+}
+
+void add_split_job(EmuSplitParams& P, const void* src, int64_t rs, int64_t ks, int rows, SliceBuf& dst, int ns,
+                   bool src_f32, int rows_valid, bool lower, int k_valid) {
+  if (rows <= 0) return;
+  EmuSplitJob& j = P.job[P.njobs++];
+  j.src = src;
+  j.rs = rs;
+  j.ks = ks;
+  j.rows = rows;
+  j.rows_alloc = dst.rows;
+  j.dst = dst.v;
+  j.e = dst.e;
+  j.ns = ns;
+  j.src_f32 = src_f32 ? 1 : 0;
+  j.rows_valid = rows_valid < 0 ? rows : rows_valid;
+  j.lower = lower ? 1 : 0;
+  j.k_valid = k_valid;
+  j.block0 = P.total_blocks;
+  P.total_blocks += (rows + 31) / 32;
+}
+
+void add_product(EmuParams& P, const SliceBuf& A, const SliceBuf& B, double* C, int64_t ldc, double alpha,
+                 double beta, int m_tiles, int n_tiles, bool lower, int a_row0, int b_row0) {
+  if (m_tiles <= 0 || n_tiles <= 0) return;
+  EmuProb& q = P.p[P.nprob++];
+  q.mapA = A.boxA;
+  q.mapB = B.boxB;
+  q.ea = A.e;
+  q.eb = B.e;
+  q.C = C;
+  q.ldc = ldc;
+  q.alpha = alpha;
+  q.beta = beta;
+  q.a_row0 = a_row0;
+  q.b_row0 = b_row0;
+  q.m_tiles = m_tiles;
+  q.n_tiles = n_tiles;
+  q.lower = lower ? 1 : 0;
+  q.tile_begin = P.total_tiles;
+  P.total_tiles += emu_tiles(q);
 }
 
 }  // namespace td

@@ -168,68 +168,6 @@ td_status talloc(T** p, size_t count, const char* what) {
   return TD_OK;
 }
 
-struct SliceBuf {        // slices [ns][rows][EK] and exponents [rows]
-  __nv_bfloat16* v = nullptr;
-  int* e = nullptr;
-  int rows = 0;
-  CUtensorMap boxA, boxB;  // 128-row (A operand) and 64-row (B operand) boxes
-};
-
-td_status slice_buf(SliceBuf& b, int rows, int ns) {
-  b.rows = rows;
-  td_status r = talloc(&b.v, (size_t)ns * rows * EK, "operand slices");
-  if (r == TD_OK) r = talloc(&b.e, (size_t)rows, "operand exponents");
-  if (r == TD_OK)
-    r = encode_3d(&b.boxA, b.v, EK, (uint64_t)rows, (uint64_t)ns, EK * 2, (uint64_t)rows * EK * 2, 32, 128,
-                  (uint32_t)ns);
-  if (r == TD_OK)
-    r = encode_3d(&b.boxB, b.v, EK, (uint64_t)rows, (uint64_t)ns, EK * 2, (uint64_t)rows * EK * 2, 32, 64,
-                  (uint32_t)ns);
-  return r;
-}
-
-void free_slice_buf(SliceBuf& b) {
-  if (b.v) cudaFree(b.v);
-  if (b.e) cudaFree(b.e);
-  b.v = nullptr;
-  b.e = nullptr;
-}
-
-void add_job(EmuSplitParams& P, const double* src, int64_t rs, int64_t ks, int rows, SliceBuf& dst, int ns) {
-  if (rows <= 0) return;
-  EmuSplitJob& j = P.job[P.njobs++];
-  j.src = src;
-  j.rs = rs;
-  j.ks = ks;
-  j.rows = rows;
-  j.rows_alloc = dst.rows;
-  j.dst = dst.v;
-  j.e = dst.e;
-  j.ns = ns;
-  j.block0 = P.total_blocks;
-  P.total_blocks += (rows + 31) / 32;
-}
-
-void add_prob(EmuParams& P, const SliceBuf& A, const SliceBuf& B, double* C, int64_t ldc, double alpha, double beta,
-              int m_tiles, int n_tiles, bool lower, int a_row0 = 0, int b_row0 = 0) {
-  if (m_tiles <= 0 || n_tiles <= 0) return;
-  EmuProb& q = P.p[P.nprob++];
-  q.mapA = A.boxA;
-  q.mapB = B.boxB;
-  q.ea = A.e;
-  q.eb = B.e;
-  q.C = C;
-  q.ldc = ldc;
-  q.alpha = alpha;
-  q.beta = beta;
-  q.a_row0 = a_row0;
-  q.b_row0 = b_row0;
-  q.m_tiles = m_tiles;
-  q.n_tiles = n_tiles;
-  q.lower = lower ? 1 : 0;
-  q.tile_begin = P.total_tiles;
-  P.total_tiles += emu_tiles(q);
-}
 }  // namespace
 
 td_status factor_tensor(td_segment* s, cudaStream_t st, int ns) {
@@ -291,25 +229,25 @@ td_status factor_tensor(td_segment* s, cudaStream_t st, int ns) {
     if (p > 0 && (e = cudaStreamWaitEvent(st, ev_p, 0)) != cudaSuccess) break;   // block factor p done
     // slices of X_pp (rows), of the panel (rows) and of block row p of B (columns)
     EmuSplitParams S1{};
-    add_job(S1, lblk, 1, PB, PB, sLI, ns);
-    add_job(S1, Lp, 1, ld, (int)T, sAP, ns);
-    add_job(S1, X + o, ld, 1, (int)o, sBP, ns);
+    add_split_job(S1, lblk, 1, PB, PB, sLI, ns);
+    add_split_job(S1, Lp, 1, ld, (int)T, sAP, ns);
+    add_split_job(S1, X + o, ld, 1, (int)o, sBP, ns);
     if ((e = launch_emu_split(S1, st)) != cudaSuccess) break;
     EmuParams G1{};
-    add_prob(G1, sAP, sLI, Lp, ld, 1.0, 0.0, (int)(T / PB), PB / 64, false);
-    add_prob(G1, sLI, sBP, X + o, ld, 1.0, 0.0, 1, (int)(o / 64), false);
+    add_product(G1, sAP, sLI, Lp, ld, 1.0, 0.0, (int)(T / PB), PB / 64, false);
+    add_product(G1, sLI, sBP, X + o, ld, 1.0, 0.0, 1, (int)(o / 64), false);
     if ((e = launch_emu_gemm(G1, ns, s->status, lim, st)) != cudaSuccess) break;
     if (T == 0) break;
     // slices of L_{>p,p} (rows) and of block row p of L^{-1} up to the diagonal (columns)
     EmuSplitParams S2{};
-    add_job(S2, Lp, 1, ld, (int)T, sP, ns);
-    add_job(S2, X + o, ld, 1, (int)(o + PB), sX, ns);
+    add_split_job(S2, Lp, 1, ld, (int)T, sP, ns);
+    add_split_job(S2, X + o, ld, 1, (int)(o + PB), sX, ns);
     if ((e = launch_emu_split(S2, st)) != cudaSuccess) break;
     // G2a: the first 128 columns of the Schur complement (all its rows) and
     // block row p+1 of the inverse
     EmuParams G2a{};
-    add_prob(G2a, sP, sP, s->L + (o + PB) * (1 + ld), ld, -1.0, 1.0, (int)(T / PB), PB / 64, false);
-    add_prob(G2a, sP, sX, X + (o + PB), ld, -1.0, 1.0, 1, (int)((o + PB) / 64), false);
+    add_product(G2a, sP, sP, s->L + (o + PB) * (1 + ld), ld, -1.0, 1.0, (int)(T / PB), PB / 64, false);
+    add_product(G2a, sP, sX, X + (o + PB), ld, -1.0, 1.0, 1, (int)((o + PB) / 64), false);
     if ((e = launch_emu_gemm(G2a, ns, s->status, lim, st)) != cudaSuccess) break;
     if ((e = cudaEventRecord(ev_a, st)) != cudaSuccess) break;
     // block factor of step p+1 beside G2b
@@ -320,9 +258,9 @@ td_status factor_tensor(td_segment* s, cudaStream_t st, int ns) {
     // G2b: the rest of the Schur complement (lower tiles) and of the inverse
     const int64_t T2 = T - PB;
     EmuParams G2b{};
-    add_prob(G2b, sP, sP, s->L + (o + 2 * PB) * (1 + ld), ld, -1.0, 1.0, (int)(T2 / PB), (int)(T2 / 64), true,
+    add_product(G2b, sP, sP, s->L + (o + 2 * PB) * (1 + ld), ld, -1.0, 1.0, (int)(T2 / PB), (int)(T2 / 64), true,
              PB, PB);
-    add_prob(G2b, sP, sX, X + (o + 2 * PB), ld, -1.0, 1.0, (int)(T2 / PB), (int)((o + PB) / 64), false, PB, 0);
+    add_product(G2b, sP, sX, X + (o + 2 * PB), ld, -1.0, 1.0, (int)(T2 / PB), (int)((o + PB) / 64), false, PB, 0);
     if ((e = launch_emu_gemm(G2b, ns, s->status, lim, st, nsm - 1)) != cudaSuccess) break;
   }
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, ev_p, 0);

@@ -22,6 +22,8 @@
 
 namespace td {
 
+constexpr int GROUP_NC = 256;   // residual columns per tile of the small-batch orientation
+
 static td_status group_alloc(void** p, size_t bytes, const char* what) {
   *p = nullptr;
   cudaError_t e = cudaMalloc(p, bytes);
@@ -136,20 +138,27 @@ static void group_free_lists(td_group* g) {
   }
 }
 
-// build work lists and maps for a tile height and chunk multiplier
+// build work lists and maps for a tile shape and chunk multiplier.  bn > 0:
+// the main kernel (128 residual columns as the MMA M, bn operator rows as
+// N); bn == 0: the small-batch kernel's orientation (128 operator rows as M,
+// up to GROUP_NC residual columns as N, each segment's last column tile only
+// as wide as its columns rounded up to 16), every item a chunk whose
+// accumulator pairs the grouped chunk reduction adds.
 static td_status group_build(td_group* g, int bn, int s_factor) {
   group_free_lists(g);
   g->bn = bn;
   g->s_factor = s_factor;
+  const bool small = bn == 0;
+  const int rows = small ? 128 : bn, cols = small ? GROUP_NC : TC_COLS;
   // work per residual-column tile summed over segments; chunk so that the
   // longest item is about 1/(2 s_factor) of an SM's even share
   int64_t tiles_work = 0;
   for (int i = 0; i < g->nseg; ++i) {
     td_segment* s = g->segs[(size_t)i];
-    const int64_t nm = s->nkp / bn, per = bn / OP_KB, nkb_max = ceil_div(s->nk, OP_KB);
+    const int64_t nm = s->nkp / rows, per = rows / OP_KB, nkb_max = ceil_div(s->nk, OP_KB);
     int64_t w = 0;
     for (int64_t m = 0; m < nm; ++m) w += std::min<int64_t>(per * (m + 1), nkb_max);
-    tiles_work += w * ceil_div(g->host_seg[(size_t)i].K, TC_COLS);
+    tiles_work += w * ceil_div(g->host_seg[(size_t)i].K, cols);
   }
   int S = (int)ceil_div(tiles_work, 2LL * s_factor * tc_num_sms());
   if (S < 4) S = 4;
@@ -158,11 +167,11 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
   int n_slots = 0;
   for (int i = 0; i < g->nseg; ++i) {
     td_segment* s = g->segs[(size_t)i];
-    plan_split_segment(i, s->nk, s->nkp, g->host_seg[(size_t)i].K, bn, S, items, units, n_slots);
+    plan_split_segment(i, s->nk, s->nkp, g->host_seg[(size_t)i].K, rows, S, items, units, n_slots, small, cols);
   }
   sort_items(items);
   td_status r;
-  const size_t wbytes = (size_t)n_slots * TC_COLS * bn * sizeof(float2);
+  const size_t wbytes = (size_t)n_slots * (small ? GROUP_NC * 128 : TC_COLS * bn) * sizeof(float2);
   if ((r = group_alloc((void**)&g->d_items, std::max<size_t>(1, items.size()) * sizeof(TcItem), "items")) != TD_OK ||
       (r = group_alloc((void**)&g->d_units, std::max<size_t>(1, units.size()) * sizeof(SplitUnit), "units")) !=
           TD_OK ||
@@ -171,8 +180,9 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
   for (int i = 0; i < g->nseg; ++i) {
     TcSegDev& sd = g->host_seg[(size_t)i];
     td_segment* s = g->segs[(size_t)i];
-    sd.a_rows = TC_COLS;
+    sd.a_rows = small ? GROUP_NC : TC_COLS;
     sd.wpart = g->wpart;
+    sd.nm = (int)(s->nkp / (small ? 128 : 64));   // chi2 partials per 128-row tile or per 64 rows
     if (sd.K == 0) continue;   // no work item refers to an empty segment
     // residual map over this segment's slice region of the group buffer
     const int64_t cap = sd.ldp;
@@ -185,7 +195,7 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
     tmp_view.scr.capK = cap;
     TcSegDev enc;
     memset(&enc, 0, sizeof enc);
-    if ((r = encode_seg_maps(&tmp_view, sd.K, g->nsl, bn, &enc, TC_COLS)) != TD_OK) {
+    if ((r = encode_seg_maps(&tmp_view, sd.K, g->nsl, rows, &enc, small ? GROUP_NC : TC_COLS)) != TD_OK) {
       tmp_view.scr.rs = nullptr;
       tmp_view.op = nullptr;
       return r;
@@ -194,8 +204,6 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
     tmp_view.op = nullptr;
     sd.mapA = enc.mapA;
     sd.mapB = enc.mapB;
-    sd.a_rows = TC_COLS;
-    sd.wpart = g->wpart;
   }
   if (cudaMemcpy(g->d_seg, g->host_seg.data(), g->host_seg.size() * sizeof(TcSegDev), cudaMemcpyHostToDevice) !=
           cudaSuccess ||
@@ -236,9 +244,14 @@ static td_status group_launch_impl(td_group* g, cudaStream_t st) {
     k_r_slices_grouped<<<gx, 256, 0, st>>>(g->d_jobs, g->nseg, g->total_cols, g->nsl);
     TD_CUDA(cudaGetLastError());
   }
-  TD_CUDA(launch_tc_cdo(g->d_items, g->n_items, g->d_seg, g->nsl, g->bn, true, g->status, g->wait_limit_ns, st,
-                        false));
-  TD_CUDA(launch_split_reduce(g->d_units, g->n_units, g->d_seg, g->bn, st, g->maxK));
+  if (g->bn == 0) {
+    TD_CUDA(launch_tc_small(g->d_items, g->n_items, g->d_seg, g->nsl, GROUP_NC, g->status, g->wait_limit_ns, st));
+    TD_CUDA(launch_small_reduce_grouped(g->d_units, g->n_units, g->d_seg, GROUP_NC, st));
+  } else {
+    TD_CUDA(launch_tc_cdo(g->d_items, g->n_items, g->d_seg, g->nsl, g->bn, true, g->status, g->wait_limit_ns, st,
+                          false));
+    TD_CUDA(launch_split_reduce(g->d_units, g->n_units, g->d_seg, g->bn, st, g->maxK));
+  }
   TD_CUDA(launch_tc_finalize(g->d_seg, g->nseg, g->maxK, st));
   if (g->joint && g->joint_K > 0) {
     k_joint_sum<<<(unsigned)ceil_div(g->joint_K, 256), 256, 0, st>>>(g->d_seg, g->nseg, g->joint_K, g->joint);
@@ -371,6 +384,7 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
   }
   if (o.path == TD_PATH_STREAM64) bn = 64;
   if (o.path == TD_PATH_STREAM) bn = 256;
+  if (o.path == TD_PATH_SMALLK) bn = 0;
   if ((r = group_build(g, bn, sf)) != TD_OK) {
     td_group_destroy(g);
     return r;
@@ -433,7 +447,8 @@ td_status td_group_graph_launch(td_group* g, void* stream) {
 td_status td_group_tune(td_group* g, void* stream, double* best_ms) {
   if (!g) return fail(TD_ERR_INVALID, "group is NULL");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  const int cand[][2] = {{256, 1}, {256, 2}, {128, 1}, {128, 2}, {128, 4}, {64, 1}, {64, 2}};
+  // tile rows (0: the small-batch orientation) and chunk multiplier
+  const int cand[][2] = {{256, 1}, {256, 2}, {128, 1}, {128, 2}, {128, 4}, {64, 1}, {64, 2}, {0, 1}, {0, 2}, {0, 4}};
   double best = 1e300;
   int bb = g->bn, bs = g->s_factor;
   cudaEvent_t a, b;

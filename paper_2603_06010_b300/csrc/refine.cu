@@ -20,6 +20,15 @@
 // alone) and the chunk reduction's modes do it.  A fixed path (TD_PATH_TENSOR*/STREAM*) fixes the shape, so a
 // column's result then does not depend on its batch.
 //
+// Mode 2 (td_options.refine = 2) forms s = r - L w~ to FP64 accuracy instead:
+// split products of six exact bf16 slices of L and of w~ on the tensor cores
+// (the factor's emulation, emu_gemm.cu), one 128-column chunk of L at a time,
+// accumulated in FP64 and rounded to FP32 once (s is small, so its FP32
+// rounding costs about 6e-8 of s); the correction delta = L^{-1} s runs with
+// at least six products (BF16X3's own bias, ~1e-5 of delta, would otherwise
+// remain at ~1e-10 of w).  The refined chi2 then carries the operator's error
+// squared, far below FP64 chi2's own summation error of the first pass.
+//
 // Needs the FP64 factor L to slice (once per factor); segments whose L was
 // released, or whose operator came from the Levinson-Durbin route, return
 // TD_ERR_UNSUPPORTED.
@@ -28,7 +37,7 @@
 #include <string>
 #include <vector>
 
-#include "td_internal.h"
+#include "emu_gemm.h"
 
 namespace td {
 
@@ -67,16 +76,24 @@ static int refine_whole_rows(const td_segment* s, int64_t K, int path) {
   return 0;
 }
 
-static td_status refine_whole_maps(td_segment* s, int64_t K, int nsl, int bn) {
+// whole-row descriptors: [0] L^{-1} with nsl slices; [1] mode 1: L's slices
+// (four), mode 2: L^{-1} with nsl1 slices (the correction's product)
+static td_status refine_whole_maps(td_segment* s, int64_t K, int nsl, int bn, int mode, int nsl1) {
   RefineState& f = s->ref;
   const Scratch& sc = s->scr;
-  if (f.whole_K == K && f.whole_nsl == nsl && f.whole_bn == bn && f.whole_rs == sc.rs && f.whole_op == s->op)
+  if (f.whole_K == K && f.whole_nsl == nsl && f.whole_bn == bn && f.whole_rs == sc.rs && f.whole_op == s->op &&
+      f.mode == mode && f.nsl1 == nsl1)
     return TD_OK;
   f.whole_K = -1;
+  f.K = -1;   // the split lists hold the other mode's descriptors
+  f.mode = mode;
+  f.nsl1 = nsl1;
   for (int w = 0; w < 2; ++w) {
     TcSegDev& d = f.whole[w];
     memset(&d, 0, sizeof d);
-    td_status r = encode_seg_maps(s, K, w == 0 ? nsl : OP_SLICES, bn, &d, TC_COLS, w == 0 ? s->op : f.lop);
+    const int ns = w == 0 ? nsl : (mode == 2 ? nsl1 : OP_SLICES);
+    const __nv_bfloat16* op = (w == 0 || mode == 2) ? s->op : f.lop;
+    td_status r = encode_seg_maps(s, K, ns, bn, &d, TC_COLS, op);
     if (r != TD_OK) return r;
     d.partials = sc.partials;
     d.nk = (int)s->nk;
@@ -104,13 +121,29 @@ static void drop_plan(RefineState& f) {
   f.whole_K = -1;
 }
 
+struct EmuRefine {          // mode 2: slices of one 128-column chunk of L and of w~
+  SliceBuf a, b;
+  int64_t cap = 0;
+};
+
+static void free_emu(RefineState& f) {
+  if (!f.emu) return;
+  EmuRefine* m = static_cast<EmuRefine*>(f.emu);
+  free_slice_buf(m->a);
+  free_slice_buf(m->b);
+  delete m;
+  f.emu = nullptr;
+}
+
 void free_refine_state(td_segment* s) {
   RefineState& f = s->ref;
   drop_plan(f);
   ref_free(f.lop);
   ref_free(f.w32);
   ref_free(f.s32);
+  ref_free(f.s64);
   ref_free(f.wpart);
+  free_emu(f);
   f.cap = 0;
   f.wpart_elems = 0;
 }
@@ -140,10 +173,10 @@ static td_status build_lop(td_segment* s, cudaStream_t st) {
   return TD_OK;
 }
 
-static td_status refine_plan(td_segment* s, int64_t K, int nsl, cudaStream_t st) {
+static td_status refine_plan(td_segment* s, int64_t K, int nsl, int mode, int nsl1, cudaStream_t st) {
   RefineState& f = s->ref;
   const Scratch& sc = s->scr;
-  if (f.K == K && f.nsl == nsl && f.rs == sc.rs && f.op == s->op) return TD_OK;
+  if (f.K == K && f.nsl == nsl && f.rs == sc.rs && f.op == s->op && f.mode == mode && f.nsl1 == nsl1) return TD_OK;
   cudaStreamSynchronize(st);   // the old lists may still be read on this stream
   drop_plan(f);
   const int S = std::max(split_chunk(s->nk, s->nkp, REF_BN), REF_MIN_CHUNK);
@@ -164,9 +197,9 @@ static td_status refine_plan(td_segment* s, int64_t K, int nsl, cudaStream_t st)
   memset(seg, 0, sizeof seg);
   const int a_rows = (int)std::min<int64_t>(TC_COLS, round_up(K, 8));
   for (int w = 0; w < 2; ++w) {
-    if ((r = encode_seg_maps(s, K, w == 0 ? nsl : OP_SLICES, REF_BN, &seg[w], a_rows, w == 0 ? s->op : f.lop)) !=
-        TD_OK)
-      return r;
+    const int ns = w == 0 ? nsl : (mode == 2 ? nsl1 : OP_SLICES);
+    const __nv_bfloat16* op = (w == 0 || mode == 2) ? s->op : f.lop;
+    if ((r = encode_seg_maps(s, K, ns, REF_BN, &seg[w], a_rows, op)) != TD_OK) return r;
     seg[w].partials = sc.partials;
     seg[w].wpart = f.wpart;
     seg[w].nk = (int)s->nk;
@@ -188,17 +221,85 @@ static td_status refine_plan(td_segment* s, int64_t K, int nsl, cudaStream_t st)
   f.n_units = (int)units.size();
   f.K = K;
   f.nsl = nsl;
+  f.whole_K = -1;   // the whole-row descriptors may hold the other mode's
+  f.mode = mode;
+  f.nsl1 = nsl1;
   f.rs = sc.rs;
   f.op = s->op;
   return TD_OK;
 }
 
+// s64 = r (kept rows, FP64), zero beyond K columns and N' rows
+__global__ void k_s64_init(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t nkp, int64_t K, int64_t Kp,
+                           double* __restrict__ s64) {
+  const int64_t n = nkp * Kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % nkp, k = e / nkp;
+    s64[e] = (i < nk && k < K) ? (double)R[i + k * ldr] : 0.0;
+  }
+}
+
+// s32 = fl32(s64)
+__global__ void k_s32_from_s64(const double* __restrict__ s64, int64_t n, float* __restrict__ s32) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    s32[e] = __double2float_rn(s64[e]);
+}
+
+// s = r - L w~ to FP64 accuracy (mode 2): for each 128-column chunk c of L,
+// the rows of L at and below the chunk's diagonal block and the columns of w~
+// over the chunk's 128 rows become six exact bf16 slices, and their split
+// product is subtracted from s64 (FP64) on the tensor cores.
+static td_status refine_residual_fp64(td_segment* s, const float* R, int64_t ldr, int64_t K, int64_t lim,
+                                      cudaStream_t st) {
+  RefineState& f = s->ref;
+  const int64_t nkp = s->nkp, nk = s->nk, Kp = round_up(K, 64);
+  td_status r;
+  EmuRefine* m = static_cast<EmuRefine*>(f.emu);
+  if (!m) {
+    m = new EmuRefine();
+    f.emu = m;
+    if ((r = slice_buf(m->a, (int)nkp, EMU_SLICES)) != TD_OK) return r;
+  }
+  if (m->cap < f.cap) {
+    cudaStreamSynchronize(st);
+    free_slice_buf(m->b);
+    ref_free(f.s64);
+    m->cap = 0;
+    if ((r = slice_buf(m->b, (int)f.cap, EMU_SLICES)) != TD_OK ||
+        (r = ref_alloc(&f.s64, (size_t)(f.cap * nkp), "FP64 refinement residual")) != TD_OK)
+      return r;
+    m->cap = f.cap;
+  }
+  const unsigned grid = (unsigned)std::min<int64_t>(4096, ceil_div(nkp * Kp, 256));
+  k_s64_init<<<grid, 256, 0, st>>>(R, ldr, nk, nkp, K, Kp, f.s64);
+  TD_CUDA(cudaGetLastError());
+  const int64_t ld = nkp;
+  for (int64_t c = 0; c * EK < nk; ++c) {
+    const int64_t c0 = c * EK, rows = nkp - c0;
+    EmuSplitParams S{};
+    add_split_job(S, s->L + c0 * (1 + ld), 1, ld, (int)rows, m->a, EMU_SLICES, false, -1, true, (int)(nk - c0));
+    add_split_job(S, f.w32 + c0, ld, 1, (int)Kp, m->b, EMU_SLICES, true, (int)K, false, (int)(nk - c0));
+    TD_CUDA(launch_emu_split(S, st));
+    EmuParams G{};
+    add_product(G, m->a, m->b, f.s64 + c0, ld, -1.0, 1.0, (int)(rows / EK), (int)(Kp / 64), false);
+    TD_CUDA(launch_emu_gemm(G, EMU_SLICES, s->status, lim, st));
+  }
+  k_s32_from_s64<<<grid, 256, 0, st>>>(f.s64, nkp * K, f.s32);
+  TD_CUDA(cudaGetLastError());
+  return TD_OK;
+}
+
 td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl,
-                       int path, int64_t wait_limit_ns, cudaStream_t st) {
+                       int mode, int path, int64_t wait_limit_ns, cudaStream_t st) {
   RefineState& f = s->ref;
   Scratch& sc = s->scr;
   td_status r;
-  if (!f.lop && (r = build_lop(s, st)) != TD_OK) return r;
+  if (!s->L)
+    return fail(TD_ERR_UNSUPPORTED,
+                "refinement needs the FP64 factor L, which this segment released or never formed "
+                "(Levinson-Durbin route)");
+  if (mode == 1 && !f.lop && (r = build_lop(s, st)) != TD_OK) return r;
+  const int nsl1 = mode == 2 ? std::max(nsl, 3) : OP_SLICES;   // slices of the second product
   if (sc.capK > f.cap) {
     cudaStreamSynchronize(st);
     ref_free(f.w32);
@@ -210,33 +311,39 @@ td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, do
     f.cap = sc.capK;
   }
   const int64_t ld = s->nkp;
+  const int ncorr = mode == 2 ? nsl1 : nsl;   // slices of the correction delta = L^{-1} s
   if (const int bn = refine_whole_rows(s, K, path)) {
-    if ((r = refine_whole_maps(s, K, nsl, bn)) != TD_OK) return r;
+    if ((r = refine_whole_maps(s, K, nsl, bn, mode, nsl1)) != TD_OK) return r;
     const int nc = (int)ceil_div(K, TC_COLS), nkb_max = (int)ceil_div(s->nk, OP_KB);
     RefineIO io;
     io.out = f.w32;
     io.ldo = ld;
     TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
     TD_CUDA(launch_tc_single_ew(f.whole[0], bn, 3, nc, nkb_max, nsl, io, s->status, wait_limit_ns, st));
-    io = RefineIO();
-    io.in = R;
-    io.ldi = ldr;
-    io.out = f.s32;
-    io.ldo = ld;
-    TD_CUDA(launch_r_slices(f.w32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, OP_SLICES, st));
-    TD_CUDA(launch_tc_single_ew(f.whole[1], bn, 4, nc, nkb_max, OP_SLICES, io, s->status, wait_limit_ns, st));
+    if (mode == 2) {
+      if ((r = refine_residual_fp64(s, R, ldr, K, wait_limit_ns, st)) != TD_OK) return r;
+    } else {
+      io = RefineIO();
+      io.in = R;
+      io.ldi = ldr;
+      io.out = f.s32;
+      io.ldo = ld;
+      TD_CUDA(launch_r_slices(f.w32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, OP_SLICES, st));
+      TD_CUDA(launch_tc_single_ew(f.whole[1], bn, 4, nc, nkb_max, OP_SLICES, io, s->status, wait_limit_ns, st));
+    }
     io = RefineIO();
     io.in = f.w32;
     io.ldi = ld;
-    TD_CUDA(launch_r_slices(f.s32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
-    TD_CUDA(launch_tc_single_ew(f.whole[0], bn, 5, nc, nkb_max, nsl, io, s->status, wait_limit_ns, st));
+    TD_CUDA(launch_r_slices(f.s32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, ncorr, st));
+    TD_CUDA(launch_tc_single_ew(f.whole[mode == 2 ? 1 : 0], bn, 5, nc, nkb_max, ncorr, io, s->status, wait_limit_ns,
+                                st));
     TD_CUDA(launch_finalize(sc.partials, sc.capK, (int)(s->nkp / 64), K, s->logdet, s->nk, logL, chi2, st));
     s->prof_kernels += 7;
     return TD_OK;
   }
-  if ((r = refine_plan(s, K, nsl, st)) != TD_OK) return r;
+  if ((r = refine_plan(s, K, nsl, mode, nsl1, st)) != TD_OK) return r;
   const TcSegDev* seg_linv = f.seg_op;
-  const TcSegDev* seg_l = f.seg_op + 1;
+  const TcSegDev* seg_l = f.seg_op + 1;   // mode 2: L^{-1} with nsl1 slices
   // w~ = L^{-1} r, rounded to FP32
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_linv, nsl, REF_BN, true, s->status, wait_limit_ns, st));
@@ -245,21 +352,26 @@ td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, do
   io.ldo = ld;
   TD_CUDA(launch_split_reduce(f.units, f.n_units, seg_linv, REF_BN, st, K, RED_WRITE, io));
   // s = r - L w~
-  TD_CUDA(launch_r_slices(f.w32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, OP_SLICES, st));
-  TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_l, OP_SLICES, REF_BN, true, s->status, wait_limit_ns, st));
-  io = RefineIO();
-  io.in = R;
-  io.ldi = ldr;
-  io.out = f.s32;
-  io.ldo = ld;
-  TD_CUDA(launch_split_reduce(f.units, f.n_units, seg_l, REF_BN, st, K, RED_RESID, io));
+  if (mode == 2) {
+    if ((r = refine_residual_fp64(s, R, ldr, K, wait_limit_ns, st)) != TD_OK) return r;
+  } else {
+    TD_CUDA(launch_r_slices(f.w32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, OP_SLICES, st));
+    TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_l, OP_SLICES, REF_BN, true, s->status, wait_limit_ns, st));
+    io = RefineIO();
+    io.in = R;
+    io.ldi = ldr;
+    io.out = f.s32;
+    io.ldo = ld;
+    TD_CUDA(launch_split_reduce(f.units, f.n_units, seg_l, REF_BN, st, K, RED_RESID, io));
+  }
   // delta = L^{-1} s; chi2 of w~ + delta
-  TD_CUDA(launch_r_slices(f.s32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
-  TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_linv, nsl, REF_BN, true, s->status, wait_limit_ns, st));
+  const TcSegDev* seg_corr = mode == 2 ? seg_l : seg_linv;
+  TD_CUDA(launch_r_slices(f.s32, ld, s->nk, K, s->nkp8, sc.capK, sc.rs, ncorr, st));
+  TD_CUDA(launch_tc_cdo(f.items, f.n_items, seg_corr, ncorr, REF_BN, true, s->status, wait_limit_ns, st));
   io = RefineIO();
   io.in = f.w32;
   io.ldi = ld;
-  TD_CUDA(launch_split_reduce(f.units, f.n_units, seg_linv, REF_BN, st, K, RED_FINAL, io));
+  TD_CUDA(launch_split_reduce(f.units, f.n_units, seg_corr, REF_BN, st, K, RED_FINAL, io));
   TD_CUDA(launch_finalize(sc.partials, sc.capK, (int)(s->nkp / 64), K, s->logdet, s->nk, logL, chi2, st));
   s->prof_kernels += 10;
   return TD_OK;

@@ -212,7 +212,6 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
     }
   } else if (warp == 1) {
     if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16_f32(BM, NC);
       int stage = 0;
       uint32_t phase = 0;
       int tl = 0;
@@ -220,6 +219,11 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
         const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
         if (idx >= n_items) continue;
         const TcItem it = items[idx];
+        // the MMA covers the item's columns rounded up to 16, not the whole tile
+        // (a segment's last column tile in a grouped launch): each column's
+        // arithmetic is the same either way
+        const int ncol_m = min(NC, segs[it.seg].K - it.c * NC);
+        const uint32_t idesc = idesc_bf16_f32(BM, (ncol_m + 15) & ~15);
         const int buf = tl % NBUF;
         const uint32_t use = (uint32_t)(tl / NBUF);
         if (!mbar_wait(&tempty[buf], (use & 1u) ^ 1u, limit_ns)) {
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
       // stores or its chi2 terms (NC = 256 would not fit in registers at once)
       float2* dst = it.slot >= 0 ? sd->wpart + (int64_t)it.slot * C::SLOT_COLS * BM + q * 32 + lane : nullptr;
 #pragma unroll 1
-      for (int h = 0; h < NC / 16; ++h) {
+      for (int h = 0; h < (ncol + 15) / 16; ++h) {
         float t0[16], t1[16];
         tmem_ld16(ta + (uint32_t)(h * 16), t0);
         tmem_ld16(ta + (uint32_t)(NC + h * 16), t1);
@@ -445,6 +449,75 @@ __global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict
   if (!sh_last) return;
   __threadfence();
   small_final_cols(sd, fin, n0, CB, sh);
+}
+
+// Chunk reduction of a grouped small-orientation launch (many segments, every
+// item a chunk): grid (units, nc / 4), 128 threads (rows of the 128-row
+// tile).  As k_small_reduce for one unit's four columns (chunk order fixed,
+// double-float, exact squares, fixed shuffle tree, the four 32-row groups in
+// order), writing the tile's chi2 partial of each column; the per-segment
+// sums over tiles are k_tc_finalize's.
+__global__ void __launch_bounds__(128) k_small_reduce_grouped(const SplitUnit* __restrict__ units,
+                                                              const TcSegDev* __restrict__ segs, int nc,
+                                                              int slot_cols) {
+  __shared__ double sh[4][4];
+  const SplitUnit u = units[blockIdx.x];
+  const TcSegDev* sd = &segs[u.seg];
+  const int ncol = min(nc, sd->K - u.c * nc);
+  const int n0 = blockIdx.y * 4;
+  if (n0 >= ncol) return;
+  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  const float2* base = sd->wpart + (int64_t)u.slot0 * slot_cols * 128 + threadIdx.x;
+  constexpr int CB = 4, CH = 4;
+  float wh[CB], wl[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
+  for (int ch0 = 0; ch0 < u.nchunk; ch0 += CH) {
+    float2 v[CH][CB];
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const int n = min(n0 + c, ncol - 1);
+        v[i][c] = ch0 + i < u.nchunk ? __ldcg(base + ((int64_t)(ch0 + i) * slot_cols + n) * 128)
+                                     : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (ch0 + i < u.nchunk) {
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          ff_add(v[i][c].x, wh[c], wl[c]);
+          ff_add(v[i][c].y, wh[c], wl[c]);
+        }
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < CB; ++c) {
+    float hi = 0.f, lo = 0.f;
+    ff_add_square2(wh[c], wl[c], hi, lo);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+      const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+      ff_add(oh, hi, lo);
+      lo += ol;
+    }
+    if (lane == 0) sh[q][c] = (double)hi + (double)lo;
+  }
+  __syncthreads();
+  if (threadIdx.x < CB && n0 + threadIdx.x < ncol) {
+    const int c = threadIdx.x;
+    sd->partials[(int64_t)u.m * sd->ldp + u.c * nc + n0 + c] = ((sh[0][c] + sh[1][c]) + sh[2][c]) + sh[3][c];
+  }
+}
+
+cudaError_t launch_small_reduce_grouped(const SplitUnit* units, int n_units, const TcSegDev* segs, int nc,
+                                        cudaStream_t st) {
+  if (n_units <= 0) return cudaSuccess;
+  k_small_reduce_grouped<<<dim3((unsigned)n_units, (unsigned)(nc / 4)), 128, 0, st>>>(units, segs, nc,
+                                                                                    nc > 128 ? nc : 128);
+  return cudaGetLastError();
 }
 
 static cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, size_t smem, cudaStream_t st, void** args) {

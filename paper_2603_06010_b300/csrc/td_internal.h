@@ -177,7 +177,11 @@ struct RefineState {          // td_options.refine
   int n_items = 0;
   td::SplitUnit* units = nullptr;
   int n_units = 0;
-  td::TcSegDev* seg_op = nullptr;   // [0]: L^{-1} slices (nsl), [1]: L slices (4)
+  td::TcSegDev* seg_op = nullptr;   // [0]: L^{-1} slices (nsl), [1]: L slices (4), or L^{-1} (mode 2)
+  int mode = 0;                     // refinement mode the cached lists were built for
+  int nsl1 = 0;                     // slices of the second product's operator
+  double* s64 = nullptr;            // mode 2: FP64 residual r - L w~, [cap][N'p]
+  void* emu = nullptr;              // mode 2: operand slice buffers of the residual's split products
   // whole-row descriptors (host copies, passed by value to the kernel)
   td::TcSegDev whole[2];
   int64_t whole_K = -1;
@@ -302,6 +306,10 @@ struct SmallFinal {
 cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
                             DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
 cudaError_t launch_small_reduce(const TcSegDev* segs, const SmallFinal& fin, cudaStream_t st);
+// the chunk reduction of a grouped small-orientation launch (nc-column tiles,
+// every item a chunk); writes each unit's chi2 partials for k_tc_finalize
+cudaError_t launch_small_reduce_grouped(const SplitUnit* units, int n_units, const TcSegDev* segs, int nc,
+                                        cudaStream_t st);
 cudaError_t launch_tc_single(const TcSegDev& seg, int bn, int nc, int nkb_max, int nslices, DevStatus* status,
                              int64_t wait_limit_ns, cudaStream_t st);
 // refinement products over whole bn-row tiles (256 or 128) with an element-wise
@@ -345,7 +353,7 @@ td_status reserve_with(td_segment* s, Scratch& sc, int64_t K, const td_options* 
 td_status scratch_init_shared(Scratch& sc, int64_t max_kept, int64_t maxK);
 void scratch_free(Scratch& sc);
 // one refinement step (td_options.refine), launched on st
-td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl,
+td_status refine_batch(td_segment* s, const float* R, int64_t ldr, int64_t K, double* logL, double* chi2, int nsl, int mode,
                        int path, int64_t wait_limit_ns, cudaStream_t st);
 void free_refine_state(td_segment* s);
 // Gohberg-Semencul path (TD_PATH_GSCE)

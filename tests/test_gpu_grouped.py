@@ -83,13 +83,36 @@ def test_grouped_plan_graph_and_tune(torch_cuda, gpu_lib):
     ms = g.tune()
     assert ms > 0
     bn, sf, ni = g.shape()
-    assert bn in (64, 128, 256) and sf >= 1 and ni > 0
+    assert bn in (0, 64, 128, 256) and sf >= 1 and ni > 0
     for x in outs:
         x.fill_(np.nan)
     g.launch()
     torch_cuda.cuda.synchronize()
     g.check()
     _check_all(outs, chis, exp_ll, exp_chi)
+    g.close()
+
+
+def test_grouped_small_orientation(torch_cuda, gpu_lib):
+    """The small-batch kernel's orientation in a grouped launch (operator rows as
+    the MMA M, up to 256 residual columns as N, each segment's last column tile
+    only as wide as its columns): oracle parity, and graph replay bit for bit."""
+    from paper_2603_06010_b300 import td
+    segs, Rs, outs, chis, exp_ll, exp_chi = _build(torch_cuda, td)
+    g = td.Group(segs, Rs, outs, chis, opt=td.options(path=td.TD_PATH_SMALLK))
+    assert g.shape()[0] == 0
+    g.launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    _check_all(outs, chis, exp_ll, exp_chi)
+    first = [x.cpu().numpy().copy() for x in outs]
+    for x in outs:
+        x.fill_(np.nan)
+    g.graph_launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    for a, b in zip(first, outs):
+        assert np.array_equal(a, b.cpu().numpy())
     g.close()
 
 

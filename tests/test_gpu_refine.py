@@ -166,3 +166,43 @@ def test_refined_whole_rows(torch_cuda, gpu_lib):
     for k in (0, 517, 899):
         one, _ = _run(torch_cuda, seg, R[k:k + 1], opt)
         assert one[0] == full[k], k
+
+
+FP64_CASES = [   # (name, n, fs, gap spans, K, path): split and whole-row shapes, ragged tiles
+    ("n1_k3", 1, 1024.0, None, 3, "auto"),
+    ("n257_gaps_k129", 257, 1024.0, [(10, 30), (100, 120)], 129, "auto"),
+    ("n2048_gaps_k300", 2048, 2048.0, [(500, 1012), (1500, 1600)], 300, "auto"),
+    ("n2100_gap_k900_whole", 2100, 2048.0, [(1000, 1100)], 900, "auto"),
+    ("n1100_k70_stream128", 1100, 4096.0, None, 70, "stream128"),
+]
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("case", FP64_CASES, ids=[c[0] for c in FP64_CASES])
+def test_refined_fp64_residual(torch_cuda, gpu_lib, case, prec):
+    """refine = 2: the residual s = r - L w~ formed to FP64 accuracy by split
+    products on the tensor cores; chi2 within 1e-10 of the oracle from either
+    first-pass precision, and with a fixed shape a column's bits do not depend
+    on its batch."""
+    from paper_2603_06010_b300 import td
+    name, n, fs, spans, K, path = case
+    p = {"bf16x3": td.TD_PREC_BF16X3, "bf16x6": td.TD_PREC_BF16X6}[prec]
+    pth = {"auto": td.TD_PATH_AUTO, "stream128": td.TD_PATH_STREAM128}[path]
+    mask = None if spans is None else _mask(n, spans)
+    acf = inputs.acf_from_psd(n, fs) if n > 1 else np.array([2.5])
+    o = oracle.OracleSegment(acf, mask)
+    rng = np.random.default_rng(zlib.crc32(name.encode()))
+    R = inputs.noise_residuals(n, fs, K, 33, mask=mask) if n > 1 else \
+        rng.standard_normal((K, 1)).astype(np.float32)
+    exp_chi = o.chi2(R)
+    exp_ll = oracle.loglike_from_chi2(exp_chi, o.logdet, o.n_kept)
+    seg = td.Segment(acf, mask)
+    opt = td.options(precision=p, refine=2, path=pth)
+    ll, chi = _run(torch_cuda, seg, R, opt)
+    rel = np.max(np.abs(chi - exp_chi) / exp_chi)
+    assert np.all(np.isfinite(ll))
+    assert rel <= 1e-10, f"{name} {prec}: chi2 rel {rel:.3e}"
+    assert np.max(np.abs(ll - exp_ll)) <= 1e-6
+    if path != "auto":   # a fixed shape: a column alone gives the bits it gives in the batch
+        one, _ = _run(torch_cuda, seg, R[K - 1:K], opt)
+        assert one[0] == ll[K - 1]

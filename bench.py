@@ -48,6 +48,10 @@ def parse():
     p.add_argument("--serve-seconds", type=float, default=5.0)
     p.add_argument("--core", action="store_true",
                    help="the headline workload, its end-to-end figure and the CPU baseline only (profiling)")
+    p.add_argument("--mix-segments", type=int, default=64,
+                   help="segments of the grouped mix (fewer: a small case for profiling)")
+    p.add_argument("--factor-n", default="16384,32768",
+                   help="segment lengths of the factor block (3 gaps of 512 each)")
     p.add_argument("--only", default=None,
                    choices=["grouped", "serving", "gapped3", "refine", "gsce", "small", "factor"],
                    help="run one extra workload alone and print its JSON object (profiling; not the bench line)")
@@ -378,10 +382,11 @@ def gapped_joint_extra(td, torch):
             "max_abs_dlogL_joint_vs_oracle": dlogl, "factor_s": factor_s, "checkpoint": ck}
 
 
-def grouped_extra(td, torch):
-    """The 64-segment uneven mix (N log-uniform in [512, 32768]) in one grouped launch."""
+def grouped_extra(td, torch, count=64):
+    """The 64-segment uneven mix (N log-uniform in [512, 32768]) in one grouped launch
+    (count < 64: the mix's first segments, a small case for profiling)."""
     from paper_2603_06010_b300 import inputs
-    specs = inputs.mix64_segments(count=64)
+    specs = inputs.mix64_segments(count=count)
     rng = np.random.default_rng(4040)
     segs, Rs, outs = [], [], []
     t0 = time.perf_counter()
@@ -427,7 +432,7 @@ def grouped_extra(td, torch):
         dlogl = worst
     except Exception as ex:
         dlogl = repr(ex)
-    return {"note": "64 segments, N log-uniform in [512, 32768], K uniform in [16, 512], own PSD each "
+    return {"note": f"{len(specs)} segments, N log-uniform in [512, 32768], K uniform in [16, 512], own PSD each "
                     "(operators by the Levinson-Durbin build); one captured-graph grouped launch",
             "segments": len(segs), "columns": cols, "ms_per_launch": ms, "evals_per_s": cols / (ms / 1e3),
             "algorithmic_tflops": flops / (ms / 1e3) / 1e12, "tile_rows": bn, "chunk_factor": sf,
@@ -435,7 +440,7 @@ def grouped_extra(td, torch):
             "max_abs_dlogL_vs_oracle_4_shortest": dlogl}
 
 
-def factor_extra(td, torch, with_fp64_cores=True):
+def factor_extra(td, torch, with_fp64_cores=True, sizes=(16384, 32768)):
     """The factor C = L L^T with L^{-1} and the operator slices (once per segment):
     gapped N=16384 (3 gaps of 512, N'=14848) and gapped N=32768 (N'=31232) on the
     tensor-core route, and the N=16384 segment on the FP64 CUDA-core route beside it."""
@@ -444,7 +449,8 @@ def factor_extra(td, torch, with_fp64_cores=True):
                    "updates as FP64-accurate split bf16 products on the tensor cores (six slices); wall time "
                    "of the synchronous call (covariance gather, factor, L^-1, log det, operator slices)",
            "runs": []}
-    for n, seed in ((16384, 3003), (32768, 3004)):
+    for n in sizes:
+        seed = {16384: 3003, 32768: 3004}.get(n, 3000 + n % 997)
         si = inputs.make_segment(n, 2048.0, seed, n_gaps=3, gap_len=512)
         runs = {}
         for route in (("tensor", 0), ("fp64_cores", td.TD_FACTOR_FP64_CORES)):
@@ -794,9 +800,10 @@ def main():
             seg = td.Segment(seg_in.acf, seg_in.mask)
             return small_batches(td, torch, seg, torch.from_numpy(R_host).cuda(), R_host.shape[1],
                                  td.TD_PREC_BF16X6, "bf16x6")
-        fn = {"grouped": lambda: grouped_extra(td, torch), "serving": lambda: serving_extra(td, torch, args.serve_seconds),
+        fsizes = tuple(int(x) for x in args.factor_n.split(","))
+        fn = {"grouped": lambda: grouped_extra(td, torch, args.mix_segments), "serving": lambda: serving_extra(td, torch, args.serve_seconds),
               "gapped3": lambda: gapped_joint_extra(td, torch), "refine": only_refine, "gsce": only_gsce,
-              "small": only_small, "factor": lambda: factor_extra(td, torch)}[args.only]
+              "small": only_small, "factor": lambda: factor_extra(td, torch, sizes=fsizes)}[args.only]
         print(json.dumps({"only": args.only, "result": fn()}), flush=True)
         return
 
@@ -974,7 +981,7 @@ def main():
         "clocks": clk,
     }
     if world == 1 and not args.core:
-        line["factor"] = factor_extra(td, torch)
+        line["factor"] = factor_extra(td, torch, sizes=tuple(int(x) for x in args.factor_n.split(",")))
         line["template_form"] = template_extra(td, torch, seg, seg_in, K)
         line["refinement"] = refine_extra(td, torch, seg, R, K)
         line["gsce"] = gsce_extra(td, torch, seg_in, R, K)
@@ -990,7 +997,7 @@ def main():
                                          "latency_ms": gj["latency_ms"],
                                          "max_abs_dlogL_vs_oracle": gj["max_abs_dlogL_joint_vs_oracle"]}}
         line["gapped_n16384_3det"] = gj
-        line["grouped"] = grouped_extra(td, torch)
+        line["grouped"] = grouped_extra(td, torch, args.mix_segments)
     if world == 1 and not args.core:
         try:
             line["peaks_extra"] = {"tf32_tflops_burst": tf32_tflops(),

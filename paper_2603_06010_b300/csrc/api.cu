@@ -339,14 +339,16 @@ static td_status get_split_plan(td_segment* s, Scratch& sc, int64_t K, int nsl, 
   if ((r = dev_alloc(&p.items, items.size(), "work items")) != TD_OK ||
       (r = dev_alloc(&p.units, std::max<size_t>(1, units.size()), "split units")) != TD_OK ||
       (r = dev_alloc(&p.segdev, 1, "segment descriptor")) != TD_OK ||
-      (nc > 0 && (r = dev_alloc(&p.counters, SMALL_GROUPS, "completion counters")) != TD_OK)) {
+      (nc > 0 && (r = dev_alloc(&p.counters, (size_t)std::max<int>(SMALL_GROUPS, (int)units.size() + 1),
+                                 "completion counters")) != TD_OK)) {
     dev_free(p.items);
     dev_free(p.units);
     dev_free(p.segdev);
     dev_free(p.counters);
     return r;
   }
-  if (p.counters) TD_CUDA(cudaMemset(p.counters, 0, SMALL_GROUPS * sizeof(int)));
+  p.n_counters = p.counters ? std::max<int>(SMALL_GROUPS, (int)units.size() + 1) : 0;
+  if (p.counters) TD_CUDA(cudaMemset(p.counters, 0, (size_t)p.n_counters * sizeof(int)));
   TD_CUDA(cudaMemcpy(p.items, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice));
   if (!units.empty())
     TD_CUDA(cudaMemcpy(p.units, units.data(), units.size() * sizeof(SplitUnit), cudaMemcpyHostToDevice));
@@ -587,16 +589,24 @@ td_status loglike_batch_with(td_segment* s, Scratch& sc, const float* R, int64_t
     const int ncs = K <= 16 ? 16 : (K <= 32 ? 32 : (K <= 64 ? 64 : (K <= 128 ? 128 : 256)));
     SplitPlan* plan = nullptr;
     if ((r = get_split_plan(s, sc, ncs, nsl, 128, st, &plan, ncs)) != TD_OK) return r;
-    // three launches chained as programmatic dependents: the slicing (which also
-    // clears the plan's completion counter), the product, the chunk reduction
-    // with chi2 and logL
-    TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st, plan->counters, SMALL_GROUPS));
-    if (pm) prof_mark(s, st, true);   // the events bracket the product kernel alone
-    TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, st));
-    if (pm) prof_mark(s, st, false);
+    // launches chained as programmatic dependents: the slicing (which also
+    // clears the plan's completion counters), the product, the chunk
+    // reduction with chi2 and logL.  Up to SMALL_FUSED_K columns the product
+    // kernel reduces in-kernel instead (one launch less; its arrival-count tail
+    // grows with the columns, the separate kernel's does not).  Up to 64
+    // columns the slicing is itself a programmatic dependent of the preceding
+    // launch (it waits for it before touching memory), so the next call's
+    // launches are resident while this one finishes.
+    const bool fused = K <= SMALL_FUSED_K;
+    TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st, plan->counters,
+                            plan->n_counters, ncs <= 64));
     const SmallFinal fin{plan->units, plan->counters, plan->n_units, (int)K, logL, chi2, std::max(TC_COLS, ncs)};
-    TD_CUDA(launch_small_reduce(plan->segdev, fin, st));
-    s->prof_kernels += 3;
+    if (pm) prof_mark(s, st, true);   // the events bracket the product kernel alone
+    TD_CUDA(launch_tc_small(plan->items, plan->n_items, plan->segdev, nsl, ncs, s->status, o.wait_limit_ns, st,
+                            fused ? &fin : nullptr));
+    if (pm) prof_mark(s, st, false);
+    if (!fused) TD_CUDA(launch_small_reduce(plan->segdev, fin, st));
+    s->prof_kernels += fused ? 2 : 3;
     return TD_OK;
   }
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));

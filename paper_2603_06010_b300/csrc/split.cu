@@ -188,6 +188,10 @@ __device__ __forceinline__ float block_max256(float mx, float* red) {
 __device__ __forceinline__ void pdl_launch_dependents() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
+// Launched as a programmatic dependent (small batches), the kernel may start
+// while the preceding launch runs: nothing is read or written before this
+// wait (a no-op otherwise).
+__device__ __forceinline__ void pdl_wait_prior() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // one CTA per column (large batches)
 __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t K,
@@ -195,6 +199,7 @@ __global__ void __launch_bounds__(256) k_r_slices(const float* __restrict__ R, i
                                                    int nslices, int* __restrict__ zero, int nzero) {
   __shared__ float red[8];
   pdl_launch_dependents();
+  pdl_wait_prior();
   if (zero && blockIdx.x == 0)
     for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0;
   const int64_t slice_stride = capK * nkp8;
@@ -218,6 +223,7 @@ __global__ void __launch_bounds__(THREADS) k_r_slices_reg(const float* __restric
                                                           int* __restrict__ zero, int nzero) {
   __shared__ float red[THREADS / 32];
   pdl_launch_dependents();
+  pdl_wait_prior();
   if (zero && blockIdx.x == 0)
     for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0;
   const int64_t k = blockIdx.x;
@@ -269,6 +275,7 @@ __global__ void __cluster_dims__(RS_CL, 1, 1) __launch_bounds__(256)
   __shared__ float red[8];
   __shared__ float cmax;
   pdl_launch_dependents();
+  pdl_wait_prior();
   if (zero && blockIdx.x == 0)
     for (int i = threadIdx.x; i < nzero; i += blockDim.x) zero[i] = 0;
   cg::cluster_group cl = cg::this_cluster();
@@ -290,12 +297,25 @@ __global__ void __cluster_dims__(RS_CL, 1, 1) __launch_bounds__(256)
 }
 
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8, int64_t capK,
-                            __nv_bfloat16* rs, int nslices, cudaStream_t st, int* zero, int nzero) {
+                            __nv_bfloat16* rs, int nslices, cudaStream_t st, int* zero, int nzero, bool pdl) {
   if (K <= 0) return cudaSuccess;
   const bool reg_ok = K <= 2147483647LL && ldr % 4 == 0 && nk % 4 == 0 &&
                       (reinterpret_cast<uintptr_t>(R) & 15) == 0 && nk <= 4 * 8 * 1024;
   if (K <= 64 || (K <= 256 && !reg_ok)) {
     // few columns: a cluster per column puts more SMs on them
+    if (pdl) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)(K * RS_CL));
+      cfg.blockDim = dim3(256);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      return cudaLaunchKernelEx(&cfg, k_r_slices_cl, R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
+    }
     k_r_slices_cl<<<(unsigned)(K * RS_CL), 256, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
   } else if (reg_ok) {
     // column in registers: 8 float4 per thread (at K = 256, N' = 8192: one

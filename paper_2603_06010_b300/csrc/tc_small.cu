@@ -88,10 +88,103 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }   // warps 2..5
 
+// Chunk pairs of one split row tile, four columns n0 .. n0+3, for the row of
+// this thread (base = its row in the unit's first slot): double-float sums in
+// chunk order (loads issued CH chunks x 4 columns ahead), the exact square,
+// then the fixed shuffle tree over the 32 rows of the warp; lane 0 returns
+// the warp's partial of each column.
+template <int CH>
+__device__ __forceinline__ void unit_cols4(const float2* base, int nchunk, int slot_cols, int n0, int kcols,
+                                           double (&part)[4]) {
+  constexpr int CB = 4;
+  float wh[CB], wl[CB];
+#pragma unroll
+  for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
+  for (int ch0 = 0; ch0 < nchunk; ch0 += CH) {
+    float2 v[CH][CB];
+    // CH x CB predicated loads in flight at once, then the additions in chunk order
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+#pragma unroll
+      for (int c = 0; c < CB; ++c) {
+        const int n = min(n0 + c, kcols - 1);
+        v[i][c] = ch0 + i < nchunk ? __ldcg(base + ((int64_t)(ch0 + i) * slot_cols + n) * 128)
+                                   : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+    for (int i = 0; i < CH; ++i)
+      if (ch0 + i < nchunk) {
+#pragma unroll
+        for (int c = 0; c < CB; ++c) {
+          ff_add(v[i][c].x, wh[c], wl[c]);
+          ff_add(v[i][c].y, wh[c], wl[c]);
+        }
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < CB; ++c) {
+    float hi = 0.f, lo = 0.f;
+    ff_add_square2(wh[c], wl[c], hi, lo);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      const float oh = __shfl_down_sync(0xffffffffu, hi, off);
+      const float ol = __shfl_down_sync(0xffffffffu, lo, off);
+      ff_add(oh, hi, lo);
+      lo += ol;
+    }
+    part[c] = (double)hi + (double)lo;
+  }
+}
+
+// chi2 and logL of columns c0 .. c0+ncols-1 from the per-tile partials of a
+// single-segment small-batch call: thread (q, lane) adds the tiles of quarter
+// q in order, then the four quarters in order.  128 threads (q = row quarter)
+// meeting at `bar`.
+template <typename Bar>
+__device__ __forceinline__ void small_final_cols(const TcSegDev* sd, const SmallFinal& fin, int c0, int ncols,
+                                                 double (*sh)[32], int q, int lane, Bar bar) {
+  const int nparts = sd->nm;
+  const int per = (nparts + 3) / 4;
+  const int p0 = q * per, p1 = min(nparts, p0 + per);
+  const int col = min(c0 + lane, fin.K - 1);
+  double s = 0.0;
+  if (lane < ncols)
+    for (int pb = p0; pb < p1; pb += 16) {
+      double v[16];   // sixteen loads in flight (clamped addresses), then the additions in order
+#pragma unroll
+      for (int i = 0; i < 16; ++i) v[i] = __ldcg(&sd->partials[(int64_t)min(pb + i, p1 - 1) * sd->ldp + col]);
+#pragma unroll
+      for (int i = 0; i < 16; ++i)
+        if (pb + i < p1) s += v[i];
+    }
+  bar();   // sh is free
+  sh[q][lane] = s;
+  bar();
+  if (q == 0 && lane < ncols && c0 + lane < fin.K) {
+    const double t = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
+    if (fin.chi2) fin.chi2[c0 + lane] = t;
+    fin.logL[c0 + lane] = -0.5 * t - 0.5 * sd->logdet - 0.5 * (double)sd->nk * LOG2PI;
+  }
+}
+
+// One 128-row tile's chi2 partials are complete (written and fenced by the
+// epilogue warps): count it; the CTA that completes the last tile of the call
+// sums every column's tile partials into chi2 and logL.  An arrival count
+// only: no thread waits on another CTA.
+__device__ __forceinline__ void small_tile_done(const TcSegDev* sd, const SmallFinal& fin, int q, int lane,
+                                                double (*sh)[32], int& sh_last) {
+  if (q == 0 && lane == 0) sh_last = atomicAdd(&fin.counters[fin.n_units], 1) == sd->nm - 1;
+  epi_bar();
+  if (sh_last) {
+    __threadfence();
+    for (int c0 = 0; c0 < fin.K; c0 += 32) small_final_cols(sd, fin, c0, 32, sh, q, lane, epi_bar);
+  }
+}
+
 template <int NSL, int NC>
 __global__ void __launch_bounds__(tsm::THREADS, 1)
     k_tc_small(const TcItem* __restrict__ items, int n_items, const TcSegDev* __restrict__ segs,
-               DevStatus* status, uint64_t limit_ns) {
+               DevStatus* status, uint64_t limit_ns, const SmallFinal red) {
   using namespace tsm;
   using C = Cfg<NSL, NC>;
   constexpr int A_STAGE = C::A_STAGE;
@@ -110,6 +203,9 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ int sh_ok[4];
   __shared__ double sh_part[4][NC];
+  // in-kernel reduction (single segment, NC <= 64): unit and final partials
+  __shared__ double sh_fin[NC <= 64 ? 4 : 1][32];
+  __shared__ int sh_last;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // The reduction kernel may be scheduled once every CTA has triggered (it
@@ -271,6 +367,11 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
     }
   } else {
     const int q = warp & 3;          // TMEM lane quarter = rows 32q .. 32q+31 of the tile
+    // in-kernel reduction: these warps read and write buffers and counters that
+    // the preceding launch may still use, so they wait for it (a no-op without
+    // a programmatic dependency)
+    const bool fused = NC <= 64 && red.logL != nullptr;
+    if (fused) pdl_wait();
     int tl = 0;
     for (int r = 0; (int64_t)r * G < n_items; ++r) {
       const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
@@ -329,11 +430,45 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
       if (it.slot < 0) {
         // the tile's four 32-row groups in a fixed order
         epi_bar();
-        if (q == 0)
+        if (q == 0) {
           for (int n = lane; n < ncol; n += 32)
             sd->partials[(int64_t)it.m * sd->ldp + it.c * NC + n] =
                 ((sh_part[0][n] + sh_part[1][n]) + sh_part[2][n]) + sh_part[3][n];
+          if (fused) __threadfence();
+        }
         epi_bar();
+        if constexpr (NC <= 64)
+          if (fused) small_tile_done(sd, red, q, lane, sh_fin, sh_last);
+      } else if constexpr (NC <= 64) {
+        if (fused) {
+          // the last chunk of a split row tile to arrive reduces the unit: the
+          // chunk pairs in chunk order, as the separate reduction kernel does
+          const SplitUnit u = red.units[it.unit];   // loaded while the fence drains
+          __threadfence();   // this thread's chunk pairs
+          epi_bar();
+          if (q == 0 && lane == 0) sh_last = atomicAdd(&red.counters[it.unit], 1) == u.nchunk - 1;
+          epi_bar();
+          if (sh_last) {
+            __threadfence();
+            const float2* base = sd->wpart + (int64_t)u.slot0 * red.slot_cols * BM + q * 32 + lane;
+            for (int n0 = 0; n0 < red.K; n0 += 4) {
+              double part[4];
+              unit_cols4<8>(base, u.nchunk, red.slot_cols, n0, red.K, part);
+              if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) sh_fin[q][c] = part[c];
+              epi_bar();
+              // the tile's four 32-row groups in a fixed order
+              if (q == 0 && lane < 4 && n0 + lane < red.K)
+                sd->partials[(int64_t)u.m * sd->ldp + u.c * 128 + n0 + lane] =
+                    ((sh_fin[0][lane] + sh_fin[1][lane]) + sh_fin[2][lane]) + sh_fin[3][lane];
+              epi_bar();
+            }
+            if (q == 0) __threadfence();
+            epi_bar();
+            small_tile_done(sd, red, q, lane, sh_fin, sh_last);
+          }
+        }
       }
       ++tl;
     }
@@ -348,94 +483,36 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
   }
 }
 
-// Chunk reduction + chi2 / logL for the small-batch kernel.  Grid: (split
-// units, column groups of 4); 128 threads, one per row of the 128-row tile.
-// A thread adds its row's chunk pairs in chunk order (double-float, loads
-// issued 4 chunks x 4 columns ahead), squares exactly; a fixed shuffle tree
-// per 32 rows and the four groups in order give the tile's partial.  The
-// last CTA of each column group (one arrival counter per group) sums its four
-// columns' tile partials in a fixed order into chi2 and logL: thread (q, c)
-// adds the tiles of quarter q in order, then the four quarters in order.
-// Without split units (short segments) one CTA does the same for all columns.
-__device__ __forceinline__ void small_final_cols(const TcSegDev* sd, const SmallFinal& fin, int c0, int ncols,
-                                                 double (*sh)[32]) {
-  const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
-  const int nparts = sd->nm;
-  const int per = (nparts + 3) / 4;
-  const int p0 = q * per, p1 = min(nparts, p0 + per);
-  const int col = min(c0 + lane, fin.K - 1);
-  double s = 0.0;
-  if (lane < ncols)
-    for (int pb = p0; pb < p1; pb += 8) {
-      double v[8];   // eight loads in flight (clamped addresses), then the additions in order
-#pragma unroll
-      for (int i = 0; i < 8; ++i) v[i] = __ldcg(&sd->partials[(int64_t)min(pb + i, p1 - 1) * sd->ldp + col]);
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-        if (pb + i < p1) s += v[i];
-    }
-  __syncthreads();   // sh is free
-  sh[q][lane] = s;
-  __syncthreads();
-  if (q == 0 && lane < ncols && c0 + lane < fin.K) {
-    const double t = ((sh[0][lane] + sh[1][lane]) + sh[2][lane]) + sh[3][lane];
-    if (fin.chi2) fin.chi2[c0 + lane] = t;
-    fin.logL[c0 + lane] = -0.5 * t - 0.5 * sd->logdet - 0.5 * (double)sd->nk * LOG2PI;
-  }
-}
-
+// Chunk reduction + chi2 / logL for the small-batch kernel when it does not
+// reduce in-kernel (NC >= 128).  Grid: (split units, column groups of 4); 128
+// threads, one per row of the 128-row tile: unit_cols4, then the four 32-row
+// groups in order give the tile's partial.  The last CTA of each column group
+// (one arrival counter per group) sums its four columns' tile partials in a
+// fixed order into chi2 and logL (small_final_cols).  Without split units
+// (short segments) one CTA does the same for all columns.
 __global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict__ segs, const SmallFinal fin) {
   __shared__ int sh_last;
   __shared__ double sh[4][32];
+  // the next call's residual slicing may become resident (it waits for this
+  // grid before it touches memory)
+  pdl_trigger();
   pdl_wait();   // the product kernel's pairs and partials are complete and visible
   const TcSegDev* sd = &segs[0];
   const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+  auto sync = [] { __syncthreads(); };
   if (fin.n_units == 0) {
-    for (int c0 = 0; c0 < fin.K; c0 += 32) small_final_cols(sd, fin, c0, 32, sh);
+    for (int c0 = 0; c0 < fin.K; c0 += 32) small_final_cols(sd, fin, c0, 32, sh, q, lane, sync);
     return;
   }
   const SplitUnit u = fin.units[blockIdx.x];
   const int n0 = blockIdx.y * 4;
   const float2* base = sd->wpart + (int64_t)u.slot0 * fin.slot_cols * 128 + threadIdx.x;
-  constexpr int CB = 4, CH = 4;
-  float wh[CB], wl[CB];
+  constexpr int CB = 4;
+  double part[CB];
+  unit_cols4<4>(base, u.nchunk, fin.slot_cols, n0, fin.K, part);
+  if (lane == 0)
 #pragma unroll
-  for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
-  for (int ch0 = 0; ch0 < u.nchunk; ch0 += CH) {
-    float2 v[CH][CB];
-    // CH x CB predicated loads in flight at once (few registers, so many CTAs
-    // per SM), then the additions in chunk order
-#pragma unroll
-    for (int i = 0; i < CH; ++i)
-#pragma unroll
-      for (int c = 0; c < CB; ++c) {
-        const int n = min(n0 + c, fin.K - 1);
-        v[i][c] = ch0 + i < u.nchunk ? __ldcg(base + ((int64_t)(ch0 + i) * fin.slot_cols + n) * 128)
-                                     : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-    for (int i = 0; i < CH; ++i)
-      if (ch0 + i < u.nchunk) {
-#pragma unroll
-        for (int c = 0; c < CB; ++c) {
-          ff_add(v[i][c].x, wh[c], wl[c]);
-          ff_add(v[i][c].y, wh[c], wl[c]);
-        }
-      }
-  }
-#pragma unroll
-  for (int c = 0; c < CB; ++c) {
-    float hi = 0.f, lo = 0.f;
-    ff_add_square2(wh[c], wl[c], hi, lo);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      const float oh = __shfl_down_sync(0xffffffffu, hi, off);
-      const float ol = __shfl_down_sync(0xffffffffu, lo, off);
-      ff_add(oh, hi, lo);
-      lo += ol;
-    }
-    if (lane == 0) sh[q][c] = (double)hi + (double)lo;
-  }
+    for (int c = 0; c < CB; ++c) sh[q][c] = part[c];
   __syncthreads();
   // the tile's four 32-row groups in a fixed order
   if (threadIdx.x < CB && n0 + threadIdx.x < fin.K) {
@@ -448,7 +525,7 @@ __global__ void __launch_bounds__(128) k_small_reduce(const TcSegDev* __restrict
   __syncthreads();
   if (!sh_last) return;
   __threadfence();
-  small_final_cols(sd, fin, n0, CB, sh);
+  small_final_cols(sd, fin, n0, CB, sh, q, lane, sync);
 }
 
 // Chunk reduction of a grouped small-orientation launch (many segments, every
@@ -536,7 +613,7 @@ static cudaError_t launch_pdl(const void* fn, dim3 grid, dim3 block, size_t smem
 
 template <int NSL, int NC>
 static cudaError_t launch_small_impl(const TcItem* items, int n_items, const TcSegDev* segs, DevStatus* status,
-                                     int64_t lim, cudaStream_t st) {
+                                     int64_t lim, cudaStream_t st, const SmallFinal* fin) {
   using C = tsm::Cfg<NSL, NC>;
   static std::atomic<unsigned long long> attr_done{0};
   if (device_needs_setup(attr_done)) {
@@ -548,14 +625,18 @@ static cudaError_t launch_small_impl(const TcItem* items, int n_items, const TcS
   int grid = tc_num_sms();
   if (grid > n_items) grid = n_items;
   uint64_t lim64 = (uint64_t)lim;
-  void* a1[] = {(void*)&items, (void*)&n_items, (void*)&segs, (void*)&status, (void*)&lim64};
+  SmallFinal f{};
+  if (fin) f = *fin;   // logL set: the kernel reduces in-kernel (NC <= 64)
+  void* a1[] = {(void*)&items, (void*)&n_items, (void*)&segs, (void*)&status, (void*)&lim64, (void*)&f};
   return launch_pdl((const void*)k_tc_small<NSL, NC>, dim3((unsigned)grid), dim3(tsm::THREADS), C::SMEM, st, a1);
 }
 
 cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
-                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st) {
+                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, const SmallFinal* fin) {
+  if (fin && nc > 64) return cudaErrorInvalidValue;   // the in-kernel reduction covers NC <= 64
 #define TD_SMALL_CASE(NSL_, NC_) \
-  if (nslices == NSL_ && nc == NC_) return launch_small_impl<NSL_, NC_>(items, n_items, segs, status, wait_limit_ns, st);
+  if (nslices == NSL_ && nc == NC_)                   \
+    return launch_small_impl<NSL_, NC_>(items, n_items, segs, status, wait_limit_ns, st, fin);
   TD_SMALL_CASE(3, 16) TD_SMALL_CASE(4, 16) TD_SMALL_CASE(2, 16)
   TD_SMALL_CASE(3, 32) TD_SMALL_CASE(4, 32) TD_SMALL_CASE(2, 32)
   TD_SMALL_CASE(3, 64) TD_SMALL_CASE(4, 64) TD_SMALL_CASE(2, 64)

@@ -76,7 +76,8 @@ struct SplitPlan {           // device work lists for one batch width (split mod
   int n_units = 0;
   int n_slots = 0;
   TcSegDev* segdev = nullptr;
-  int* counters = nullptr;    // small-batch plans: one arrival count per 4-column group (SMALL_GROUPS)
+  int* counters = nullptr;    // small-batch plans: arrival counts (n_counters, see SmallFinal)
+  int n_counters = 0;
   const void* op = nullptr;   // operator the tensor maps in segdev were encoded for
   double logdet = 0.0;        // and the log det copied into it
   uint64_t last_use = 0;
@@ -268,10 +269,12 @@ cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64
 cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t nkp, const double* qrow,
                              __nv_bfloat16* op, cudaStream_t st, bool row_major = false);
 // zero / nzero: ints the launch clears first (the next small-batch kernel's counters).
-// The kernel lets a programmatic dependent launch start early.
+// The kernel lets a programmatic dependent launch start early.  pdl (K <= 64):
+// launched as a programmatic dependent of the preceding kernel; it waits for
+// that kernel before it reads R or writes anything.
 cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, int64_t nkp8,
                             int64_t capK, __nv_bfloat16* rs, int nslices, cudaStream_t st, int* zero = nullptr,
-                            int nzero = 0);
+                            int nzero = 0, bool pdl = false);
 
 // tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
 // pdl: launch as a programmatic dependent of the preceding kernel (which
@@ -294,17 +297,25 @@ cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSeg
 // run inside the kernel (the last chunk of a row tile, then the last CTA);
 // launched as a programmatic dependent of the residual slicing.
 constexpr int SMALL_GROUPS = 64;   // 4-column groups of the widest small batch (256 columns)
+constexpr int SMALL_FUSED_K = 4;   // small batches up to this width reduce inside the product kernel
 struct SmallFinal {
   const SplitUnit* units;
-  int* counters;     // [SMALL_GROUPS] arrivals per 4-column group; zero at launch
+  // zero at launch.  Separate reduction kernel: [SMALL_GROUPS] arrivals per
+  // 4-column group.  In-kernel reduction: [n_units] chunk arrivals per split
+  // unit, then [1] completed 128-row tiles.
+  int* counters;
   int n_units;
   int K;             // columns of this call (the plan may be wider)
   double* logL;
   double* chi2;      // optional
   int slot_cols;     // columns per split slot: max(128, the kernel's column tile)
 };
+// fin: a single-segment call whose chunk reduction, chi2 and logL the kernel
+// does itself (NC <= 64); nullptr: chunk pairs and partials only (a separate
+// reduction follows)
 cudaError_t launch_tc_small(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int nc,
-                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st);
+                            DevStatus* status, int64_t wait_limit_ns, cudaStream_t st,
+                            const SmallFinal* fin = nullptr);
 cudaError_t launch_small_reduce(const TcSegDev* segs, const SmallFinal& fin, cudaStream_t st);
 // the chunk reduction of a grouped small-orientation launch (nc-column tiles,
 // every item a chunk); writes each unit's chi2 partials for k_tc_finalize

@@ -145,29 +145,16 @@ cudaError_t launch_op_slices(const double* Linv, int64_t ld, int64_t nk, int64_t
   return cudaGetLastError();
 }
 
-// Residual slices: the column's power-of-two quantum p_k
-// (max_j |R_jk| <= 255 p_k), then R = p_k b0 + r with r in up to three
-// floating bf16 slices (all four slices hold a float32 exactly).
-__device__ __forceinline__ float r_quantum(float mx) {
-  float p = 1.f;
-  if (mx > 0.f) {
-    p = exp2f(ceilf(log2f(mx / 255.f)));
-    if (mx / p > 255.f) p *= 2.f;
-  }
-  return p;
-}
-
+// Residual slices (r_quantum, r_slice_value): rows j0 .. j1-1 of one column.
 __device__ __forceinline__ void r_slice_rows(const float* __restrict__ col, int64_t j0, int64_t j1, float p,
                                              __nv_bfloat16* __restrict__ dst, int64_t slice_stride, int nslices) {
   for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
-    const float x = col[j];
-    const float hi = p * rintf(x / p);
-    __nv_bfloat16 a, b, c;
-    split3_f32(x - hi, a, b, c);
-    dst[j] = __float2bfloat16_rn(hi);
-    dst[j + slice_stride] = a;
-    if (nslices > 2) dst[j + 2 * slice_stride] = b;
-    if (nslices > 3) dst[j + 3 * slice_stride] = c;
+    __nv_bfloat16 o[4];
+    r_slice_value(col[j], p, o);
+    dst[j] = o[0];
+    dst[j + slice_stride] = o[1];
+    if (nslices > 2) dst[j + 2 * slice_stride] = o[2];
+    if (nslices > 3) dst[j + 3 * slice_stride] = o[3];
   }
 }
 
@@ -255,9 +242,10 @@ __global__ void __launch_bounds__(THREADS) k_r_slices_reg(const float* __restric
     __align__(8) __nv_bfloat16 o[4][4];
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const float hi = p * rintf(xs[e] / p);
-      o[0][e] = __float2bfloat16_rn(hi);
-      split3_f32(xs[e] - hi, o[1][e], o[2][e], o[3][e]);
+      __nv_bfloat16 t[4];
+      r_slice_value(xs[e], p, t);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) o[u][e] = t[u];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)

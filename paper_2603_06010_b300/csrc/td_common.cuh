@@ -174,6 +174,23 @@ __device__ __forceinline__ void split3_f32(float x, __nv_bfloat16& s0, __nv_bflo
   s2 = __float2bfloat16_rn(r);
 }
 
+// Residual slices: the column's power-of-two quantum p_k
+// (max_j |R_jk| <= 255 p_k), then R = p_k b0 + r with r in up to three
+// floating bf16 slices (all four slices hold a float32 exactly).
+__device__ __forceinline__ float r_quantum(float mx) {
+  float p = 1.f;
+  if (mx > 0.f) {
+    p = exp2f(ceilf(log2f(mx / 255.f)));
+    if (mx / p > 255.f) p *= 2.f;
+  }
+  return p;
+}
+__device__ __forceinline__ void r_slice_value(float x, float p, __nv_bfloat16 (&o)[4]) {
+  const float hi = p * rintf(x / p);
+  o[0] = __float2bfloat16_rn(hi);
+  split3_f32(x - hi, o[1], o[2], o[3]);
+}
+
 // exact square w*w = p + e and compensated accumulation into (hi, lo)
 __device__ __forceinline__ void ff_add_square(float w, float& hi, float& lo) {
   float p = w * w;

@@ -31,27 +31,64 @@ namespace td {
 // gives hi*hi partial sums that are integer multiples of q_i p_k below 2^24
 // of them: exactly representable in FP32, so the tensor-core accumulation of
 // that product is exact.  (Integers up to 256 are exact in bf16.)
-__global__ void k_row_quantum(const double* __restrict__ Linv, int64_t ld, int64_t nk, int64_t nkp,
-                              double* __restrict__ qrow) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nkp; i += (int64_t)gridDim.x * blockDim.x) {
-    double mx = 0.0;
-    const int64_t jmax = (i < nk) ? i : -1;
-    for (int64_t j = 0; j <= jmax; ++j) mx = fmax(mx, fabs(Linv[i + j * ld]));
-    if (!(mx > 0.0)) {
-      qrow[i] = 1.0;
-      continue;
+// Column-major L^-1: a block of 32 rows x 8 column groups (warps), so a warp
+// reads 32 consecutive rows of one column; the maximum as an integer compare
+// of the magnitude bits (exact), the sum of integers |round(x / q_i)| in FP64
+// (exact: below 2^53), both in any order -- the same q_i as a row-at-a-time
+// scan.  q_i is a power of two, so x / q_i is x * (1 / q_i) exactly.
+__global__ void __launch_bounds__(256) k_row_quantum(const double* __restrict__ Linv, int64_t ld, int64_t nk,
+                                                     int64_t nkp, double* __restrict__ qrow) {
+  __shared__ unsigned long long smx[8][32];
+  __shared__ double sl1[8][32];
+  __shared__ double sq[32];
+  __shared__ int sbad;
+  const int r = threadIdx.x & 31, g = threadIdx.x >> 5;
+  const int64_t i = (int64_t)blockIdx.x * 32 + r;
+  const int64_t jmax = (i < nk) ? i : -1;
+  const double* row = Linv + i;
+  unsigned long long mb = 0ull;
+#pragma unroll 4
+  for (int64_t j = g; j <= jmax; j += 8)
+    mb = max(mb, (unsigned long long)__double_as_longlong(row[j * ld]) & 0x7fffffffffffffffull);
+  smx[g][r] = mb;
+  __syncthreads();
+  if (g == 0) {
+    unsigned long long m = smx[0][r];
+#pragma unroll
+    for (int h = 1; h < 8; ++h) m = max(m, smx[h][r]);
+    const double mx = __longlong_as_double((long long)m);
+    double q = 1.0;
+    if (mx > 0.0) {
+      q = ldexp(1.0, (int)ceil(log2(mx / 255.0)));
+      if (mx / q > 255.0) q *= 2.0;
     }
-    int e = (int)ceil(log2(mx / 255.0));
-    double q = ldexp(1.0, e);
-    if (mx / q > 255.0) q *= 2.0;
-    for (int it = 0; it < 64; ++it) {
-      double l1 = 0.0;
-      for (int64_t j = 0; j <= jmax; ++j) l1 += fabs(rint(Linv[i + j * ld] / q));
-      if (l1 <= 65536.0) break;
-      q *= 2.0;
-    }
-    qrow[i] = q;
+    sq[r] = q;
   }
+  __syncthreads();
+  for (int it = 0; it < 64; ++it) {
+    const double q = sq[r];
+    const double iq = 1.0 / q;   // exact: q is a power of two
+    double l1 = 0.0;
+#pragma unroll 4
+    for (int64_t j = g; j <= jmax; j += 8) l1 += fabs(rint(row[j * ld] * iq));
+    sl1[g][r] = l1;
+    if (threadIdx.x == 0) sbad = 0;
+    __syncthreads();
+    if (g == 0) {
+      double t = 0.0;
+#pragma unroll
+      for (int h = 0; h < 8; ++h) t += sl1[h][r];
+      if (t > 65536.0) {
+        sq[r] = q * 2.0;
+        sbad = 1;
+      }
+    }
+    __syncthreads();
+    const int bad = sbad;
+    __syncthreads();   // sbad and sl1 are rewritten by the next pass
+    if (!bad) break;
+  }
+  if (g == 0 && i < nkp) qrow[i] = sq[r];
 }
 
 // The same quantum for an operator stored row-major (row i at Linv + i ld):
@@ -74,7 +111,8 @@ __global__ void k_row_quantum_rm(const double* __restrict__ Linv, int64_t ld, in
       if (mx / q > 255.0) q *= 2.0;
       for (int it = 0; it < 64; ++it) {
         double l1 = 0.0;
-        for (int64_t j = lane; j <= jmax; j += 32) l1 += fabs(rint(row[j] / q));
+        const double iq = 1.0 / q;   // exact: q is a power of two
+        for (int64_t j = lane; j <= jmax; j += 32) l1 += fabs(rint(row[j] * iq));
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, off);
         if (l1 <= 65536.0) break;
@@ -91,15 +129,15 @@ cudaError_t launch_row_quantum(const double* Linv, int64_t ld, int64_t nk, int64
     const int64_t blocks = ceil_div(nkp, 8);
     k_row_quantum_rm<<<(unsigned)(blocks < 65535 * 4 ? blocks : 65535 * 4), 256, 0, st>>>(Linv, ld, nk, nkp, qrow);
   } else {
-    k_row_quantum<<<(unsigned)ceil_div(nkp, 128), 128, 0, st>>>(Linv, ld, nk, nkp, qrow);
+    k_row_quantum<<<(unsigned)ceil_div(nkp, 32), 256, 0, st>>>(Linv, ld, nk, nkp, qrow);
   }
   return cudaGetLastError();
 }
 
 // x = q a0 + r,  a0 = rint(x / q) (|a0| <= 255, exact in bf16 as q a0),
 // r = x - q a0 split into three floating bf16 slices.
-__device__ __forceinline__ void split4_fixed_f64(double x, double q, __nv_bfloat16 (&s)[4]) {
-  const double hi = q * rint(x / q);
+__device__ __forceinline__ void split4_fixed_f64(double x, double q, double iq, __nv_bfloat16 (&s)[4]) {
+  const double hi = q * rint(x * iq);   // iq = 1 / q exactly (q a power of two)
   s[0] = __double2bfloat16(hi);
   split3_f64(x - hi, s[1], s[2], s[3]);
 }
@@ -114,13 +152,14 @@ __global__ void __launch_bounds__(256) k_op_slices(const double* __restrict__ Li
   const int64_t i = (int64_t)m * OP_ROWS + r;
   const int64_t blk = (OP_ROWS / OP_KB) * (int64_t)m * (m + 1) / 2 + kb;
   const double q = qrow[i];
+  const double iq = 1.0 / q;
   __align__(16) __nv_bfloat16 sl[OP_SLICES][OP_KB];
 #pragma unroll 4
   for (int c = 0; c < OP_KB; ++c) {
     const int64_t j = (int64_t)kb * OP_KB + c;
     const double x = (i < nk && j < nk && j <= i) ? Linv[RM ? i * ld + j : i + j * ld] : 0.0;
     __nv_bfloat16 s4[4];
-    split4_fixed_f64(x, q, s4);
+    split4_fixed_f64(x, q, iq, s4);
 #pragma unroll
     for (int u = 0; u < OP_SLICES; ++u) sl[u][c] = s4[u];
   }

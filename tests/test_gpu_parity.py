@@ -142,11 +142,14 @@ def test_column_alone_equals_in_batch(torch_cuda, gpu_lib):
             opt = td.options(precision=prec, path=path)
             # the small-batch kernel takes up to 256 columns: its widths 16 ... 256
             # (whole rows reduced in the kernel below 128 columns, all rows by
-            # the chunk reduction from 128) give the same bits
+            # the chunk reduction from 128; up to 4 columns split rows and the
+            # final sums reduced inside the product kernel too) give the same bits
             last = 255 if path == td.TD_PATH_SMALLK else 299
             full = run(Rd[:last + 1], opt)
             for k in (0, 1, 127, 128, last):
                 assert run(Rd[k:k + 1], opt)[0] == full[k], (prec, path, k)
+            for k0, k1 in ((10, 12), (30, 34), (200, 205)):
+                assert np.array_equal(run(Rd[k0:k1], opt), full[k0:k1]), (prec, path, k0, k1)
             assert np.array_equal(run(Rd[100:229], opt), full[100:229]), (prec, path)
             assert np.array_equal(run(Rd[60:100], opt), full[60:100]), (prec, path)
             assert np.array_equal(run(Rd[20:120], opt), full[20:120]), (prec, path)

@@ -584,6 +584,50 @@ def host_mem_bytes():
     return None
 
 
+def fp64_per_request(td, torch, fleet, pools, served):
+    """The plain per-request FP64 solve the serving workload is compared with:
+    the FP64 factor L and the blocked FP64 forward substitution, one request
+    at a time with no batching, on the first gapped segment of each length.
+    Its service time per (N, K), and over the phase-1 requests (their N and K)
+    the rate and latency it would give without any queueing."""
+    from paper_2603_06010_b300 import inputs
+    segs_p, Ks_p = served[0], served[1]
+    o64 = td.options(precision=td.TD_PREC_FP64)
+    svc = {}
+    for n in (4096, 8192, 16384, 32768):
+        i = next(j for j, sp in enumerate(fleet) if sp["n"] == n and sp["gaps"] > 0)
+        sp = fleet[i]
+        seg = td.Segment(inputs.acf_from_psd(sp["n"], sp["fs"]), sp["mask"])
+        for k in (1, 8, 64, 512):
+            R = pools[i][:k].contiguous()
+            out = torch.empty(k, dtype=torch.float64, device="cuda")
+            seg.loglike_into(R, out, o64)
+            torch.cuda.synchronize()
+            seg.check()
+            reps = 5 if n * k <= 32768 * 8 else 2
+            times = []
+            for _ in range(reps):
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                seg.loglike_into(R, out, o64)
+                b.record()
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+            svc[(n, k)] = float(np.median(times))
+        seg.close()
+    t = np.array([svc[(fleet[int(sg)]["n"], int(k))] for sg, k in zip(segs_p, Ks_p)])
+    mean_ms = float(t.mean())
+    return {"note": "plain FP64 solve per request (FP64 L, blocked forward substitution on the FP64 cores, "
+                    "no batching), on the first gapped segment of each N; service time per (N, K), median "
+                    "of repeats; then over the phase-1 requests (their N and K, no queueing): mean service "
+                    "time, the request rate one GPU could sustain, evals/s and latency percentiles",
+            "service_ms": {f"N={n} gapped": {f"K={k}": svc[(n, k)] for k in (1, 8, 64, 512)}
+                           for n in (4096, 8192, 16384, 32768)},
+            "mean_service_ms": mean_ms, "max_requests_per_s": 1e3 / mean_ms,
+            "evals_per_s": float(np.mean(Ks_p)) * 1e3 / mean_ms,
+            "p50_ms_no_queue": float(np.percentile(t, 50)), "p99_ms_no_queue": float(np.percentile(t, 99))}
+
+
 def serving_extra(td, torch, seconds, evict_seconds=4.0):
     """The serving workload: 200 resident segments (N uniform over 4096, 8192,
     16384, 32768 at 2048 Hz, 0-3 gaps of 512 each), open-loop Poisson arrivals
@@ -674,6 +718,7 @@ def serving_extra(td, torch, seconds, evict_seconds=4.0):
     srv.set_budget(budget)
     p2, _ = phase(50.0, evict_seconds)
     srv.close()
+    fp64 = fp64_per_request(td, torch, fleet, pools, served)
     by_n = {k: {"segments": len(v), "mean_s": float(np.mean(v)), "max_s": float(np.max(v))}
             for k, v in sorted(factor_by_n.items())}
     out = {"note": "200 resident segments: N uniform over {4096, 8192, 16384, 32768} at 2048 Hz, 0-3 gaps of "
@@ -683,7 +728,7 @@ def serving_extra(td, torch, seconds, evict_seconds=4.0):
                    "run through it)",
            "segments": len(fleet), "operator_GB": fleet_bytes / 1e9,
            "setup_s": setup_s, "factor_s_by_kind": by_n,
-           "fleet": p1, "served_accuracy": checked,
+           "fleet": p1, "served_accuracy": checked, "fp64_per_request": fp64,
            "eviction": dict(p2, budget_GB=budget / 1e9, host_spill_pool_GB=spill / 1e9,
                             note="budget lowered at run time to 16 GB below the fleet's operator bytes; "
                                  "evicted operators go to pinned host memory (a pool pinned at server creation) "

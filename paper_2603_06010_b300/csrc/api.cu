@@ -565,12 +565,11 @@ td_status loglike_batch_with(td_segment* s, Scratch& sc, const float* R, int64_t
     const int nt = (int)(s->nkp / FT);
     const bool pm = s->prof && s->ev_used + 2 <= 8192;
     if (pm) prof_mark(s, st, true);
-    for (int I = 0; I < nt; ++I)
-      TD_CUDA(launch_trsm_f64_row(s->L, s->nkp, s->dinv, I, R, ldr, s->nk, K, sc.w64, s->nkp, sc.partials, ldp,
-                                  st));
+    TD_CUDA(launch_fp64_solve(s->L, s->nkp, s->dinv, R, ldr, s->nk, s->nkp, K, sc.w64, s->nkp, sc.partials, ldp,
+                              st));
     if (pm) prof_mark(s, st, false);
     TD_CUDA(launch_finalize(sc.partials, ldp, nt, K, s->logdet, s->nk, logL, chi2, st));
-    s->prof_kernels += nt + 1;
+    s->prof_kernels += 2 * nt + 1;
     return TD_OK;
   }
   const int nsl = nslices_for(o.precision, s->nk);

@@ -260,6 +260,11 @@ cudaError_t launch_syrk(double* A, int64_t ld, int j, int nt, cudaStream_t st);
 cudaError_t launch_trsm_f64_row(const double* L, int64_t ld, const double* dinv, int I, const float* rhs32,
                                 int64_t ldr, int64_t nk, int64_t ncols, double* W, int64_t ldw,
                                 double* partials, int64_t ldp, cudaStream_t st);
+// the plain FP64 evaluation: W = L^{-1} R by right-looking 64-row blocks into
+// T (N'p x K FP64, leading dimension ldw), chi2 partials per 64 rows
+cudaError_t launch_fp64_solve(const double* L, int64_t ld, const double* dinv, const float* R, int64_t ldr,
+                              int64_t nk, int64_t nkp, int64_t K, double* T, int64_t ldw, double* partials,
+                              int64_t ldp, cudaStream_t st);
 cudaError_t launch_finalize(const double* partials, int64_t ldp, int nparts, int64_t K, double logdet,
                             int64_t nk, double* logL, double* chi2, cudaStream_t st);
 

@@ -7,6 +7,8 @@
 // Each CTA owns 32 columns.  With no right-hand side given, R is the
 // identity and the launches build L^{-1} itself (columns right of the
 // diagonal block are zero and skipped).
+#include <algorithm>
+
 #include "td_internal.h"
 
 namespace td {
@@ -96,6 +98,155 @@ __global__ void __launch_bounds__(256) k_trsm_f64_row(const double* __restrict__
       if (col < ncols) partials[(int64_t)I * ldp + col] = s;
     }
   }
+}
+
+// Right-looking FP64 forward substitution for residual batches (the plain
+// FP64 evaluation path), T = R in FP64 first, then per 64-row block I:
+//   W_I = L_II^{-1} T_I            (k_f64_diag: up to 32 columns per CTA)
+//   T_J -= L_JI W_I for J > I      (k_f64_update: one thread per row and 1 to
+//                                   8 columns, all rows below block I at once)
+// so every step spreads over the rows below it, whatever K is.  (The row-wise
+// kernel above takes one CTA per 32 columns and loops over the blocks left of
+// its row: at K <= 32 a single CTA per step, hundreds of times slower.)
+__global__ void k_f64_init(const float* __restrict__ R, int64_t ldr, int64_t nk, int64_t nkp, int64_t K,
+                           double* __restrict__ T, int64_t ldw) {
+  const int64_t n = nkp * K;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % nkp, c = e / nkp;
+    T[i + c * ldw] = i < nk ? (double)R[i + c * ldr] : 0.0;
+  }
+}
+
+// W_I = Dinv_I T_I in place (rows 64 I .. 64 I + 63 of T), and the chi2 share
+// of these rows per column (fixed shuffle tree over each warp's 32 rows, then
+// the two warps of a column group in order).  256 threads load Dinv_I and T_I
+// (16-byte loads, all in flight at once); the first 64 CG compute: row
+// r = tid & 63, columns CT cg .. + CT - 1 of the CTA's CT CG.  The column
+// counts follow K, since every idle multiply-add still costs FP64 issue slots.
+template <int CT, int CG>
+__global__ void __launch_bounds__(256) k_f64_diag(const double* __restrict__ dinv, int I, int64_t K,
+                                                  double* __restrict__ T, int64_t ldw, double* __restrict__ partials,
+                                                  int64_t ldp) {
+  constexpr int NC = CT * CG;
+  __shared__ __align__(16) double Ds[FT * FT];
+  __shared__ double Ts[FT * NC];
+  __shared__ double red[2 * CG][CT];
+  const int tid = threadIdx.x;
+  const int64_t col0 = (int64_t)blockIdx.x * NC;
+  const double2* D = reinterpret_cast<const double2*>(dinv + (int64_t)I * FT * FT);   // D[rr + 64 k]
+#pragma unroll
+  for (int v = 0; v < FT * FT / 2 / 256; ++v) reinterpret_cast<double2*>(Ds)[tid + 256 * v] = D[tid + 256 * v];
+  for (int e = tid; e < FT * NC; e += 256) {
+    const int k = e % FT, c = e / FT;
+    const int64_t col = col0 + c;
+    Ts[k * NC + c] = col < K ? T[(int64_t)I * FT + k + col * ldw] : 0.0;
+  }
+  __syncthreads();
+  if (tid >= 64 * CG) return;
+  const int r = tid & 63, cg = tid >> 6;
+  double out[CT];
+#pragma unroll
+  for (int q = 0; q < CT; ++q) out[q] = 0.0;
+  for (int k = 0; k <= r; ++k) {
+    const double a = Ds[k * FT + r];
+#pragma unroll
+    for (int q = 0; q < CT; ++q) out[q] = fma(a, Ts[k * NC + cg * CT + q], out[q]);
+  }
+  const int64_t row = (int64_t)I * FT + r;
+#pragma unroll
+  for (int q = 0; q < CT; ++q) {
+    const int64_t col = col0 + cg * CT + q;
+    if (col < K) T[row + col * ldw] = out[q];
+  }
+  const int warp = tid >> 5, lane = tid & 31;
+#pragma unroll
+  for (int q = 0; q < CT; ++q) {
+    double v = out[q] * out[q];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    if (lane == 0) red[warp][q] = v;
+  }
+  asm volatile("bar.sync 1, %0;" ::"r"(64 * CG) : "memory");   // the computing threads only
+  if (tid < NC) {
+    const int g = tid / CT, q = tid % CT;
+    const int64_t col = col0 + tid;
+    if (col < K) partials[(int64_t)I * ldp + col] = red[2 * g][q] + red[2 * g + 1][q];
+  }
+}
+
+// T_J -= L_JI W_I for the rows below block I.  128 threads = 32 rows x 4
+// quarters of the 64-long contraction (16 loads of L in flight per thread,
+// consecutive rows per warp); the quarters' partial sums are added in a fixed
+// order.  The CTA's CT columns (blockIdx.y) of W_I sit in shared memory.
+template <int CT>
+__global__ void __launch_bounds__(128) k_f64_update(const double* __restrict__ L, int64_t ld, int I, int64_t nkp,
+                                                    int64_t K, double* __restrict__ T, int64_t ldw) {
+  __shared__ double Ws[FT * CT];
+  __shared__ double part[4][32][CT];
+  const int64_t c0 = (int64_t)blockIdx.y * CT;
+  for (int e = threadIdx.x; e < FT * CT; e += 128) {
+    const int k = e / CT, q = e % CT;
+    Ws[e] = c0 + q < K ? T[(int64_t)I * FT + k + (c0 + q) * ldw] : 0.0;
+  }
+  __syncthreads();
+  const int rr = threadIdx.x & 31, kq = threadIdx.x >> 5;
+  const int64_t i = (int64_t)(I + 1) * FT + (int64_t)blockIdx.x * 32 + rr;
+  double acc[CT];
+#pragma unroll
+  for (int q = 0; q < CT; ++q) acc[q] = 0.0;
+  if (i < nkp) {
+    const double* Lrow = L + i + ((int64_t)I * FT + kq * 16) * ld;
+    double a[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) a[k] = Lrow[(int64_t)k * ld];
+#pragma unroll
+    for (int k = 0; k < 16; ++k)
+#pragma unroll
+      for (int q = 0; q < CT; ++q) acc[q] = fma(a[k], Ws[(kq * 16 + k) * CT + q], acc[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < CT; ++q) part[kq][rr][q] = acc[q];
+  __syncthreads();
+  if (kq == 0 && i < nkp) {
+#pragma unroll
+    for (int q = 0; q < CT; ++q)
+      if (c0 + q < K)
+        T[i + (c0 + q) * ldw] -= ((part[0][rr][q] + part[1][rr][q]) + part[2][rr][q]) + part[3][rr][q];
+  }
+}
+
+template <int CT, int CG>
+static void fp64_steps(const double* L, int64_t ld, const double* dinv, int64_t nkp, int64_t K, double* T,
+                       int64_t ldw, double* partials, int64_t ldp, cudaStream_t st) {
+  const int nt = (int)(nkp / FT);
+  for (int I = 0; I < nt; ++I) {
+    k_f64_diag<CT, CG><<<(unsigned)ceil_div(K, CT * CG), 256, 0, st>>>(dinv, I, K, T, ldw, partials, ldp);
+    const int64_t rows = nkp - (int64_t)(I + 1) * FT;
+    if (rows > 0)
+      k_f64_update<CT><<<dim3((unsigned)ceil_div(rows, 32), (unsigned)ceil_div(K, CT)), 128, 0, st>>>(
+          L, ld, I, nkp, K, T, ldw);
+  }
+}
+
+cudaError_t launch_fp64_solve(const double* L, int64_t ld, const double* dinv, const float* R, int64_t ldr,
+                              int64_t nk, int64_t nkp, int64_t K, double* T, int64_t ldw, double* partials,
+                              int64_t ldp, cudaStream_t st) {
+  if (K <= 0) return cudaSuccess;
+  const int64_t n = nkp * K;
+  k_f64_init<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4096), 256, 0, st>>>(R, ldr, nk, nkp, K, T, ldw);
+  if (K == 1)
+    fp64_steps<1, 1>(L, ld, dinv, nkp, K, T, ldw, partials, ldp, st);
+  else if (K == 2)
+    fp64_steps<2, 1>(L, ld, dinv, nkp, K, T, ldw, partials, ldp, st);
+  else if (K <= 4)
+    fp64_steps<4, 1>(L, ld, dinv, nkp, K, T, ldw, partials, ldp, st);
+  else if (K <= 8)
+    fp64_steps<8, 1>(L, ld, dinv, nkp, K, T, ldw, partials, ldp, st);
+  else if (K <= 16)
+    fp64_steps<8, 2>(L, ld, dinv, nkp, K, T, ldw, partials, ldp, st);
+  else
+    fp64_steps<8, 4>(L, ld, dinv, nkp, K, T, ldw, partials, ldp, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_trsm_f64_row(const double* L, int64_t ld, const double* dinv, int I, const float* rhs32,

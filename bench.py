@@ -996,7 +996,7 @@ def main():
                 "algorithmic": "N'^2 K flops per launch (N'^2/2 multiply-adds per residual column)"}
     else:
         roof = {"bound": "alu", "achieved": flops / (kern_avg_ms / 1e3) / 1e12, "peak": 1.25,
-                "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": "k_trsm_f64_row",
+                "unit": "TFLOP/s", "frac": None, "traffic": None, "kernel": "k_f64_update + k_f64_diag",
                 "kernel_ms": kern_avg_ms, "peak_basis": "nominal FP64 1.25 TF/s"}
         roof["frac"] = roof["achieved"] / roof["peak"]
 

@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--no-grouped", action="store_true")
     p.add_argument("--no-serving", action="store_true")
-    p.add_argument("--serve-seconds", type=float, default=5.0)
+    p.add_argument("--serve-seconds", type=float, default=20.0,
+                   help="timed seconds of the serving fleet's open-loop stream (after a 2 s warm-up)")
     p.add_argument("--core", action="store_true",
                    help="the headline workload, its end-to-end figure and the CPU baseline only (profiling)")
     p.add_argument("--mix-segments", type=int, default=64,
@@ -696,7 +697,7 @@ def serving_extra(td, torch, seconds, evict_seconds=4.0):
         return res, (segs[warm:], Ks[warm:], outs[warm:], tickets)
 
     fleet_bytes = srv.stats()["resident_bytes"]
-    p1, served = phase(2000.0, seconds)
+    p1, served = phase(2000.0, seconds, warm_s=2.0)
     # served results on the first gapped N=8192 and N=16384 segments against the
     # stored oracle logL of their request pools (a request takes the first K columns)
     checked = None

@@ -101,15 +101,17 @@ __global__ void __launch_bounds__(512) k_potrf_blk(double* __restrict__ A, doubl
     if (lane == 0) logd[c] = log(a[pk(c, c)]);
   }
   __syncthreads();
-  // inverses of the two 64 x 64 diagonal halves, one column per thread
+  // inverses of the two 64 x 64 diagonal halves, one column per thread; the
+  // divisions by d_r use the reciprocals the pivots already formed (an FP64
+  // division is a long instruction sequence on this part)
   if (tid < PB) {
     const int h = tid >> 6, c = tid;   // column c of half h
     const int end = 64 * h + 64;
-    x[pk(c, c)] = 1.0 / a[pk(c, c)];
+    x[pk(c, c)] = idg[c];
     for (int r = c + 1; r < end; ++r) {
       double sacc = 0.0;
       for (int k = c; k < r; ++k) sacc += a[pk(r, k)] * x[pk(k, c)];
-      x[pk(r, c)] = -sacc / a[pk(r, r)];
+      x[pk(r, c)] = -sacc * idg[r];
     }
   }
   __syncthreads();

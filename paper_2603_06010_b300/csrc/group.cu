@@ -22,7 +22,7 @@
 
 namespace td {
 
-constexpr int GROUP_NC = 256;   // residual columns per tile of the small-batch orientation
+constexpr int GROUP_NC = 256;   // default residual columns per tile of the small-batch orientation
 
 static td_status group_alloc(void** p, size_t bytes, const char* what) {
   *p = nullptr;
@@ -99,6 +99,7 @@ struct td_group {
   int nsl = 3;
   int bn = 256;
   int s_factor = 1;           // chunk size multiplier chosen by the autotuner
+  int small_nc = GROUP_NC;    // small-batch orientation: residual columns per tile (128 or 256)
   int64_t wait_limit_ns = 1000000000LL;
   int64_t total_cols = 0;
   int64_t maxK = 0;
@@ -141,15 +142,18 @@ static void group_free_lists(td_group* g) {
 // build work lists and maps for a tile shape and chunk multiplier.  bn > 0:
 // the main kernel (128 residual columns as the MMA M, bn operator rows as
 // N); bn == 0: the small-batch kernel's orientation (128 operator rows as M,
-// up to GROUP_NC residual columns as N, each segment's last column tile only
-// as wide as its columns rounded up to 16), every item a chunk whose
-// accumulator pairs the grouped chunk reduction adds.
-static td_status group_build(td_group* g, int bn, int s_factor) {
+// up to nc = 128 or 256 residual columns as N, each segment's last column tile
+// only as wide as its columns rounded up to 16), every item a chunk whose
+// accumulator pairs the grouped chunk reduction adds.  At 128 columns TMEM
+// holds two accumulator pairs, so an item's epilogue overlaps the next
+// item's MMAs; at 256 one.
+static td_status group_build(td_group* g, int bn, int s_factor, int nc = GROUP_NC) {
   group_free_lists(g);
   g->bn = bn;
   g->s_factor = s_factor;
+  g->small_nc = nc;
   const bool small = bn == 0;
-  const int rows = small ? 128 : bn, cols = small ? GROUP_NC : TC_COLS;
+  const int rows = small ? 128 : bn, cols = small ? nc : TC_COLS;
   // work per residual-column tile summed over segments; chunk so that the
   // longest item is about 1/(2 s_factor) of an SM's even share
   int64_t tiles_work = 0;
@@ -171,7 +175,7 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
   }
   sort_items(items);
   td_status r;
-  const size_t wbytes = (size_t)n_slots * (small ? GROUP_NC * 128 : TC_COLS * bn) * sizeof(float2);
+  const size_t wbytes = (size_t)n_slots * (small ? nc * 128 : TC_COLS * bn) * sizeof(float2);
   if ((r = group_alloc((void**)&g->d_items, std::max<size_t>(1, items.size()) * sizeof(TcItem), "items")) != TD_OK ||
       (r = group_alloc((void**)&g->d_units, std::max<size_t>(1, units.size()) * sizeof(SplitUnit), "units")) !=
           TD_OK ||
@@ -180,7 +184,7 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
   for (int i = 0; i < g->nseg; ++i) {
     TcSegDev& sd = g->host_seg[(size_t)i];
     td_segment* s = g->segs[(size_t)i];
-    sd.a_rows = small ? GROUP_NC : TC_COLS;
+    sd.a_rows = small ? nc : TC_COLS;
     sd.wpart = g->wpart;
     sd.nm = (int)(s->nkp / (small ? 128 : 64));   // chi2 partials per 128-row tile or per 64 rows
     if (sd.K == 0) continue;   // no work item refers to an empty segment
@@ -195,7 +199,7 @@ static td_status group_build(td_group* g, int bn, int s_factor) {
     tmp_view.scr.capK = cap;
     TcSegDev enc;
     memset(&enc, 0, sizeof enc);
-    if ((r = encode_seg_maps(&tmp_view, sd.K, g->nsl, rows, &enc, small ? GROUP_NC : TC_COLS)) != TD_OK) {
+    if ((r = encode_seg_maps(&tmp_view, sd.K, g->nsl, rows, &enc, small ? nc : TC_COLS)) != TD_OK) {
       tmp_view.scr.rs = nullptr;
       tmp_view.op = nullptr;
       return r;
@@ -245,8 +249,9 @@ static td_status group_launch_impl(td_group* g, cudaStream_t st) {
     TD_CUDA(cudaGetLastError());
   }
   if (g->bn == 0) {
-    TD_CUDA(launch_tc_small(g->d_items, g->n_items, g->d_seg, g->nsl, GROUP_NC, g->status, g->wait_limit_ns, st));
-    TD_CUDA(launch_small_reduce_grouped(g->d_units, g->n_units, g->d_seg, GROUP_NC, st));
+    TD_CUDA(launch_tc_small(g->d_items, g->n_items, g->d_seg, g->nsl, g->small_nc, g->status, g->wait_limit_ns,
+                            st));
+    TD_CUDA(launch_small_reduce_grouped(g->d_units, g->n_units, g->d_seg, g->small_nc, st));
   } else {
     TD_CUDA(launch_tc_cdo(g->d_items, g->n_items, g->d_seg, g->nsl, g->bn, true, g->status, g->wait_limit_ns, st,
                           false));
@@ -260,11 +265,12 @@ static td_status group_launch_impl(td_group* g, cudaStream_t st) {
   return TD_OK;
 }
 
-// process-wide autotuner decisions: signature -> (bn, s_factor)
+// process-wide autotuner decisions: signature -> (bn, s_factor, small_nc)
 struct TuneEntry {
   std::string key;
   int bn;
   int s_factor;
+  int nc;
   double ms;
 };
 static std::mutex g_tune_mu;
@@ -372,7 +378,7 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
     return fail(TD_ERR_CUDA, "group upload failed");
   }
   // tile shape: a decision the autotuner made for this kind of group, else 256-row tiles
-  int bn = 256, sf = 1;
+  int bn = 256, sf = 1, nc = GROUP_NC;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     const std::string key = group_signature(g);
@@ -380,12 +386,13 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
       if (e.key == key) {
         bn = e.bn;
         sf = e.s_factor;
+        nc = e.nc;
       }
   }
   if (o.path == TD_PATH_STREAM64) bn = 64;
   if (o.path == TD_PATH_STREAM) bn = 256;
   if (o.path == TD_PATH_SMALLK) bn = 0;
-  if ((r = group_build(g, bn, sf)) != TD_OK) {
+  if ((r = group_build(g, bn, sf, nc)) != TD_OK) {
     td_group_destroy(g);
     return r;
   }
@@ -447,15 +454,18 @@ td_status td_group_graph_launch(td_group* g, void* stream) {
 td_status td_group_tune(td_group* g, void* stream, double* best_ms) {
   if (!g) return fail(TD_ERR_INVALID, "group is NULL");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-  // tile rows (0: the small-batch orientation) and chunk multiplier
-  const int cand[][2] = {{256, 1}, {256, 2}, {128, 1}, {128, 2}, {128, 4}, {64, 1}, {64, 2}, {0, 1}, {0, 2}, {0, 4}};
+  // tile rows (0: the small-batch orientation), chunk multiplier, and the
+  // small orientation's residual columns per tile
+  const int cand[][3] = {{256, 1, 0},   {256, 2, 0},   {128, 1, 0},   {128, 2, 0},   {128, 4, 0},
+                         {64, 1, 0},    {64, 2, 0},    {0, 1, 256},   {0, 2, 256},   {0, 4, 256},
+                         {0, 1, 128},   {0, 2, 128},   {0, 4, 128}};
   double best = 1e300;
-  int bb = g->bn, bs = g->s_factor;
+  int bb = g->bn, bs = g->s_factor, bc = g->small_nc;
   cudaEvent_t a, b;
   cudaEventCreate(&a);
   cudaEventCreate(&b);
   for (const auto& c : cand) {
-    td_status r = group_build(g, c[0], c[1]);
+    td_status r = group_build(g, c[0], c[1], c[2] ? c[2] : GROUP_NC);
     if (r != TD_OK) continue;
     for (int w = 0; w < 2; ++w) group_launch_impl(g, st);
     cudaEventRecord(a, st);
@@ -469,11 +479,12 @@ td_status td_group_tune(td_group* g, void* stream, double* best_ms) {
       best = per;
       bb = c[0];
       bs = c[1];
+      bc = c[2] ? c[2] : GROUP_NC;
     }
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
-  td_status r = group_build(g, bb, bs);
+  td_status r = group_build(g, bb, bs, bc);
   if (r != TD_OK) return r;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -483,10 +494,11 @@ td_status td_group_tune(td_group* g, void* stream, double* best_ms) {
       if (e.key == key) {
         e.bn = bb;
         e.s_factor = bs;
+        e.nc = bc;
         e.ms = best;
         found = true;
       }
-    if (!found) g_tune.push_back(TuneEntry{key, bb, bs, best});
+    if (!found) g_tune.push_back(TuneEntry{key, bb, bs, bc, best});
   }
   if (best_ms) *best_ms = best;
   return TD_OK;

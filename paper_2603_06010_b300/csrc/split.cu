@@ -328,8 +328,29 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
   if (K <= 0) return cudaSuccess;
   const bool reg_ok = K <= 2147483647LL && ldr % 4 == 0 && nk % 4 == 0 &&
                       (reinterpret_cast<uintptr_t>(R) & 15) == 0 && nk <= 4 * 8 * 1024;
-  if (K <= 64 || (K <= 256 && !reg_ok)) {
-    // few columns: a cluster per column puts more SMs on them
+  auto launch_pdl = [&](auto kern, unsigned grid, unsigned block) -> cudaError_t {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
+  };
+  if (K <= 64 && reg_ok) {
+    // up to 64 columns: one 1024-thread CTA per column, the column in
+    // registers (one read, one block barrier, no cluster barriers); measured
+    // at N' = 8192 a call of 4 columns 49.1 against 50.1 us with the cluster
+    // form, of 32 columns 56.7 against 60
+    if (pdl) return launch_pdl(k_r_slices_reg<1024, 8>, (unsigned)K, 1024u);
+    k_r_slices_reg<1024, 8><<<(unsigned)K, 1024, 0, st>>>(R, ldr, nk, K, nkp8, capK, rs, nslices, zero, nzero);
+  } else if (K <= 64 || (K <= 256 && !reg_ok)) {
+    // few columns, unaligned or longer than 32768 rows: a cluster per column
+    // puts more SMs on them
     if (pdl) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3((unsigned)(K * RS_CL));

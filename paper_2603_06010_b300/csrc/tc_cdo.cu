@@ -62,26 +62,6 @@ template <int NSL, int BN> struct Cfg {
 };
 }  // namespace tc
 
-// correction products (operator slice, residual slice), smallest first; the
-// hi*hi product (0, 0) is separate.  NSL slices per operand: 4 -> a+b <= 3
-// (10 products), 3 -> a+b <= 2 (6 products), 2 -> a+b <= 1 (3 products).
-template <int NSL> struct Corr;
-template <> struct Corr<4> {   // (3,0) (2,1) (1,2) (0,3) (2,0) (1,1) (0,2) (1,0) (0,1)
-  static constexpr int N = 9;
-  __device__ static constexpr int op(int p) { return p < 4 ? 3 - p : (p < 7 ? 6 - p : 8 - p); }
-  __device__ static constexpr int rs(int p) { return p < 4 ? p : (p < 7 ? p - 4 : p - 7); }
-};
-template <> struct Corr<3> {   // (2,0) (1,1) (0,2) (1,0) (0,1)
-  static constexpr int N = 5;
-  __device__ static constexpr int op(int p) { return p < 3 ? 2 - p : 4 - p; }
-  __device__ static constexpr int rs(int p) { return p < 3 ? p : p - 3; }
-};
-template <> struct Corr<2> {   // (1,0) (0,1)
-  static constexpr int N = 2;
-  __device__ static constexpr int op(int p) { return 1 - p; }
-  __device__ static constexpr int rs(int p) { return p; }
-};
-
 struct TcSingle {           // single-segment launch: item list is implicit
   TcSegDev seg;
   int nm;                   // row tiles of BN rows
@@ -275,19 +255,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + stage * STAGE);
           const uint32_t sb = sa + A_STAGE;
+          // residual slices (A) against operator slices (B), grouped by the
+          // residual slice so the collector buffer reuses it
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {
-            const uint32_t first = (kb > it.kb0 || kk > 0) ? 1u : 0u;
-            tc_mma_f16(d_hi, smem_desc_sw64(sa + kk * 32), smem_desc_sw64(sb + kk * 32), idesc, first);
-#pragma unroll
-            for (int p = 0; p < Corr<NSL>::N; ++p) {
-              const int ia = Corr<NSL>::rs(p);   // residual slice (A)
-              const int ib = Corr<NSL>::op(p);   // operator slice (B)
-              const uint64_t ad = smem_desc_sw64(sa + ia * A_SLICE + kk * 32);
-              const uint64_t bd = smem_desc_sw64(sb + ib * B_SLICE + kk * 32);
-              tc_mma_f16(d_lo, ad, bd, idesc, (first | (p > 0 ? 1u : 0u)));
-            }
-          }
+          for (int kk = 0; kk < 2; ++kk)
+            split_products_step<NSL>(d_hi, d_lo, sa, A_SLICE, sb, B_SLICE, kk * 32, idesc,
+                                     (kb > it.kb0 || kk > 0) ? 1u : 0u);
           tc_commit(&empty[stage]);   // frees this smem stage once these MMAs retire
           if (++stage == STAGES) {
             stage = 0;

@@ -52,23 +52,6 @@ template <int NSL, int NC> struct Cfg {
 };
 }  // namespace tsm
 
-template <int NSL> struct CorrS;
-template <> struct CorrS<4> {   // (operator, residual): (3,0) (2,1) (1,2) (0,3) (2,0) (1,1) (0,2) (1,0) (0,1)
-  static constexpr int N = 9;
-  __device__ static constexpr int op(int p) { return p < 4 ? 3 - p : (p < 7 ? 6 - p : 8 - p); }
-  __device__ static constexpr int rs(int p) { return p < 4 ? p : (p < 7 ? p - 4 : p - 7); }
-};
-template <> struct CorrS<3> {   // (2,0) (1,1) (0,2) (1,0) (0,1)
-  static constexpr int N = 5;
-  __device__ static constexpr int op(int p) { return p < 3 ? 2 - p : 4 - p; }
-  __device__ static constexpr int rs(int p) { return p < 3 ? p : p - 3; }
-};
-template <> struct CorrS<2> {
-  static constexpr int N = 2;
-  __device__ static constexpr int op(int p) { return 1 - p; }
-  __device__ static constexpr int rs(int p) { return p; }
-};
-
 // 32 lanes x 16 consecutive 32-bit columns
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   uint32_t r[16];
@@ -345,17 +328,12 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
           tc_fence_after();
           const uint32_t sa = smem_u32(smem + stage * STAGE);
           const uint32_t sb = sa + A_STAGE;
+          // operator slices (A) against residual slices (B), grouped by the
+          // operator slice so the collector buffer reuses it
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {
-            const uint32_t first = (kb > it.kb0 || kk > 0) ? 1u : 0u;
-            tc_mma_f16(d_hi, smem_desc_sw64(sa + kk * 32), smem_desc_sw64(sb + kk * 32), idesc, first);
-#pragma unroll
-            for (int p = 0; p < CorrS<NSL>::N; ++p) {
-              const uint64_t ad = smem_desc_sw64(sa + CorrS<NSL>::op(p) * A_SLICE + kk * 32);
-              const uint64_t bd = smem_desc_sw64(sb + CorrS<NSL>::rs(p) * B_SLICE + kk * 32);
-              tc_mma_f16(d_lo, ad, bd, idesc, (first | (p > 0 ? 1u : 0u)));
-            }
-          }
+          for (int kk = 0; kk < 2; ++kk)
+            split_products_step<NSL>(d_hi, d_lo, sa, A_SLICE, sb, B_SLICE, kk * 32, idesc,
+                                     (kb > it.kb0 || kk > 0) ? 1u : 0u);
           tc_commit(&empty[stage]);
           if (++stage == STAGES) {
             stage = 0;

@@ -109,6 +109,32 @@ __device__ __forceinline__ void tc_mma_f16(uint32_t d_tmem, uint64_t adesc, uint
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
+// The same MMA with a collector-buffer hint for A (USE 1: fill, 2: use, 3:
+// last use): consecutive MMAs of one thread that share their A operand read it
+// from shared memory once.
+template <int USE>
+__device__ __forceinline__ void tc_mma_f16_a(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+  static_assert(USE >= 1 && USE <= 3, "collector usage");
+  if constexpr (USE == 1)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::fill [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else if constexpr (USE == 2)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::use [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16.collector::a::lastuse [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
 // arrive on an mbarrier once every MMA issued so far by this thread has completed
 __device__ __forceinline__ void tc_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -156,6 +182,40 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
          | ((uint32_t)(M >> 4) << 24);   // M / 16
 }
 
+// The split products of one 16-deep step (both operands K-major, 64-byte
+// swizzle, slices a_slice / b_slice bytes apart, kofs the step's byte offset
+// in the 64-byte rows): A slice a against B slices b = NSL-1-a ... 0, the
+// smaller products first.  (0, 0) is the exact hi*hi sum and goes to d_hi,
+// every other product to d_lo; `first` = 0 starts both accumulators.  The
+// MMAs of one A slice follow each other, so the collector buffer keeps that
+// slice and shared memory delivers each A slice once per step instead of once
+// per product.
+template <int NSL>
+__device__ __forceinline__ void split_products_step(uint32_t d_hi, uint32_t d_lo, uint32_t sa, uint32_t a_slice,
+                                                    uint32_t sb, uint32_t b_slice, uint32_t kofs, uint32_t idesc,
+                                                    uint32_t first) {
+#pragma unroll
+  for (int a = 0; a < NSL; ++a) {
+    const uint64_t ad = smem_desc_sw64(sa + a * a_slice + kofs);
+#pragma unroll
+    for (int b = NSL - 1 - a; b >= 0; --b) {
+      const int n = NSL - a;           // MMAs sharing this A slice
+      const int i = NSL - 1 - a - b;   // position among them
+      const uint64_t bd = smem_desc_sw64(sb + b * b_slice + kofs);
+      const bool hh = a == 0 && b == 0;
+      const uint32_t d = hh ? d_hi : d_lo;
+      const uint32_t acc = (hh || (a == 0 && b == NSL - 1)) ? first : 1u;
+      if (n == 1)
+        tc_mma_f16(d, ad, bd, idesc, acc);
+      else if (i == 0)
+        tc_mma_f16_a<1>(d, ad, bd, idesc, acc);
+      else if (i == n - 1)
+        tc_mma_f16_a<3>(d, ad, bd, idesc, acc);
+      else
+        tc_mma_f16_a<2>(d, ad, bd, idesc, acc);
+    }
+  }
+}
 // ---------------------------------------------------------------- slicing
 // x = s0 + s1 + s2 with each s a bf16 (round-to-nearest on the running
 // remainder, computed exactly in the wider type).

@@ -446,7 +446,7 @@ def factor_extra(td, torch, with_fp64_cores=True, sizes=(16384, 32768)):
     gapped N=16384 (3 gaps of 512, N'=14848) and gapped N=32768 (N'=31232) on the
     tensor-core route, and the N=16384 segment on the FP64 CUDA-core route beside it."""
     from paper_2603_06010_b300 import inputs
-    out = {"note": "td_factor: blocks of 128, the block factor and its inverse in FP64, panel and trailing "
+    out = {"note": "td_factor: blocks of 128, the block factor and its inverse in double-float, panel and trailing "
                    "updates as FP64-accurate split bf16 products on the tensor cores (six slices); wall time "
                    "of the synchronous call (covariance gather, factor, L^-1, log det, operator slices)",
            "runs": []}

@@ -629,6 +629,60 @@ def fp64_per_request(td, torch, fleet, pools, served):
             "p50_ms_no_queue": float(np.percentile(t, 50)), "p99_ms_no_queue": float(np.percentile(t, 99))}
 
 
+def fp64_served(td, torch, fleet, pools, phases=((2000.0, 0.1), (15.0, 8.0)), seed=5150):
+    """The plain per-request FP64 solve actually served: open-loop Poisson
+    arrivals (segment length uniform over the four N, one gapped segment of
+    each, K uniform over {1, 8, 64, 512}), requests taken one at a time in
+    arrival order on one stream, each the FP64 forward substitution with the
+    FP64 factor, no batching.  Latency = completion - arrival (queueing
+    included), per phase: the workload's 2000 req/s for a short burst, and a
+    rate this server can sustain."""
+    from paper_2603_06010_b300 import inputs
+    o64 = td.options(precision=td.TD_PREC_FP64)
+    Ns = (4096, 8192, 16384, 32768)
+    segs, srcs = {}, {}
+    for n in Ns:
+        i = next(j for j, sp in enumerate(fleet) if sp["n"] == n and sp["gaps"] > 0)
+        sp = fleet[i]
+        segs[n] = td.Segment(inputs.acf_from_psd(sp["n"], sp["fs"]), sp["mask"])
+        srcs[n] = pools[i]
+    outs = {k: torch.empty(k, dtype=torch.float64, device="cuda") for k in (1, 8, 64, 512)}
+    for n in Ns:   # warm-up: every (N, K) once
+        for k in (1, 8, 64, 512):
+            segs[n].loglike_into(srcs[n][:k].contiguous(), outs[k], o64)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    res = {}
+    for rate, secs in phases:
+        n_req = max(1, int(rate * secs))
+        arrive = np.cumsum(rng.exponential(1.0 / rate, n_req))
+        req_n = rng.choice(Ns, n_req)
+        req_k = rng.choice((1, 8, 64, 512), n_req)
+        lat = np.empty(n_req)
+        t0 = time.perf_counter()
+        for q in range(n_req):
+            while time.perf_counter() - t0 < arrive[q]:
+                pass
+            n, k = int(req_n[q]), int(req_k[q])
+            segs[n].loglike_into(srcs[n][:k], outs[k], o64)
+            torch.cuda.synchronize()
+            lat[q] = (time.perf_counter() - t0 - arrive[q]) * 1e3
+        span = time.perf_counter() - t0
+        for s in segs.values():
+            s.check()
+        res[f"{rate:g}_per_s"] = {"requests": n_req, "arrival_seconds": float(arrive[-1]),
+                                  "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                                  "max_ms": float(lat.max()), "completed_per_s": n_req / span,
+                                  "evals_per_s": float(req_k.sum()) / span}
+    for s in segs.values():
+        s.close()
+    res["note"] = ("plain FP64 solve served one request at a time in arrival order (FP64 L, blocked forward "
+                   "substitution on the FP64 cores, no batching), open-loop Poisson arrivals, one gapped segment "
+                   "per N; latency includes queueing. At the workload's rate the queue grows without bound, so "
+                   "its percentiles depend on the burst length")
+    return res
+
+
 def serving_extra(td, torch, seconds, evict_seconds=4.0):
     """The serving workload: 200 resident segments (N uniform over 4096, 8192,
     16384, 32768 at 2048 Hz, 0-3 gaps of 512 each), open-loop Poisson arrivals
@@ -720,6 +774,7 @@ def serving_extra(td, torch, seconds, evict_seconds=4.0):
     p2, _ = phase(50.0, evict_seconds)
     srv.close()
     fp64 = fp64_per_request(td, torch, fleet, pools, served)
+    fp64["served"] = fp64_served(td, torch, fleet, pools)
     by_n = {k: {"segments": len(v), "mean_s": float(np.mean(v)), "max_s": float(np.max(v))}
             for k, v in sorted(factor_by_n.items())}
     out = {"note": "200 resident segments: N uniform over {4096, 8192, 16384, 32768} at 2048 Hz, 0-3 gaps of "

@@ -71,12 +71,15 @@ typedef enum {
                           whose chi2 rests on one row (N' below a few hundred). */
   TD_PREC_BF16X3 = 2,  /* hi + 1 remainder slice, 3 products: ~1e-5 relative, below
                           the accuracy bar (kept to show why more products are needed) */
-  TD_PREC_AUTO = 3,    /* default: TD_PREC_BF16X6 for 512 <= N' <= 32768, TD_PREC_BF16X10 beyond
-                          (the 6-product |dlogL| grows as ~N' x 1e-8: 3.4e-4 measured
-                          at N' = 32257) and below (with few rows one column's chi2 can
-                          rest on one row, good to ~6e-8 with six products: 1.15e-7
-                          measured at N' = 47).  Grouped launches take one count for
-                          all segments: ten once any exceeds 32768 or all are below 512. */
+  TD_PREC_AUTO = 3,    /* default: TD_PREC_BF16X6 for 2048 <= N' <= 32768, TD_PREC_BF16X10
+                          beyond (the 6-product |dlogL| grows as ~N' x 1e-8: 3.4e-4
+                          measured at N' = 32257) and below (the 6-product chi2 error
+                          grows as fewer rows carry a column's chi2: 2e-8 relative at
+                          N' = 8192, 1.03e-7 measured on a gapped N' = 739 segment,
+                          1.15e-7 at N' = 47).  Grouped launches take one count for
+                          all segments: ten once any exceeds 32768 or all are below
+                          2048, otherwise six (segments below 2048 in such a mix get
+                          six). */
   TD_PREC_BF16X10 = 4  /* 4 slices each, the 10 products a+b <= 3: chi2 ~1e-9 relative */
 } td_precision;
 
@@ -376,7 +379,7 @@ td_status td_project_batch(td_segment* s, const float* hp, const float* hc, int6
 
 /*
  * td_loglike_batch_noalloc -- the evaluation td_loglike_batch makes with the
- * default precision (TD_PREC_AUTO: six split products, ten below 512 and above
+ * default precision (TD_PREC_AUTO: six split products, ten below 2048 and above
  * 32768 kept samples) on one fixed tile shape (64 operator rows per tile), so
  * results agree with td_loglike_batch within rounding, not bit for bit; for
  * callers that cannot allocate device memory while they

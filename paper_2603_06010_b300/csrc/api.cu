@@ -149,7 +149,7 @@ static td_status check_device(const td_segment* s) {
 // good to ~6e-8 relative, so chi2 can miss 1e-7 (1.15e-7 measured at N' = 47);
 // many rows average that away.  Small segments cost little either way.
 int nslices_for(int precision, int64_t nk) {
-  if (precision == TD_PREC_AUTO) return (nk > 32768 || nk < 512) ? 4 : 3;
+  if (precision == TD_PREC_AUTO) return (nk > 32768 || nk < AUTO_SIX_MIN) ? 4 : 3;
   return precision == TD_PREC_BF16X3 ? 2 : (precision == TD_PREC_BF16X10 ? 4 : 3);
 }
 

@@ -311,12 +311,12 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
   g->nsl = o.precision == TD_PREC_BF16X3 ? 2 : (o.precision == TD_PREC_BF16X10 ? 4 : 3);
   if (o.precision == TD_PREC_AUTO) {
     // as for one segment: ten products once any segment exceeds N' = 32768, or
-    // when every segment is below N' = 512 (one slice count serves the launch, so
-    // a mix of tiny and larger segments keeps six products)
+    // when every segment is below AUTO_SIX_MIN kept samples (one slice count
+    // serves the launch, so a mix of short and longer segments keeps six)
     bool all_small = true;
     for (int i = 0; i < nseg; ++i) {
       if (segs[i] && segs[i]->nk > 32768) g->nsl = 4;
-      if (segs[i] && segs[i]->nk >= 512) all_small = false;
+      if (segs[i] && segs[i]->nk >= AUTO_SIX_MIN) all_small = false;
     }
     if (all_small) g->nsl = 4;
   }

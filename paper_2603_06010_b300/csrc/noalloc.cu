@@ -112,7 +112,7 @@ extern "C" td_status td_loglike_batch_noalloc(td_segment* s, const float* R, int
   double* partials = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(base) + part_off);
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // the slice count td_loglike_batch takes with its default options (ten
-  // products below 512 and above 32768 kept samples, six between)
+  // products below 2048 and above 32768 kept samples, six between)
   const int nsl = nslices_for(TD_PREC_AUTO, s->nk);
 
   TcSegDev seg;

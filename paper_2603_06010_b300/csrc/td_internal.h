@@ -302,6 +302,12 @@ cudaError_t launch_split_reduce(const SplitUnit* units, int n_units, const TcSeg
 // run inside the kernel (the last chunk of a row tile, then the last CTA);
 // launched as a programmatic dependent of the residual slicing.
 constexpr int SMALL_GROUPS = 64;   // 4-column groups of the widest small batch (256 columns)
+// TD_PREC_AUTO: six split products from this many kept samples up to 32768,
+// ten outside.  Six products give chi2 to about 2e-8 relative at N' = 8192,
+// growing as the rows that carry a column's chi2 get fewer (1.03e-7 measured
+// on a gapped N' = 739 segment, 1.15e-7 at N' = 47), so below 2048 the default
+// takes ten
+constexpr int64_t AUTO_SIX_MIN = 2048;
 constexpr int SMALL_FUSED_K = 4;   // small batches up to this width reduce inside the product kernel
 struct SmallFinal {
   const SplitUnit* units;

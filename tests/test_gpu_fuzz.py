@@ -77,9 +77,10 @@ def test_random_case(torch_cuda, gpu_lib, i):
     seg.check()
     got_chi, got_ll = chi2.cpu().numpy(), logL.cpu().numpy()
     rel_tol, ll_tol = (1e-11, 1e-7) if path == td.TD_PATH_FP64 else (1e-7, 1e-3)
-    if prec == td.TD_PREC_BF16X6 and not refine and not gsce and o.n_kept < 512:
-        # six products represent each row to ~2^-24; a column of a few rows can
-        # carry its chi2 on one row, twice that relative (no averaging)
+    if prec == td.TD_PREC_BF16X6 and not refine and not gsce and o.n_kept < 2048:
+        # six products represent each row to ~2^-24; with few rows a column's
+        # chi2 rests on few of them (less averaging): up to ~1.2e-7 measured,
+        # which is why the default precision takes ten products below 2048
         rel_tol = 2.5e-7
     what = f"n={n} gaps={mask is not None} K={K} path={path} prec={prec} refine={refine}"
     rel = np.max(np.abs(got_chi - exp_chi) / exp_chi)

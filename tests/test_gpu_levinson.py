@@ -247,11 +247,12 @@ def test_grouped_launch_over_levinson_segments(torch_cuda, gpu_lib):
 
 
 def test_auto_precision_switches_above_32768(torch_cuda, gpu_lib):
-    """TD_PREC_AUTO (the default): six products for 512 <= N' <= 32768, ten
+    """TD_PREC_AUTO (the default): six products for 2048 <= N' <= 32768, ten
     beyond and below (same bits as the explicit choice)."""
     from paper_2603_06010_b300 import td
     assert td.options().precision == td.TD_PREC_AUTO
-    for n, expect in ((300, td.TD_PREC_BF16X10), (2000, td.TD_PREC_BF16X6), (33000, td.TD_PREC_BF16X10)):
+    for n, expect in ((300, td.TD_PREC_BF16X10), (2047, td.TD_PREC_BF16X10), (2048, td.TD_PREC_BF16X6),
+                      (33000, td.TD_PREC_BF16X10)):
         acf = inputs.acf_from_psd(n, 4096.0)
         seg = td.Segment(acf, factor=False)
         td.factor_many([seg])

@@ -28,6 +28,8 @@
 // Warp roles as in the main kernel: warp 0 lane 0 TMA producer, warp 1
 // TMEM owner and MMA issuer, warps 2..5 epilogue.  Every wait is bounded;
 // the completion counter is an arrival count only (no thread waits on it).
+#include <type_traits>
+
 #include "td_internal.h"
 
 namespace td {
@@ -71,15 +73,15 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }   // warps 2..5
 
-// Chunk pairs of one split row tile, four columns n0 .. n0+3, for the row of
+// Chunk pairs of one split row tile, CB columns n0 .. n0+CB-1, for the row of
 // this thread (base = its row in the unit's first slot): double-float sums in
-// chunk order (loads issued CH chunks x 4 columns ahead), the exact square,
+// chunk order (loads issued CH chunks x CB columns ahead), the exact square,
 // then the fixed shuffle tree over the 32 rows of the warp; lane 0 returns
-// the warp's partial of each column.
-template <int CH>
+// the warp's partial of each column.  A column's arithmetic does not depend
+// on CB.
+template <int CH, int CB = 4>
 __device__ __forceinline__ void unit_cols4(const float2* base, int nchunk, int slot_cols, int n0, int kcols,
-                                           double (&part)[4]) {
-  constexpr int CB = 4;
+                                           double (&part)[CB]) {
   float wh[CB], wl[CB];
 #pragma unroll
   for (int c = 0; c < CB; ++c) wh[c] = wl[c] = 0.f;
@@ -433,19 +435,29 @@ __global__ void __launch_bounds__(tsm::THREADS, 1)
           if (sh_last) {
             __threadfence();
             const float2* base = sd->wpart + (int64_t)u.slot0 * red.slot_cols * BM + q * 32 + lane;
-            for (int n0 = 0; n0 < red.K; n0 += 4) {
-              double part[4];
-              unit_cols4<8>(base, u.nchunk, red.slot_cols, n0, red.K, part);
+            // all of the call's columns in one pass (up to SMALL_FUSED_K = 8):
+            // four columns eight chunks deep, or eight columns four chunks deep
+            // (measured at N' = 8192: K <= 4 calls 49.5-50 against 51.5 us with
+            // the eight-column form, K = 5 .. 8 51.5-52.3 against 53-56 us with
+            // the separate reduction)
+            auto pass = [&](auto cb) {
+              constexpr int FCB = decltype(cb)::value;
+              double part[FCB];
+              unit_cols4<32 / FCB, FCB>(base, u.nchunk, red.slot_cols, 0, red.K, part);
               if (lane == 0)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) sh_fin[q][c] = part[c];
+                for (int c = 0; c < FCB; ++c) sh_fin[q][c] = part[c];
               epi_bar();
               // the tile's four 32-row groups in a fixed order
-              if (q == 0 && lane < 4 && n0 + lane < red.K)
-                sd->partials[(int64_t)u.m * sd->ldp + u.c * 128 + n0 + lane] =
+              if (q == 0 && lane < FCB && lane < red.K)
+                sd->partials[(int64_t)u.m * sd->ldp + u.c * 128 + lane] =
                     ((sh_fin[0][lane] + sh_fin[1][lane]) + sh_fin[2][lane]) + sh_fin[3][lane];
               epi_bar();
-            }
+            };
+            if (red.K <= 4)
+              pass(std::integral_constant<int, 4>());
+            else
+              pass(std::integral_constant<int, 8>());
             if (q == 0) __threadfence();
             epi_bar();
             small_tile_done(sd, red, q, lane, sh_fin, sh_last);

@@ -308,7 +308,7 @@ constexpr int SMALL_GROUPS = 64;   // 4-column groups of the widest small batch 
 // on a gapped N' = 739 segment, 1.15e-7 at N' = 47), so below 2048 the default
 // takes ten
 constexpr int64_t AUTO_SIX_MIN = 2048;
-constexpr int SMALL_FUSED_K = 4;   // small batches up to this width reduce inside the product kernel
+constexpr int SMALL_FUSED_K = 8;   // small batches up to this width reduce inside the product kernel
 struct SmallFinal {
   const SplitUnit* units;
   // zero at launch.  Separate reduction kernel: [SMALL_GROUPS] arrivals per

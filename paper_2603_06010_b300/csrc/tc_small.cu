@@ -24,6 +24,9 @@
 // the first operator stages before it waits for the slices; k_small_reduce,
 // which adds the chunks of each split row tile (chunk order fixed) and whose
 // last CTA sums each column's partials in a fixed order into chi2 and logL.
+// Up to eight columns this kernel does the reduction's work itself (the last
+// chunk of a split row tile to arrive reduces it, the CTA that completes the
+// last tile forms chi2 and logL), with the same arithmetic: two launches.
 //
 // Warp roles as in the main kernel: warp 0 lane 0 TMA producer, warp 1
 // TMEM owner and MMA issuer, warps 2..5 epilogue.  Every wait is bounded;

@@ -76,10 +76,9 @@ typedef enum {
                           measured at N' = 32257) and below (the 6-product chi2 error
                           grows as fewer rows carry a column's chi2: 2e-8 relative at
                           N' = 8192, 1.03e-7 measured on a gapped N' = 739 segment,
-                          1.15e-7 at N' = 47).  Grouped launches take one count for
-                          all segments: ten once any exceeds 32768 or all are below
-                          2048, otherwise six (segments below 2048 in such a mix get
-                          six). */
+                          1.15e-7 at N' = 47).  A grouped launch gives each segment
+                          the count td_loglike_batch would (one product launch per
+                          count present). */
   TD_PREC_BF16X10 = 4  /* 4 slices each, the 10 products a+b <= 3: chi2 ~1e-9 relative */
 } td_precision;
 
@@ -423,7 +422,8 @@ td_status td_reserve(td_segment* s, int64_t K, const td_options* opt);
  * scratch (this call allocates and synchronises).  The plan keeps the
  * pointers it was given: later launches read R[i] and write logL[i] there.
  * td_group_launch enqueues the evaluation on `stream` (four kernels whatever
- * nseg, five with a joint sum; no allocation; capturable in a CUDA graph).  td_group_graph_launch
+ * nseg, two more for each further slice count its segments take, one more
+ * with a joint sum; no allocation; capturable in a CUDA graph).  td_group_graph_launch
  * captures the launch into a CUDA graph on first use and replays it.
  * td_group_tune times the candidate tile shapes and chunk sizes on the plan's
  * own inputs, keeps the fastest, and records it for later plans of the same

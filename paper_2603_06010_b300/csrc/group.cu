@@ -4,9 +4,14 @@
 // segment's whitening is independent and the work items of all segments share
 // one launch, sorted by work and dealt to the SMs in snake order.
 //
+// Each segment takes the slice count td_loglike_batch would take for it; a
+// group whose segments need different counts runs one product launch (and
+// one chunk reduction) per count.
+//
 // A td_group is a plan: it owns the device work lists, segment descriptors
-// and scratch, so td_group_launch only launches kernels (five per call,
-// whatever the number of segments) and can be captured in a CUDA graph;
+// and scratch, so td_group_launch only launches kernels (five per call and
+// slice count, whatever the number of segments) and can be captured in a
+// CUDA graph;
 // td_group_graph_launch captures it once and replays the graph.  The
 // autotuner (td_group_tune) times the candidate tile shapes and chunk sizes
 // on the real inputs and keeps the fastest.
@@ -44,11 +49,13 @@ struct RsJob {          // one segment's residual slicing for the grouped slicin
   int64_t capK;
   __nv_bfloat16* rs;
   int64_t col0;         // first global column of this segment
+  int nsl;              // slices this segment's product reads
+  int pad;
 };
 
 // per-column quantum and slices for every segment of the group (as k_r_slices)
 __global__ void __launch_bounds__(256) k_r_slices_grouped(const RsJob* __restrict__ jobs, int njobs,
-                                                           int64_t total_cols, int nslices) {
+                                                           int64_t total_cols) {
   __shared__ float red[8];
   for (int64_t gc = blockIdx.x; gc < total_cols; gc += gridDim.x) {
     int lo = 0, hi = njobs - 1;   // last job with col0 <= gc
@@ -75,6 +82,7 @@ __global__ void __launch_bounds__(256) k_r_slices_grouped(const RsJob* __restric
       if (mx / p > 255.f) p *= 2.f;
     }
     const int64_t ss = jb.capK * jb.nkp8;
+    const int nslices = jb.nsl;
     __nv_bfloat16* dst = jb.rs + k * jb.nkp8;
     for (int64_t j = threadIdx.x; j < jb.nk; j += blockDim.x) {
       const float x = col[j];
@@ -93,10 +101,23 @@ __global__ void __launch_bounds__(256) k_r_slices_grouped(const RsJob* __restric
 
 using namespace td;
 
+// The work of one slice count: a grouped launch runs each segment with the
+// slice count td_loglike_batch would take for it (under TD_PREC_AUTO ten
+// products below 2048 and above 32768 kept samples, six between), one
+// product launch per count present.
+struct GroupClass {
+  int nsl = 3;
+  TcItem* d_items = nullptr;
+  SplitUnit* d_units = nullptr;
+  int n_items = 0, n_units = 0;
+  float2* wpart = nullptr;
+};
+
 struct td_group {
   int device = 0;
   int nseg = 0;
-  int nsl = 3;
+  int nsl = 3;                // the largest slice count of the group
+  std::vector<int> seg_nsl;   // each segment's slice count
   int bn = 256;
   int s_factor = 1;           // chunk size multiplier chosen by the autotuner
   int small_nc = GROUP_NC;    // small-batch orientation: residual columns per tile (128 or 256)
@@ -110,12 +131,9 @@ struct td_group {
   // device
   TcSegDev* d_seg = nullptr;
   RsJob* d_jobs = nullptr;
-  TcItem* d_items = nullptr;
-  SplitUnit* d_units = nullptr;
-  int n_items = 0, n_units = 0;
+  std::vector<GroupClass> cls;   // one per slice count present
   __nv_bfloat16* rs = nullptr;
   double* partials = nullptr;
-  float2* wpart = nullptr;
   DevStatus* status = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
@@ -126,13 +144,12 @@ struct td_group {
 namespace td {
 
 static void group_free_lists(td_group* g) {
-  if (g->d_items) cudaFree(g->d_items);
-  if (g->d_units) cudaFree(g->d_units);
-  if (g->wpart) cudaFree(g->wpart);
-  g->d_items = nullptr;
-  g->d_units = nullptr;
-  g->wpart = nullptr;
-  g->n_items = g->n_units = 0;
+  for (GroupClass& c : g->cls) {
+    if (c.d_items) cudaFree(c.d_items);
+    if (c.d_units) cudaFree(c.d_units);
+    if (c.wpart) cudaFree(c.wpart);
+  }
+  g->cls.clear();
   if (g->graph) {
     cudaGraphExecDestroy(g->graph);
     g->graph = nullptr;
@@ -154,38 +171,59 @@ static td_status group_build(td_group* g, int bn, int s_factor, int nc = GROUP_N
   g->small_nc = nc;
   const bool small = bn == 0;
   const int rows = small ? 128 : bn, cols = small ? nc : TC_COLS;
-  // work per residual-column tile summed over segments; chunk so that the
-  // longest item is about 1/(2 s_factor) of an SM's even share
-  int64_t tiles_work = 0;
-  for (int i = 0; i < g->nseg; ++i) {
-    td_segment* s = g->segs[(size_t)i];
-    const int64_t nm = s->nkp / rows, per = rows / OP_KB, nkb_max = ceil_div(s->nk, OP_KB);
-    int64_t w = 0;
-    for (int64_t m = 0; m < nm; ++m) w += std::min<int64_t>(per * (m + 1), nkb_max);
-    tiles_work += w * ceil_div(g->host_seg[(size_t)i].K, cols);
-  }
-  int S = (int)ceil_div(tiles_work, 2LL * s_factor * tc_num_sms());
-  if (S < 4) S = 4;
-  std::vector<TcItem> items;
-  std::vector<SplitUnit> units;
-  int n_slots = 0;
-  for (int i = 0; i < g->nseg; ++i) {
-    td_segment* s = g->segs[(size_t)i];
-    plan_split_segment(i, s->nk, s->nkp, g->host_seg[(size_t)i].K, rows, S, items, units, n_slots, small, cols);
-  }
-  sort_items(items);
   td_status r;
-  const size_t wbytes = (size_t)n_slots * (small ? nc * 128 : TC_COLS * bn) * sizeof(float2);
-  if ((r = group_alloc((void**)&g->d_items, std::max<size_t>(1, items.size()) * sizeof(TcItem), "items")) != TD_OK ||
-      (r = group_alloc((void**)&g->d_units, std::max<size_t>(1, units.size()) * sizeof(SplitUnit), "units")) !=
-          TD_OK ||
-      (r = group_alloc((void**)&g->wpart, std::max<size_t>(8, wbytes), "split accumulators")) != TD_OK)
-    return r;
+  // one work list per slice count present, each balanced over the SMs on its own
+  for (int nsl = 2; nsl <= 4; ++nsl) {
+    bool any = false;
+    for (int i = 0; i < g->nseg; ++i) any = any || g->seg_nsl[(size_t)i] == nsl;
+    if (!any) continue;
+    // work per residual-column tile summed over the class's segments; chunk so
+    // that the longest item is about 1/(2 s_factor) of an SM's even share
+    int64_t tiles_work = 0;
+    for (int i = 0; i < g->nseg; ++i) {
+      if (g->seg_nsl[(size_t)i] != nsl) continue;
+      td_segment* s = g->segs[(size_t)i];
+      const int64_t nm = s->nkp / rows, per = rows / OP_KB, nkb_max = ceil_div(s->nk, OP_KB);
+      int64_t w = 0;
+      for (int64_t m = 0; m < nm; ++m) w += std::min<int64_t>(per * (m + 1), nkb_max);
+      tiles_work += w * ceil_div(g->host_seg[(size_t)i].K, cols);
+    }
+    int S = (int)ceil_div(tiles_work, 2LL * s_factor * tc_num_sms());
+    if (S < 4) S = 4;
+    std::vector<TcItem> items;
+    std::vector<SplitUnit> units;
+    int n_slots = 0;
+    for (int i = 0; i < g->nseg; ++i) {
+      if (g->seg_nsl[(size_t)i] != nsl) continue;
+      td_segment* s = g->segs[(size_t)i];
+      plan_split_segment(i, s->nk, s->nkp, g->host_seg[(size_t)i].K, rows, S, items, units, n_slots, small, cols);
+    }
+    sort_items(items);
+    g->cls.push_back(GroupClass());
+    GroupClass& c = g->cls.back();
+    c.nsl = nsl;
+    const size_t wbytes = (size_t)n_slots * (small ? nc * 128 : TC_COLS * bn) * sizeof(float2);
+    if ((r = group_alloc((void**)&c.d_items, std::max<size_t>(1, items.size()) * sizeof(TcItem), "items")) !=
+            TD_OK ||
+        (r = group_alloc((void**)&c.d_units, std::max<size_t>(1, units.size()) * sizeof(SplitUnit), "units")) !=
+            TD_OK ||
+        (r = group_alloc((void**)&c.wpart, std::max<size_t>(8, wbytes), "split accumulators")) != TD_OK)
+      return r;
+    if ((!items.empty() &&
+         cudaMemcpy(c.d_items, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (!units.empty() && cudaMemcpy(c.d_units, units.data(), units.size() * sizeof(SplitUnit),
+                                      cudaMemcpyHostToDevice) != cudaSuccess))
+      return fail(TD_ERR_CUDA, "upload of group work lists failed");
+    c.n_items = (int)items.size();
+    c.n_units = (int)units.size();
+  }
   for (int i = 0; i < g->nseg; ++i) {
     TcSegDev& sd = g->host_seg[(size_t)i];
     td_segment* s = g->segs[(size_t)i];
+    const int nsl = g->seg_nsl[(size_t)i];
     sd.a_rows = small ? nc : TC_COLS;
-    sd.wpart = g->wpart;
+    for (const GroupClass& c : g->cls)
+      if (c.nsl == nsl) sd.wpart = c.wpart;
     sd.nm = (int)(s->nkp / (small ? 128 : 64));   // chi2 partials per 128-row tile or per 64 rows
     if (sd.K == 0) continue;   // no work item refers to an empty segment
     // residual map over this segment's slice region of the group buffer
@@ -199,7 +237,7 @@ static td_status group_build(td_group* g, int bn, int s_factor, int nc = GROUP_N
     tmp_view.scr.capK = cap;
     TcSegDev enc;
     memset(&enc, 0, sizeof enc);
-    if ((r = encode_seg_maps(&tmp_view, sd.K, g->nsl, rows, &enc, small ? nc : TC_COLS)) != TD_OK) {
+    if ((r = encode_seg_maps(&tmp_view, sd.K, nsl, rows, &enc, small ? nc : TC_COLS)) != TD_OK) {
       tmp_view.scr.rs = nullptr;
       tmp_view.op = nullptr;
       return r;
@@ -210,14 +248,8 @@ static td_status group_build(td_group* g, int bn, int s_factor, int nc = GROUP_N
     sd.mapB = enc.mapB;
   }
   if (cudaMemcpy(g->d_seg, g->host_seg.data(), g->host_seg.size() * sizeof(TcSegDev), cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      (!items.empty() &&
-       cudaMemcpy(g->d_items, items.data(), items.size() * sizeof(TcItem), cudaMemcpyHostToDevice) != cudaSuccess) ||
-      (!units.empty() &&
-       cudaMemcpy(g->d_units, units.data(), units.size() * sizeof(SplitUnit), cudaMemcpyHostToDevice) != cudaSuccess))
+      cudaSuccess)
     return fail(TD_ERR_CUDA, "upload of group work lists failed");
-  g->n_items = (int)items.size();
-  g->n_units = (int)units.size();
   g->ops.clear();
   for (td_segment* sp : g->segs) g->ops.push_back(sp->op);
   return TD_OK;
@@ -245,17 +277,18 @@ __global__ void k_joint_sum(const TcSegDev* __restrict__ segs, int nseg, int64_t
 static td_status group_launch_impl(td_group* g, cudaStream_t st) {
   int gx = (int)std::min<int64_t>(g->total_cols, 8192);
   if (gx > 0) {
-    k_r_slices_grouped<<<gx, 256, 0, st>>>(g->d_jobs, g->nseg, g->total_cols, g->nsl);
+    k_r_slices_grouped<<<gx, 256, 0, st>>>(g->d_jobs, g->nseg, g->total_cols);
     TD_CUDA(cudaGetLastError());
   }
-  if (g->bn == 0) {
-    TD_CUDA(launch_tc_small(g->d_items, g->n_items, g->d_seg, g->nsl, g->small_nc, g->status, g->wait_limit_ns,
-                            st));
-    TD_CUDA(launch_small_reduce_grouped(g->d_units, g->n_units, g->d_seg, g->small_nc, st));
-  } else {
-    TD_CUDA(launch_tc_cdo(g->d_items, g->n_items, g->d_seg, g->nsl, g->bn, true, g->status, g->wait_limit_ns, st,
-                          false));
-    TD_CUDA(launch_split_reduce(g->d_units, g->n_units, g->d_seg, g->bn, st, g->maxK));
+  for (const GroupClass& c : g->cls) {
+    if (g->bn == 0) {
+      TD_CUDA(launch_tc_small(c.d_items, c.n_items, g->d_seg, c.nsl, g->small_nc, g->status, g->wait_limit_ns, st));
+      TD_CUDA(launch_small_reduce_grouped(c.d_units, c.n_units, g->d_seg, g->small_nc, st));
+    } else {
+      TD_CUDA(launch_tc_cdo(c.d_items, c.n_items, g->d_seg, c.nsl, g->bn, true, g->status, g->wait_limit_ns, st,
+                            false));
+      TD_CUDA(launch_split_reduce(c.d_units, c.n_units, g->d_seg, g->bn, st, g->maxK));
+    }
   }
   TD_CUDA(launch_tc_finalize(g->d_seg, g->nseg, g->maxK, st));
   if (g->joint && g->joint_K > 0) {
@@ -285,7 +318,10 @@ static std::string group_signature(const td_group* g) {
     const double n = (double)g->segs[(size_t)i]->nk;
     work += n * n * (double)g->host_seg[(size_t)i].K;
   }
-  return std::string(prop.name) + "|nsl" + std::to_string(g->nsl) + "|w" +
+  std::string classes;   // the slice counts present
+  for (int ns = 2; ns <= 4; ++ns)
+    if (std::find(g->seg_nsl.begin(), g->seg_nsl.end(), ns) != g->seg_nsl.end()) classes += std::to_string(ns);
+  return std::string(prop.name) + "|nsl" + std::to_string(g->nsl) + classes + "|w" +
          std::to_string((int)std::log2(std::max(1.0, work))) + "|s" +
          std::to_string((int)std::log2((double)std::max(1, g->nseg)));
 }
@@ -308,17 +344,12 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
   td_group* g = new td_group();
   cudaGetDevice(&g->device);
   g->nseg = nseg;
-  g->nsl = o.precision == TD_PREC_BF16X3 ? 2 : (o.precision == TD_PREC_BF16X10 ? 4 : 3);
-  if (o.precision == TD_PREC_AUTO) {
-    // as for one segment: ten products once any segment exceeds N' = 32768, or
-    // when every segment is below AUTO_SIX_MIN kept samples (one slice count
-    // serves the launch, so a mix of short and longer segments keeps six)
-    bool all_small = true;
-    for (int i = 0; i < nseg; ++i) {
-      if (segs[i] && segs[i]->nk > 32768) g->nsl = 4;
-      if (segs[i] && segs[i]->nk >= AUTO_SIX_MIN) all_small = false;
-    }
-    if (all_small) g->nsl = 4;
+  // each segment with the slice count td_loglike_batch takes for it
+  g->nsl = 2;
+  for (int i = 0; i < nseg; ++i) {
+    const int ns = nslices_for(o.precision, segs[i] ? segs[i]->nk : 0);
+    g->seg_nsl.push_back(ns);
+    g->nsl = std::max(g->nsl, ns);
   }
   g->wait_limit_ns = o.wait_limit_ns > 0 ? o.wait_limit_ns : 1000000000LL;
   int64_t rs_elems = 0, part_elems = 0;
@@ -362,7 +393,7 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
     sd.logL = logL[i];
     sd.chi2 = chi2 ? chi2[i] : nullptr;
     g->host_seg.push_back(sd);
-    RsJob jb{R[i], ldr[i], s->nk, K[i], s->nkp8, cap, g->rs + rs_off, col0};
+    RsJob jb{R[i], ldr[i], s->nk, K[i], s->nkp8, cap, g->rs + rs_off, col0, g->seg_nsl[(size_t)i], 0};
     g->host_jobs.push_back(jb);
     rs_off += OP_SLICES * cap * s->nkp8;
     part_off += (s->nkp / 64) * cap;
@@ -522,7 +553,10 @@ int td_group_shape(const td_group* g, int* bn, int* s_factor, int* n_items) {
   if (!g) return -1;
   if (bn) *bn = g->bn;
   if (s_factor) *s_factor = g->s_factor;
-  if (n_items) *n_items = g->n_items;
+  if (n_items) {
+    *n_items = 0;
+    for (const GroupClass& c : g->cls) *n_items += c.n_items;
+  }
   return 0;
 }
 

@@ -116,6 +116,38 @@ def test_grouped_small_orientation(torch_cuda, gpu_lib):
     g.close()
 
 
+def test_grouped_mixed_slice_counts(torch_cuda, gpu_lib):
+    """Under the default precision each segment takes the slice count one
+    segment alone would (ten products below 2048 kept samples, six from 2048):
+    a group of both kinds runs one product launch per count and meets the bar
+    on every segment."""
+    from paper_2603_06010_b300 import td
+    specs = [(300, [], 20), (2600, [(500, 700)], 37), (3000, [], 129), (1200, [(0, 50)], 5)]
+    segs, Rs, outs, chis, exp_ll, exp_chi = [], [], [], [], [], []
+    for i, (n, gaps, K) in enumerate(specs):
+        mask = None
+        if gaps:
+            mask = np.ones(n, np.uint8)
+            for s0, s1 in gaps:
+                mask[s0:s1] = 0
+        acf = inputs.acf_from_psd(n, 4096.0)
+        R = inputs.noise_residuals(n, 4096.0, K, 300 + i, mask=mask)
+        o = oracle.OracleSegment(acf, mask)
+        c = o.chi2(R)
+        exp_chi.append(c)
+        exp_ll.append(oracle.loglike_from_chi2(c, o.logdet, o.n_kept))
+        segs.append(td.Segment(acf, mask))
+        Rs.append(torch_cuda.from_numpy(np.ascontiguousarray(R)).cuda())
+        outs.append(torch_cuda.full((K,), np.nan, dtype=torch_cuda.float64, device="cuda"))
+        chis.append(torch_cuda.full((K,), np.nan, dtype=torch_cuda.float64, device="cuda"))
+    g = td.Group(segs, Rs, outs, chis)
+    g.graph_launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    _check_all(outs, chis, exp_ll, exp_chi)
+    g.close()
+
+
 def test_grouped_one_shot_matches_per_segment(torch_cuda, gpu_lib):
     from paper_2603_06010_b300 import td
     segs, Rs, outs, chis, exp_ll, exp_chi = _build(torch_cuda, td)

@@ -187,3 +187,41 @@ def test_grouped_joint_three_detectors(torch_cuda, gpu_lib):
     assert np.array_equal(j, (per[0] + per[1]) + per[2])
     assert np.max(np.abs(j - joint_exp)) <= 3e-3
     g.close()
+
+
+@pytest.mark.parametrize("case", range(8))
+def test_grouped_random_case(torch_cuda, gpu_lib, case):
+    """Seeded random groups: 1-6 segments (N' 40 ... 4500, gaps or none, K from 0
+    to 300, two sample rates), a random tile family and precision, one captured
+    launch, every segment against the oracle at the bar."""
+    from paper_2603_06010_b300 import td
+    rng = np.random.default_rng(777000 + case)
+    segs, Rs, outs, chis, exp_ll, exp_chi = [], [], [], [], [], []
+    for i in range(int(rng.integers(1, 7))):
+        n = int(rng.integers(40, 4500))
+        mask = None
+        if n > 200 and rng.random() < 0.5:
+            mask = np.ones(n, np.uint8)
+            a = int(rng.integers(0, n - 50))
+            mask[a:a + int(rng.integers(1, n // 6))] = 0
+        K = int(rng.choice([0, 1, 3, 16, 40, 127, 128, 129, 300]))
+        fs = float(rng.choice([1024.0, 4096.0]))
+        acf = inputs.acf_from_psd(n, fs)
+        o = oracle.OracleSegment(acf, mask)
+        R = inputs.noise_residuals(n, fs, max(K, 1), 5000 + 10 * case + i, mask=mask)[:K]
+        c = o.chi2(R) if K else np.zeros(0)
+        exp_chi.append(c)
+        exp_ll.append(oracle.loglike_from_chi2(c, o.logdet, o.n_kept) if K else np.zeros(0))
+        segs.append(td.Segment(acf, mask))
+        Rs.append(torch_cuda.from_numpy(np.ascontiguousarray(R)).cuda() if K else
+                  torch_cuda.zeros((0, o.n_kept), dtype=torch_cuda.float32, device="cuda"))
+        outs.append(torch_cuda.full((K,), np.nan, dtype=torch_cuda.float64, device="cuda"))
+        chis.append(torch_cuda.full((K,), np.nan, dtype=torch_cuda.float64, device="cuda"))
+    path = int(rng.choice([td.TD_PATH_AUTO, td.TD_PATH_STREAM, td.TD_PATH_SMALLK, td.TD_PATH_STREAM64]))
+    prec = int(rng.choice([td.TD_PREC_AUTO, td.TD_PREC_BF16X10]))
+    g = td.Group(segs, Rs, outs, chis, opt=td.options(precision=prec, path=path))
+    g.graph_launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    _check_all(outs, chis, exp_ll, exp_chi)
+    g.close()

@@ -452,6 +452,13 @@ void td_group_destroy(td_group* g);
  */
 td_status td_group_set_joint(td_group* g, double* joint);
 
+/*
+ * td_group_clock -- as td_profile_clock, for the product launches of this
+ * group (direct, graph or autotuner launches) since the previous call or
+ * td_group_create.
+ */
+td_status td_group_clock(td_group* g, void* stream, double* mhz);
+
 /* One-shot grouped evaluation: create, launch, check, destroy (synchronises). */
 td_status td_loglike_grouped(td_segment* const* segs, const float* const* R,
                              const int64_t* ldr, const int64_t* K, double* const* logL,
@@ -476,6 +483,20 @@ td_status td_check(td_segment* s, void* stream);
 td_status td_profile_enable(td_segment* s, int enable);
 td_status td_profile_read(td_segment* s, double* ms_total, int64_t* dominant_launches,
                           int64_t* kernels_launched);
+
+/*
+ * td_profile_clock -- the SM clock (MHz) the split-product kernel (the
+ * 256/128/64-row tensor-core kernel, single or list mode, refinement
+ * included) actually ran at on this segment's work since the previous read
+ * or td_profile_enable: each CTA's MMA-issuing thread counts SM cycles
+ * (clock64) and global-timer nanoseconds from its start until its last MMA
+ * retired, the sums over CTAs and launches are kept in the segment's device
+ * status word, and *mhz = 1000 x cycles / ns.  A reading below the nominal
+ * clock under load is the power or thermal limit at work.  Synchronises
+ * `stream`, then clears the sums.  TD_ERR_INVALID when no such kernel ran
+ * since the last read (the small-batch kernel does not record).
+ */
+td_status td_profile_clock(td_segment* s, void* stream, double* mhz);
 
 /* Release a segment and all device memory it owns (synchronises its work). */
 void td_segment_destroy(td_segment* s);

@@ -367,6 +367,19 @@ td_status read_status(td_segment* s, cudaStream_t st, DevStatus* out) {
   return TD_OK;
 }
 
+// the clock sums of a device status word: read, convert, clear
+td_status read_clock(DevStatus* dst, cudaStream_t st, double* mhz) {
+  if (!mhz) return fail(TD_ERR_INVALID, "mhz is NULL");
+  unsigned long long v[2] = {0, 0};
+  TD_CUDA(cudaMemcpyAsync(v, &dst->mma_cycles, sizeof v, cudaMemcpyDeviceToHost, st));
+  TD_CUDA(cudaStreamSynchronize(st));
+  TD_CUDA(cudaMemsetAsync(&dst->mma_cycles, 0, sizeof v, st));
+  TD_CUDA(cudaStreamSynchronize(st));
+  if (v[1] == 0) return fail(TD_ERR_INVALID, "no split-product kernel ran since the last clock read");
+  *mhz = 1000.0 * (double)v[0] / (double)v[1];
+  return TD_OK;
+}
+
 td_status reset_status(td_segment* s, cudaStream_t st) {
   DevStatus h{0, 0, LLONG_MAX};
   TD_CUDA(cudaMemcpyAsync(s->status, &h, sizeof h, cudaMemcpyHostToDevice, st));
@@ -674,7 +687,16 @@ td_status td_profile_enable(td_segment* s, int enable) {
   s->prof = enable != 0;
   s->ev_used = 0;
   s->prof_kernels = 0;
+  TD_CUDA(cudaDeviceSynchronize());   // no kernel of this segment still adds to the clock sums
+  TD_CUDA(cudaMemset(&s->status->mma_cycles, 0, 2 * sizeof(unsigned long long)));
+  TD_CUDA(cudaDeviceSynchronize());
   return TD_OK;
+}
+
+
+td_status td_profile_clock(td_segment* s, void* stream, double* mhz) {
+  if (!s) return fail(TD_ERR_INVALID, "segment is NULL");
+  return read_clock(s->status, reinterpret_cast<cudaStream_t>(stream), mhz);
 }
 
 td_status td_profile_read(td_segment* s, double* ms_total, int64_t* dominant_launches, int64_t* kernels_launched) {

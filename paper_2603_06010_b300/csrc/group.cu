@@ -53,10 +53,18 @@ struct RsJob {          // one segment's residual slicing for the grouped slicin
   int pad;
 };
 
-// per-column quantum and slices for every segment of the group (as k_r_slices)
-__global__ void __launch_bounds__(256) k_r_slices_grouped(const RsJob* __restrict__ jobs, int njobs,
-                                                           int64_t total_cols) {
-  __shared__ float red[8];
+// per-column quantum and slices for every segment of the group (the same
+// r_quantum / r_slice_value arithmetic as k_r_slices, so a column's slices
+// do not depend on the group).  One CTA per column at a time; each thread
+// takes row pairs (2t, 2t + 1) + 512 i.  The maximum pass keeps 16 loads in
+// flight per thread; the slicing pass loads 8 values before any store and
+// writes bf16 pairs (4-byte stores: a slice column starts 16-byte aligned).
+// Rows at or beyond N' are never written.
+constexpr int RSG_THREADS = 256;
+__global__ void __launch_bounds__(RSG_THREADS) k_r_slices_grouped(const RsJob* __restrict__ jobs, int njobs,
+                                                                  int64_t total_cols) {
+  __shared__ float red[RSG_THREADS / 32];
+  constexpr int64_t STEP = 2 * RSG_THREADS;   // rows per pass of the CTA
   for (int64_t gc = blockIdx.x; gc < total_cols; gc += gridDim.x) {
     int lo = 0, hi = njobs - 1;   // last job with col0 <= gc
     while (lo < hi) {
@@ -65,34 +73,62 @@ __global__ void __launch_bounds__(256) k_r_slices_grouped(const RsJob* __restric
     }
     const RsJob& jb = jobs[lo];
     const int64_t k = gc - jb.col0;
+    const int64_t nk = jb.nk;
     const float* col = jb.R + k * jb.ldr;
     float mx = 0.f;
-    for (int64_t j = threadIdx.x; j < jb.nk; j += blockDim.x) mx = fmaxf(mx, fabsf(col[j]));
+    for (int64_t j0 = 2 * threadIdx.x; j0 < nk; j0 += 8 * STEP) {
+      float x[16];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int64_t j = j0 + u * STEP;
+        x[2 * u] = j < nk ? col[j] : 0.f;
+        x[2 * u + 1] = j + 1 < nk ? col[j + 1] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 16; ++u) mx = fmaxf(mx, fabsf(x[u]));
+    }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
     __syncthreads();
     mx = red[0];
 #pragma unroll
-    for (int w = 1; w < 8; ++w) mx = fmaxf(mx, red[w]);
-    __syncthreads();
-    float p = 1.f;
-    if (mx > 0.f) {
-      p = exp2f(ceilf(log2f(mx / 255.f)));
-      if (mx / p > 255.f) p *= 2.f;
-    }
+    for (int w = 1; w < RSG_THREADS / 32; ++w) mx = fmaxf(mx, red[w]);
+    __syncthreads();   // red is reused by the next column
+    const float p = r_quantum(mx);
     const int64_t ss = jb.capK * jb.nkp8;
     const int nslices = jb.nsl;
     __nv_bfloat16* dst = jb.rs + k * jb.nkp8;
-    for (int64_t j = threadIdx.x; j < jb.nk; j += blockDim.x) {
-      const float x = col[j];
-      const float h = p * rintf(x / p);
-      __nv_bfloat16 a, b, c;
-      split3_f32(x - h, a, b, c);
-      dst[j] = __float2bfloat16_rn(h);
-      dst[j + ss] = a;
-      if (nslices > 2) dst[j + 2 * ss] = b;
-      if (nslices > 3) dst[j + 3 * ss] = c;
+    for (int64_t j0 = 2 * threadIdx.x; j0 < nk; j0 += 4 * STEP) {
+      float x[8];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t j = j0 + u * STEP;
+        x[2 * u] = j < nk ? col[j] : 0.f;
+        x[2 * u + 1] = j + 1 < nk ? col[j + 1] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int64_t j = j0 + u * STEP;
+        if (j >= nk) break;
+        __nv_bfloat16 a[4], b[4];
+        r_slice_value(x[2 * u], p, a);
+        r_slice_value(x[2 * u + 1], p, b);
+        if (j + 1 < nk) {
+#pragma unroll
+          for (int sl = 0; sl < 4; ++sl)
+            if (sl < nslices) {
+              __nv_bfloat162 v;
+              v.x = a[sl];
+              v.y = b[sl];
+              *reinterpret_cast<__nv_bfloat162*>(dst + sl * ss + j) = v;
+            }
+        } else {
+#pragma unroll
+          for (int sl = 0; sl < 4; ++sl)
+            if (sl < nslices) dst[sl * ss + j] = a[sl];
+        }
+      }
     }
   }
 }
@@ -277,7 +313,7 @@ __global__ void k_joint_sum(const TcSegDev* __restrict__ segs, int nseg, int64_t
 static td_status group_launch_impl(td_group* g, cudaStream_t st) {
   int gx = (int)std::min<int64_t>(g->total_cols, 8192);
   if (gx > 0) {
-    k_r_slices_grouped<<<gx, 256, 0, st>>>(g->d_jobs, g->nseg, g->total_cols);
+    k_r_slices_grouped<<<gx, RSG_THREADS, 0, st>>>(g->d_jobs, g->nseg, g->total_cols);
     TD_CUDA(cudaGetLastError());
   }
   for (const GroupClass& c : g->cls) {
@@ -547,6 +583,11 @@ td_status td_group_check(td_group* g, void* stream) {
     return fail(hs.code == ST_TIMEOUT ? TD_ERR_TIMEOUT : (td_status)hs.code, "device reported an error");
   }
   return TD_OK;
+}
+
+td_status td_group_clock(td_group* g, void* stream, double* mhz) {
+  if (!g) return fail(TD_ERR_INVALID, "group is NULL");
+  return read_clock(g->status, reinterpret_cast<cudaStream_t>(stream), mhz);
 }
 
 int td_group_shape(const td_group* g, int* bn, int* s_factor, int* n_items) {

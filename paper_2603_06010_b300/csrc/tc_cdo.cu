@@ -230,6 +230,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       int stage = 0;
       uint32_t phase = 0;
       int tl = 0;
+      const uint64_t g0 = globaltimer_ns();
+      const long long c0 = clock64();
       for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
         const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
         if (idx >= n_total) continue;
@@ -273,6 +275,12 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       }
       tc_commit(fin);                 // all MMAs issued by this thread retired
       mbar_wait(fin, 0, limit_ns);
+      if (tl > 0) {   // the clock this SM ran at over its share of the work
+        const long long c1 = clock64();
+        const uint64_t g1 = globaltimer_ns();
+        atomicAdd(&status->mma_cycles, (unsigned long long)(c1 - c0));
+        atomicAdd(&status->mma_ns, (unsigned long long)(g1 - g0));
+      }
     }
   } else {
     // -------------------------------------------------- epilogue (warps 2..5)

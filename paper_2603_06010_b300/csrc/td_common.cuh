@@ -16,6 +16,11 @@ struct DevStatus {
   int code;          // first error code (atomicCAS from 0)
   int where;         // which wait ran out (kernel-specific tag)
   long long pivot;   // min failing pivot (factor)
+  // measurement: SM cycles and global-timer nanoseconds over the spans the
+  // split-product kernel's MMA-issuing threads ran (summed over CTAs); their
+  // ratio is the SM clock the kernel actually ran at
+  unsigned long long mma_cycles;
+  unsigned long long mma_ns;
 };
 
 __device__ __forceinline__ void set_status(DevStatus* st, int code, int where) {

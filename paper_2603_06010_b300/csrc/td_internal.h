@@ -360,6 +360,7 @@ constexpr int EMU_SLICES = 6;   // bf16 slices per FP64 operand value in the ten
 td_status factor_begin(td_segment* s, cudaStream_t st);
 td_status factor_end(td_segment* s, double* linv, cudaStream_t st);
 td_status read_status(td_segment* s, cudaStream_t st, DevStatus* out);
+td_status read_clock(DevStatus* dst, cudaStream_t st, double* mhz);
 td_status reset_status(td_segment* s, cudaStream_t st);
 
 // tensor maps of one segment: residual slices (A, boxes of a_rows columns)

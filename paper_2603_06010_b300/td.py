@@ -60,6 +60,7 @@ SIGNATURES = {
     "td_group_graph_launch": (_c.c_int, [_vp, _vp]),
     "td_group_tune": (_c.c_int, [_vp, _vp, _c.POINTER(_c.c_double)]),
     "td_group_check": (_c.c_int, [_vp, _vp]),
+    "td_group_clock": (_c.c_int, [_vp, _vp, _c.POINTER(_c.c_double)]),
     "td_group_shape": (_c.c_int, [_vp, _c.POINTER(_c.c_int), _c.POINTER(_c.c_int), _c.POINTER(_c.c_int)]),
     "td_group_destroy": (None, [_vp]),
     "td_segment_release_fp64": (_c.c_int, [_vp]),
@@ -81,6 +82,7 @@ SIGNATURES = {
     "td_server_destroy": (None, [_vp]),
     "td_profile_enable": (_c.c_int, [_vp, _c.c_int]),
     "td_profile_read": (_c.c_int, [_vp, _c.POINTER(_c.c_double), _c.POINTER(_i64), _c.POINTER(_i64)]),
+    "td_profile_clock": (_c.c_int, [_vp, _vp, _c.POINTER(_c.c_double)]),
 }
 
 
@@ -302,6 +304,12 @@ class Segment:
         _check(lib().td_profile_read(self.handle, ctypes.byref(ms), ctypes.byref(nd), ctypes.byref(nk)))
         return ms.value, nd.value, nk.value
 
+    def profile_clock(self, stream=None) -> float:
+        """SM clock (MHz) the split-product kernel ran at since the last read."""
+        mhz = ctypes.c_double()
+        _check(lib().td_profile_clock(self.handle, _stream_ptr(stream), ctypes.byref(mhz)))
+        return mhz.value
+
     def check(self, stream=None):
         _check(lib().td_check(self.handle, _stream_ptr(stream)))
 
@@ -375,6 +383,12 @@ class Group:
 
     def check(self, stream=None):
         _check(lib().td_group_check(self.handle, _stream_ptr(stream)))
+
+    def clock(self, stream=None) -> float:
+        """SM clock (MHz) the product launches ran at since the last read."""
+        mhz = ctypes.c_double()
+        _check(lib().td_group_clock(self.handle, _stream_ptr(stream), ctypes.byref(mhz)))
+        return mhz.value
 
     def shape(self):
         bn, sf, ni = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

@@ -2,7 +2,9 @@
 // persistent tensor-core launch.  The joint covariance of disjoint segments
 // and detectors is block-diagonal (Sec. II.B items 1 and 3), so each
 // segment's whitening is independent and the work items of all segments share
-// one launch, sorted by work and dealt to the SMs in snake order.
+// one launch.  The main kernel takes them from a work counter as its CTAs
+// become free (segment by segment, most work first); the small-batch
+// orientation deals them in snake order, longest first.
 //
 // Each segment takes the slice count td_loglike_batch would take for it; a
 // group whose segments need different counts runs one product launch (and
@@ -173,6 +175,7 @@ struct td_group {
   DevStatus* status = nullptr;
   cudaGraphExec_t graph = nullptr;
   cudaStream_t graph_stream = nullptr;
+  int* sched = nullptr;       // work counter of the product kernel's dynamic schedule
   double* joint = nullptr;    // optional: sum over the segments of logL (all with joint_K columns)
   int64_t joint_K = 0;
 };
@@ -234,7 +237,12 @@ static td_status group_build(td_group* g, int bn, int s_factor, int nc = GROUP_N
       td_segment* s = g->segs[(size_t)i];
       plan_split_segment(i, s->nk, s->nkp, g->host_seg[(size_t)i].K, rows, S, items, units, n_slots, small, cols);
     }
-    sort_items(items);
+    // the small-batch kernel deals its items round by round, longest first;
+    // the main kernel takes them dynamically, segment by segment
+    if (small)
+      sort_items(items);
+    else
+      sort_items_by_segment(items, g->nseg);
     g->cls.push_back(GroupClass());
     GroupClass& c = g->cls.back();
     c.nsl = nsl;
@@ -321,8 +329,9 @@ static td_status group_launch_impl(td_group* g, cudaStream_t st) {
       TD_CUDA(launch_tc_small(c.d_items, c.n_items, g->d_seg, c.nsl, g->small_nc, g->status, g->wait_limit_ns, st));
       TD_CUDA(launch_small_reduce_grouped(c.d_units, c.n_units, g->d_seg, g->small_nc, st));
     } else {
+      TD_CUDA(cudaMemsetAsync(g->sched, 0, sizeof(int), st));
       TD_CUDA(launch_tc_cdo(c.d_items, c.n_items, g->d_seg, c.nsl, g->bn, true, g->status, g->wait_limit_ns, st,
-                            false));
+                            false, g->sched));
       TD_CUDA(launch_split_reduce(c.d_units, c.n_units, g->d_seg, g->bn, st, g->maxK));
     }
   }
@@ -410,7 +419,8 @@ td_status td_group_create(td_segment* const* segs, const float* const* R, const 
       (r = group_alloc((void**)&g->partials, (size_t)part_elems * 8, "group partials")) != TD_OK ||
       (r = group_alloc((void**)&g->d_seg, (size_t)nseg * sizeof(TcSegDev), "segment descriptors")) != TD_OK ||
       (r = group_alloc((void**)&g->d_jobs, (size_t)nseg * sizeof(RsJob), "slicing jobs")) != TD_OK ||
-      (r = group_alloc((void**)&g->status, sizeof(DevStatus), "status")) != TD_OK) {
+      (r = group_alloc((void**)&g->status, sizeof(DevStatus), "status")) != TD_OK ||
+      (r = group_alloc((void**)&g->sched, sizeof(int), "work counter")) != TD_OK) {
     td_group_destroy(g);
     return r;
   }
@@ -610,6 +620,7 @@ void td_group_destroy(td_group* g) {
   if (g->d_seg) cudaFree(g->d_seg);
   if (g->d_jobs) cudaFree(g->d_jobs);
   if (g->status) cudaFree(g->status);
+  if (g->sched) cudaFree(g->sched);
   delete g;
 }
 

@@ -64,4 +64,21 @@ void sort_items(std::vector<TcItem>& items) {
   std::stable_sort(items.begin(), items.end(), [](const TcItem& a, const TcItem& b) { return a.nkb > b.nkb; });
 }
 
+// Segment by segment (most work first), each segment's items longest first
+// with the column tiles of a row tile (or chunk) kept together.  Taken in
+// this order by the dynamic schedule, the CTAs at work at any time share a
+// few segments, so each segment's residual slices are read from HBM about
+// once per pass of the CTAs over it and then from L2 by its other row tiles.
+void sort_items_by_segment(std::vector<TcItem>& items, int nseg) {
+  std::vector<int64_t> work((size_t)nseg, 0);
+  for (const TcItem& it : items) work[(size_t)it.seg] += it.nkb;
+  std::stable_sort(items.begin(), items.end(), [&](const TcItem& a, const TcItem& b) {
+    if (a.seg != b.seg) {
+      const int64_t wa = work[(size_t)a.seg], wb = work[(size_t)b.seg];
+      return wa != wb ? wa > wb : a.seg < b.seg;
+    }
+    return a.nkb > b.nkb;
+  });
+}
+
 }  // namespace td

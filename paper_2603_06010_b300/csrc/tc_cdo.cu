@@ -27,8 +27,9 @@
 //
 // Work: one output tile = (segment, row tile m, column tile c); the row tile
 // needs the k-blocks up to its diagonal (the lower triangle).  Tiles are
-// sorted by work (largest first) and dealt to the persistent CTAs in snake
-// order.
+// dealt to the persistent CTAs in snake order (one segment: largest first),
+// or, for a list with a work counter, taken in list order as CTAs become free
+// (see the item-order note in the kernel).
 //
 // Warp roles (192 threads, one CTA per SM):
 //   warp 0 lane 0 : TMA producer, STAGES-deep ring of (A, B) slice stages
@@ -47,7 +48,8 @@ namespace tc {
 constexpr int BM = TC_COLS;      // 128 residual columns
 constexpr int BK = OP_KB;        // 32
 constexpr int A_SLICE = BM * BK * 2;   // 8 KB
-constexpr int BAR_BYTES = 256;
+constexpr int BAR_BYTES = 512;
+constexpr int NRING = 8;         // item-index ring of the dynamic schedule
 constexpr int THREADS = 192;
 template <int NSL, int BN> struct Cfg {
   static constexpr int B_SLICE = BN * BK * 2;
@@ -67,6 +69,7 @@ struct TcSingle {           // single-segment launch: item list is implicit
   int nm;                   // row tiles of BN rows
   int nc;                   // column tiles
   int nkb_max;              // k-blocks available (ceil(N'/32))
+  int* sched;               // list modes: work counter of the dynamic schedule (zero at launch), or null
   RefineIO io;              // element-wise modes 3..5: element (i, k) of in / out at [i + k ld]
 };
 
@@ -109,8 +112,11 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   uint64_t* tfull = empty + STAGES;
   uint64_t* tempty = tfull + NBUF;
   uint64_t* fin = tempty + NBUF;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(fin + 1);
+  uint64_t* ring_full = fin + 1;          // NRING: item index published
+  uint64_t* ring_empty = ring_full + NRING;   // NRING: read by the MMA thread and the four epilogue warps
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(ring_empty + NRING);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  volatile int* ring = abort_flag + 1;    // NRING item indices (-1: no more work)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the kernels after this one may be scheduled now; they wait for this grid
@@ -125,6 +131,10 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       mbar_init(&tempty[b], 4);
     }
     mbar_init(fin, 1);
+    for (int i = 0; i < NRING; ++i) {
+      mbar_init(&ring_full[i], 1);
+      mbar_init(&ring_empty[i], 5);
+    }
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -148,6 +158,24 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   const uint32_t tmem_base = *tmem_slot;
   const int G = gridDim.x, b = blockIdx.x;
   const int n_total = GROUPED ? n_items : single.nm * single.nc;
+  // Item order.  Static: round r of CTA b takes item r G + b (G - 1 - b on odd
+  // rounds).  Dynamic (list modes with a work counter): the producer takes the
+  // next item from the counter when it starts one and publishes its index to
+  // the MMA thread and the epilogue through a ring in shared memory.  Items
+  // that read the same operator tile (the column tiles of one row tile) sit
+  // next to each other in the list, so the dynamic order starts them within
+  // microseconds of each other and all but the first read its k-blocks from
+  // L2; dealt statically, CTAs reach the same round at different times and
+  // each would stream the tile from HBM again.
+  const bool dyn = GROUPED && single.sched != nullptr;
+  // consumers: the next item index (-1: none), false when the wait ran out
+  auto ring_take = [&](int& j, int& idx) -> bool {
+    const int slot = j % NRING;
+    if (!mbar_wait(&ring_full[slot], (uint32_t)(j / NRING) & 1u, limit_ns)) return false;
+    idx = ring[slot];
+    ++j;
+    return true;
+  };
 
   if (warp == 0) {
     if (lane == 0) {
@@ -177,9 +205,36 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
         pend_n = 0;
       };
-      for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
-        const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
-        if (idx >= n_total) continue;
+      int jpub = 0;
+      bool ended = false;   // the end marker is in the ring
+      auto publish = [&](int idx) -> bool {
+        const int slot = jpub % NRING;
+        if (!mbar_wait(&ring_empty[slot], ((uint32_t)(jpub / NRING) & 1u) ^ 1u, limit_ns)) return false;
+        ring[slot] = idx;
+        mbar_arrive(&ring_full[slot]);
+        ++jpub;
+        return true;
+      };
+      for (int r = 0;; ++r) {
+        int idx;
+        if (dyn) {
+          idx = *abort_flag ? -1 : atomicAdd(single.sched, 1);
+          if (idx >= n_total) idx = -1;
+          if (!publish(idx)) {
+            set_status(status, ST_TIMEOUT, 11);
+            *abort_flag = 1;
+            ended = true;   // the consumers' own bounded waits end them
+            break;
+          }
+          if (idx < 0) {
+            ended = true;
+            break;
+          }
+        } else {
+          if ((int64_t)r * G >= n_total || *abort_flag) break;
+          idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+          if (idx >= n_total) continue;
+        }
         const TcItem it = GROUPED ? items[idx] : single_item<BN>(single, idx);
         const TcSegDev* sd = GROUPED ? &segs[it.seg] : &single.seg;
         const int row0 = it.m * BN;                      // first W row of the tile
@@ -218,6 +273,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
         if (!ok) break;
       }
+      if (dyn && !ended) publish(-1);   // after an abort: let the consumers stop
       if (!dep) flush();
       // every issued copy must land before the CTA may exit
       for (int s = 0; s < STAGES; ++s)
@@ -232,9 +288,23 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
       int tl = 0;
       const uint64_t g0 = globaltimer_ns();
       const long long c0 = clock64();
-      for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
-        const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
-        if (idx >= n_total) continue;
+      int jtake = 0;
+      for (int r = 0;; ++r) {
+        int idx;
+        if (dyn) {
+          const int slot = jtake % NRING;
+          if (!ring_take(jtake, idx)) {
+            set_status(status, ST_TIMEOUT, 22);
+            *abort_flag = 1;
+            break;
+          }
+          mbar_arrive(&ring_empty[slot]);
+          if (idx < 0) break;
+        } else {
+          if ((int64_t)r * G >= n_total || *abort_flag) break;
+          idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+          if (idx >= n_total) continue;
+        }
         const TcItem it = GROUPED ? items[idx] : single_item<BN>(single, idx);
         const int buf = tl % NBUF;
         const uint32_t use = (uint32_t)(tl / NBUF);
@@ -286,9 +356,24 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     // -------------------------------------------------- epilogue (warps 2..5)
     const int q = warp & 3;   // TMEM lane quarter this warp may access
     int tl = 0;
-    for (int r = 0; (int64_t)r * G < n_total && !*abort_flag; ++r) {
-      const int idx = r * G + ((r & 1) ? (G - 1 - b) : b);
-      if (idx >= n_total) continue;
+    int jtake = 0;
+    for (int r = 0;; ++r) {
+      int idx;
+      if (dyn) {
+        const int slot = jtake % NRING;
+        if (!ring_take(jtake, idx)) {
+          if (lane == 0) set_status(status, ST_TIMEOUT, 32);
+          *abort_flag = 1;
+          break;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ring_empty[slot]);
+        if (idx < 0) break;
+      } else {
+        if ((int64_t)r * G >= n_total || *abort_flag) break;
+        idx = r * G + ((r & 1) ? (G - 1 - b) : b);
+        if (idx >= n_total) continue;
+      }
       const TcItem it = GROUPED ? items[idx] : single_item<BN>(single, idx);
       const TcSegDev* sd = GROUPED ? &segs[it.seg] : &single.seg;
       const int buf = tl % NBUF;
@@ -493,8 +578,10 @@ cudaError_t launch_tc_single_ew(const TcSegDev& seg, int bn, int mode, int nc, i
 }
 
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
-                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl) {
+                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl,
+                          int* sched) {
   TcSingle p{};
+  p.sched = sched;
   if (split) return dispatch<2>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st, pdl);
   return dispatch<1>(nslices, bn, p, items, n_items, segs, status, wait_limit_ns, st, pdl);
 }

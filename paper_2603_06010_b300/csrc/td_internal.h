@@ -138,6 +138,7 @@ int nslices_for(int precision, int64_t nk);
 void plan_split_segment(int seg, int64_t nk, int64_t nkp, int64_t K, int bn, int S, std::vector<TcItem>& items,
                         std::vector<SplitUnit>& units, int& n_slots, bool all_slots = false, int cols = TC_COLS);
 void sort_items(std::vector<TcItem>& items);
+void sort_items_by_segment(std::vector<TcItem>& items, int nseg);
 
 }  // namespace td
 
@@ -283,9 +284,13 @@ cudaError_t launch_r_slices(const float* R, int64_t ldr, int64_t nk, int64_t K, 
 
 // tensor-core CDO product + chi2 partials (one per 64-row group) over a work list
 // pdl: launch as a programmatic dependent of the preceding kernel (which
-// must trigger early); off for the grouped path, where it measured slower
+// must trigger early); off for the grouped path, where it measured slower.
+// sched: a device int that is zero when the kernel starts: items are then
+// taken in list order as CTAs become free (the dynamic schedule), instead of
+// dealt round by round
 cudaError_t launch_tc_cdo(const TcItem* items, int n_items, const TcSegDev* segs, int nslices, int bn,
-                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl = true);
+                          bool split, DevStatus* status, int64_t wait_limit_ns, cudaStream_t st, bool pdl = true,
+                          int* sched = nullptr);
 // partials per 64-row group; max_cols: the widest column tile of the units
 // (one CTA per 64 rows and 16 columns).  mode: RED_CHI2, or one of the
 // refinement modes (element-wise output or chi2 of in + w, through io).

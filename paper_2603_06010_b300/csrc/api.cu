@@ -107,12 +107,14 @@ static Shape choose_shape(const td_segment* s, int64_t K, int path) {
   // rows win from K = 1024 (250 us vs 275 us for 128-row); 128-row whole rows
   // (two TMEM accumulator pairs, so epilogues overlap MMAs) at K = 384..512
   // (155 us vs 238 us for 256-row); 128-row tiles with k-chunks below that
-  // (K = 128: 91 us vs 149 us whole rows; K = 256: a tie at 155 us)
+  // (K = 128: 91 us vs 149 us whole rows; K = 256: a tie at 155 us).  Whole
+  // 128-row tiles from half an item per SM: N' = 4096, K = 384 (96 items)
+  // 83 us against 109 us in k-chunks
   const int64_t nc = ceil_div(K, TC_COLS);
   const int64_t items256 = (s->nkp / OP_ROWS) * nc;
   const int64_t items128 = (s->nkp / 128) * nc;
   if (2 * items256 >= 3 * (int64_t)tc_num_sms()) return {256, false};
-  if (4 * items128 >= 3 * (int64_t)tc_num_sms()) return {128, false};
+  if (2 * items128 >= (int64_t)tc_num_sms()) return {128, false};
   return {128, true};
 }
 

@@ -225,3 +225,48 @@ def test_grouped_random_case(torch_cuda, gpu_lib, case):
     g.check()
     _check_all(outs, chis, exp_ll, exp_chi)
     g.close()
+
+
+@pytest.mark.parametrize("path_name", ["STREAM", "STREAM64"])
+def test_grouped_many_segments(torch_cuda, gpu_lib, path_name):
+    """36 seeded segments of uneven size (N' 40 ... 3000, gaps, K from 0 to 300)
+    in one launch: many items per CTA, taken from the work counter segment by
+    segment; every segment against the oracle, graph replay equal to a direct
+    launch bit for bit."""
+    from paper_2603_06010_b300 import td
+    rng = np.random.default_rng(424242)
+    segs, Rs, outs, chis, exp_ll, exp_chi = [], [], [], [], [], []
+    for i in range(36):
+        n = int(rng.integers(40, 3000))
+        mask = None
+        if n > 300 and rng.random() < 0.4:
+            mask = np.ones(n, np.uint8)
+            a = int(rng.integers(0, n - 100))
+            mask[a:a + int(rng.integers(1, n // 5))] = 0
+        K = int(rng.choice([0, 1, 7, 64, 128, 129, 200, 300]))
+        acf = inputs.acf_from_psd(n, 4096.0, a=float(rng.uniform(-4.5, -3.5)), floor=float(rng.uniform(1, 3)))
+        o = oracle.OracleSegment(acf, mask)
+        R = inputs.noise_residuals(n, 4096.0, max(K, 1), 9100 + i, mask=mask)[:K]
+        c = o.chi2(R) if K else np.zeros(0)
+        exp_chi.append(c)
+        exp_ll.append(oracle.loglike_from_chi2(c, o.logdet, o.n_kept) if K else np.zeros(0))
+        segs.append(td.Segment(acf, mask))
+        Rs.append(torch_cuda.from_numpy(np.ascontiguousarray(R)).cuda() if K else
+                  torch_cuda.zeros((0, o.n_kept), dtype=torch_cuda.float32, device="cuda"))
+        outs.append(torch_cuda.full((K,), np.nan, dtype=torch_cuda.float64, device="cuda"))
+        chis.append(torch_cuda.full((K,), np.nan, dtype=torch_cuda.float64, device="cuda"))
+    g = td.Group(segs, Rs, outs, chis, opt=td.options(path=getattr(td, "TD_PATH_" + path_name)))
+    g.launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    _check_all(outs, chis, exp_ll, exp_chi)
+    first = [o.clone() for o in outs]
+    for o in outs:
+        o.fill_(np.nan)
+    g.graph_launch()
+    g.graph_launch()
+    torch_cuda.cuda.synchronize()
+    g.check()
+    for a, b in zip(first, outs):
+        assert torch_cuda.equal(a, b)
+    g.close()

@@ -423,7 +423,10 @@ td_status td_reserve(td_segment* s, int64_t K, const td_options* opt);
  * pointers it was given: later launches read R[i] and write logL[i] there.
  * td_group_launch enqueues the evaluation on `stream` (four kernels whatever
  * nseg, two more for each further slice count its segments take, one more
- * with a joint sum; no allocation; capturable in a CUDA graph).  td_group_graph_launch
+ * with a joint sum, and before each product kernel of the main orientation a
+ * 4-byte memset of its work counter: the product takes its items, segment by
+ * segment, as its CTAs become free; no allocation; capturable in a CUDA
+ * graph).  td_group_graph_launch
  * captures the launch into a CUDA graph on first use and replays it.
  * td_group_tune times the candidate tile shapes and chunk sizes on the plan's
  * own inputs, keeps the fastest, and records it for later plans of the same

@@ -11,9 +11,9 @@
 // one chunk reduction) per count.
 //
 // A td_group is a plan: it owns the device work lists, segment descriptors
-// and scratch, so td_group_launch only launches kernels (five per call and
-// slice count, whatever the number of segments) and can be captured in a
-// CUDA graph;
+// and scratch, so td_group_launch only launches kernels (and zeroes the
+// product kernel's work counter before each product launch), whatever the
+// number of segments, and can be captured in a CUDA graph;
 // td_group_graph_launch captures it once and replays the graph.  The
 // autotuner (td_group_tune) times the candidate tile shapes and chunk sizes
 // on the real inputs and keeps the fastest.

@@ -608,6 +608,21 @@ int64_t td_resident_bytes(const td_segment* s);
  */
 td_status td_debug_bounded_wait(int64_t limit_ns, void* stream);
 
+/*
+ * td_debug_plan -- the work list the grouped launch of the main orientation
+ * would build (host code only; no device is touched).  For nseg segments of
+ * nk[i] kept samples and K[i] columns, operator tiles of bn rows (256, 128 or
+ * 64) and k-chunks of S k-blocks (32 kept samples each), writes one record of
+ * six ints per work item to out: segment, row tile, column tile (128
+ * columns), first k-block, k-blocks, chunk slot (-1 for a whole row), in
+ * launch order: segment by segment (by_segment != 0, the order the dynamic
+ * schedule takes) or longest first.  Returns the item count, or -count when
+ * cap (in records) is too small (nothing written), or -1 on bad arguments.
+ * Exists to test the planning logic on a machine without a GPU.
+ */
+int td_debug_plan(const int64_t* nk, const int64_t* K, int nseg, int bn, int S, int by_segment, int* out,
+                  int cap);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,3 +82,34 @@ void sort_items_by_segment(std::vector<TcItem>& items, int nseg) {
 }
 
 }  // namespace td
+
+extern "C" int td_debug_plan(const int64_t* nk, const int64_t* K, int nseg, int bn, int S, int by_segment, int* out,
+                             int cap) {
+  using namespace td;
+  if (!nk || !K || nseg <= 0 || (bn != 256 && bn != 128 && bn != 64) || S < 1 || cap < 0) return -1;
+  std::vector<TcItem> items;
+  std::vector<SplitUnit> units;
+  int n_slots = 0;
+  for (int i = 0; i < nseg; ++i) {
+    if (nk[i] < 1 || K[i] < 0) return -1;
+    plan_split_segment(i, nk[i], round_up(nk[i], OP_ROWS), K[i], bn, S, items, units, n_slots, false, TC_COLS);
+  }
+  if (by_segment)
+    sort_items_by_segment(items, nseg);
+  else
+    sort_items(items);
+  const int n = (int)items.size();
+  if (n > cap) return -n;
+  for (int j = 0; j < n; ++j) {
+    const TcItem& it = items[(size_t)j];
+    int* r = out + 6 * (size_t)j;
+    r[0] = it.seg;
+    r[1] = it.m;
+    r[2] = it.c;
+    r[3] = it.kb0;
+    r[4] = it.nkb;
+    r[5] = it.slot;
+  }
+  return n;
+}
+

@@ -44,6 +44,8 @@ SIGNATURES = {
     "td_last_error": (_c.c_char_p, []),
     "td_resident_bytes": (_i64, [_vp]),
     "td_debug_bounded_wait": (_c.c_int, [_i64, _vp]),
+    "td_debug_plan": (_c.c_int, [_c.POINTER(_i64), _c.POINTER(_i64), _c.c_int, _c.c_int, _c.c_int, _c.c_int,
+                                 _c.POINTER(_c.c_int), _c.c_int]),
     "td_loglike_batch_noalloc": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp]),
     "td_loglike_batch_host": (_c.c_int, [_vp, _vp, _i64, _i64, _vp, _vp, _vp, _vp]),
     "td_set_data": (_c.c_int, [_vp, _vp, _vp, _vp]),

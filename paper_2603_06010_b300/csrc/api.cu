@@ -87,7 +87,25 @@ td_status encode_seg_maps(td_segment* s, int64_t K, int nsl, int bn, TcSegDev* o
 struct Shape {
   int bn;
   bool split;
+  int S = 0;   // split: chunk length in k-blocks (0: split_chunk's, which depends on N' alone)
 };
+
+// Whole rows of bn rows over nc column tiles: when the longest row alone is
+// longer than twice an SM's mean share of the work, it holds the launch back;
+// the chunk length that splits only the rows above the mean share (else 0:
+// keep whole rows).  Measured on B300, one call after an L2 flush: N' = 4096,
+// K = 300 / 384 / 512 (longest row 2.2 to 3 mean shares): 67 / 66 / 74 us
+// against 83 / 82 / 88 us whole; at 1.5 mean shares it is a toss-up
+// (N' = 8192, K = 384: 141 against 153 us; N' = 4096, K = 768: 92 against 86)
+static int balanced_chunk(const td_segment* s, int bn, int64_t nc) {
+  const int64_t per = bn / OP_KB, nm = s->nkp / bn, nkb_max = ceil_div(s->nk, OP_KB);
+  int64_t total = 0;
+  for (int64_t m = 0; m < nm; ++m) total += std::min<int64_t>(per * (m + 1), nkb_max);
+  total *= nc;
+  const int64_t mean = ceil_div(total, (int64_t)tc_num_sms());
+  const int64_t longest = std::min<int64_t>(per * nm, nkb_max);
+  return longest > 2 * mean ? (int)std::max<int64_t>(mean, 4) : 0;
+}
 static Shape choose_shape(const td_segment* s, int64_t K, int path) {
   if (path == TD_PATH_TENSOR) return {256, false};
   if (path == TD_PATH_STREAM) return {256, true};
@@ -113,8 +131,14 @@ static Shape choose_shape(const td_segment* s, int64_t K, int path) {
   const int64_t nc = ceil_div(K, TC_COLS);
   const int64_t items256 = (s->nkp / OP_ROWS) * nc;
   const int64_t items128 = (s->nkp / 128) * nc;
-  if (2 * items256 >= 3 * (int64_t)tc_num_sms()) return {256, false};
-  if (2 * items128 >= (int64_t)tc_num_sms()) return {128, false};
+  if (2 * items256 >= 3 * (int64_t)tc_num_sms()) {
+    const int S = balanced_chunk(s, 256, nc);
+    return S > 0 ? Shape{256, true, S} : Shape{256, false};
+  }
+  if (2 * items128 >= (int64_t)tc_num_sms()) {
+    const int S = balanced_chunk(s, 128, nc);
+    return S > 0 ? Shape{128, true, S} : Shape{128, false};
+  }
   return {128, true};
 }
 
@@ -251,8 +275,9 @@ static int64_t plan_width(int64_t K) {
 // nc > 0: plan for the small-batch kernel (128-row operator tiles as the MMA
 // M dimension, nc residual columns per tile, chi2 partials per 32 rows).
 static td_status get_split_plan(td_segment* s, Scratch& sc, int64_t K, int nsl, int bn, cudaStream_t st,
-                                SplitPlan** out, int nc = 0) {
+                                SplitPlan** out, int nc = 0, int S_force = 0) {
   ++sc.use_clock;
+  const int S = S_force > 0 ? S_force : split_chunk(s->nk, s->nkp, bn);
   const int key_bn = nc > 0 ? -nc : bn;
   // a re-factored segment (new log det) drops its plans; an operator that only
   // moved (evicted and reloaded by a server) keeps them: their operator maps
@@ -279,12 +304,11 @@ static td_status get_split_plan(td_segment* s, Scratch& sc, int64_t K, int nsl, 
       p.op = s->op;
     }
   for (SplitPlan& p : sc.plans)
-    if (p.seg == (const void*)s && p.K == K && p.nsl == nsl && p.bn == key_bn) {
+    if (p.seg == (const void*)s && p.K == K && p.nsl == nsl && p.bn == key_bn && p.S == S) {
       p.last_use = sc.use_clock;
       *out = &p;
       return TD_OK;
     }
-  const int S = split_chunk(s->nk, s->nkp, bn);
   std::vector<TcItem> items;
   std::vector<SplitUnit> units;
   int n_slots = 0;
@@ -522,7 +546,7 @@ td_status reserve_with(td_segment* s, Scratch& sc, int64_t K, const td_options* 
       return r;
   for (int64_t k = 8; k <= K; k = (k < TC_COLS) ? 2 * k : k + TC_COLS) {
     const Shape sh = choose_shape(s, k, o.path);
-    if (sh.bn != 0 && sh.split && (r = get_split_plan(s, sc, plan_width(k), nsl, sh.bn, 0, &plan)) != TD_OK)
+    if (sh.bn != 0 && sh.split && (r = get_split_plan(s, sc, plan_width(k), nsl, sh.bn, 0, &plan, 0, sh.S)) != TD_OK)
       return r;
   }
   return TD_OK;
@@ -626,7 +650,7 @@ td_status loglike_batch_with(td_segment* s, Scratch& sc, const float* R, int64_t
   TD_CUDA(launch_r_slices(R, ldr, s->nk, K, s->nkp8, sc.capK, sc.rs, nsl, st));
   if (shape.split) {
     SplitPlan* plan = nullptr;
-    if ((r = get_split_plan(s, sc, plan_width(K), nsl, bn, st, &plan)) != TD_OK) return r;
+    if ((r = get_split_plan(s, sc, plan_width(K), nsl, bn, st, &plan, 0, shape.S)) != TD_OK) return r;
     if (pm) prof_mark(s, st, true);   // the events bracket the product kernel alone
     TD_CUDA(launch_tc_cdo(plan->items, plan->n_items, plan->segdev, nsl, bn, true, s->status, o.wait_limit_ns,
                           st));

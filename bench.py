@@ -433,7 +433,12 @@ def grouped_extra(td, torch, count=64):
     achieved = flops / (ms / 1e3) / 1e12
     sm_mhz = kern_mhz
     clock_peak = 8192.0 * tc_sms() * sm_mhz * 1e6 / 6 / 1e12
+    traffic = profile_traffic("k_tc_cdo_mix64_grouped_dram.md") if count == 64 else None
     roof = {"achieved": achieved, "unit": "TFLOP/s", "sm_mhz_in_kernel": kern_mhz,
+            "traffic": traffic, "traffic_over_algorithmic": traffic / 31.7e9 if traffic else None,
+            "traffic_source": "profiles/k_tc_cdo_mix64_grouped_dram.md (ncu dram__bytes_read.sum + "
+                              "dram__bytes_write.sum of the six-product launch, one pass); algorithmic: operator "
+                              "and residual slices once, 31.7 GB" if traffic else None,
             "frac_burst": achieved / (pk["bf16_tflops"] / 6),
             "frac_sustained": achieved / (pk["bf16_tflops_sustained"] / 6),
             "frac_clock_normalized": achieved / clock_peak if clock_peak else None,

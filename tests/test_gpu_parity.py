@@ -363,10 +363,13 @@ def test_host_buffers_match_device_path(torch_cuda, gpu_lib):
     seg.close()
 
 
-@pytest.mark.parametrize("n,K", [(1, 1000), (40, 70000), (2000, 33), (2000, 129), (2000, 257), (2000, 513)])
+@pytest.mark.parametrize("n,K", [(1, 1000), (40, 70000), (2000, 33), (2000, 129), (2000, 257), (2000, 513),
+                                 (4096, 300), (4096, 384), (3500, 512)])
 def test_extreme_and_transition_shapes(torch_cuda, gpu_lib, n, K):
     """Very wide batches on tiny segments and the batch sizes where the automatic
-    tile shape changes: every column finite, sampled columns against the oracle."""
+    tile shape changes (the last three: whole 128-row tiles whose rows above an
+    SM's mean share are cut into chunks): every column finite, sampled columns
+    against the oracle."""
     from paper_2603_06010_b300 import td
     mask = _mask(n, [(700, 780)]) if n > 1000 else None
     acf = inputs.acf_from_psd(n, 2048.0) if n > 1 else np.array([1.7])

@@ -7,6 +7,8 @@
 // the same bits as on the device-buffer path with the same options.
 #include <algorithm>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "td_internal.h"
 
@@ -80,17 +82,26 @@ extern "C" td_status td_loglike_batch_host(td_segment* s, const float* R, int64_
   if (dev != s->device) return fail(TD_ERR_INVALID, "segment belongs to another device; set it current first");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   // chunks of 512 columns: small enough that the first copy is short, large
-  // enough that each evaluation still fills the GPU
+  // enough that each evaluation still fills the GPU.  The copies set the pace
+  // and the last evaluation is the only one nothing overlaps, so the last
+  // chunk is at most 128 columns (N' = 8192, K = 4096: 2.6 against 2.7 ms)
   const int64_t cols = std::min<int64_t>(K, 512);
+  std::vector<std::pair<int64_t, int64_t>> chunks;   // (first column, columns)
+  for (int64_t c0 = 0; c0 < K;) {
+    const int64_t left = K - c0;
+    const int64_t kc = left > cols + 128 ? cols : (left > 128 ? left - 128 : left);
+    chunks.emplace_back(c0, kc);
+    c0 += kc;
+  }
   td_status r = ensure_stage(s, cols, K);
   if (r != TD_OK) return r;
   if ((r = td_reserve(s, cols, opt)) != TD_OK) return r;
   HostStage& h = s->hst;
   const int64_t nk = s->nk;
-  const int64_t nch = (K + cols - 1) / cols;
+  const int64_t nch = (int64_t)chunks.size();
   for (int64_t j = 0; j < nch; ++j) {
     const int b = (int)(j & 1);
-    const int64_t c0 = j * cols, kc = std::min(cols, K - c0);
+    const int64_t c0 = chunks[(size_t)j].first, kc = chunks[(size_t)j].second;
     if (j >= 2) TD_CUDA(cudaStreamWaitEvent(h.copy, h.consumed[b], 0));   // buffer free again
     TD_CUDA(cudaMemcpy2DAsync(h.buf[b], (size_t)nk * sizeof(float), R + c0 * ldr, (size_t)ldr * sizeof(float),
                               (size_t)nk * sizeof(float), (size_t)kc, cudaMemcpyHostToDevice, h.copy));
